@@ -223,3 +223,15 @@ def diff_batch(batch: int, n: int, q: int, r: int, seed: int, device="cpu"):
     B = torch.randn((batch, r, n), generator=g, dtype=torch.float64, device=device)
     W = torch.randn((batch, r, n), generator=g, dtype=torch.float64, device=device)
     return Qd, J, B, W
+
+
+# ---------------------------------------------------------------------------
+# Workload shapes of the size sweep: square problems of these orders, each
+# point's batch chosen so that its operands total about 2 GiB.
+SWEEP_N = (4, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256)
+SWEEP_BYTES = 2 ** 31
+
+
+def sweep_batch(n: int, ld: int, operands: int) -> int:
+    """Problems per sweep point: floor(2 GiB / (operands * ld * n * 8 bytes))."""
+    return SWEEP_BYTES // (operands * ld * n * 8)

@@ -1,0 +1,163 @@
+/*
+ * bfgpu.h -- C ABI of the batched small-matrix FP64 BLAS/LAPACK library for
+ * one GB300 (sm_103a).
+ *
+ * The routines keep the BLAS/LAPACK calling conventions that the paper keeps
+ * for its "BLAS API" (section 1; section 2.1 "Notation"): column-major
+ * storage with a leading dimension, char options ('N'/'T', 'L'/'U', ...),
+ * destructive in-place output.  Every call additionally exists in batched
+ * forms.  Each call switches by size between kernel variants (section 2.4,
+ * "Proposed approach"): a direct kernel on the column-major operands, and
+ * kernels that first pack operands into a panel layout in shared memory.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers to matrices, pointer arrays and info arrays are DEVICE
+ *    pointers owned by the caller; the library never allocates device memory
+ *    on the call path (the paper's variants avoid dynamic allocation for
+ *    small sizes, section 2.2 algorithm 'C').
+ *  - Element (i, j) of a matrix X with leading dimension ldx is X[i + j*ldx].
+ *  - Strided batches: problem b's matrix starts at X + b*strideX.
+ *    Pointer-array batches: problem b's matrix starts at Xarray[b].
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL is the
+ *    legacy default stream).
+ *  - Return value: 0 on success; -i when the i-th argument (1-based position
+ *    in the call's argument list) is illegal, in which case nothing is
+ *    launched (LAPACK's info < 0 rule); BF_ERR_CUDA when a launch failed;
+ *    BF_ERR_NOT_SUPPORTED for a legal option this library does not implement.
+ *  - Numerical failures are reported per problem in a device `info` array
+ *    (LAPACK's info > 0 rule); calls never abort or trap.
+ */
+#ifndef BFGPU_H
+#define BFGPU_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* bf_stream_t; /* identical to cudaStream_t */
+
+#define BF_SUCCESS 0
+#define BF_ERR_CUDA 1001
+#define BF_ERR_NOT_SUPPORTED 1002
+
+#define BF_ROUTINE_DGEMM 0
+#define BF_ROUTINE_DTRSM 1
+#define BF_ROUTINE_DPOTRF 2
+
+/* Kernel variants of the size switch (values of `variant` in bf_tune_set). */
+#define BF_VARIANT_DIRECT 0  /* native column-major operands, no packing (algorithm 'D') */
+#define BF_VARIANT_PACKED 1  /* operands packed into shared-memory panels ('B'/'C')     */
+#define BF_VARIANT_BLOCKED 2 /* dpotrf only: right-looking sequence of the above kernels */
+
+/* ------------------------------------------------------------------------ */
+/* dgemm (section 2.1): C <= alpha * op(A) * op(B) + beta * C,               */
+/* op(X) = X ('N') or X^T ('T'); C is m x n, op(A) m x k, op(B) k x n.        */
+/* beta == 0: C is written without being read.  alpha == 0 or k == 0: C is   */
+/* only scaled by beta.  lda >= max(1, rows of A), ldb >= max(1, rows of B), */
+/* ldc >= max(1, m).                                                         */
+/* ------------------------------------------------------------------------ */
+int bf_dgemm(char transa, char transb, int m, int n, int k, double alpha,
+             const double* A, int lda, const double* B, int ldb, double beta,
+             double* C, int ldc, bf_stream_t stream);
+
+/* strideC >= ldc*n when batch > 1 (outputs may not overlap); strideA and    */
+/* strideB may be 0 (the same operand for every problem).                    */
+int bf_dgemm_strided_batched(char transa, char transb, int m, int n, int k, double alpha,
+                             const double* A, int lda, long long strideA,
+                             const double* B, int ldb, long long strideB, double beta,
+                             double* C, int ldc, long long strideC, int batch,
+                             bf_stream_t stream);
+
+/* Aarray, Barray, Carray: device arrays of `batch` device pointers. */
+int bf_dgemm_batched(char transa, char transb, int m, int n, int k, double alpha,
+                     const double* const* Aarray, int lda, const double* const* Barray, int ldb,
+                     double beta, double* const* Carray, int ldc, int batch, bf_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* dtrsm (section 3.1 "dtrsm"): solve op(A) X = alpha B (side 'L') or         */
+/* X op(A) = alpha B (side 'R'); X overwrites B (m x n).  A is triangular    */
+/* ('L' lower / 'U' upper stored), diag 'U' = unit diagonal (not read).       */
+/* A is m x m for side 'L' and n x n for side 'R'; lda >= max(1, that order),*/
+/* ldb >= max(1, m).  alpha == 0 sets B to zero without reading A.           */
+/* ------------------------------------------------------------------------ */
+int bf_dtrsm(char side, char uplo, char transa, char diag, int m, int n, double alpha,
+             const double* A, int lda, double* B, int ldb, bf_stream_t stream);
+
+int bf_dtrsm_strided_batched(char side, char uplo, char transa, char diag, int m, int n,
+                             double alpha, const double* A, int lda, long long strideA,
+                             double* B, int ldb, long long strideB, int batch,
+                             bf_stream_t stream);
+
+int bf_dtrsm_batched(char side, char uplo, char transa, char diag, int m, int n, double alpha,
+                     const double* const* Aarray, int lda, double* const* Barray, int ldb,
+                     int batch, bf_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* dpotrf (section 3.1 "dpotrf"): Cholesky factorisation A = L L^T of SPD    */
+/* matrices, uplo 'L': the lower triangle of A is read and overwritten by L; */
+/* the strict upper triangle and the padding rows (lda > n) are not touched. */
+/* info (device, one int per problem): 0 on success, j > 0 when the leading  */
+/* minor of order j is not positive definite (or NaN); that problem's        */
+/* factorisation stops at column j.  info may be NULL.  uplo 'U' returns     */
+/* BF_ERR_NOT_SUPPORTED.                                                      */
+/* ------------------------------------------------------------------------ */
+int bf_dpotrf(char uplo, int n, double* A, int lda, int* info, bf_stream_t stream);
+
+int bf_dpotrf_strided_batched(char uplo, int n, double* A, int lda, long long strideA,
+                              int* info, int batch, bf_stream_t stream);
+
+int bf_dpotrf_batched(char uplo, int n, double* const* Aarray, int lda, int* info, int batch,
+                      bf_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* dpotrs: solve A X = B with the factor from bf_dpotrf ('L'): the forward  */
+/* solve L Y = B then the backward solve L^T X = Y (section 3.1 "dtrsm"       */
+/* left variants).  B (n x nrhs, ldb >= max(1, n)) is overwritten by X.       */
+/* ------------------------------------------------------------------------ */
+int bf_dpotrs(char uplo, int n, int nrhs, const double* A, int lda, double* B, int ldb,
+              bf_stream_t stream);
+
+int bf_dpotrs_strided_batched(char uplo, int n, int nrhs, const double* A, int lda,
+                              long long strideA, double* B, int ldb, long long strideB,
+                              int batch, bf_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* The size switch (section 2.4: the switch point between variants depends  */
+/* on the routine and the architecture and is set by measurement).           */
+/* bf_tune_set adds a table entry, consulted before the built-in defaults:    */
+/*   routine  BF_ROUTINE_*                                                    */
+/*   code     dgemm: 2*transA + transB; dtrsm: 8*right + 4*upper + 2*trans +  */
+/*            unit; dpotrf: 0.  -1 matches every code.                        */
+/*   [n_lo, n_hi]  matrix order range (dgemm: max(m, n); dtrsm: order of A)   */
+/*   variant  BF_VARIANT_*                                                    */
+/*   p0..p3   dgemm: TM, TN, KC, P (super-tile rows/cols, k-slice, problems   */
+/*            per CTA; 0 = default); dtrsm: MR (4/8), P; dpotrf: T, NB.       */
+/* Later entries take precedence.  bf_tune_clear removes all entries.         */
+/* bf_tune_query writes the configuration a call would use into out[5]:       */
+/* {variant, p0, p1, p2, p3} in the order above (dgemm: variant,TM,TN,KC,P).  */
+/* ------------------------------------------------------------------------ */
+int bf_tune_set(int routine, int code, int n_lo, int n_hi, int variant, int p0, int p1, int p2,
+                int p3);
+void bf_tune_clear(void);
+int bf_tune_query(int routine, int code, int m, int n, int k, long long batch, int* out);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement support (no counterpart in the paper).                        */
+/* bf_launch_count: number of kernels this library has launched since it was */
+/* loaded (host-side counter; differences over a region count its launches). */
+/* bf_probe_fp64: launches `blocks` CTAs of 256 threads, each issuing        */
+/* iters * 8 independent FP64 fused multiply-adds (2 flops each) and writing */
+/* one double per thread to out (device, blocks * 256 doubles).  Timed by    */
+/* the caller, it measures the FP64 FMA throughput that bounds the routines. */
+/* ------------------------------------------------------------------------ */
+unsigned long long bf_launch_count(void);
+int bf_probe_fp64(int blocks, int iters, double* out, bf_stream_t stream);
+
+/* Human-readable text for a return code. */
+const char* bf_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFGPU_H */

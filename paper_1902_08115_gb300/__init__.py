@@ -1,0 +1,195 @@
+"""Batched small-matrix FP64 BLAS/LAPACK for one GB300 (sm_103a).
+
+Thin Python binding of the C ABI in include/bfgpu.h: argument marshalling
+only.  Every step of every routine runs in the library's CUDA kernels
+(libbfgpu.so); there is no CPU fallback, and importing this package fails
+loudly when the compiled library is missing.
+
+Tensor convention: a batch of column-major matrices with ``ncols`` columns and
+leading dimension ``ld`` is a contiguous float64 CUDA tensor of shape
+``(batch, ncols, ld)``; element (i, j) of problem b is ``X[b, j, i]`` (the
+BLAS storage the paper keeps, section 2.1).  Work is enqueued on torch's
+current CUDA stream.
+
+The functions with a ``bf_`` prefix are the raw C entry points (ctypes
+functions taking device pointers); the lower-case helpers take tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libbfgpu.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build the CUDA library first "
+        "(python -m paper_1902_08115_gb300.build); there is no CPU fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+_c = ctypes.c_char
+_i = ctypes.c_int
+_ll = ctypes.c_longlong
+_d = ctypes.c_double
+_vp = ctypes.c_void_p
+_ip = ctypes.POINTER(ctypes.c_int)
+
+_SIGS = {
+    "bf_dgemm": [_c, _c, _i, _i, _i, _d, _vp, _i, _vp, _i, _d, _vp, _i, _vp],
+    "bf_dgemm_strided_batched": [_c, _c, _i, _i, _i, _d, _vp, _i, _ll, _vp, _i, _ll, _d, _vp, _i, _ll,
+                                 _i, _vp],
+    "bf_dgemm_batched": [_c, _c, _i, _i, _i, _d, _vp, _i, _vp, _i, _d, _vp, _i, _i, _vp],
+    "bf_dtrsm": [_c, _c, _c, _c, _i, _i, _d, _vp, _i, _vp, _i, _vp],
+    "bf_dtrsm_strided_batched": [_c, _c, _c, _c, _i, _i, _d, _vp, _i, _ll, _vp, _i, _ll, _i, _vp],
+    "bf_dtrsm_batched": [_c, _c, _c, _c, _i, _i, _d, _vp, _i, _vp, _i, _i, _vp],
+    "bf_dpotrf": [_c, _i, _vp, _i, _vp, _vp],
+    "bf_dpotrf_strided_batched": [_c, _i, _vp, _i, _ll, _vp, _i, _vp],
+    "bf_dpotrf_batched": [_c, _i, _vp, _i, _vp, _i, _vp],
+    "bf_dpotrs": [_c, _i, _i, _vp, _i, _vp, _i, _vp],
+    "bf_dpotrs_strided_batched": [_c, _i, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _vp],
+    "bf_tune_set": [_i, _i, _i, _i, _i, _i, _i, _i, _i],
+    "bf_tune_clear": [],
+    "bf_tune_query": [_i, _i, _i, _i, _i, _ll, _ip],
+    "bf_status_string": [_i],
+    "bf_launch_count": [],
+    "bf_probe_fp64": [_i, _i, _vp, _vp],
+}
+_RES = {"bf_tune_clear": None, "bf_status_string": ctypes.c_char_p,
+        "bf_launch_count": ctypes.c_ulonglong}
+
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _RES.get(_name, _i)
+    globals()[_name] = _f
+
+ROUTINE_DGEMM, ROUTINE_DTRSM, ROUTINE_DPOTRF = 0, 1, 2
+VARIANT_DIRECT, VARIANT_PACKED, VARIANT_BLOCKED = 0, 1, 2
+ERR_CUDA, ERR_NOT_SUPPORTED = 1001, 1002
+
+
+class BFError(RuntimeError):
+    """A library call returned a nonzero status."""
+
+    def __init__(self, name: str, status: int):
+        self.status = status
+        msg = bf_status_string(status).decode()
+        super().__init__(f"{name} returned {status}: {msg}")
+
+
+def _check(name: str, status: int) -> None:
+    if status != 0:
+        raise BFError(name, status)
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _ch(c: str) -> bytes:
+    return c.encode("ascii")
+
+
+def _batch_dims(X):
+    """(batch, ncols, ld, stride) of a (batch, ncols, ld) tensor with unit inner stride."""
+    if X.dim() != 3:
+        raise ValueError("expected a (batch, ncols, ld) tensor")
+    if X.stride(2) != 1 or X.stride(1) != X.shape[2]:
+        raise ValueError("each problem must be a contiguous column-major (ncols, ld) block")
+    if X.dtype.itemsize != 8:
+        raise ValueError("float64 tensors expected")
+    return X.shape[0], X.shape[1], X.shape[2], X.stride(0)
+
+
+def _square(*Xs):
+    """Common order when every tensor is an unpadded square batch, else None."""
+    n = Xs[0].shape[1]
+    return n if all(X.shape[1] == X.shape[2] == n for X in Xs) else None
+
+
+def dgemm(transa: str, transb: str, alpha: float, A, B, beta: float, C, m=None, n=None, k=None,
+          stream=None):
+    """C <= alpha op(A) op(B) + beta C for every problem of a strided batch (in place on C).
+
+    m, n, k may be omitted only when A, B and C are unpadded square batches of
+    one order (the leading dimension cannot tell padding from rows otherwise).
+    """
+    bA, cA, ldA, sA = _batch_dims(A)
+    bB, cB, ldB, sB = _batch_dims(B)
+    bC, cC, ldC, sC = _batch_dims(C)
+    if m is None or n is None or k is None:
+        sq = _square(A, B, C)
+        if sq is None:
+            raise ValueError("pass m, n, k explicitly for padded or non-square operands")
+        m = sq if m is None else m
+        n = sq if n is None else n
+        k = sq if k is None else k
+    _check("bf_dgemm_strided_batched", bf_dgemm_strided_batched(
+        _ch(transa), _ch(transb), m, n, k, alpha, _ptr(A), ldA, sA if bA > 1 else 0, _ptr(B), ldB,
+        sB if bB > 1 else 0, beta, _ptr(C), ldC, sC, bC, _stream(stream)))
+    return C
+
+
+def dtrsm(side: str, uplo: str, transa: str, diag: str, alpha: float, A, B, m=None, n=None,
+          stream=None):
+    """op(A) X = alpha B (side 'L') or X op(A) = alpha B (side 'R'); X overwrites B.
+
+    m, n may be omitted only for unpadded square batches of one order.
+    """
+    bA, cA, ldA, sA = _batch_dims(A)
+    bB, cB, ldB, sB = _batch_dims(B)
+    if m is None or n is None:
+        sq = _square(A, B)
+        if sq is None:
+            raise ValueError("pass m, n explicitly for padded or non-square operands")
+        m = sq if m is None else m
+        n = sq if n is None else n
+    _check("bf_dtrsm_strided_batched", bf_dtrsm_strided_batched(
+        _ch(side), _ch(uplo), _ch(transa), _ch(diag), m, n, alpha, _ptr(A), ldA, sA if bA > 1 else 0,
+        _ptr(B), ldB, sB, bB, _stream(stream)))
+    return B
+
+
+def dpotrf(A, n=None, info=None, uplo: str = "L", stream=None):
+    """Cholesky of every problem in place (lower); returns the device int32 info tensor."""
+    import torch
+    bA, cA, ldA, sA = _batch_dims(A)
+    n = cA if n is None else n
+    if info is None:
+        info = torch.empty(bA, dtype=torch.int32, device=A.device)
+    _check("bf_dpotrf_strided_batched", bf_dpotrf_strided_batched(
+        _ch(uplo), n, _ptr(A), ldA, sA, _ptr(info), bA, _stream(stream)))
+    return info
+
+
+def dpotrs(L, B, n=None, nrhs=None, uplo: str = "L", stream=None):
+    """Solve A X = B with the Cholesky factor L of A (in place on B)."""
+    bL, cL, ldL, sL = _batch_dims(L)
+    bB, cB, ldB, sB = _batch_dims(B)
+    n = cL if n is None else n
+    nrhs = cB if nrhs is None else nrhs
+    _check("bf_dpotrs_strided_batched", bf_dpotrs_strided_batched(
+        _ch(uplo), n, nrhs, _ptr(L), ldL, sL, _ptr(B), ldB, sB, bB, _stream(stream)))
+    return B
+
+
+def tune_query(routine: int, code: int, m: int, n: int, k: int, batch: int):
+    out = (ctypes.c_int * 5)()
+    _check("bf_tune_query", bf_tune_query(routine, code, m, n, k, batch, out))
+    return list(out)
+
+
+def tune_set(routine: int, code: int, n_lo: int, n_hi: int, variant: int, p0=0, p1=0, p2=0, p3=0):
+    _check("bf_tune_set", bf_tune_set(routine, code, n_lo, n_hi, variant, p0, p1, p2, p3))
+
+
+def tune_clear():
+    bf_tune_clear()

@@ -1,0 +1,245 @@
+// bf_dpotrf.cu -- batched FP64 Cholesky, lower (section 3.1 "dpotrf").
+//
+// The paper implements dpotrf as nested loops of tailored kernels whose block
+// size is the kernel size, each kernel being "dgemm_nt inner loop, then a
+// register-resident edge, then a (lower) store" (section 3.2.1, the
+// kernel_dpotrf_nt_l listing).  Here:
+//
+//  * lane kernels (small n): one thread factors one whole problem, so all 32
+//    lanes of a warp execute the same FP64 instruction stream on 32 problems
+//    (on this GPU an FP64 warp instruction costs the same whatever its active
+//    mask, so per-problem lanes are the only way to keep the triangular loop
+//    and the pivot square roots fully utilised).  Left-looking by 4-column
+//    blocks: for the diagonal block, D = A_JJ - L_J L_J^T (dgemm loop), then
+//    a 4x4 Cholesky in registers (edge); for each 4-row block below it,
+//    acc = A_IJ - L_I L_J^T (dgemm loop), then acc L_JJ^{-T} (trsm edge).
+//    DIRECT works in place in global memory; PACKED first copies the CTA's
+//    problems into shared memory, problem-interleaved so that the 32 lanes
+//    of a warp touch 32 consecutive words.
+//
+//  * blocked (large n, small batches): right-looking with block NB, as a
+//    sequence of launches of the library's own kernels on sub-matrices --
+//    lane Cholesky of the NB x NB diagonal blocks, row-parallel trsm of the
+//    panel below, lower-only dgemm_nt trailing update.
+//
+// info follows LAPACK: 0, or the 1-based column j whose pivot is not
+// positive (or NaN); the problem's factorisation stops there.
+#include "bf_internal.h"
+
+namespace bf {
+
+struct GAcc {  // a problem in global memory
+    double* a;
+    int lda;
+    __device__ __forceinline__ double ld(int i, int j) const { return a[i + (long long)j * lda]; }
+    __device__ __forceinline__ void st(int i, int j, double v) const { a[i + (long long)j * lda] = v; }
+};
+
+struct SAcc {  // a problem in shared memory, interleaved with the CTA's other problems
+    double* s;
+    int n, T;
+    __device__ __forceinline__ double ld(int i, int j) const { return s[(i + j * n) * T]; }
+    __device__ __forceinline__ void st(int i, int j, double v) const { s[(i + j * n) * T] = v; }
+};
+
+// Factor one problem in place through the accessor.  Returns info (0 or 1-based column).
+template <class Acc>
+__device__ __forceinline__ int potrf_lane(const Acc& M, int n) {
+    for (int J = 0; J < n; J += 4) {
+        const int jb = imin(4, n - J);
+        int jr[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) jr[r] = imin(J + r, n - 1);
+        // ---- diagonal block: D = A_JJ - sum_p L(J:J+4, p) L(J:J+4, p)^T (lower part) ----
+        double d[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c <= r; c++) d[r][c] = M.ld(jr[r], jr[c]);
+        for (int pp = 0; pp < J; pp++) {
+            double l[4];
+#pragma unroll
+            for (int r = 0; r < 4; r++) l[r] = M.ld(jr[r], pp);
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c <= r; c++) d[r][c] = fma(-l[r], l[c], d[r][c]);
+        }
+        // pad the block beyond n with the identity
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            if (r >= jb) {
+#pragma unroll
+                for (int c = 0; c < r; c++) d[r][c] = 0.0;
+                d[r][r] = 1.0;
+            }
+        }
+        // ---- 4x4 Cholesky edge in registers ----
+        double rinv[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const double piv = d[c][c];
+            if (!(piv > 0.0)) return J + c + 1;
+            const double rs = rsqrt(piv);
+            rinv[c] = rs;
+            d[c][c] = piv * rs;
+#pragma unroll
+            for (int r = c + 1; r < 4; r++) d[r][c] *= rs;
+#pragma unroll
+            for (int r = c + 1; r < 4; r++)
+#pragma unroll
+                for (int c2 = c + 1; c2 <= r; c2++) d[r][c2] = fma(-d[r][c], d[c2][c], d[r][c2]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c <= r; c++)
+                if (r < jb) M.st(J + r, J + c, d[r][c]);
+        // ---- 4-row blocks below: acc = A_IJ - L_I L_J^T, then acc L_JJ^{-T} ----
+        for (int I = J + 4; I < n; I += 4) {
+            const int ib = imin(4, n - I);
+            int ir[4];
+#pragma unroll
+            for (int r = 0; r < 4; r++) ir[r] = imin(I + r, n - 1);
+            double acc[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[r][c] = M.ld(ir[r], jr[c]);
+            for (int pp = 0; pp < J; pp++) {
+                double a[4], b[4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) a[r] = M.ld(ir[r], pp);
+#pragma unroll
+                for (int c = 0; c < 4; c++) b[c] = M.ld(jr[c], pp);
+#pragma unroll
+                for (int r = 0; r < 4; r++)
+#pragma unroll
+                    for (int c = 0; c < 4; c++) acc[r][c] = fma(-a[r], b[c], acc[r][c]);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+#pragma unroll
+                for (int c2 = 0; c2 < c; c2++)
+#pragma unroll
+                    for (int r = 0; r < 4; r++) acc[r][c] = fma(-acc[r][c2], d[c][c2], acc[r][c]);
+#pragma unroll
+                for (int r = 0; r < 4; r++) acc[r][c] *= rinv[c];
+            }
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++)
+                    if (r < ib && c < jb) M.st(I + r, J + c, acc[r][c]);
+        }
+    }
+    return 0;
+}
+
+__global__ void __launch_bounds__(256) dpotrf_lane_direct_kernel(PotrfParams p) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= p.batch) return;
+    if (p.skip && p.skip[q] != 0) return;
+    GAcc M{p.A.mptr(q), p.lda};
+    const int info = potrf_lane(M, p.n);
+    if (info && p.info) p.info[q] = info + p.info_off;
+}
+
+__global__ void __launch_bounds__(256) dpotrf_lane_packed_kernel(PotrfParams p) {
+    extern __shared__ double smem[];
+    const int T = blockDim.x;
+    const long long q0 = blockIdx.x * (long long)T;
+    const int n = p.n;
+    const int per = n * n;
+    // coalesced copy of the lower triangles of the CTA's problems into shared memory
+    for (int e = threadIdx.x; e < T * per; e += T) {
+        const int qq = e / per;
+        const int rem = e - qq * per;
+        const int j = rem / n, i = rem - j * n;
+        const long long qg = q0 + qq;
+        double v = 0.0;
+        if (qg < p.batch && i >= j) v = p.A.ptr(qg)[i + (long long)j * p.lda];
+        smem[(i + j * n) * T + qq] = v;
+    }
+    __syncthreads();
+    const long long q = q0 + threadIdx.x;
+    int info = 0;
+    bool active = q < p.batch && !(p.skip && p.skip[q] != 0);
+    if (active) {
+        SAcc M{smem + threadIdx.x, n, T};
+        info = potrf_lane(M, n);
+        if (info && p.info) p.info[q] = info + p.info_off;
+    }
+    __syncthreads();
+    // write back the lower triangles of the problems that succeeded
+    for (int e = threadIdx.x; e < T * per; e += T) {
+        const int qq = e / per;
+        const int rem = e - qq * per;
+        const int j = rem / n, i = rem - j * n;
+        const long long qg = q0 + qq;
+        if (qg < p.batch && i >= j) {
+            if (p.skip && p.skip[qg] != 0) continue;
+            if (p.info && p.info[qg] != 0) continue;
+            p.A.mptr(qg)[i + (long long)j * p.lda] = smem[(i + j * n) * T + qq];
+        }
+    }
+}
+
+cudaError_t launch_dpotrf_lane(int n, MatRef A, int lda, long long batch, int* info, int info_off,
+                               const int* skip, const PotrfConfig& cfg, cudaStream_t s) {
+    PotrfParams p;
+    p.n = n; p.A = A; p.lda = lda; p.batch = batch; p.info = info; p.info_off = info_off; p.skip = skip;
+    if (cfg.variant == VAR_PACKED) {
+        const int T = cfg.T;
+        size_t smem = sizeof(double) * (size_t)T * n * n;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(dpotrf_lane_packed_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        long long blocks = (batch + T - 1) / T;
+        dpotrf_lane_packed_kernel<<<(unsigned)blocks, T, smem, s>>>(p);
+        count_launch();
+        return cudaGetLastError();
+    }
+    const int T = cfg.T > 0 ? cfg.T : 128;
+    long long blocks = (batch + T - 1) / T;
+    dpotrf_lane_direct_kernel<<<(unsigned)blocks, T, 0, s>>>(p);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dpotrf(int n, MatRef A, int lda, long long batch, int* info,
+                          const PotrfConfig& cfg, cudaStream_t s) {
+    if (batch == 0) return cudaSuccess;
+    if (info) {
+        cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int) * (size_t)batch, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (n == 0) return cudaSuccess;
+    if (cfg.variant != VAR_BLOCKED) return launch_dpotrf_lane(n, A, lda, batch, info, 0, nullptr, cfg, s);
+    // right-looking blocked factorisation built from the library's kernels
+    const int NB = cfg.NB;
+    PotrfConfig lane{VAR_DIRECT, 128, 0};
+    for (int J = 0; J < n; J += NB) {
+        const int jb = (n - J < NB) ? (n - J) : NB;
+        cudaError_t e = launch_dpotrf_lane(jb, mat_sub(A, J, J, lda), lda, batch, info, J, info, lane, s);
+        if (e != cudaSuccess) return e;
+        const int rest = n - J - jb;
+        if (rest <= 0) break;
+        // panel: L(J+jb:n, J:J+jb) = A(J+jb:n, J:J+jb) L_JJ^{-T}
+        TrsmConfig tc = choose_trsm(1, 0, 1, 0, rest, jb, batch);
+        e = launch_dtrsm(1, 0, 1, 0, rest, jb, 1.0, mat_sub(A, J, J, lda), lda,
+                         mat_sub(A, J + jb, J, lda), lda, batch, tc, info, s);
+        if (e != cudaSuccess) return e;
+        // trailing update (lower part only): A22 -= L21 L21^T
+        MatRef P = mat_sub(A, J + jb, J, lda);
+        GemmConfig gc = choose_gemm(false, true, rest, rest, jb, lda, batch);
+        e = launch_dgemm(false, true, rest, rest, jb, -1.0, P, lda, P, lda, 1.0,
+                         mat_sub(A, J + jb, J + jb, lda), lda, batch, gc, 1, info, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace bf

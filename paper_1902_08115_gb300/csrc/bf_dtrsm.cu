@@ -1,0 +1,211 @@
+// bf_dtrsm.cu -- batched FP64 triangular solve (section 3.1 "dtrsm").
+//
+// The paper implements only the right-side kernels, because they solve many
+// small independent row systems with the triangle broadcast (vector
+// friendly), and obtains the left side by transposition:
+// op(A)^{-1} B = (B^T op(A)^{-T})^T (section 3.1 "dtrsm").  The same holds on
+// the GPU: every row of the right-hand side is an independent system, so one
+// thread solves MR rows and all threads of a warp run the same instruction
+// stream.  A left solve is the right solve of B^T against op(A)^T, i.e. the
+// same kernel reading B transposed ("bt") and A with the opposite transpose.
+//
+// Kernel structure per 4-column block J (the paper's dtrsm kernel: a dgemm
+// loop followed by a register-resident triangular edge):
+//   acc = alpha R(rows, J)  -  X(rows, solved) T(solved, J)     (dgemm loop)
+//   acc = acc T(J, J)^{-1}                                       (edge, in registers)
+//   R(rows, J) = acc                                             (store)
+// T upper is solved forward (j = 0..n-1), T lower backward (j = n-1..0).
+#include "bf_internal.h"
+
+namespace bf {
+
+template <int MR, bool PACKED>
+__global__ void __launch_bounds__(256)
+dtrsm_rows_kernel(TrsmParams p) {
+    extern __shared__ double smem[];
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long q = gt / p.tpp;
+    const int rr = (int)(gt - q * p.tpp);
+    const int n = p.n;
+    // PACKED: the CTA's problems' triangles and reciprocal diagonals in shared memory
+    const long long q0 = (blockIdx.x * (long long)blockDim.x) / p.tpp;
+    const int ldt = n + 1;
+    double* sT = smem;
+    double* sR = smem + (size_t)p.P * n * ldt;
+    if (PACKED) {
+        const int per = n * n;
+        for (int e = threadIdx.x; e < p.P * per; e += blockDim.x) {
+            const int qq = e / per;
+            const int rem = e - qq * per;
+            const int j = rem / n, i = rem - j * n;
+            const long long qg = q0 + qq;
+            double v = 0.0;
+            const bool inT = p.upper ? (i <= j) : (i >= j);
+            if (qg < p.batch && inT && !(p.unit && i == j)) {
+                const double* Aq = p.A.ptr(qg);
+                v = p.et ? ldg(Aq + j + (long long)i * p.lda) : ldg(Aq + i + (long long)j * p.lda);
+            }
+            sT[qq * n * ldt + i + j * ldt] = v;  // sT(i, j) = T(i, j)
+        }
+        __syncthreads();
+        if (!p.unit) {
+            for (int e = threadIdx.x; e < p.P * n; e += blockDim.x) {
+                const int qq = e / n, j = e - (e / n) * n;
+                sR[qq * n + j] = 1.0 / sT[qq * n * ldt + j + j * ldt];
+            }
+            __syncthreads();
+        }
+    }
+    if (q >= p.batch) return;
+    if (p.skip && p.skip[q] != 0) return;
+
+    const double* A = p.A.ptr(q);
+    double* B = p.B.mptr(q);
+    const double* Ts = PACKED ? (sT + (q - q0) * n * ldt) : nullptr;
+    const double* Rs = PACKED ? (sR + (q - q0) * n) : nullptr;
+
+    int rows[MR];
+    long long roff[MR];
+#pragma unroll
+    for (int s = 0; s < MR; s++) {
+        rows[s] = rr + p.tpp * s;
+        const int rc = imin(rows[s], p.m - 1);
+        roff[s] = p.bt ? (long long)rc * p.ldb : rc;
+    }
+    const long long cstep = p.bt ? 1 : p.ldb;  // R(r, j + 1) - R(r, j)
+
+    auto Tel = [&](int i, int j) -> double {
+        if (PACKED) return Ts[i + j * ldt];
+        return p.et ? ldg(A + j + (long long)i * p.lda) : ldg(A + i + (long long)j * p.lda);
+    };
+
+    const int nblk = (n + 3) / 4;
+    for (int bi = 0; bi < nblk; bi++) {
+        const int blk = p.upper ? bi : (nblk - 1 - bi);
+        const int J = blk * 4;
+        const int jb = imin(4, n - J);
+        double acc[MR][4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const int jc = imin(J + c, n - 1);
+#pragma unroll
+            for (int s = 0; s < MR; s++) acc[s][c] = B[roff[s] + jc * cstep];
+        }
+        if (p.alpha != 1.0) {
+#pragma unroll
+            for (int s = 0; s < MR; s++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[s][c] *= p.alpha;
+        }
+        // dgemm loop over the already solved columns
+        const int pb = p.upper ? 0 : J + jb;
+        const int pe = p.upper ? J : n;
+#pragma unroll 2
+        for (int pp = pb; pp < pe; pp++) {
+            double x[MR], tv[4];
+#pragma unroll
+            for (int s = 0; s < MR; s++) x[s] = B[roff[s] + pp * cstep];
+#pragma unroll
+            for (int c = 0; c < 4; c++) tv[c] = Tel(pp, imin(J + c, n - 1));
+#pragma unroll
+            for (int s = 0; s < MR; s++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[s][c] = fma(-x[s], tv[c], acc[s][c]);
+        }
+        // triangular edge on the jb x jb diagonal block, in registers
+        double tb[4][4], rinv[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+#pragma unroll
+            for (int c2 = 0; c2 < 4; c2++) {
+                const bool need = p.upper ? (c2 < c) : (c2 > c);
+                tb[c2][c] = (need && c < jb && c2 < jb) ? Tel(J + c2, J + c) : 0.0;
+            }
+            if (!p.unit) {
+                if (PACKED) rinv[c] = (c < jb) ? Rs[J + c] : 1.0;
+                else rinv[c] = (c < jb) ? 1.0 / Tel(J + c, J + c) : 1.0;
+            }
+        }
+        if (p.upper) {
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+#pragma unroll
+                for (int c2 = 0; c2 < c; c2++)
+#pragma unroll
+                    for (int s = 0; s < MR; s++) acc[s][c] = fma(-acc[s][c2], tb[c2][c], acc[s][c]);
+                if (!p.unit)
+#pragma unroll
+                    for (int s = 0; s < MR; s++) acc[s][c] *= rinv[c];
+            }
+        } else {
+#pragma unroll
+            for (int c = 3; c >= 0; c--) {
+#pragma unroll
+                for (int c2 = c + 1; c2 < 4; c2++)
+#pragma unroll
+                    for (int s = 0; s < MR; s++) acc[s][c] = fma(-acc[s][c2], tb[c2][c], acc[s][c]);
+                if (!p.unit)
+#pragma unroll
+                    for (int s = 0; s < MR; s++) acc[s][c] *= rinv[c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            if (c < jb) {
+#pragma unroll
+                for (int s = 0; s < MR; s++)
+                    if (rows[s] < p.m) B[roff[s] + (J + c) * cstep] = acc[s][c];
+            }
+        }
+    }
+}
+
+template <int MR, bool PACKED>
+static cudaError_t launch_rows(const TrsmParams& p, long long threads, int block, size_t smem,
+                               cudaStream_t s) {
+    auto kfn = dtrsm_rows_kernel<MR, PACKED>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    long long blocks = (threads + block - 1) / block;
+    kfn<<<(unsigned)blocks, block, smem, s>>>(p);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dtrsm(int side, int uplo, int trans, int unit, int m, int n, double alpha,
+                         MatRef A, int lda, MatRef B, int ldb, long long batch,
+                         const TrsmConfig& cfg, const int* skip, cudaStream_t s) {
+    if (m == 0 || n == 0 || batch == 0) return cudaSuccess;
+    TrsmParams p;
+    const bool right = (side == 1);
+    // rows of R: right -> rows of B (m x n, T is n x n); left -> columns of B (R = B^T, T is m x m)
+    p.m = right ? m : n;
+    p.n = right ? n : m;
+    p.alpha = alpha;
+    p.A = A; p.lda = lda; p.B = B; p.ldb = ldb;
+    p.batch = batch;
+    p.bt = right ? 0 : 1;
+    p.et = right ? trans : !trans;
+    p.upper = (uplo == 1) ^ p.et;
+    p.unit = unit;
+    p.skip = skip;
+    const int MR = cfg.MR;
+    p.tpp = (p.m + MR - 1) / MR;
+    long long threads = batch * p.tpp;
+    if (cfg.variant == VAR_PACKED) {
+        // one CTA holds P whole problems (block = P * tpp threads)
+        p.P = cfg.P;
+        int block = p.P * p.tpp;
+        size_t smem = sizeof(double) * ((size_t)p.P * p.n * (p.n + 1) + (size_t)p.P * p.n);
+        threads = ((batch + p.P - 1) / p.P) * (long long)block;
+        return MR == 8 ? launch_rows<8, true>(p, threads, block, smem, s)
+                       : launch_rows<4, true>(p, threads, block, smem, s);
+    }
+    p.P = 1;
+    return MR == 8 ? launch_rows<8, false>(p, threads, 256, 0, s)
+                   : launch_rows<4, false>(p, threads, 256, 0, s);
+}
+
+}  // namespace bf

@@ -1,0 +1,104 @@
+// bf_internal.h -- declarations shared by the CUDA translation units of the
+// library (not part of the public C ABI, which is include/bfgpu.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "bf_common.cuh"
+
+namespace bf {
+
+// Kernel variants the size switch chooses between (section 2.4: direct 'D'
+// for very small sizes, packing variants for larger ones).
+enum Variant : int { VAR_DIRECT = 0, VAR_PACKED = 1, VAR_BLOCKED = 2 };
+
+struct GemmConfig {
+    int variant;  // VAR_DIRECT or VAR_PACKED
+    int TM, TN;   // super-tile of C covered by one CTA (multiples of 4)
+    int KC;       // k-slice staged in shared memory (packed)
+    int P;        // problems per CTA
+};
+
+struct GemmParams {
+    int m, n, k;
+    double alpha, beta;
+    int mode;
+    MatRef A;
+    int lda;
+    MatRef B;
+    int ldb;
+    MatRef C;
+    int ldc;
+    long long batch;
+    int TM, TN, KC, P;
+    int tilesM, tilesN;
+    int lower;
+    const int* skip;
+};
+
+struct TrsmConfig {
+    int variant;  // VAR_DIRECT or VAR_PACKED
+    int MR;       // rows of the right-hand side per thread (4 or 8)
+    int P;        // problems per CTA (packed)
+};
+
+// Row-parallel triangular solve X T = alpha R (every row of R independent).
+// T(p, j) = et ? A[j + p*lda] : A[p + j*lda]; R(r, j) = bt ? B[j + r*ldb] : B[r + j*ldb].
+struct TrsmParams {
+    int m, n;
+    double alpha;
+    MatRef A;
+    int lda;
+    MatRef B;
+    int ldb;
+    long long batch;
+    int et, upper, unit, bt;
+    int tpp;  // threads per problem = ceil(m / MR)
+    int P;
+    const int* skip;
+};
+
+struct PotrfConfig {
+    int variant;  // VAR_DIRECT (lane per problem, in place), VAR_PACKED (lane per problem,
+                  // shared memory), VAR_BLOCKED (right-looking sequence of kernels)
+    int T;        // threads (= problems) per CTA for the lane kernels
+    int NB;       // block size of the blocked variant
+};
+
+struct PotrfParams {
+    int n;
+    MatRef A;
+    int lda;
+    long long batch;
+    int* info;      // per-problem LAPACK info (device), may be null
+    int info_off;   // added to a failing column (blocked use on a sub-matrix)
+    const int* skip;
+};
+
+// Increments the library's kernel-launch counter (bf_launch_count).
+void count_launch();
+
+size_t gemm_smem_bytes(const GemmConfig& c);
+
+cudaError_t launch_dgemm(bool ta, bool tb, int m, int n, int k, double alpha, MatRef A, int lda,
+                         MatRef B, int ldb, double beta, MatRef C, int ldc, long long batch,
+                         const GemmConfig& cfg, int lower, const int* skip, cudaStream_t s);
+
+// side: 0 = left, 1 = right; uplo: 0 = lower, 1 = upper; trans, unit: 0/1
+cudaError_t launch_dtrsm(int side, int uplo, int trans, int unit, int m, int n, double alpha,
+                         MatRef A, int lda, MatRef B, int ldb, long long batch,
+                         const TrsmConfig& cfg, const int* skip, cudaStream_t s);
+
+cudaError_t launch_dpotrf_lane(int n, MatRef A, int lda, long long batch, int* info, int info_off,
+                               const int* skip, const PotrfConfig& cfg, cudaStream_t s);
+
+cudaError_t launch_dpotrf(int n, MatRef A, int lda, long long batch, int* info,
+                          const PotrfConfig& cfg, cudaStream_t s);
+
+// Configuration choice (the size switch), in bf_tune.cu.
+GemmConfig choose_gemm(bool ta, bool tb, int m, int n, int k, int lda, long long batch);
+TrsmConfig choose_trsm(int side, int uplo, int trans, int unit, int m, int n, long long batch);
+PotrfConfig choose_potrf(int n, int lda, long long batch);
+
+}  // namespace bf

@@ -1,0 +1,196 @@
+// bf_tune.cu -- the size switch: which kernel variant and tiling a call uses.
+//
+// The paper switches by matrix size between algorithmic variants, with a
+// switch point that depends on the routine and the architecture and is found
+// by measurement (section 2.4; section 3.1 gives 64..400 on its CPUs).  Here
+// the switch is a table: built-in defaults below, overridden entry by entry
+// through bf_tune_set() by the autotuner, which measures every candidate on
+// the GPU it runs on.
+#include <mutex>
+#include <vector>
+
+#include "bf_internal.h"
+#include "../../include/bfgpu.h"
+
+namespace bf {
+
+struct TuneEntry {
+    int routine, code, lo, hi;
+    int variant, p0, p1, p2, p3;
+};
+
+static std::mutex g_mu;
+static std::vector<TuneEntry> g_table;
+
+static bool lookup(int routine, int code, int n, TuneEntry* out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto it = g_table.rbegin(); it != g_table.rend(); ++it) {
+        if (it->routine == routine && (it->code == code || it->code < 0) && n >= it->lo && n <= it->hi) {
+            *out = *it;
+            return true;
+        }
+    }
+    return false;
+}
+
+static int ceil4(int x) { return x < 4 ? 4 : (x + 3) / 4 * 4; }
+
+static const size_t kSmemBudget = 200 * 1024;  // per CTA, below the 227 KB opt-in limit
+
+// Make a dgemm configuration launchable: tiles are multiples of 4 no larger
+// than the (rounded) problem, at most 512 threads per CTA (the kernel's launch
+// bound), and the packed k-slice fits in shared memory.
+static void sanitize_gemm(GemmConfig& c, int m, int n, int k) {
+    if (c.variant != VAR_DIRECT && c.variant != VAR_PACKED) c.variant = VAR_PACKED;
+    c.TM = ceil4(c.TM < ceil4(m) ? c.TM : ceil4(m));
+    c.TN = ceil4(c.TN < ceil4(n) ? c.TN : ceil4(n));
+    while ((c.TM / 4) * (c.TN / 4) > 512) {
+        if (c.TM >= c.TN) c.TM = ceil4(c.TM / 2);
+        else c.TN = ceil4(c.TN / 2);
+    }
+    const int tpp = (c.TM / 4) * (c.TN / 4);
+    if (c.P < 1) c.P = 1;
+    while (c.P > 1 && c.P * tpp > 512) c.P--;
+    if (c.KC < 1 || c.KC > k) c.KC = k > 0 ? k : 1;
+    if (c.variant == VAR_PACKED) {
+        while (c.KC > 1 && gemm_smem_bytes(c) > kSmemBudget) c.KC = (c.KC + 1) / 2;
+        while (c.P > 1 && gemm_smem_bytes(c) > kSmemBudget) c.P--;
+    }
+}
+
+GemmConfig choose_gemm(bool ta, bool tb, int m, int n, int k, int lda, long long batch) {
+    (void)lda;
+    (void)batch;
+    GemmConfig c;
+    const int size = m > n ? m : n;
+    // built-in default: whole small problems per CTA, 64 x 64 super-tiles for large ones
+    if (m <= 64 && n <= 64) {
+        c.TM = ceil4(m);
+        c.TN = ceil4(n);
+    } else {
+        // split each dimension into the fewest super-tiles of at most 64, as even as possible
+        c.TM = ceil4((m + (m + 63) / 64 - 1) / ((m + 63) / 64));
+        c.TN = ceil4((n + (n + 63) / 64 - 1) / ((n + 63) / 64));
+    }
+    int tpp = (c.TM / 4) * (c.TN / 4);
+    c.P = 256 / tpp > 0 ? 256 / tpp : 1;
+    while ((c.P * tpp) % 32 != 0 && (c.P + 1) * tpp <= 512) c.P++;  // whole warps
+    c.variant = (size <= 8) ? VAR_DIRECT : VAR_PACKED;
+    c.KC = (m <= 64 && n <= 64) ? k : (k < 32 ? k : 32);
+    TuneEntry e;
+    if (lookup(BF_ROUTINE_DGEMM, (ta ? 2 : 0) + (tb ? 1 : 0), size, &e)) {
+        c.variant = e.variant;
+        if (e.p0 > 0) c.TM = e.p0;
+        if (e.p1 > 0) c.TN = e.p1;
+        if (e.p2 > 0) c.KC = e.p2;
+        if (e.p3 > 0) {
+            c.P = e.p3;
+        } else {
+            tpp = (ceil4(c.TM < ceil4(m) ? c.TM : ceil4(m)) / 4) * (ceil4(c.TN < ceil4(n) ? c.TN : ceil4(n)) / 4);
+            c.P = 256 / tpp > 0 ? 256 / tpp : 1;
+        }
+    }
+    sanitize_gemm(c, m, n, k);
+    return c;
+}
+
+static size_t trsm_smem(int P, int order) {
+    return sizeof(double) * ((size_t)P * order * (order + 1) + (size_t)P * order);
+}
+
+TrsmConfig choose_trsm(int side, int uplo, int trans, int unit, int m, int n, long long batch) {
+    (void)batch;
+    TrsmConfig c;
+    const int rows = side == 1 ? m : n;
+    const int order = side == 1 ? n : m;
+    const int code = side * 8 + uplo * 4 + trans * 2 + unit;
+    c.variant = VAR_DIRECT;
+    c.MR = rows >= 16 ? 8 : 4;
+    c.P = 1;
+    TuneEntry e;
+    if (lookup(BF_ROUTINE_DTRSM, code, order, &e)) {
+        c.variant = e.variant == VAR_PACKED ? VAR_PACKED : VAR_DIRECT;
+        if (e.p0 == 4 || e.p0 == 8) c.MR = e.p0;
+        c.P = e.p1 > 0 ? e.p1 : 0;
+    }
+    if (c.variant == VAR_PACKED) {
+        const int tpp = (rows + c.MR - 1) / c.MR;
+        if (tpp > 256) {
+            c.variant = VAR_DIRECT;  // a problem's rows do not fit one CTA
+        } else {
+            if (c.P <= 0) c.P = 128 / tpp > 0 ? 128 / tpp : 1;
+            while (c.P > 1 && c.P * tpp > 256) c.P--;
+            while (c.P > 1 && trsm_smem(c.P, order) > kSmemBudget) c.P--;
+            if (trsm_smem(c.P, order) > kSmemBudget) c.variant = VAR_DIRECT;
+        }
+    }
+    if (c.variant == VAR_DIRECT) c.P = 1;
+    return c;
+}
+
+PotrfConfig choose_potrf(int n, int lda, long long batch) {
+    (void)lda;
+    PotrfConfig c;
+    c.NB = 32;
+    c.T = 128;
+    if (n <= 8) {
+        c.variant = VAR_PACKED;
+    } else if (n <= 64 || batch >= 40000) {
+        c.variant = VAR_DIRECT;
+    } else {
+        c.variant = VAR_BLOCKED;
+    }
+    TuneEntry e;
+    if (lookup(BF_ROUTINE_DPOTRF, 0, n, &e)) {
+        c.variant = e.variant;
+        if (e.p0 > 0) c.T = e.p0;
+        if (e.p1 > 0) c.NB = e.p1;
+    }
+    if (c.T < 32) c.T = 32;
+    if (c.T > 256) c.T = 256;
+    c.T = c.T / 32 * 32;
+    if (c.NB < 4) c.NB = 4;
+    if (c.variant == VAR_PACKED) {
+        while (c.T > 32 && (size_t)c.T * n * n * sizeof(double) > kSmemBudget) c.T -= 32;
+        if ((size_t)c.T * n * n * sizeof(double) > kSmemBudget) c.variant = VAR_DIRECT;
+    }
+    return c;
+}
+
+}  // namespace bf
+
+extern "C" int bf_tune_set(int routine, int code, int n_lo, int n_hi, int variant, int p0, int p1,
+                           int p2, int p3) {
+    if (routine < BF_ROUTINE_DGEMM || routine > BF_ROUTINE_DPOTRF) return -1;
+    if (n_lo > n_hi) return -3;
+    if (variant < 0 || variant > 2) return -5;
+    std::lock_guard<std::mutex> lk(bf::g_mu);
+    bf::g_table.push_back(bf::TuneEntry{routine, code, n_lo, n_hi, variant, p0, p1, p2, p3});
+    return 0;
+}
+
+extern "C" void bf_tune_clear(void) {
+    std::lock_guard<std::mutex> lk(bf::g_mu);
+    bf::g_table.clear();
+}
+
+extern "C" int bf_tune_query(int routine, int code, int m, int n, int k, long long batch, int* out) {
+    if (!out) return -7;
+    if (routine == BF_ROUTINE_DGEMM) {
+        bf::GemmConfig c = bf::choose_gemm(code & 2, code & 1, m, n, k, m, batch);
+        out[0] = c.variant; out[1] = c.TM; out[2] = c.TN; out[3] = c.KC; out[4] = c.P;
+        return 0;
+    }
+    if (routine == BF_ROUTINE_DTRSM) {
+        bf::TrsmConfig c = bf::choose_trsm((code >> 3) & 1, (code >> 2) & 1, (code >> 1) & 1, code & 1,
+                                           m, n, batch);
+        out[0] = c.variant; out[1] = c.MR; out[2] = c.P; out[3] = 0; out[4] = 0;
+        return 0;
+    }
+    if (routine == BF_ROUTINE_DPOTRF) {
+        bf::PotrfConfig c = bf::choose_potrf(n, n, batch);
+        out[0] = c.variant; out[1] = c.T; out[2] = c.NB; out[3] = 0; out[4] = 0;
+        return 0;
+    }
+    return -1;
+}

@@ -1,0 +1,155 @@
+"""The C ABI library loads, exports every symbol include/*.h declares, and its
+host-side logic works without a GPU: argument checking (LAPACK's rule: the
+return value is minus the 1-based position of the first illegal argument,
+and nothing is launched) and the size-switch table.
+
+Every call here either fails its argument check or is a quick return, so no
+kernel is ever launched (the non-null pointers are placeholders that must
+never reach a kernel).
+"""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def lib():
+    from bfhelp import build_lib
+    return build_lib()
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(bf_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for required in ("bf_dgemm", "bf_dgemm_strided_batched", "bf_dgemm_batched", "bf_dtrsm",
+                     "bf_dpotrf", "bf_dpotrf_strided_batched", "bf_dpotrs"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in declared_symbols() if not hasattr(so, n)]
+    assert not missing, missing
+
+
+NULL = None
+
+
+def test_dgemm_illegal_arguments(lib):
+    f = lib.bf_dgemm
+    args = dict(ta=b"N", tb=b"N", m=4, n=4, k=4, alpha=1.0, A=1, lda=4, B=1, ldb=4, beta=0.0, C=1,
+                ldc=4)
+
+    def call(**kw):
+        a = dict(args, **kw)
+        return f(a["ta"], a["tb"], a["m"], a["n"], a["k"], a["alpha"], a["A"], a["lda"], a["B"],
+                 a["ldb"], a["beta"], a["C"], a["ldc"], NULL)
+
+    assert call(ta=b"X") == -1
+    assert call(tb=b"?") == -2
+    assert call(m=-1) == -3
+    assert call(n=-1) == -4
+    assert call(k=-2) == -5
+    assert call(lda=3) == -8
+    assert call(ta=b"T", lda=1, k=2) == -8  # op(A) = A^T: A has k rows
+    assert call(ldb=3) == -10
+    assert call(ldc=3) == -13
+    assert call(A=NULL) == -7
+    assert call(B=NULL) == -9
+    assert call(C=NULL) == -12
+    # quick returns launch nothing and succeed even without a GPU
+    assert call(m=0) == 0
+    assert call(n=0) == 0
+    assert call(k=0, beta=1.0) == 0
+    assert call(alpha=0.0, beta=1.0, A=NULL, B=NULL) == 0
+
+
+def test_dgemm_strided_positions(lib):
+    f = lib.bf_dgemm_strided_batched
+    base = [b"N", b"T", 4, 4, 4, 1.0, 1, 4, 16, 1, 4, 16, 1.0, 1, 4, 16, 10, NULL]
+    assert f(*base[:16], -1, NULL) == -17
+    bad = list(base)
+    bad[15] = 15  # strideC < ldc * n
+    assert f(*bad) == -16
+    bad = list(base)
+    bad[10] = 3  # ldb < n for transb = 'T'
+    assert f(*bad) == -11
+    bad = list(base)
+    bad[8] = -1
+    assert f(*bad) == -9
+
+
+def test_dtrsm_illegal_arguments(lib):
+    f = lib.bf_dtrsm
+    base = [b"R", b"L", b"T", b"U", 5, 3, 1.0, 1, 3, 1, 5, NULL]
+    for pos, bad in ((0, b"X"), (1, b"Q"), (2, b"Z"), (3, b"A")):
+        a = list(base)
+        a[pos] = bad
+        assert f(*a) == -(pos + 1)
+    a = list(base)
+    a[4] = -1
+    assert f(*a) == -5
+    a = list(base)
+    a[8] = 2  # lda < n for side 'R'
+    assert f(*a) == -9
+    a = list(base)
+    a[0] = b"L"  # side 'L': A is m x m, lda = 3 < m = 5
+    assert f(*a) == -9
+    a = list(base)
+    a[10] = 4
+    assert f(*a) == -11
+    a = list(base)
+    a[4] = 0
+    assert f(*a) == 0
+
+
+def test_dpotrf_and_dpotrs_arguments(lib):
+    assert lib.bf_dpotrf(b"X", 4, 1, 4, NULL, NULL) == -1
+    assert lib.bf_dpotrf(b"L", -1, 1, 4, NULL, NULL) == -2
+    assert lib.bf_dpotrf(b"L", 4, NULL, 4, NULL, NULL) == -3
+    assert lib.bf_dpotrf(b"L", 4, 1, 3, NULL, NULL) == -4
+    assert lib.bf_dpotrf(b"U", 4, 1, 4, NULL, NULL) == lib.ERR_NOT_SUPPORTED
+    assert lib.bf_dpotrf_strided_batched(b"L", 4, 1, 4, 15, NULL, 2, NULL) == -5
+    assert lib.bf_dpotrf_strided_batched(b"L", 4, 1, 4, 16, NULL, -1, NULL) == -7
+    assert lib.bf_dpotrf_strided_batched(b"L", 0, NULL, 1, 0, NULL, 5, NULL) == 0  # n = 0, no info
+    assert lib.bf_dpotrs(b"L", 4, 2, 1, 4, 1, 3, NULL) == -7
+    assert lib.bf_dpotrs(b"L", 4, -2, 1, 4, 1, 4, NULL) == -3
+    assert lib.bf_dpotrs_strided_batched(b"L", 4, 2, 1, 4, 16, 1, 4, 7, 3, NULL) == -9
+
+
+def test_status_strings(lib):
+    assert lib.bf_status_string(0) == b"success"
+    assert b"illegal" in lib.bf_status_string(-3)
+
+
+def test_tune_table(lib):
+    lib.tune_clear()
+    try:
+        default = lib.tune_query(lib.ROUTINE_DGEMM, 1, 24, 24, 24, 1000)
+        assert default[1] == 24 and default[2] == 24  # whole 24 x 24 problem per super-tile
+        lib.tune_set(lib.ROUTINE_DGEMM, 1, 16, 32, lib.VARIANT_DIRECT, 12, 24, 8, 2)
+        got = lib.tune_query(lib.ROUTINE_DGEMM, 1, 24, 24, 24, 1000)
+        assert got == [lib.VARIANT_DIRECT, 12, 24, 8, 2]
+        # other trans codes and sizes keep the default
+        assert lib.tune_query(lib.ROUTINE_DGEMM, 0, 24, 24, 24, 1000) == default
+        assert lib.tune_query(lib.ROUTINE_DGEMM, 1, 40, 40, 40, 1000)[1] == 40
+        lib.tune_set(lib.ROUTINE_DPOTRF, 0, 1, 300, lib.VARIANT_BLOCKED, 128, 16)
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 100, 100, 0, 10)[:3] == [lib.VARIANT_BLOCKED, 128, 16]
+        with pytest.raises(lib.BFError):
+            lib.tune_set(7, 0, 1, 2, 0)
+    finally:
+        lib.tune_clear()
