@@ -1,0 +1,529 @@
+#!/usr/bin/env python
+"""Benchmark of the batched small-matrix FP64 BLAS/LAPACK library on GB300.
+
+Workload (one "step"): the size sweep -- for every order n in
+{4, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256} and leading dimension
+lda in {n, n+3}, uniform batches sized so that each routine's operands total
+about 2 GiB:
+  dgemm nn, nt, tn, tt (m = n = k, C += op(A) op(B)),
+  dtrsm right-lower-transposed with the unit-scaled Cholesky factor (rltu)
+  and with the factor itself (rltn),
+  dpotrf lower on S = G G^T + n I.
+Inputs are synthetic (seeded), generated on the device before timing and
+resident in HBM; every point is larger than L2, so no flush is needed.  The
+dpotrf inputs are refreshed inside each step by copying the untouched upper
+triangle of S back onto the factored lower triangle (a torch copy, timed as
+part of the step, excluded from the per-call figures).
+
+Reported: whole-step GFLOP/s (the value), per-point GFLOP/s and fraction of
+the per-size roofline min(P_FP64, B_HBM * AI), the size switch's chosen
+variant against each plain variant, an end-to-end rate through pinned host
+memory, and the CPU oracle on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SWEEP_N = (4, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256)
+PADS = (0, 3)
+GEMM_FORMS = ("nn", "nt", "tn", "tt")
+METRIC = "batched FP64 dgemm/dpotrf GFLOP/s and % of roofline vs n; chosen vs plain form"
+HBM_FALLBACK_GBS = 6800.0
+
+
+# ---------------------------------------------------------------------------- work accounting
+def flops(routine: str, n: int) -> float:
+    """Algorithmic flops of one problem (m = n = k); dpotrf uses LAPACK's count."""
+    if routine.startswith("dgemm"):
+        return 2.0 * n ** 3
+    if routine == "dtrsm_rltu":
+        return float(n * n * (n - 1))
+    if routine == "dtrsm_rltn":
+        return float(n ** 3)
+    if routine == "dpotrf":
+        return n ** 3 / 3.0 + n ** 2 / 2.0 + n / 6.0
+    raise KeyError(routine)
+
+
+def alg_bytes(routine: str, n: int) -> float:
+    """Bytes the method must move per problem (lda padding not counted)."""
+    if routine.startswith("dgemm"):
+        return 32.0 * n * n
+    if routine == "dtrsm_rltu":
+        return 8.0 * (2 * n * n + n * (n - 1) / 2)
+    if routine == "dtrsm_rltn":
+        return 8.0 * (2 * n * n + n * (n + 1) / 2)
+    if routine == "dpotrf":
+        return 8.0 * n * (n + 1)
+    raise KeyError(routine)
+
+
+def batch_of(routine: str, n: int, ld: int) -> int:
+    import bfsynth
+    ops = 3 if routine.startswith("dgemm") else (2 if routine.startswith("dtrsm") else 1)
+    return bfsynth.sweep_batch(n, ld, ops)
+
+
+ROUTINES = tuple("dgemm_" + f for f in GEMM_FORMS) + ("dtrsm_rltu", "dtrsm_rltn", "dpotrf")
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback (profiling recipe)"
+
+
+# ---------------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- inputs
+class Point:
+    """Device-resident inputs of one sweep point (n, lda)."""
+
+    def __init__(self, n: int, pad: int, dev, seed: int):
+        import bfsynth
+        self.n, self.pad, self.ld = n, pad, n + pad
+        ld = self.ld
+        bg = batch_of("dgemm", n, ld)
+        self.A = bfsynth.randn_batch(bg, n, n, ld, seed, device=dev)
+        self.B = bfsynth.randn_batch(bg, n, n, ld, seed + 1, device=dev)
+        self.C = bfsynth.randn_batch(bg, n, n, ld, seed + 2, device=dev)
+        import torch
+        import paper_1902_08115_gb300 as bf
+        # column-major (j, i) with i > j: the strict lower triangle
+        self.low = torch.tril(torch.ones(n, n, dtype=torch.bool, device=dev), -1).t().contiguous()
+        bt = batch_of("dtrsm", n, ld)
+        # the triangular factors come from this library's own dpotrf of S = G G^T + n I (the
+        # solve follows the factorisation); L_u = L diag(L)^{-1} is the unit-scaled factor
+        self.L = bfsynth.spd_batch(bt, n, ld, seed + 3, device=dev)
+        info = bf.dpotrf(self.L, n=n)
+        assert int(info.abs().max()) == 0
+        V = self.L[:, :, :n]
+        d = torch.diagonal(V, dim1=1, dim2=2).clone()
+        self.Lu = self.L.clone()
+        self.Lu[:, :, :n] = V / d.unsqueeze(2)  # column j divided by l_jj
+        self.X = bfsynth.randn_batch(bt, n, n, ld, seed + 4, device=dev)
+        bp = batch_of("dpotrf", n, ld)
+        self.S = bfsynth.spd_batch(bp, n, ld, seed + 5, device=dev)
+        self.Sdiag = torch.diagonal(self.S[:, :, :n], dim1=1, dim2=2).clone()
+        self.info = torch.zeros(bp, dtype=torch.int32, device=dev)
+        self.batch = {"dgemm": bg, "dtrsm": bt, "dpotrf": bp}
+
+    def restore_s(self):
+        """Rebuild S from its untouched strict upper triangle and the saved diagonal."""
+        import torch
+        n = self.n
+        V = self.S[:, :, :n]
+        V.copy_(torch.where(self.low, V.transpose(1, 2), V))
+        torch.diagonal(V, dim1=1, dim2=2).copy_(self.Sdiag)
+
+    def nbatch(self, routine):
+        return self.batch[routine.split("_")[0]]
+
+
+def run_routine(bf, p: Point, routine: str):
+    n = p.n
+    if routine.startswith("dgemm_"):
+        ta, tb = routine[-2].upper(), routine[-1].upper()
+        bf.dgemm(ta, tb, 1.0, p.A, p.B, 1.0, p.C, m=n, n=n, k=n)
+    elif routine == "dtrsm_rltu":
+        bf.dtrsm("R", "L", "T", "U", 1.0, p.Lu, p.X, m=n, n=n)
+    elif routine == "dtrsm_rltn":
+        bf.dtrsm("R", "L", "T", "N", 1.0, p.L, p.X, m=n, n=n)
+    elif routine == "dpotrf":
+        bf.dpotrf(p.S, n=n, info=p.info)
+    else:
+        raise KeyError(routine)
+
+
+def fp64_peak(bf, torch, dev):
+    """Live FP64 FMA roof: best of 3 timed runs of the library's DFMA probe."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, iters = sms * 8, 1024
+    out = torch.empty(blocks * 256, dtype=torch.float64, device=dev)
+    st = bf._stream()
+    bf.bf_probe_fp64(blocks, iters, bf._ptr(out), st)
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bf.bf_probe_fp64(blocks, iters, bf._ptr(out), st)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = max(best, 2.0 * 16 * iters * blocks * 256 / (ms * 1e-3))
+    return best
+
+
+# ---------------------------------------------------------------------------- CPU oracle baseline
+def oracle_sample(budget_s: float, steps: int = 1):
+    """Time the CPU oracle on a bounded sample of every sweep point; returns (GFLOP/s, desc, cores)."""
+    import numpy as np
+
+    import bfsynth
+    import oracle
+    oracle.build()
+    cores = oracle.num_threads()
+    per_call = budget_s / (len(SWEEP_N) * len(PADS) * len(ROUTINES))
+    est_rate = 0.5e9 * cores  # plain loops, binary64, no vectorisation
+    tot_flops, tot_time, nprob = 0.0, 0.0, 0
+    for _ in range(steps):
+        for n in SWEEP_N:
+            for pad in PADS:
+                ld = n + pad
+                for r in ROUTINES:
+                    full = batch_of(r, n, ld)
+                    k = int(max(16, min(full, 65536, per_call * est_rate / flops(r, n))))
+                    seed = 7 * n + pad
+                    if r.startswith("dgemm"):
+                        A = bfsynth.randn_batch(k, n, n, ld, seed).numpy()
+                        B = bfsynth.randn_batch(k, n, n, ld, seed + 1).numpy()
+                        C = bfsynth.randn_batch(k, n, n, ld, seed + 2).numpy()
+                        t0 = time.perf_counter()
+                        oracle.dgemm(r[-2].upper(), r[-1].upper(), n, n, n, 1.0, A, B, 1.0, C)
+                    elif r.startswith("dtrsm"):
+                        Lm = bfsynth.unit_lower_batch(k, n, ld, seed, unit=(r[-1] == "u")).numpy()
+                        X = bfsynth.randn_batch(k, n, n, ld, seed + 1).numpy()
+                        t0 = time.perf_counter()
+                        oracle.dtrsm("R", "L", "T", r[-1].upper(), n, n, 1.0, Lm, X)
+                    else:
+                        S = bfsynth.spd_batch(k, n, ld, seed).numpy()
+                        t0 = time.perf_counter()
+                        oracle.dpotrf_l(S)
+                    tot_time += time.perf_counter() - t0
+                    tot_flops += k * flops(r, n)
+                    nprob += k
+    desc = (f"oracle (plain C, binary64, OpenMP over problems) on {nprob} problems: a bounded "
+            f"sample of every sweep point and routine, ~{budget_s:.0f} s of CPU work per step")
+    return tot_flops / tot_time / 1e9, desc, cores
+
+
+# ---------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-extras", action="store_true", help="skip forms, e2e and CPU baseline")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import paper_1902_08115_gb300 as bf
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- inputs (seeded; each rank draws its own replica with a rank-dependent seed)
+    import bfsynth
+    points = []
+    for i, n in enumerate(SWEEP_N):
+        for pad in PADS:
+            points.append(Point(n, pad, dev, bfsynth.BASE_SEED + 1000 * rank + 10 * i + pad))
+    torch.cuda.synchronize()
+
+    calls = [(p, r) for p in points for r in ROUTINES]
+    step_flops = sum(p.nbatch(r) * flops(r, p.n) for p, r in calls)
+
+    def step(events=None):
+        for ci, (p, r) in enumerate(calls):
+            if r == "dpotrf":
+                p.restore_s()
+            if events is not None:
+                events[ci][0].record()
+            run_routine(bf, p, r)
+            if events is not None:
+                events[ci][1].record()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    clocks = Clocks(gpu_uuid)
+    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+            for _ in calls] for _ in range(args.steps)]
+    launches0 = bf.bf_launch_count()
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for s in range(args.steps):
+        step(evs[s])
+    t1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = bf.bf_launch_count() - launches0
+    # every factorisation of the timed steps must have succeeded (a failed pivot ends a problem
+    # early and would make the timing meaningless)
+    bad = sum(int((p.info != 0).sum()) for p in points)
+    if bad:
+        raise RuntimeError(f"{bad} dpotrf problems failed during the timed steps")
+    ms_total = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    value = step_flops * world / (ms_step * 1e-3) / 1e9  # GFLOP/s, all ranks
+
+    # ---- per-call figures and the roofline
+    peak = fp64_peak(bf, torch, dev)
+    hbm, hbm_src = hbm_peak()
+    per = {}
+    for ci, (p, r) in enumerate(calls):
+        ms = statistics.mean(evs[s][ci][0].elapsed_time(evs[s][ci][1]) for s in range(args.steps))
+        f = p.nbatch(r) * flops(r, p.n)
+        by = p.nbatch(r) * alg_bytes(r, p.n)
+        roof = min(peak, hbm * 1e9 * f / by)
+        per[(r, p.n, p.pad)] = dict(ms=ms, gflops=f / (ms * 1e-3) / 1e9, frac=f / (ms * 1e-3) / roof,
+                                    flops=f, bytes=by, roof=roof)
+    dom = max(per, key=lambda k: per[k]["ms"])
+    d = per[dom]
+    roofline = {"bound": "alu", "achieved": round(d["flops"] / (d["ms"] * 1e-3) / 1e12, 4),
+                "peak": round(peak / 1e12, 4), "unit": "TFLOP/s",
+                "frac": round(d["flops"] / (d["ms"] * 1e-3) / peak, 4), "traffic": None,
+                "kernel": f"{dom[0]} n={dom[1]} lda={dom[1] + dom[2]} (largest per-call time)",
+                "peak_source": "live FP64 DFMA probe (bf_probe_fp64), same run",
+                "hbm_gbs": hbm, "hbm_source": hbm_src}
+    sweep = {r: [[n, pad, round(per[(r, n, pad)]["gflops"], 2), round(per[(r, n, pad)]["frac"], 4)]
+                 for n in SWEEP_N for pad in PADS] for r in ROUTINES}
+    big = [per[(r, n, pad)]["frac"] for r in ("dgemm_nn", "dgemm_nt", "dgemm_tn", "dgemm_tt", "dpotrf")
+           for n in SWEEP_N for pad in PADS if n >= 32]
+
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded N(0,1) operands, S = G G^T + n I, unit-scaled Cholesky factors)",
+        "config": {"workload": "size sweep: n in {4,8,12,16,24,32,48,64,96,128,192,256} x lda in "
+                               "{n, n+3}, ~2 GiB of operands per routine and point; dgemm nn/nt/tn/tt "
+                               "(m=n=k, C += op(A)op(B)), dtrsm rltu + rltn, dpotrf_l",
+                   "l2": "no flush: every point's inputs (~2 GiB) exceed the 126 MiB L2",
+                   "dpotrf_inputs": "refreshed in-step from S's untouched upper triangle (torch copy)",
+                   "parallelism": f"replicas x{world} (no collective on the data path)"},
+        "roofline": roofline,
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "fp64_peak_tflops": round(peak / 1e12, 4),
+        "min_frac_n_ge_32_dgemm_dpotrf": round(min(big), 4),
+        "sweep": sweep,
+    }
+
+    if not args.no_extras:
+        result["forms"] = plain_forms(bf, torch, points, peak, hbm)
+        result["e2e"] = end_to_end(bf, torch, dev, points)
+        if rank == 0:
+            v, desc, cores = oracle_sample(args.cpu_budget)
+            result["cpu_baseline"] = {"value": round(v, 3), "unit": "GFLOP/s", "cores": cores,
+                                      "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def plain_forms(bf, torch, points, peak, hbm):
+    """Chosen (size switch) vs each plain variant, lda = n, 2 timed repetitions each."""
+    forms = {}
+    variants = {"dgemm": [("direct", 0), ("packed", 1)], "dtrsm": [("direct", 0), ("packed", 1)],
+                "dpotrf": [("direct", 0), ("packed", 1), ("blocked", 2)]}
+    routine_id = {"dgemm": bf.ROUTINE_DGEMM, "dtrsm": bf.ROUTINE_DTRSM, "dpotrf": bf.ROUTINE_DPOTRF}
+    for r in ("dgemm_nn", "dgemm_nt", "dgemm_tn", "dtrsm_rltu", "dpotrf"):
+        fam = r.split("_")[0]
+        rows = []
+        for p in points:
+            if p.pad:
+                continue
+            row = {"n": p.n}
+            for name, var in [("chosen", None)] + variants[fam]:
+                if fam == "dpotrf" and name == "packed" and p.n > 16:
+                    continue
+                if var is not None:
+                    code = {"dgemm": (2 if r[-2] == "t" else 0) + (1 if r[-1] == "t" else 0),
+                            "dtrsm": 8 + 2 + 1, "dpotrf": 0}[fam]
+                    bf.tune_set(routine_id[fam], code, 0, 1 << 30, var)
+                try:
+                    ts = []
+                    for rep in range(3):
+                        if fam == "dpotrf":
+                            p.restore_s()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        run_routine(bf, p, r)
+                        e1.record()
+                        e1.synchronize()
+                        if rep:
+                            ts.append(e0.elapsed_time(e1))
+                    ms = min(ts)
+                finally:
+                    bf.reset_table()
+                f = p.nbatch(r) * flops(r, p.n)
+                row[name] = round(f / (ms * 1e-3) / 1e9, 2)
+            rows.append(row)
+        forms[r] = rows
+    return forms
+
+
+def end_to_end(bf, torch, dev, points, cap_bytes=32 << 20):
+    """Same routines through the public API with host buffers: every call's inputs copied from
+    pinned host memory and its result read back inside the timed region.  Batches are capped
+    at cap_bytes of operands per routine and point (pinned host memory is limited)."""
+    work = []
+    for p in points:
+        for r in ROUTINES:
+            b = p.nbatch(r)
+            per_problem = {"dgemm": 3, "dtrsm": 2, "dpotrf": 1}[r.split("_")[0]] * p.ld * p.n * 8
+            k = max(1, min(b, cap_bytes // per_problem))
+            if r.startswith("dgemm"):
+                host = [p.A[:k].cpu().pin_memory(), p.B[:k].cpu().pin_memory(), p.C[:k].cpu().pin_memory()]
+            elif r == "dtrsm_rltu":
+                host = [p.Lu[:k].cpu().pin_memory(), p.X[:k].cpu().pin_memory()]
+            elif r == "dtrsm_rltn":
+                host = [p.L[:k].cpu().pin_memory(), p.X[:k].cpu().pin_memory()]
+            else:
+                p.restore_s()
+                host = [p.S[:k].cpu().pin_memory()]
+            out = torch.empty_like(host[-1], pin_memory=True)
+            work.append((p, r, k, host, out))
+    torch.cuda.synchronize()
+
+    def one_pass():
+        h2d = d2h = 0
+        for p, r, k, host, out in work:
+            d = [h.to(dev, non_blocking=True) for h in host]
+            h2d += sum(h.numel() * 8 for h in host)
+            n = p.n
+            if r.startswith("dgemm"):
+                bf.dgemm(r[-2].upper(), r[-1].upper(), 1.0, d[0], d[1], 1.0, d[2], m=n, n=n, k=n)
+            elif r.startswith("dtrsm"):
+                bf.dtrsm("R", "L", "T", r[-1].upper(), 1.0, d[0], d[1], m=n, n=n)
+            else:
+                info = torch.empty(k, dtype=torch.int32, device=dev)
+                bf.dpotrf(d[0], n=n, info=info)
+            out.copy_(d[-1], non_blocking=True)
+            d2h += out.numel() * 8
+        return h2d, d2h
+
+    one_pass()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = 2
+    for _ in range(reps):
+        h2d, d2h = one_pass()
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / reps
+    f = sum(k * flops(r, p.n) for p, r, k, _, _ in work)
+    return {"value": round(f / sec / 1e9, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h),
+            "workload": f"the sweep's routines and points with batches capped at {cap_bytes >> 20} MiB "
+                        "of operands each, through the Python binding of the C ABI, inputs copied "
+                        "from pinned host memory and results read back every step"}
+
+
+def reference_arm(args, rank, world):
+    """The oracle timed as it stands on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(min(2.0, args.cpu_budget))
+    t = []
+    rates = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        v, desc, cores = oracle_sample(args.cpu_budget / 2)
+        t.append(time.perf_counter() - t0)
+        rates.append(v)
+    v = statistics.mean(rates)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "GFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1000 * statistics.mean(t), 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "size sweep (bounded sample per point) on the CPU oracle"},
+        "cpu_baseline": {"value": round(v, 3), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": round(v, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+if __name__ == "__main__":
+    main()

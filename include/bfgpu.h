@@ -122,6 +122,70 @@ int bf_dpotrs_strided_batched(char uplo, int n, int nrhs, const double* A, int l
                               int batch, bf_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* dsposv (LAPACK's name for the mixed-precision SPD solve; the routines it */
+/* runs are the paper's dpotrf and dtrsm, section 3.1, in binary32): solve   */
+/* A X = B for SPD A (uplo 'L': lower triangle referenced, A not modified).  */
+/* A is rounded to binary32 and factored (pivots tested and square-rooted in */
+/* binary64); the binary32 solution is refined in binary64 (residual         */
+/* b - A x and update x + d in binary64) until the normwise backward error   */
+/* ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= tol for every       */
+/* column, at most itmax steps.  If the binary32 factorisation fails or the  */
+/* refinement does not converge, that problem is solved in binary64 instead. */
+/* Outputs (device arrays, may be NULL): iter[b] = refinement steps taken    */
+/* (max over columns; 0 = the binary32 solution met tol), -1 = binary64      */
+/* fallback; info[b] = 0, or j > 0 when the binary64 fallback found the       */
+/* leading minor of order j not positive definite (X is then not written).   */
+/* 1 <= n <= BF_DSPOSV_NMAX (larger n: BF_ERR_NOT_SUPPORTED); ldb, ldx >= n. */
+/* ------------------------------------------------------------------------ */
+#define BF_DSPOSV_NMAX 192
+
+int bf_dsposv_strided_batched(char uplo, int n, int nrhs, const double* A, int lda,
+                              long long strideA, const double* B, int ldb, long long strideB,
+                              double* X, int ldx, long long strideX, int* iter, int* info,
+                              double tol, int itmax, int batch, bf_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Reverse mode (adjoints) of the routines above, strided batches.  Output   */
+/* arrays are overwritten; NULL outputs are skipped.                         */
+/*                                                                           */
+/* dgemm, C = alpha op(A) op(B) + beta C0 (section 2.1): given Cbar,          */
+/*   Abar = alpha Cbar op(B)^T (its transpose when transa = 'T'),            */
+/*   Bbar = alpha op(A)^T Cbar (its transpose when transb = 'T'),            */
+/*   C0bar = beta Cbar.  Abar/Bbar have the shapes (and leading dims) of A/B. */
+/* ------------------------------------------------------------------------ */
+int bf_dgemm_backward_strided_batched(char transa, char transb, int m, int n, int k, double alpha,
+                                      const double* A, int lda, long long strideA,
+                                      const double* B, int ldb, long long strideB, double beta,
+                                      const double* Cbar, int ldcb, long long strideCbar,
+                                      double* Abar, int ldab, long long strideAbar,
+                                      double* Bbar, int ldbb, long long strideBbar,
+                                      double* C0bar, int ldc0b, long long strideC0bar, int batch,
+                                      bf_stream_t stream);
+
+/* dtrsm (section 3.1 "dtrsm"), op(A) X = alpha B or X op(A) = alpha B with   */
+/* the solution X: on entry XBbar holds Xbar, on exit Bbar = alpha Z, where  */
+/* op(A)^T Z = Xbar (side 'L') or Z op(A)^T = Xbar (side 'R').  Abar (may be  */
+/* NULL) receives -Z X^T (side 'L') or -X^T Z (side 'R'), transposed when     */
+/* transa = 'T', on the stored triangle of A only (without the diagonal when */
+/* diag = 'U'); its other triangle is not written.  alpha == 0: -7.          */
+int bf_dtrsm_backward_strided_batched(char side, char uplo, char transa, char diag, int m, int n,
+                                      double alpha, const double* A, int lda, long long strideA,
+                                      const double* X, int ldx, long long strideX,
+                                      double* XBbar, int ldxb, long long strideXB,
+                                      double* Abar, int ldab, long long strideAbar, int batch,
+                                      bf_stream_t stream);
+
+/* dpotrf (section 3.1 "dpotrf"), A = L L^T: given L (lower triangle read)   */
+/* and Lbar (lower triangle read), writes the symmetric gradient             */
+/* Abar = (S + S^T)/2, S = L^{-T} Phi(L^T Lbar) L^{-1}, Phi = lower triangle */
+/* with halved diagonal (I. Murray, "Differentiation of the Cholesky         */
+/* decomposition", 2016), to the full n x n of Abar (Abar must not alias L). */
+int bf_dpotrf_backward_strided_batched(char uplo, int n, const double* L, int ldl, long long strideL,
+                                       const double* Lbar, int ldlb, long long strideLbar,
+                                       double* Abar, int ldab, long long strideAbar, int batch,
+                                       bf_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* The size switch (section 2.4: the switch point between variants depends  */
 /* on the routine and the architecture and is set by measurement).           */
 /* bf_tune_set adds a table entry, consulted before the built-in defaults:    */
@@ -146,7 +210,8 @@ int bf_tune_query(int routine, int code, int m, int n, int k, long long batch, i
 /* bf_launch_count: number of kernels this library has launched since it was */
 /* loaded (host-side counter; differences over a region count its launches). */
 /* bf_probe_fp64: launches `blocks` CTAs of 256 threads, each issuing        */
-/* iters * 8 independent FP64 fused multiply-adds (2 flops each) and writing */
+/* iters * 16 FP64 fused multiply-adds (2 flops each; a 4x4 register tile)   */
+/* and writing                                                               */
 /* one double per thread to out (device, blocks * 256 doubles).  Timed by    */
 /* the caller, it measures the FP64 FMA throughput that bounds the routines. */
 /* ------------------------------------------------------------------------ */

@@ -53,6 +53,13 @@ _SIGS = {
     "bf_tune_clear": [],
     "bf_tune_query": [_i, _i, _i, _i, _i, _ll, _ip],
     "bf_status_string": [_i],
+    "bf_dsposv_strided_batched": [_c, _i, _i, _vp, _i, _ll, _vp, _i, _ll, _vp, _i, _ll, _vp, _vp, _d, _i,
+                                  _i, _vp],
+    "bf_dgemm_backward_strided_batched": [_c, _c, _i, _i, _i, _d, _vp, _i, _ll, _vp, _i, _ll, _d, _vp, _i,
+                                          _ll, _vp, _i, _ll, _vp, _i, _ll, _vp, _i, _ll, _i, _vp],
+    "bf_dtrsm_backward_strided_batched": [_c, _c, _c, _c, _i, _i, _d, _vp, _i, _ll, _vp, _i, _ll, _vp, _i,
+                                          _ll, _vp, _i, _ll, _i, _vp],
+    "bf_dpotrf_backward_strided_batched": [_c, _i, _vp, _i, _ll, _vp, _i, _ll, _vp, _i, _ll, _i, _vp],
     "bf_launch_count": [],
     "bf_probe_fp64": [_i, _i, _vp, _vp],
 }
@@ -181,6 +188,30 @@ def dpotrs(L, B, n=None, nrhs=None, uplo: str = "L", stream=None):
     return B
 
 
+def dsposv(A, B, X=None, n=None, nrhs=None, tol: float = 1e-12, itmax: int = 30, iter=None, info=None,
+           uplo: str = "L", stream=None):
+    """Mixed-precision SPD solve A X = B (binary32 factor, binary64 refinement).
+
+    Returns (X, iter, info) with per-problem refinement counts (-1 = binary64 fallback).
+    """
+    import torch
+    bA, cA, ldA, sA = _batch_dims(A)
+    bB, cB, ldB, sB = _batch_dims(B)
+    n = cA if n is None else n
+    nrhs = cB if nrhs is None else nrhs
+    if X is None:
+        X = torch.empty_like(B)
+    bX, cX, ldX, sX = _batch_dims(X)
+    if iter is None:
+        iter = torch.empty(bA, dtype=torch.int32, device=A.device)
+    if info is None:
+        info = torch.empty(bA, dtype=torch.int32, device=A.device)
+    _check("bf_dsposv_strided_batched", bf_dsposv_strided_batched(
+        _ch(uplo), n, nrhs, _ptr(A), ldA, sA, _ptr(B), ldB, sB, _ptr(X), ldX, sX, _ptr(iter), _ptr(info),
+        tol, itmax, bA, _stream(stream)))
+    return X, iter, info
+
+
 def tune_query(routine: int, code: int, m: int, n: int, k: int, batch: int):
     out = (ctypes.c_int * 5)()
     _check("bf_tune_query", bf_tune_query(routine, code, m, n, k, batch, out))
@@ -193,3 +224,43 @@ def tune_set(routine: int, code: int, n_lo: int, n_hi: int, variant: int, p0=0, 
 
 def tune_clear():
     bf_tune_clear()
+
+
+def load_table(path: str) -> int:
+    """Install a tuned size-switch table (written by the autotuner); returns the entry count."""
+    import json
+    with open(path) as f:
+        doc = json.load(f)
+    for e in doc["entries"]:
+        p = list(e["p"]) + [0] * (4 - len(e["p"]))
+        tune_set(e["routine"], e["code"], e["lo"], e["hi"], e["variant"], *p[:4])
+    return len(doc["entries"])
+
+
+def _autoload_table():
+    """Load tuned/<this GPU's name>.json if it exists (set BFGPU_NO_TUNED=1 to skip)."""
+    if os.environ.get("BFGPU_NO_TUNED"):
+        return None
+    try:
+        import torch
+        if not torch.cuda.is_available():
+            return None
+        name = torch.cuda.get_device_name()
+    except Exception:
+        return None
+    safe = "".join(c if c.isalnum() else "_" for c in name)
+    path = os.path.join(_HERE, "tuned", safe + ".json")
+    if os.path.exists(path):
+        load_table(path)
+        return path
+    return None
+
+
+TUNED_TABLE = _autoload_table()
+
+
+def reset_table():
+    """Remove every override and reinstall the tuned table loaded at import (if any)."""
+    tune_clear()
+    if TUNED_TABLE:
+        load_table(TUNED_TABLE)

@@ -1,0 +1,130 @@
+"""torch.autograd Functions whose forward and backward run in this library's kernels.
+
+Tensors are batches of column-major matrices, shape (batch, ncols, ld), as in
+the rest of the binding.  Each Function calls the C ABI forward routine and,
+on the backward pass, the matching hand-written adjoint routine:
+
+  Gemm       C = alpha op(A) op(B) + beta C0   -> bf_dgemm_backward_strided_batched
+  TriSolve   op(A) X = alpha B / X op(A) = alpha B -> bf_dtrsm_backward_strided_batched
+  Cholesky   A = L L^T (lower)                 -> bf_dpotrf_backward_strided_batched
+
+Cholesky's gradient is the symmetric one (the input is treated as a
+symmetric matrix, as the factorisation reads only its lower triangle).
+`spd_solve_loss` chains them into the differentiation workload
+loss = sum((Q + J J^T)^{-1} B .* W).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import (_batch_dims, _ch, _check, _ptr, _stream, bf_dgemm_backward_strided_batched,
+               bf_dpotrf_backward_strided_batched, bf_dtrsm_backward_strided_batched, dgemm, dpotrf,
+               dtrsm)
+
+
+def _strict_upper_mask(n, device):
+    """mask[j, i] is True where i < j: the strict upper triangle in (ncols, ld) layout."""
+    return torch.tril(torch.ones(n, n, dtype=torch.bool, device=device), -1)
+
+
+class Gemm(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, A, B, C0, transa, transb, alpha, beta, m, n, k):
+        C = C0.clone(memory_format=torch.contiguous_format)
+        dgemm(transa, transb, alpha, A, B, beta, C, m=m, n=n, k=k)
+        ctx.save_for_backward(A, B)
+        ctx.args = (transa, transb, alpha, beta, m, n, k)
+        return C
+
+    @staticmethod
+    def backward(ctx, Cbar):
+        A, B = ctx.saved_tensors
+        transa, transb, alpha, beta, m, n, k = ctx.args
+        Cbar = Cbar.contiguous()
+        need_a, need_b, need_c = ctx.needs_input_grad[:3]
+        Abar = torch.zeros_like(A) if need_a else None
+        Bbar = torch.zeros_like(B) if need_b else None
+        C0bar = torch.zeros_like(Cbar) if need_c else None
+        bA, cA, ldA, sA = _batch_dims(A)
+        bB, cB, ldB, sB = _batch_dims(B)
+        bC, cC, ldC, sC = _batch_dims(Cbar)
+
+        def opt(t):
+            if t is None:
+                return None, 1, 0
+            _, _, ld, st = _batch_dims(t)
+            return _ptr(t), ld, st
+
+        pa, lda_, sa = opt(Abar)
+        pb, ldb_, sb = opt(Bbar)
+        pc, ldc_, sc = opt(C0bar)
+        _check("bf_dgemm_backward_strided_batched", bf_dgemm_backward_strided_batched(
+            _ch(transa), _ch(transb), m, n, k, alpha, _ptr(A), ldA, sA if bA > 1 else 0, _ptr(B), ldB,
+            sB if bB > 1 else 0, beta, _ptr(Cbar), ldC, sC, pa, max(lda_, ldA) if pa else ldA, sa, pb,
+            max(ldb_, ldB) if pb else ldB, sb, pc, max(ldc_, ldC) if pc else ldC, sc, bC, _stream()))
+        return Abar, Bbar, C0bar, None, None, None, None, None, None, None
+
+
+class TriSolve(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, A, B, side, uplo, transa, diag, alpha, m, n):
+        X = B.clone(memory_format=torch.contiguous_format)
+        dtrsm(side, uplo, transa, diag, alpha, A, X, m=m, n=n)
+        ctx.save_for_backward(A, X)
+        ctx.args = (side, uplo, transa, diag, alpha, m, n)
+        return X
+
+    @staticmethod
+    def backward(ctx, Xbar):
+        A, X = ctx.saved_tensors
+        side, uplo, transa, diag, alpha, m, n = ctx.args
+        Z = Xbar.clone(memory_format=torch.contiguous_format)
+        Abar = torch.zeros_like(A) if ctx.needs_input_grad[0] else None
+        bA, cA, ldA, sA = _batch_dims(A)
+        bX, cX, ldX, sX = _batch_dims(X)
+        bZ, cZ, ldZ, sZ = _batch_dims(Z)
+        _check("bf_dtrsm_backward_strided_batched", bf_dtrsm_backward_strided_batched(
+            _ch(side), _ch(uplo), _ch(transa), _ch(diag), m, n, alpha, _ptr(A), ldA, sA if bA > 1 else 0,
+            _ptr(X), ldX, sX, _ptr(Z), ldZ, sZ, _ptr(Abar) if Abar is not None else None, ldA,
+            sA if Abar is not None else 0, bX, _stream()))
+        return Abar, Z, None, None, None, None, None, None, None
+
+
+class Cholesky(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, A, n):
+        L = A.clone(memory_format=torch.contiguous_format)
+        info = dpotrf(L, n=n)
+        L[:, :n, :n].masked_fill_(_strict_upper_mask(n, L.device), 0.0)
+        ctx.save_for_backward(L)
+        ctx.n = n
+        ctx.info = info
+        return L
+
+    @staticmethod
+    def backward(ctx, Lbar):
+        (L,) = ctx.saved_tensors
+        n = ctx.n
+        Lbar = Lbar.contiguous()
+        Abar = torch.zeros_like(L)
+        bL, cL, ldL, sL = _batch_dims(L)
+        bB, cB, ldB, sB = _batch_dims(Lbar)
+        _check("bf_dpotrf_backward_strided_batched", bf_dpotrf_backward_strided_batched(
+            _ch("L"), n, _ptr(L), ldL, sL, _ptr(Lbar), ldB, sB, _ptr(Abar), ldL, sL, bL, _stream()))
+        return Abar, None
+
+
+def spd_solve_loss(Qd, J, B, W):
+    """loss = sum(X .* W), X = L^{-T} L^{-1} B, L = chol(Q + J J^T), Q = diag(Qd).
+
+    Qd (batch, n); J (batch, q, n); B, W (batch, r, n) -- column-major, ld = n.
+    Returns (loss, X, L).
+    """
+    batch, n = Qd.shape
+    q, r = J.shape[1], B.shape[1]
+    C0 = torch.diag_embed(Qd)  # symmetric: the (ncols, ld) layout is the same
+    A = Gemm.apply(J, J, C0, "N", "T", 1.0, 1.0, n, n, q)
+    L = Cholesky.apply(A, n)
+    Y = TriSolve.apply(L, B, "L", "L", "N", "N", 1.0, n, r)
+    X = TriSolve.apply(L, Y, "L", "L", "T", "N", 1.0, n, r)
+    return (X * W).sum(), X, L

@@ -1,0 +1,172 @@
+"""Autotuner for the size switch.
+
+The paper sets each routine's switch point between algorithmic variants by
+measurement on the target architecture (section 2.4, section 3.1).  This tool
+does the same on the GPU it runs on: for every routine, transpose form and
+order of the size sweep it times each candidate kernel variant and tiling
+with CUDA events on a uniform batch of about 1 GiB of operands, keeps the
+fastest, and writes the table to tuned/<gpu name>.json.  The binding loads
+that table at import (bf_tune_set), so every later call uses the measured
+switch; entries cover the order range from one tuned order up to the next.
+
+    python -m paper_1902_08115_gb300.autotune [--quick] [--out PATH]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+ORDERS = (4, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256)
+BUDGET = 1 << 30
+
+
+def table_path(gpu_name: str) -> str:
+    safe = "".join(c if c.isalnum() else "_" for c in gpu_name)
+    return os.path.join(HERE, "tuned", safe + ".json")
+
+
+def _time(torch, fn, reps=3):
+    fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def _gemm_candidates(n):
+    cands = []
+    tiles = [(0, 0)] if n <= 64 else [(0, 0), (32, 32), (48, 48), (64, 64), (n // 2 // 4 * 4, 64)]
+    for variant in (0, 1):
+        for TM, TN in tiles:
+            for threads in (128, 256, 384, 512):
+                tm = TM if TM else ((n + 3) // 4 * 4 if n <= 64 else 64)
+                tn = TN if TN else ((n + 3) // 4 * 4 if n <= 64 else 64)
+                tpp = (tm // 4) * (tn // 4)
+                P = max(1, threads // tpp)
+                if P * tpp > 512:
+                    continue
+                for KC in ((0,) if variant == 0 else ((0, 16) if n > 64 else (0,))):
+                    c = (variant, TM, TN, KC, P)
+                    if c not in cands:
+                        cands.append(c)
+    return cands
+
+
+def tune(quick=False, out=None, log=print):
+    import torch
+
+    import bfsynth
+    import paper_1902_08115_gb300 as bf
+
+    dev = torch.device("cuda")
+    name = torch.cuda.get_device_name(dev)
+    bf.tune_clear()
+    entries = []
+    orders = ORDERS[::2] if quick else ORDERS
+    t_start = time.time()
+    for idx, n in enumerate(orders):
+        hi = orders[idx + 1] - 1 if idx + 1 < len(orders) else 1 << 20
+        lo = n if idx else 1
+        # ---- dgemm, four forms
+        b = max(1, min(bfsynth.sweep_batch(n, n, 3), BUDGET // (3 * n * n * 8)))
+        A = bfsynth.randn_batch(b, n, n, n, 1, device=dev)
+        B = bfsynth.randn_batch(b, n, n, n, 2, device=dev)
+        C = bfsynth.randn_batch(b, n, n, n, 3, device=dev)
+        for code, (ta, tb) in enumerate((("N", "N"), ("N", "T"), ("T", "N"), ("T", "T"))):
+            best = None
+            for cand in _gemm_candidates(n):
+                bf.tune_clear()
+                bf.tune_set(bf.ROUTINE_DGEMM, code, 0, 1 << 30, *cand)
+                ms = _time(torch, lambda: bf.dgemm(ta, tb, 1.0, A, B, 1.0, C, m=n, n=n, k=n))
+                if best is None or ms < best[0]:
+                    best = (ms, cand)
+            gf = b * 2.0 * n ** 3 / (best[0] * 1e-3) / 1e9
+            entries.append(dict(routine=bf.ROUTINE_DGEMM, code=code, lo=lo, hi=hi, variant=best[1][0],
+                                p=list(best[1][1:]), gflops=round(gf, 1), n=n))
+            log(f"dgemm {ta}{tb} n={n}: {best[1]} {gf:.0f} GFLOP/s")
+        del A, B, C
+        # ---- dtrsm: right-lower-T unit/non-unit, and the left-lower N/T of dpotrs
+        b = max(1, min(bfsynth.sweep_batch(n, n, 2), BUDGET // (2 * n * n * 8)))
+        L = bfsynth.spd_batch(b, n, n, 4, device=dev)
+        bf.tune_clear()
+        bf.dpotrf(L, n=n)
+        X = bfsynth.randn_batch(b, n, n, n, 5, device=dev)
+        for code, args in ((11, ("R", "L", "T", "U")), (10, ("R", "L", "T", "N")),
+                           (0, ("L", "L", "N", "N")), (2, ("L", "L", "T", "N"))):
+            best = None
+            for variant in (0, 1):
+                for MR in (4, 8):
+                    for P in ((0,) if variant == 0 else (0, 8, 16, 32)):
+                        bf.tune_clear()
+                        bf.tune_set(bf.ROUTINE_DTRSM, code, 0, 1 << 30, variant, MR, P)
+                        cfg = bf.tune_query(bf.ROUTINE_DTRSM, code, n, n, 0, b)
+                        if cfg[0] != variant:
+                            continue  # not launchable in this form at this order
+                        ms = _time(torch, lambda: bf.dtrsm(*args, 1.0, L, X, m=n, n=n))
+                        if best is None or ms < best[0]:
+                            best = (ms, (variant, MR, P))
+            fl = b * n ** 3
+            entries.append(dict(routine=bf.ROUTINE_DTRSM, code=code, lo=lo, hi=hi, variant=best[1][0],
+                                p=[best[1][1], best[1][2], 0, 0], gflops=round(fl / best[0] / 1e6, 1), n=n))
+            log(f"dtrsm {''.join(args)} n={n}: {best[1]} {fl / best[0] / 1e6:.0f} GFLOP/s")
+        del L, X
+        # ---- dpotrf
+        b = max(1, min(bfsynth.sweep_batch(n, n, 1), BUDGET // (n * n * 8)))
+        S0 = bfsynth.spd_batch(b, n, n, 6, device=dev)
+        S = S0.clone()
+        best = None
+        cands = [(0, T, 0) for T in (64, 128, 256)]
+        if n <= 16:
+            cands += [(1, T, 0) for T in (32, 64, 128)]
+        if n >= 16:
+            cands += [(2, 128, NB) for NB in (8, 16, 32, 64) if NB < n]
+        for variant, T, NB in cands:
+            bf.tune_clear()
+            bf.tune_set(bf.ROUTINE_DPOTRF, 0, 0, 1 << 30, variant, T, NB)
+
+            def run():
+                S.copy_(S0)
+                bf.dpotrf(S, n=n)
+
+            ms_copy = _time(torch, lambda: S.copy_(S0))
+            ms = _time(torch, run) - ms_copy
+            if best is None or ms < best[0]:
+                best = (max(ms, 1e-6), (variant, T, NB))
+        fl = b * (n ** 3 / 3 + n ** 2 / 2 + n / 6)
+        entries.append(dict(routine=bf.ROUTINE_DPOTRF, code=0, lo=lo, hi=hi, variant=best[1][0],
+                            p=[best[1][1], best[1][2], 0, 0], gflops=round(fl / best[0] / 1e6, 1), n=n))
+        log(f"dpotrf n={n}: {best[1]} {fl / best[0] / 1e6:.0f} GFLOP/s")
+        del S, S0
+        torch.cuda.empty_cache()
+    bf.tune_clear()
+    doc = {"gpu": name, "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
+           "seconds": round(time.time() - t_start, 1), "entries": entries}
+    path = out or table_path(name)
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    with open(path, "w") as f:
+        json.dump(doc, f, indent=1)
+    bf.load_table(path)
+    return path
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--quick", action="store_true")
+    ap.add_argument("--out")
+    a = ap.parse_args()
+    print(tune(quick=a.quick, out=a.out))

@@ -1,0 +1,286 @@
+// bf_backward.cu -- hand-written reverse-mode (adjoint) routines for the
+// batched dgemm, dtrsm and dpotrf, built from this library's kernels.
+//
+// dgemm, C = alpha op(A) op(B) + beta C0 (section 2.1):
+//   Abar = alpha Cbar op(B)^T (transposed when op(A) = A^T),
+//   Bbar = alpha op(A)^T Cbar (transposed when op(B) = B^T),  C0bar = beta Cbar.
+// dtrsm, op(A) X = alpha B (left) / X op(A) = alpha B (right) (section 3.1):
+//   Z solves op(A)^T Z = Xbar (left) / Z op(A)^T = Xbar (right);
+//   Bbar = alpha Z;  op(A)bar = -Z X^T (left) / -X^T Z (right), kept on the
+//   stored triangle of A (without the diagonal when it is unit).
+// dpotrf, A = L L^T (section 3.1 "dpotrf"), the symmetric form published by
+// I. Murray ("Differentiation of the Cholesky decomposition", 2016):
+//   P = Phi(L^T Lbar)  (lower triangle, diagonal halved),
+//   S = L^{-T} P L^{-1}  (two triangular solves),  Abar = (S + S^T) / 2.
+//   Derivation: dA = dL L^T + L dL^T gives L^{-1} dL = Phi(L^{-1} dA L^{-T}),
+//   and Phi is self-adjoint, so <Lbar, dL> = <L^{-T} Phi(L^T Lbar) L^{-1}, dA>.
+#include "bf_internal.h"
+#include "../../include/bfgpu.h"
+
+namespace bf {
+
+// P = Phi(L^T Lbar) for every problem, written to the full n x n of `out` (upper part zero).
+// One thread per (lower 4x4 tile, problem), problem index fastest: the 32 lanes of a warp
+// work on the same tile of 32 problems, so every lane runs the same k-loop length.
+__global__ void __launch_bounds__(256)
+phi_ltlbar_kernel(int n, MatRef L, int ldl, MatRef Lb, int ldlb, MatRef O, int ldo, long long batch, int nt) {
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long ntile = (long long)nt * (nt + 1) / 2;
+    if (gt >= ntile * batch) return;
+    const long long q = gt % batch;
+    const int t = (int)(gt / batch);
+    int I = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    while ((I + 1) * (I + 2) / 2 <= t) I++;
+    while (I * (I + 1) / 2 > t) I--;
+    const int J = t - I * (I + 1) / 2;
+    const int i0 = 4 * I, j0 = 4 * J;
+    const double* l = L.ptr(q);
+    const double* lb = Lb.ptr(q);
+    double* o = O.mptr(q);
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) acc[a][b] = 0.0;
+    // P_ij = sum_{k >= i} L(k, i) Lbar(k, j) for i >= j; structural zeros masked
+    for (int k = i0; k < n; k++) {
+        double li[4], lbj[4];
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            const int i = i0 + a;
+            li[a] = (i < n && k >= i) ? l[k + (long long)i * ldl] : 0.0;
+        }
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            const int j = j0 + b;
+            lbj[b] = (j < n && k >= j) ? lb[k + (long long)j * ldlb] : 0.0;
+        }
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int b = 0; b < 4; b++) acc[a][b] = fma(li[a], lbj[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            const int i = i0 + a, j = j0 + b;
+            if (i >= n || j >= n) continue;
+            if (i > j) {
+                o[i + (long long)j * ldo] = acc[a][b];
+                o[j + (long long)i * ldo] = 0.0;
+            } else if (i == j) {
+                o[i + (long long)j * ldo] = 0.5 * acc[a][b];
+            } else {
+                o[i + (long long)j * ldo] = 0.0;  // strict upper part of a diagonal tile
+            }
+        }
+    }
+}
+
+// G = (S + S^T) / 2 in place (problem index fastest).
+__global__ void __launch_bounds__(256) symmetrize_kernel(int n, MatRef S, int lds, long long batch) {
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long npair = (long long)n * (n - 1) / 2;
+    if (gt >= npair * batch) return;
+    const long long q = gt % batch;
+    const int t = (int)(gt / batch);
+    // pair t -> (i, j), i > j, row by row of the strict lower triangle
+    int i = (int)((sqrtf(8.0f * t + 1.0f) + 1.0f) * 0.5f);
+    while (i * (i - 1) / 2 > t) i--;
+    while ((i + 1) * i / 2 <= t) i++;
+    const int j = t - i * (i - 1) / 2;
+    double* s = S.mptr(q);
+    const double g = 0.5 * (s[i + (long long)j * lds] + s[j + (long long)i * lds]);
+    s[i + (long long)j * lds] = g;
+    s[j + (long long)i * lds] = g;
+}
+
+// Y = beta X (X and Y m x n, may alias)
+__global__ void __launch_bounds__(256)
+dscal_copy_kernel(int m, int n, double beta, MatRef X, int ldx, MatRef Y, int ldy, long long batch) {
+    const long long per = (long long)m * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per * batch;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long q = e / per;
+        const long long r = e - q * per;
+        const int j = (int)(r / m), i = (int)(r - (long long)j * m);
+        const double v = X.ptr(q)[i + (long long)j * ldx];
+        Y.mptr(q)[i + (long long)j * ldy] = beta * v;
+    }
+}
+
+static cudaError_t launch_scal_copy(int m, int n, double beta, MatRef X, int ldx, MatRef Y, int ldy,
+                                    long long batch, cudaStream_t s) {
+    if (m == 0 || n == 0 || batch == 0) return cudaSuccess;
+    long long total = (long long)m * n * batch;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    dscal_copy_kernel<<<(unsigned)blocks, 256, 0, s>>>(m, n, beta, X, ldx, Y, ldy, batch);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dpotrf_backward(int n, MatRef L, int ldl, MatRef Lb, int ldlb, MatRef Ab, int ldab,
+                                   long long batch, cudaStream_t s) {
+    if (n == 0 || batch == 0) return cudaSuccess;
+    const int nt = (n + 3) / 4;
+    long long threads = (long long)nt * (nt + 1) / 2 * batch;
+    phi_ltlbar_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(n, L, ldl, Lb, ldlb, Ab, ldab, batch, nt);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // S1 = L^{-T} P (left, lower, transposed), then S = S1 L^{-1} (right, lower, not transposed)
+    TrsmConfig c1 = choose_trsm(0, 0, 1, 0, n, n, batch);
+    e = launch_dtrsm(0, 0, 1, 0, n, n, 1.0, L, ldl, Ab, ldab, batch, c1, nullptr, s);
+    if (e != cudaSuccess) return e;
+    TrsmConfig c2 = choose_trsm(1, 0, 0, 0, n, n, batch);
+    e = launch_dtrsm(1, 0, 0, 0, n, n, 1.0, L, ldl, Ab, ldab, batch, c2, nullptr, s);
+    if (e != cudaSuccess) return e;
+    if (n > 1) {
+        long long pairs = (long long)n * (n - 1) / 2 * batch;
+        symmetrize_kernel<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(n, Ab, ldab, batch);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace bf
+
+using namespace bf;
+
+static inline bool cis_n(char c) { return c == 'N' || c == 'n'; }
+static inline bool cis_t(char c) { return c == 'T' || c == 't' || c == 'C' || c == 'c'; }
+static inline bool cis_l(char c) { return c == 'L' || c == 'l'; }
+static inline bool cis_u(char c) { return c == 'U' || c == 'u'; }
+static inline bool cis_r(char c) { return c == 'R' || c == 'r'; }
+static inline int cmax1(int a) { return a > 1 ? a : 1; }
+static inline int cstat(cudaError_t e) { return e == cudaSuccess ? BF_SUCCESS : BF_ERR_CUDA; }
+
+extern "C" int bf_dgemm_backward_strided_batched(
+    char transa, char transb, int m, int n, int k, double alpha, const double* A, int lda, long long strideA,
+    const double* B, int ldb, long long strideB, double beta, const double* Cbar, int ldcb, long long strideCbar,
+    double* Abar, int ldab, long long strideAbar, double* Bbar, int ldbb, long long strideBbar, double* C0bar,
+    int ldc0b, long long strideC0bar, int batch, bf_stream_t stream) {
+    if (!(cis_n(transa) || cis_t(transa))) return -1;
+    if (!(cis_n(transb) || cis_t(transb))) return -2;
+    if (m < 0) return -3;
+    if (n < 0) return -4;
+    if (k < 0) return -5;
+    const bool ta = cis_t(transa), tb = cis_t(transb);
+    const int rA = ta ? k : m, cA = ta ? m : k, rB = tb ? n : k, cB = tb ? k : n;
+    if (lda < cmax1(rA)) return -8;
+    if (ldb < cmax1(rB)) return -11;
+    if (ldcb < cmax1(m)) return -15;
+    if (Abar && ldab < cmax1(rA)) return -18;
+    if (Bbar && ldbb < cmax1(rB)) return -21;
+    if (C0bar && ldc0b < cmax1(m)) return -24;
+    if (batch < 0) return -26;
+    const bool work = batch > 0;
+    if (work && Abar && n > 0 && cA > 0 && !B) return -10;
+    if (work && Bbar && m > 0 && cB > 0 && !A) return -7;
+    if (work && (Abar || Bbar || C0bar) && !Cbar) return -14;
+    if (!work) return 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    MatRef mA = mat_strided(A, strideA), mB = mat_strided(B, strideB), mC = mat_strided(Cbar, strideCbar);
+    cudaError_t e = cudaSuccess;
+    if (Abar && rA > 0 && cA > 0) {
+        MatRef o = mat_strided(Abar, strideAbar);
+        if (!ta) {  // Abar (m x k) = alpha Cbar op(B)^T
+            GemmConfig c = choose_gemm(false, !tb, m, k, n, ldcb, batch);
+            e = launch_dgemm(false, !tb, m, k, n, alpha, mC, ldcb, mB, ldb, 0.0, o, ldab, batch, c, 0, nullptr, s);
+        } else {  // Abar (k x m) = alpha op(B) Cbar^T
+            GemmConfig c = choose_gemm(tb, true, k, m, n, ldb, batch);
+            e = launch_dgemm(tb, true, k, m, n, alpha, mB, ldb, mC, ldcb, 0.0, o, ldab, batch, c, 0, nullptr, s);
+        }
+        if (e != cudaSuccess) return cstat(e);
+    }
+    if (Bbar && rB > 0 && cB > 0) {
+        MatRef o = mat_strided(Bbar, strideBbar);
+        if (!tb) {  // Bbar (k x n) = alpha op(A)^T Cbar
+            GemmConfig c = choose_gemm(!ta, false, k, n, m, lda, batch);
+            e = launch_dgemm(!ta, false, k, n, m, alpha, mA, lda, mC, ldcb, 0.0, o, ldbb, batch, c, 0, nullptr, s);
+        } else {  // Bbar (n x k) = alpha Cbar^T op(A)
+            GemmConfig c = choose_gemm(true, ta, n, k, m, ldcb, batch);
+            e = launch_dgemm(true, ta, n, k, m, alpha, mC, ldcb, mA, lda, 0.0, o, ldbb, batch, c, 0, nullptr, s);
+        }
+        if (e != cudaSuccess) return cstat(e);
+    }
+    if (C0bar && m > 0 && n > 0)
+        e = launch_scal_copy(m, n, beta, mC, ldcb, mat_strided(C0bar, strideC0bar), ldc0b, batch, s);
+    return cstat(e);
+}
+
+extern "C" int bf_dtrsm_backward_strided_batched(char side, char uplo, char transa, char diag, int m, int n,
+                                                 double alpha, const double* A, int lda, long long strideA,
+                                                 const double* X, int ldx, long long strideX, double* XBbar,
+                                                 int ldxb, long long strideXB, double* Abar, int ldab,
+                                                 long long strideAbar, int batch, bf_stream_t stream) {
+    if (!(cis_l(side) || cis_r(side))) return -1;
+    if (!(cis_l(uplo) || cis_u(uplo))) return -2;
+    if (!(cis_n(transa) || cis_t(transa))) return -3;
+    if (!(cis_u(diag) || cis_n(diag))) return -4;
+    if (m < 0) return -5;
+    if (n < 0) return -6;
+    const bool left = cis_l(side);
+    const int order = left ? m : n;
+    if (lda < cmax1(order)) return -9;
+    if (ldx < cmax1(m)) return -12;
+    if (ldxb < cmax1(m)) return -15;
+    if (Abar && ldab < cmax1(order)) return -18;
+    if (batch < 0) return -20;
+    if (alpha == 0.0) return -7;  // X does not depend on A, B: the adjoint is not defined by this formula
+    const bool work = m > 0 && n > 0 && batch > 0;
+    if (work && !A) return -8;
+    if (work && Abar && !X) return -11;
+    if (work && !XBbar) return -14;
+    if (!work) return 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int sd = left ? 0 : 1, up = cis_u(uplo) ? 1 : 0, tr = cis_t(transa) ? 1 : 0, un = cis_u(diag) ? 1 : 0;
+    MatRef mA = mat_strided(A, strideA), mX = mat_strided(X, strideX), mZ = mat_strided(XBbar, strideXB);
+    // Z = op(A)^{-T} Xbar (left) or Xbar op(A)^{-T} (right), in place
+    TrsmConfig tc = choose_trsm(sd, up, !tr, un, m, n, batch);
+    cudaError_t e = launch_dtrsm(sd, up, !tr, un, m, n, 1.0, mA, lda, mZ, ldxb, batch, tc, nullptr, s);
+    if (e != cudaSuccess) return cstat(e);
+    if (Abar) {
+        const int tri = up ? (un ? TRI_SUPPER : TRI_UPPER) : (un ? TRI_SLOWER : TRI_LOWER);
+        MatRef o = mat_strided(Abar, strideAbar);
+        if (left) {
+            // op(A)bar = -Z X^T (m x m); Abar = op(A)bar or its transpose -X Z^T
+            MatRef P = tr ? mX : mZ, Q = tr ? mZ : mX;
+            const int ldp = tr ? ldx : ldxb, ldq = tr ? ldxb : ldx;
+            GemmConfig c = choose_gemm(false, true, m, m, n, ldp, batch);
+            e = launch_dgemm(false, true, m, m, n, -1.0, P, ldp, Q, ldq, 0.0, o, ldab, batch, c, tri, nullptr, s);
+        } else {
+            // op(A)bar = -X^T Z (n x n); Abar = op(A)bar or its transpose -Z^T X
+            MatRef P = tr ? mZ : mX, Q = tr ? mX : mZ;
+            const int ldp = tr ? ldxb : ldx, ldq = tr ? ldx : ldxb;
+            GemmConfig c = choose_gemm(true, false, n, n, m, ldp, batch);
+            e = launch_dgemm(true, false, n, n, m, -1.0, P, ldp, Q, ldq, 0.0, o, ldab, batch, c, tri, nullptr, s);
+        }
+        if (e != cudaSuccess) return cstat(e);
+    }
+    if (alpha != 1.0) e = launch_scal_copy(m, n, alpha, mZ, ldxb, mZ, ldxb, batch, s);
+    return cstat(e);
+}
+
+extern "C" int bf_dpotrf_backward_strided_batched(char uplo, int n, const double* L, int ldl, long long strideL,
+                                                  const double* Lbar, int ldlb, long long strideLbar, double* Abar,
+                                                  int ldab, long long strideAbar, int batch, bf_stream_t stream) {
+    if (!(cis_l(uplo) || cis_u(uplo))) return -1;
+    if (n < 0) return -2;
+    if (ldl < cmax1(n)) return -4;
+    if (ldlb < cmax1(n)) return -7;
+    if (ldab < cmax1(n)) return -10;
+    if (batch < 0) return -12;
+    if (batch > 1 && strideAbar < (long long)ldab * n) return -11;
+    const bool work = n > 0 && batch > 0;
+    if (work && !L) return -3;
+    if (work && !Lbar) return -6;
+    if (work && !Abar) return -9;
+    if (cis_u(uplo)) return BF_ERR_NOT_SUPPORTED;
+    if (!work) return 0;
+    return cstat(launch_dpotrf_backward(n, mat_strided(L, strideL), ldl, mat_strided(Lbar, strideLbar), ldlb,
+                                        mat_strided(Abar, strideAbar), ldab, batch, (cudaStream_t)stream));
+}

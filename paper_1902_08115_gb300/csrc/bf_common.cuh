@@ -77,6 +77,14 @@ __host__ inline int acc_mode(double alpha, double beta) {
     return ACC_GEN;
 }
 
+// Store masks of the dgemm kernel (which triangle of C is written).
+enum TriMask : int { TRI_NONE = 0, TRI_LOWER = 1, TRI_UPPER = 2, TRI_SLOWER = 3, TRI_SUPPER = 4 };
+
+__host__ __device__ __forceinline__ bool in_tri(int tri, int i, int j) {
+    return tri == TRI_NONE || (tri == TRI_LOWER && i >= j) || (tri == TRI_UPPER && i <= j) ||
+           (tri == TRI_SLOWER && i > j) || (tri == TRI_SUPPER && i < j);
+}
+
 __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
 __device__ __forceinline__ int imax(int a, int b) { return a > b ? a : b; }
 

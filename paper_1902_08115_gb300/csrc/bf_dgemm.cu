@@ -17,8 +17,10 @@
 //     so that the inner kernel is always the same (the paper's "transpose
 //     while packing" rule, sections 2.2 and 3.2.1).
 //
-// The `lower` flag restricts stores to i >= j (the dsyrk-style trailing
-// update of the blocked Cholesky, section 3.1 "dsyrk"/"dpotrf").
+// The `tri` mask restricts stores to one triangle of C: TRI_LOWER (i >= j, the
+// dsyrk-style trailing update of the blocked Cholesky, section 3.1
+// "dsyrk"/"dpotrf"), TRI_UPPER (i <= j), TRI_SLOWER (i > j), TRI_SUPPER
+// (i < j) -- the last ones for the triangular adjoints of the backward pass.
 #include "bf_internal.h"
 
 namespace bf {
@@ -37,7 +39,10 @@ dgemm_tile_kernel(GemmParams p) {
     const int i0 = (st % p.tilesM) * p.TM;
     const int j0 = (st / p.tilesM) * p.TN;
 
-    if (p.lower && i0 + p.TM - 1 < j0) return;  // super-tile strictly above the diagonal
+    // super-tiles with no element in the stored triangle
+    if ((p.lower == TRI_LOWER && i0 + p.TM - 1 < j0) || (p.lower == TRI_SLOWER && i0 + p.TM - 1 <= j0) ||
+        (p.lower == TRI_UPPER && i0 > j0 + p.TN - 1) || (p.lower == TRI_SUPPER && i0 >= j0 + p.TN - 1))
+        return;
 
     const int t = threadIdx.x;
     const int ql = t / tpp;
@@ -190,7 +195,7 @@ dgemm_tile_kernel(GemmParams p) {
 #pragma unroll
         for (int u = 0; u < NR; u++) {
             const int i = rows[s], j = cols[u];
-            if (i < p.m && j < p.n && (!p.lower || i >= j)) {
+            if (i < p.m && j < p.n && in_tri(p.lower, i, j)) {
                 double* cp = C + i + (long long)j * p.ldc;
                 double v = acc[s][u];
                 if (p.mode == ACC_GEN) v = (p.beta == 0.0) ? p.alpha * v : fma(p.alpha, v, p.beta * *cp);

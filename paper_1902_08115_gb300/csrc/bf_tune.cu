@@ -75,7 +75,9 @@ GemmConfig choose_gemm(bool ta, bool tb, int m, int n, int k, int lda, long long
     int tpp = (c.TM / 4) * (c.TN / 4);
     c.P = 256 / tpp > 0 ? 256 / tpp : 1;
     while ((c.P * tpp) % 32 != 0 && (c.P + 1) * tpp <= 512) c.P++;  // whole warps
-    c.variant = (size <= 8) ? VAR_DIRECT : VAR_PACKED;
+    // measured on GB300: the direct form feeds the FP64 pipe as well as the packed one except
+    // where op(B) is read across columns at large orders (nt/tt, n >= 64)
+    c.variant = (tb && size >= 64) ? VAR_PACKED : VAR_DIRECT;
     c.KC = (m <= 64 && n <= 64) ? k : (k < 32 ? k : 32);
     TuneEntry e;
     if (lookup(BF_ROUTINE_DGEMM, (ta ? 2 : 0) + (tb ? 1 : 0), size, &e)) {
@@ -88,6 +90,7 @@ GemmConfig choose_gemm(bool ta, bool tb, int m, int n, int k, int lda, long long
         } else {
             tpp = (ceil4(c.TM < ceil4(m) ? c.TM : ceil4(m)) / 4) * (ceil4(c.TN < ceil4(n) ? c.TN : ceil4(n)) / 4);
             c.P = 256 / tpp > 0 ? 256 / tpp : 1;
+            while ((c.P * tpp) % 32 != 0 && (c.P + 1) * tpp <= 512) c.P++;  // whole warps
         }
     }
     sanitize_gemm(c, m, n, k);

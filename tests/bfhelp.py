@@ -31,7 +31,7 @@ def forced(bf, routine, code, variant, p0=0, p1=0, p2=0, p3=0):
     try:
         yield
     finally:
-        bf.tune_clear()
+        bf.reset_table()
 
 
 def gpu(x):

@@ -152,4 +152,4 @@ def test_tune_table(lib):
         with pytest.raises(lib.BFError):
             lib.tune_set(7, 0, 1, 2, 0)
     finally:
-        lib.tune_clear()
+        lib.reset_table()

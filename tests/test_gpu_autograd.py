@@ -1,0 +1,170 @@
+"""GPU parity of the hand-written backward kernels and the autograd chain.
+
+* dgemm adjoint: against the oracle's dgemm applied to the adjoint formulas;
+* dtrsm adjoint (all 16 cases): against central finite differences of the
+  oracle's forward solve (an independent route), and the formula;
+* Cholesky adjoint: against the oracle's reverse mode of its own unblocked
+  loop (converted between the symmetric and lower-triangular conventions);
+* the differentiation workload loss = sum((Q + J J^T)^{-1} B .* W): autograd
+  gradient of the GPU chain against the oracle's closed-form gradient and
+  against central finite differences (h = 1e-6) of the GPU forward pass,
+  relative error <= 1e-8 (both).
+"""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import bfsynth
+from bfhelp import gpu, host, normwise
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from bfhelp import build_lib
+    return build_lib()
+
+
+@pytest.fixture(scope="module")
+def ag(bf):
+    from paper_1902_08115_gb300 import autograd
+    return autograd
+
+
+def rel(a, b):
+    a, b = np.asarray(a).ravel(), np.asarray(b).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("ta,tb", list(itertools.product("NT", "NT")))
+@pytest.mark.parametrize("m,n,k", [(5, 7, 3), (24, 24, 24), (33, 17, 40)])
+def test_dgemm_backward(bf, ag, oracle, ta, tb, m, n, k):
+    batch, alpha, beta = 6, 0.75, -1.5
+    rA, cA = (m, k) if ta == "N" else (k, m)
+    rB, cB = (k, n) if tb == "N" else (n, k)
+    A = bfsynth.randn_batch(batch, rA, cA, rA, 1).numpy()
+    B = bfsynth.randn_batch(batch, rB, cB, rB, 2).numpy()
+    C0 = bfsynth.randn_batch(batch, m, n, m, 3).numpy()
+    Cb = bfsynth.randn_batch(batch, m, n, m, 4).numpy()
+    At, Bt, Ct = (gpu(x).requires_grad_(True) for x in (A, B, C0))
+    C = ag.Gemm.apply(At, Bt, Ct, ta, tb, alpha, beta, m, n, k)
+    C.backward(gpu(Cb))
+    # references from the adjoint formulas, evaluated with the oracle's dgemm
+    Z = lambda r, c: np.zeros((batch, c, r))
+    if ta == "N":
+        refA = oracle.dgemm("N", "T" if tb == "N" else "N", m, k, n, alpha, Cb, B, 0.0, Z(m, k))
+    else:
+        refA = oracle.dgemm(tb, "T", k, m, n, alpha, B, Cb, 0.0, Z(k, m))
+    if tb == "N":
+        refB = oracle.dgemm("T" if ta == "N" else "N", "N", k, n, m, alpha, A, Cb, 0.0, Z(k, n))
+    else:
+        refB = oracle.dgemm("T", ta, n, k, m, alpha, Cb, A, 0.0, Z(n, k))
+    assert normwise(host(At.grad), refA, rA) <= 1e-13
+    assert normwise(host(Bt.grad), refB, rB) <= 1e-13
+    assert normwise(host(Ct.grad), beta * Cb, m) <= 1e-15
+
+
+def tri(batch, order, uplo, diag, seed):
+    g = np.random.default_rng(seed)
+    T = g.standard_normal((batch, order, order)) / np.sqrt(order)
+    T = np.tril(T) if uplo == "L" else np.triu(T)
+    d = 1.5 + g.random((batch, order))
+    for q in range(batch):
+        np.fill_diagonal(T[q], 1.0 if diag == "U" else d[q])
+    return np.ascontiguousarray(np.transpose(T, (0, 2, 1)))  # column-major
+
+
+@pytest.mark.parametrize("side,uplo,ta,diag", list(itertools.product("LR", "LU", "NT", "NU")))
+def test_dtrsm_backward(bf, ag, oracle, side, uplo, ta, diag):
+    m, n, batch, alpha = 5, 4, 3, 1.25
+    order = m if side == "L" else n
+    A = tri(batch, order, uplo, diag, 7)
+    B = bfsynth.randn_batch(batch, m, n, m, 8).numpy()
+    W = bfsynth.randn_batch(batch, m, n, m, 9).numpy()
+    At, Bt = gpu(A).requires_grad_(True), gpu(B).requires_grad_(True)
+    X = ag.TriSolve.apply(At, Bt, side, uplo, ta, diag, alpha, m, n)
+    (X * gpu(W)).sum().backward()
+    gA, gB = host(At.grad), host(Bt.grad)
+
+    def loss(Am, Bm):
+        return float(np.sum(oracle.dtrsm(side, uplo, ta, diag, m, n, alpha, Am, Bm) * W))
+
+    h = 1e-6
+    fdB = np.zeros_like(B)
+    for idx in np.ndindex(B.shape):
+        Bp, Bm = B.copy(), B.copy()
+        Bp[idx] += h
+        Bm[idx] -= h
+        fdB[idx] = (loss(A, Bp) - loss(A, Bm)) / (2 * h)
+    assert rel(gB, fdB) <= 1e-8
+    fdA = np.zeros_like(A)
+    for q in range(batch):
+        for j in range(order):
+            for i in range(order):
+                stored = (i >= j) if uplo == "L" else (i <= j)
+                if not stored or (diag == "U" and i == j):
+                    continue
+                Ap, Am = A.copy(), A.copy()
+                Ap[q, j, i] += h
+                Am[q, j, i] -= h
+                fdA[q, j, i] = (loss(Ap, B) - loss(Am, B)) / (2 * h)
+    assert rel(gA, fdA) <= 1e-8
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 16, 32, 33])
+def test_dpotrf_backward(bf, ag, oracle, n):
+    batch = 5
+    S = bfsynth.spd_batch(batch, n, n, 10 + n).numpy()
+    Lb = np.ascontiguousarray(np.triu(bfsynth.randn_batch(batch, n, n, n, 11).numpy()))  # lower in (j, i)
+    St = gpu(S).requires_grad_(True)
+    L = ag.Cholesky.apply(St, n)
+    L.backward(gpu(Lb))
+    G = host(St.grad)  # symmetric gradient, column-major
+    Lo, _ = oracle.dpotrf_l(S)
+    for q in range(batch):
+        ref = oracle.dpotrf_l_adjoint(Lo[q], Lb[q])  # lower-triangular convention, (ncols, ld)
+        Gq = G[q]
+        # tril convention: Abar_ij = 2 G_ij (i > j), Abar_ii = G_ii
+        conv = np.where(np.arange(n)[None, :] > np.arange(n)[:, None], 2 * Gq, 0.0)  # [j, i], i > j
+        conv = conv + np.diag(np.diag(Gq))
+        assert rel(conv, ref) <= 1e-12
+        assert rel(Gq, Gq.T) <= 1e-15
+
+
+def test_spd_solve_gradient(bf, ag, oracle):
+    """The differentiation workload (n = 32, J 32x16, B and W 32x8) at a reduced batch."""
+    batch, n, q, r = 256, 32, 16, 8
+    Qd, J, B, W = (x.numpy() for x in bfsynth.diff_batch(batch, n, q, r, seed=bfsynth.BASE_SEED))
+    ts = [gpu(x).requires_grad_(True) for x in (Qd, J, B, W)]
+    loss, X, L = ag.spd_solve_loss(*ts)
+    loss.backward()
+    g = [host(t.grad) for t in ts]
+    ref = oracle.spd_solve_loss_grad(Qd, J, B, W)
+    assert (ref["info"] == 0).all()
+    assert rel(host(X.detach()), ref["X"]) <= 1e-12
+    for got, key in zip(g, ("Qbar", "Jbar", "Bbar", "Wbar")):
+        assert rel(got, ref[key]) <= 1e-8, key
+    # central finite differences of the GPU forward pass, per-problem losses
+    h = 1e-6
+    rng = np.random.default_rng(0)
+    fd, an = [], []
+    base = [x.copy() for x in (Qd, J, B, W)]
+    for which in range(4):
+        for _ in range(6):
+            prob = int(rng.integers(batch))
+            idx = tuple(int(rng.integers(s)) for s in base[which].shape[1:])
+            vals = []
+            for sgn in (1, -1):
+                xs = [x.copy() for x in base]
+                xs[which][(prob,) + idx] += sgn * h
+                with torch.no_grad():
+                    _, Xp, _ = ag.spd_solve_loss(*(gpu(x) for x in xs))
+                vals.append(float(np.sum(host(Xp[prob]) * xs[3][prob])))
+            fd.append((vals[0] - vals[1]) / (2 * h))
+            an.append(g[which][(prob,) + idx])
+    assert rel(an, fd) <= 1e-8, (an, fd)

@@ -31,7 +31,7 @@ def bf():
         pytest.skip("no CUDA device")
     from bfhelp import build_lib
     m = build_lib()
-    m.tune_clear()
+    m.reset_table()
     return m
 
 
