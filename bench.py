@@ -390,6 +390,14 @@ def main():
     if not args.no_extras:
         result["forms"] = plain_forms(bf, torch, points, peak, hbm)
         result["e2e"] = end_to_end(bf, torch, dev, points)
+        del points
+        torch.cuda.empty_cache()
+        result["ragged"] = ragged_form(bf, torch, dev, rank)
+        torch.cuda.empty_cache()
+        result["diff"] = diff_form(bf, torch, dev, rank)
+        torch.cuda.empty_cache()
+        result["precision"] = precision_form(bf, torch, dev, rank)
+        torch.cuda.empty_cache()
         if rank == 0:
             v, desc, cores = oracle_sample(args.cpu_budget)
             result["cpu_baseline"] = {"value": round(v, 3), "unit": "GFLOP/s", "cores": cores,
@@ -497,6 +505,157 @@ def end_to_end(bf, torch, dev, points, cap_bytes=32 << 20):
             "workload": f"the sweep's routines and points with batches capped at {cap_bytes >> 20} MiB "
                         "of operands each, through the Python binding of the C ABI, inputs copied "
                         "from pinned host memory and results read back every step"}
+
+
+def _events_ms(torch, fn, reps=3, before=None):
+    """min over reps of the CUDA-event time of fn() (before() runs untimed ahead of each rep)."""
+    best = float("inf")
+    for _ in range(reps):
+        if before is not None:
+            before()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def ragged_form(bf, torch, dev, rank, count=200000, nrhs=4):
+    """Ragged batch (n log-uniform in [2, 200], dpotrf + dpotrs with 4 right-hand sides): one
+    persistent graph-captured launch against plain per-size launches of the uniform path."""
+    import ctypes
+
+    import numpy as np
+
+    import bfsynth
+    ns_t = bfsynth.ragged_orders(count, 2, 200, bfsynth.BASE_SEED + 3 + rank)
+    S0, offS, B0, offB = bfsynth.ragged_spd(ns_t, nrhs, bfsynth.BASE_SEED + 4 + rank, device=dev)
+    ns = ns_t.numpy().astype(np.int64)
+    S, B = S0.clone(), B0.clone()
+    flops = float(np.sum(ns ** 3 / 3.0 + ns ** 2 / 2.0 + ns / 6.0 + 2.0 * nrhs * ns ** 2))
+    cfg = bf.ragged_config()
+    plan = bf.RaggedPlan(ns_t.numpy(), S, offS.numpy(), B, offB.numpy(), nrhs, **cfg)
+
+    def restore():
+        S.copy_(S0)
+        B.copy_(B0)
+
+    t_graph = _events_ms(torch, plan.launch, reps=3, before=restore)
+    ok_graph = int((plan.info != 0).sum()) == 0
+    # plain per-size launches: one pointer-array dpotrf and two dtrsm per distinct order
+    groups = []
+    sbase, bbase = S.data_ptr(), B.data_ptr()
+    for n in np.unique(ns):
+        idx = np.nonzero(ns == n)[0]
+        pa = torch.tensor(sbase + 8 * offS.numpy()[idx], dtype=torch.int64, device=dev)
+        pb = torch.tensor(bbase + 8 * offB.numpy()[idx], dtype=torch.int64, device=dev)
+        info = torch.zeros(len(idx), dtype=torch.int32, device=dev)
+        groups.append((int(n), len(idx), pa, pb, info))
+    st = bf._stream()
+
+    def per_size():
+        for n, cnt, pa, pb, info in groups:
+            pav, pbv = ctypes.c_void_p(pa.data_ptr()), ctypes.c_void_p(pb.data_ptr())
+            bf._check("bf_dpotrf_batched", bf.bf_dpotrf_batched(b"L", n, pav, n, ctypes.c_void_p(info.data_ptr()),
+                                                               cnt, st))
+            bf._check("bf_dtrsm_batched", bf.bf_dtrsm_batched(b"L", b"L", b"N", b"N", n, nrhs, 1.0, pav, n, pbv,
+                                                             n, cnt, st))
+            bf._check("bf_dtrsm_batched", bf.bf_dtrsm_batched(b"L", b"L", b"T", b"N", n, nrhs, 1.0, pav, n, pbv,
+                                                             n, cnt, st))
+
+    t_sizes = _events_ms(torch, per_size, reps=3, before=restore)
+    ok_sizes = all(int((g[4] != 0).sum()) == 0 for g in groups)
+    return {"problems": count, "nrhs": nrhs, "orders": "log-uniform in [2, 200]",
+            "S_bytes": int(S0.numel() * 8), "gflop": round(flops / 1e9, 3),
+            "persistent_graph_ms": round(t_graph, 3), "persistent_gflops": round(flops / t_graph / 1e6, 2),
+            "per_size_launches_ms": round(t_sizes, 3), "per_size_gflops": round(flops / t_sizes / 1e6, 2),
+            "speedup": round(t_sizes / t_graph, 3), "distinct_orders": len(groups), "plan": plan.describe(),
+            "config": cfg, "all_info_zero": bool(ok_graph and ok_sizes)}
+
+
+def diff_form(bf, torch, dev, rank, batch=65536, n=32, q=16, r=8):
+    """Differentiation workload: loss = sum((Q + J J^T)^{-1} B .* W) through the autograd
+    Functions; forward, forward + backward, and the plain forward calls without autograd."""
+    import bfsynth
+    from paper_1902_08115_gb300 import autograd as ag
+    Qd, J, B, W = bfsynth.diff_batch(batch, n, q, r, seed=bfsynth.BASE_SEED + 5 + rank, device=dev)
+    ts = [x.clone().requires_grad_(True) for x in (Qd, J, B, W)]
+
+    def fwd():
+        with torch.no_grad():
+            ag.spd_solve_loss(Qd, J, B, W)
+
+    def fwd_bwd():
+        for t in ts:
+            t.grad = None
+        loss, _, _ = ag.spd_solve_loss(*ts)
+        loss.backward()
+
+    C0 = torch.diag_embed(Qd)
+    A = torch.empty_like(C0)
+    X = torch.empty_like(B)
+
+    def plain():
+        A.copy_(C0)
+        bf.dgemm("N", "T", 1.0, J, J, 1.0, A, m=n, n=n, k=q)
+        bf.dpotrf(A, n=n)
+        X.copy_(B)
+        bf.dpotrs(A, X, n=n, nrhs=r)
+
+    t_f = _events_ms(torch, fwd)
+    t_fb = _events_ms(torch, fwd_bwd)
+    t_p = _events_ms(torch, plain)
+    flops_f = batch * (2.0 * n * n * q + n ** 3 / 3 + n * n / 2 + n / 6 + 2.0 * 2 * n * n * r)
+    return {"batch": batch, "n": n, "q": q, "r": r, "forward_ms": round(t_f, 3),
+            "forward_backward_ms": round(t_fb, 3), "plain_forward_ms": round(t_p, 3),
+            "backward_over_forward": round((t_fb - t_f) / t_f, 3),
+            "forward_gflops": round(flops_f / t_f / 1e6, 2)}
+
+
+def precision_form(bf, torch, dev, rank, batch=16384, n=128):
+    """Mixed-precision SPD solve (binary32 factor + binary64 refinement) against the all-binary64
+    dpotrf + dpotrs, cond(A) in {1e2, 1e4, 1e6} (one third each); accuracy by the oracle."""
+    import numpy as np
+
+    import bfsynth
+    import oracle
+    kappas = (1e2, 1e4, 1e6)
+    A, b, kap = bfsynth.precision_batch(batch, n, kappas, seed=bfsynth.BASE_SEED + 6 + rank, device=dev)
+    Bm = b.unsqueeze(1).contiguous()
+    X = torch.empty_like(Bm)
+    it = torch.empty(batch, dtype=torch.int32, device=dev)
+    info = torch.empty(batch, dtype=torch.int32, device=dev)
+    t_mixed = _events_ms(torch, lambda: bf.dsposv(A, Bm, X=X, iter=it, info=info))
+    L = torch.empty_like(A)
+    X64 = torch.empty_like(Bm)
+
+    def fp64():
+        L.copy_(A)
+        bf.dpotrf(L)
+        X64.copy_(Bm)
+        bf.dpotrs(L, X64)
+
+    t_copy = _events_ms(torch, lambda: (L.copy_(A), X64.copy_(Bm)))
+    t_fp64 = _events_ms(torch, fp64) - t_copy
+    itn, kapn = it.cpu().numpy(), kap.numpy()
+    # accuracy, per result: backward error of every solution, computed by the oracle in binary64
+    An, xn, bn = A.cpu().numpy(), X[:, 0, :].cpu().numpy(), b.cpu().numpy()
+    eta = oracle.backward_error(An, xn, bn)
+    eta64 = oracle.backward_error(An, X64[:, 0, :].cpu().numpy(), bn)
+    x64 = X64[:, 0, :].cpu().numpy()
+    fwd = np.abs(xn - x64).max(1) / np.abs(x64).max(1)
+    per = {}
+    for k in kappas:
+        m = kapn == k
+        per[f"{k:.0e}"] = {"iters_mean": round(float(itn[m].mean()), 3), "iters_max": int(itn[m].max()),
+                           "fallbacks": int((itn[m] < 0).sum()), "eta_max": float(eta[m].max()),
+                           "eta_fp64_max": float(eta64[m].max()), "fwd_diff_max": float(fwd[m].max())}
+    return {"batch": batch, "n": n, "mixed_ms": round(t_mixed, 3), "fp64_ms": round(t_fp64, 3),
+            "speedup": round(t_fp64 / t_mixed, 3), "eta_max": float(eta.max()),
+            "all_info_zero": int((info != 0).sum()) == 0, "per_kappa": per}
 
 
 def reference_arm(args, rank, world):

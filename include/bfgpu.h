@@ -186,6 +186,40 @@ int bf_dpotrf_backward_strided_batched(char uplo, int n, const double* L, int ld
                                        bf_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Ragged batches (problems of different orders; no counterpart in the       */
+/* paper, which treats one matrix per call): factor every SPD matrix with     */
+/* dpotrf ('L') and solve S_b X_b = B_b (nrhs columns) in place, in ONE       */
+/* persistent kernel launch captured in a CUDA graph.                        */
+/*   n_host[b]      order of problem b (host array, read at plan creation)   */
+/*   S + offS_host[b]  its matrix, column-major with leading dimension n_b   */
+/*   B + offB_host[b]  its n_b x nrhs right-hand sides (ld n_b), overwritten  */
+/*   info[b]        (device) LAPACK info of problem b                        */
+/*   workspace      device memory of bf_ragged_workspace_bytes(batch) bytes, */
+/*                  owned by the caller, kept for the plan's lifetime        */
+/*   lane_max       orders <= lane_max are factored one problem per thread,  */
+/*                  larger ones one problem per CTA in shared memory         */
+/*   threads        CTA size: 128, 256 or 512                                */
+/* Plan creation sorts the problems (largest first), copies the queue into   */
+/* the workspace on `stream` (synchronously) and instantiates the graph; the */
+/* device pointers and offsets are fixed in the plan.  bf_ragged_plan_launch */
+/* enqueues the graph on `stream`.  Orders above the shared-memory limit     */
+/* (lower triangle of the largest order + its right-hand sides > 227 KB)     */
+/* return BF_ERR_NOT_SUPPORTED.  bf_ragged_plan_info writes {BIG problems,   */
+/* queue items, CTAs, threads, shared bytes} into out[5].                    */
+/* ------------------------------------------------------------------------ */
+typedef struct bf_ragged_plan_st* bf_ragged_plan_t;
+
+size_t bf_ragged_workspace_bytes(int batch);
+int bf_ragged_potrf_potrs_plan_create(int batch, const int* n_host, int nrhs, double* S,
+                                      const long long* offS_host, double* B,
+                                      const long long* offB_host, int* info, void* workspace,
+                                      size_t workspace_bytes, int lane_max, int threads,
+                                      bf_stream_t stream, bf_ragged_plan_t* plan);
+int bf_ragged_plan_launch(bf_ragged_plan_t plan, bf_stream_t stream);
+int bf_ragged_plan_info(bf_ragged_plan_t plan, int* out);
+int bf_ragged_plan_destroy(bf_ragged_plan_t plan);
+
+/* ------------------------------------------------------------------------ */
 /* The size switch (section 2.4: the switch point between variants depends  */
 /* on the routine and the architecture and is set by measurement).           */
 /* bf_tune_set adds a table entry, consulted before the built-in defaults:    */

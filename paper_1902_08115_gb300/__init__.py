@@ -60,10 +60,16 @@ _SIGS = {
     "bf_dtrsm_backward_strided_batched": [_c, _c, _c, _c, _i, _i, _d, _vp, _i, _ll, _vp, _i, _ll, _vp, _i,
                                           _ll, _vp, _i, _ll, _i, _vp],
     "bf_dpotrf_backward_strided_batched": [_c, _i, _vp, _i, _ll, _vp, _i, _ll, _vp, _i, _ll, _i, _vp],
+    "bf_ragged_workspace_bytes": [_i],
+    "bf_ragged_potrf_potrs_plan_create": [_i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _i, _i,
+                                          _vp, ctypes.POINTER(_vp)],
+    "bf_ragged_plan_launch": [_vp, _vp],
+    "bf_ragged_plan_info": [_vp, _ip],
+    "bf_ragged_plan_destroy": [_vp],
     "bf_launch_count": [],
     "bf_probe_fp64": [_i, _i, _vp, _vp],
 }
-_RES = {"bf_tune_clear": None, "bf_status_string": ctypes.c_char_p,
+_RES = {"bf_tune_clear": None, "bf_status_string": ctypes.c_char_p, "bf_ragged_workspace_bytes": ctypes.c_size_t,
         "bf_launch_count": ctypes.c_ulonglong}
 
 for _name, _args in _SIGS.items():
@@ -212,6 +218,45 @@ def dsposv(A, B, X=None, n=None, nrhs=None, tol: float = 1e-12, itmax: int = 30,
     return X, iter, info
 
 
+class RaggedPlan:
+    """One persistent, graph-captured launch that factors and solves a ragged batch in place.
+
+    ns: host int32 orders; S, B: flat float64 device tensors; offS, offB: host int64 element
+    offsets (matrix b at S[offS[b]:], ld = n_b; its right-hand sides at B[offB[b]:], ld = n_b).
+    The workspace and info tensors are owned by the plan object.
+    """
+
+    def __init__(self, ns, S, offS, B, offB, nrhs, lane_max=48, threads=256, stream=None):
+        import numpy as np
+        import torch
+        self.ns = np.ascontiguousarray(ns, dtype=np.int32)
+        self.offS = np.ascontiguousarray(offS, dtype=np.int64)
+        self.offB = np.ascontiguousarray(offB, dtype=np.int64)
+        batch = len(self.ns)
+        self.S, self.B = S, B
+        self.info = torch.zeros(batch, dtype=torch.int32, device=S.device)
+        wb = bf_ragged_workspace_bytes(batch)
+        self.work = torch.empty(wb, dtype=torch.uint8, device=S.device)
+        self._plan = ctypes.c_void_p()
+        _check("bf_ragged_potrf_potrs_plan_create", bf_ragged_potrf_potrs_plan_create(
+            batch, self.ns.ctypes.data_as(ctypes.c_void_p), nrhs, _ptr(S),
+            self.offS.ctypes.data_as(ctypes.c_void_p), _ptr(B), self.offB.ctypes.data_as(ctypes.c_void_p),
+            _ptr(self.info), _ptr(self.work), wb, lane_max, threads, _stream(stream), ctypes.byref(self._plan)))
+
+    def launch(self, stream=None):
+        _check("bf_ragged_plan_launch", bf_ragged_plan_launch(self._plan, _stream(stream)))
+
+    def describe(self):
+        out = (ctypes.c_int * 5)()
+        _check("bf_ragged_plan_info", bf_ragged_plan_info(self._plan, out))
+        return dict(big=out[0], items=out[1], ctas=out[2], threads=out[3], smem=out[4])
+
+    def __del__(self):
+        if getattr(self, "_plan", None) and self._plan.value:
+            bf_ragged_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+
 def tune_query(routine: int, code: int, m: int, n: int, k: int, batch: int):
     out = (ctypes.c_int * 5)()
     _check("bf_tune_query", bf_tune_query(routine, code, m, n, k, batch, out))
@@ -226,6 +271,15 @@ def tune_clear():
     bf_tune_clear()
 
 
+_RAGGED_DEFAULT = {"lane_max": 48, "threads": 256}
+_ragged_cfg = dict(_RAGGED_DEFAULT)
+
+
+def ragged_config():
+    """The ragged plan's threshold and CTA size: tuned if a table provided them, else defaults."""
+    return dict(_ragged_cfg)
+
+
 def load_table(path: str) -> int:
     """Install a tuned size-switch table (written by the autotuner); returns the entry count."""
     import json
@@ -234,6 +288,8 @@ def load_table(path: str) -> int:
     for e in doc["entries"]:
         p = list(e["p"]) + [0] * (4 - len(e["p"]))
         tune_set(e["routine"], e["code"], e["lo"], e["hi"], e["variant"], *p[:4])
+    if "ragged" in doc:
+        _ragged_cfg.update({k: int(doc["ragged"][k]) for k in ("lane_max", "threads")})
     return len(doc["entries"])
 
 

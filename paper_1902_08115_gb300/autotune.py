@@ -154,7 +154,8 @@ def tune(quick=False, out=None, log=print):
         del S, S0
         torch.cuda.empty_cache()
     bf.tune_clear()
-    doc = {"gpu": name, "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
+    ragged = tune_ragged(torch, bf, dev, log, count=20000 if quick else 50000)
+    doc = {"gpu": name, "ragged": ragged, "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
            "seconds": round(time.time() - t_start, 1), "entries": entries}
     path = out or table_path(name)
     os.makedirs(os.path.dirname(path), exist_ok=True)
@@ -162,6 +163,38 @@ def tune(quick=False, out=None, log=print):
         json.dump(doc, f, indent=1)
     bf.load_table(path)
     return path
+
+
+def tune_ragged(torch, bf, dev, log, count=50000, nrhs=4):
+    """Threshold between the per-thread and per-CTA ragged forms, and the CTA size."""
+    import numpy as np
+
+    import bfsynth
+    ns_t = bfsynth.ragged_orders(count, 2, 200, 99)
+    S0, offS, B0, offB = bfsynth.ragged_spd(ns_t, nrhs, 100, device=dev)
+    S, B = S0.clone(), B0.clone()
+    best = None
+    for lane_max in (16, 24, 32, 48, 64, 96):
+        for threads in (256, 512):
+            plan = bf.RaggedPlan(ns_t.numpy(), S, offS.numpy(), B, offB.numpy(), nrhs, lane_max=lane_max,
+                                 threads=threads)
+            ts = []
+            for _ in range(3):
+                S.copy_(S0)
+                B.copy_(B0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                plan.launch()
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = min(ts)
+            log(f"ragged lane_max={lane_max} threads={threads}: {ms:.3f} ms")
+            if best is None or ms < best[0]:
+                best = (ms, lane_max, threads)
+            del plan
+    return {"lane_max": best[1], "threads": best[2], "ms": round(best[0], 3), "problems": count}
 
 
 if __name__ == "__main__":
