@@ -251,6 +251,13 @@ int bf_tune_query(int routine, int code, int m, int n, int k, long long batch, i
 /* ------------------------------------------------------------------------ */
 unsigned long long bf_launch_count(void);
 int bf_probe_fp64(int blocks, int iters, double* out, bf_stream_t stream);
+/* bf_probe_fp64_ex: the same measurement with `threads` per CTA (multiple of */
+/* 32), only `active` lanes of each warp issuing (0..32; FP64 issue cost vs  */
+/* lane mask), and chains = 0 (4x4 tile pattern, 16 FMAs per iteration) or 1 */
+/* (one dependent chain a = fma(a, b, c), 16 per iteration).  out holds       */
+/* blocks * threads doubles.                                                 */
+int bf_probe_fp64_ex(int blocks, int threads, int iters, int active, int chains, double* out,
+                     bf_stream_t stream);
 
 /* Human-readable text for a return code. */
 const char* bf_status_string(int status);

@@ -68,6 +68,7 @@ _SIGS = {
     "bf_ragged_plan_destroy": [_vp],
     "bf_launch_count": [],
     "bf_probe_fp64": [_i, _i, _vp, _vp],
+    "bf_probe_fp64_ex": [_i, _i, _i, _i, _i, _vp, _vp],
 }
 _RES = {"bf_tune_clear": None, "bf_status_string": ctypes.c_char_p, "bf_ragged_workspace_bytes": ctypes.c_size_t,
         "bf_launch_count": ctypes.c_ulonglong}

@@ -33,8 +33,8 @@ __global__ void __launch_bounds__(256) dpotrf_lane_direct_kernel(PotrfParams p) 
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= p.batch) return;
     if (p.skip && p.skip[q] != 0) return;
-    GAcc M{p.A.mptr(q), p.lda};
-    const int info = potrf_lane(M, p.n);
+    double* a = p.A.mptr(q);
+    const int info = strips_aligned(a, p.lda) ? potrf_lane(GAccV{a, p.lda}, p.n) : potrf_lane(GAcc{a, p.lda}, p.n);
     if (info && p.info) p.info[q] = info + p.info_off;
 }
 

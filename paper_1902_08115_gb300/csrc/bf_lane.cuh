@@ -6,6 +6,12 @@
 // 4-row block below it a dgemm loop, then the triangular edge with the
 // reciprocal pivots.  Shared by the uniform (bf_dpotrf.cu) and ragged
 // (bf_ragged.cu) kernels.
+//
+// Operands are reached through an accessor.  ld4/st4 move a strip of four
+// consecutive rows of one column (rows clamped to n - 1 on loads at the end
+// of the matrix); the aligned global accessor does it with two 16-byte
+// accesses, which halves the L1 requests of these uncoalesced per-lane
+// streams (the lane kernels are bound by L1 request throughput, not DRAM).
 #pragma once
 
 #include "bf_common.cuh"
@@ -17,6 +23,48 @@ struct GAcc {  // a problem in global memory
     int lda;
     __device__ __forceinline__ double ld(int i, int j) const { return a[i + (long long)j * lda]; }
     __device__ __forceinline__ void st(int i, int j, double v) const { a[i + (long long)j * lda] = v; }
+    __device__ __forceinline__ void ld4(int i, int j, int n, double* o) const {
+#pragma unroll
+        for (int r = 0; r < 4; r++) o[r] = ld(imin(i + r, n - 1), j);
+    }
+    __device__ __forceinline__ void st4(int i, int j, int cnt, const double* v) const {
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+            if (r < cnt) st(i + r, j, v[r]);
+    }
+};
+
+// Global memory, base 16-byte aligned and lda even: a strip starting at a row
+// multiple of 4 is 16-byte aligned.
+struct GAccV {
+    double* a;
+    int lda;
+    __device__ __forceinline__ double ld(int i, int j) const { return a[i + (long long)j * lda]; }
+    __device__ __forceinline__ void st(int i, int j, double v) const { a[i + (long long)j * lda] = v; }
+    __device__ __forceinline__ void ld4(int i, int j, int n, double* o) const {
+        if (i + 3 < n) {
+            const double2* p = reinterpret_cast<const double2*>(a + i + (long long)j * lda);
+            const double2 x = p[0], y = p[1];
+            o[0] = x.x;
+            o[1] = x.y;
+            o[2] = y.x;
+            o[3] = y.y;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; r++) o[r] = ld(imin(i + r, n - 1), j);
+        }
+    }
+    __device__ __forceinline__ void st4(int i, int j, int cnt, const double* v) const {
+        if (cnt == 4) {
+            double2* p = reinterpret_cast<double2*>(a + i + (long long)j * lda);
+            p[0] = make_double2(v[0], v[1]);
+            p[1] = make_double2(v[2], v[3]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+                if (r < cnt) st(i + r, j, v[r]);
+        }
+    }
 };
 
 struct SAcc {  // a problem in shared memory, interleaved with the CTA's other problems
@@ -24,6 +72,15 @@ struct SAcc {  // a problem in shared memory, interleaved with the CTA's other p
     int n, T;
     __device__ __forceinline__ double ld(int i, int j) const { return s[(i + j * n) * T]; }
     __device__ __forceinline__ void st(int i, int j, double v) const { s[(i + j * n) * T] = v; }
+    __device__ __forceinline__ void ld4(int i, int j, int nn, double* o) const {
+#pragma unroll
+        for (int r = 0; r < 4; r++) o[r] = ld(imin(i + r, nn - 1), j);
+    }
+    __device__ __forceinline__ void st4(int i, int j, int cnt, const double* v) const {
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+            if (r < cnt) st(i + r, j, v[r]);
+    }
 };
 
 // Factor one problem in place through the accessor.  Returns info (0 or 1-based column).
@@ -37,13 +94,16 @@ __device__ __forceinline__ int potrf_lane(const Acc& M, int n) {
         // ---- diagonal block: D = A_JJ - sum_p L(J:J+4, p) L(J:J+4, p)^T (lower part) ----
         double d[4][4];
 #pragma unroll
-        for (int r = 0; r < 4; r++)
+        for (int c = 0; c < 4; c++) {
+            double col[4];
+            M.ld4(J, jr[c], n, col);  // rows above c are read but not used (strict upper triangle)
 #pragma unroll
-            for (int c = 0; c <= r; c++) d[r][c] = M.ld(jr[r], jr[c]);
+            for (int r = c; r < 4; r++) d[r][c] = col[r];
+        }
+#pragma unroll 2
         for (int pp = 0; pp < J; pp++) {
             double l[4];
-#pragma unroll
-            for (int r = 0; r < 4; r++) l[r] = M.ld(jr[r], pp);
+            M.ld4(J, pp, n, l);
 #pragma unroll
             for (int r = 0; r < 4; r++)
 #pragma unroll
@@ -74,6 +134,7 @@ __device__ __forceinline__ int potrf_lane(const Acc& M, int n) {
 #pragma unroll
                 for (int c2 = c + 1; c2 <= r; c2++) d[r][c2] = fma(-d[r][c], d[c2][c], d[r][c2]);
         }
+        // lower part of the diagonal block only (the strict upper triangle is never written)
 #pragma unroll
         for (int r = 0; r < 4; r++)
 #pragma unroll
@@ -82,20 +143,19 @@ __device__ __forceinline__ int potrf_lane(const Acc& M, int n) {
         // ---- 4-row blocks below: acc = A_IJ - L_I L_J^T, then acc L_JJ^{-T} ----
         for (int I = J + 4; I < n; I += 4) {
             const int ib = imin(4, n - I);
-            int ir[4];
-#pragma unroll
-            for (int r = 0; r < 4; r++) ir[r] = imin(I + r, n - 1);
             double acc[4][4];
 #pragma unroll
-            for (int r = 0; r < 4; r++)
+            for (int c = 0; c < 4; c++) {
+                double col[4];
+                M.ld4(I, jr[c], n, col);
 #pragma unroll
-                for (int c = 0; c < 4; c++) acc[r][c] = M.ld(ir[r], jr[c]);
+                for (int r = 0; r < 4; r++) acc[r][c] = col[r];
+            }
+#pragma unroll 2
             for (int pp = 0; pp < J; pp++) {
                 double a[4], b[4];
-#pragma unroll
-                for (int r = 0; r < 4; r++) a[r] = M.ld(ir[r], pp);
-#pragma unroll
-                for (int c = 0; c < 4; c++) b[c] = M.ld(jr[c], pp);
+                M.ld4(I, pp, n, a);
+                M.ld4(J, pp, n, b);
 #pragma unroll
                 for (int r = 0; r < 4; r++)
 #pragma unroll
@@ -111,13 +171,22 @@ __device__ __forceinline__ int potrf_lane(const Acc& M, int n) {
                 for (int r = 0; r < 4; r++) acc[r][c] *= rinv[c];
             }
 #pragma unroll
-            for (int r = 0; r < 4; r++)
+            for (int c = 0; c < 4; c++) {
+                if (c < jb) {
+                    double col[4];
 #pragma unroll
-                for (int c = 0; c < 4; c++)
-                    if (r < ib && c < jb) M.st(I + r, J + c, acc[r][c]);
+                    for (int r = 0; r < 4; r++) col[r] = acc[r][c];
+                    M.st4(I, J + c, ib, col);
+                }
+            }
         }
     }
     return 0;
+}
+
+// 16-byte alignment of every 4-row strip: base aligned and lda even
+__device__ __forceinline__ bool strips_aligned(const double* a, int lda) {
+    return ((reinterpret_cast<unsigned long long>(a) & 15ull) == 0) && ((lda & 1) == 0);
 }
 
 }  // namespace bf

@@ -45,7 +45,58 @@ __global__ void __launch_bounds__(256) probe_fp64_kernel(double* out, int iters,
     out[blockIdx.x * (long long)blockDim.x + threadIdx.x] = r;
 }
 
+// Variants for the machine-model measurements: `active` lanes of every warp issue the FMAs
+// (the others are masked off), `chains` = 0 uses the 4x4 tile pattern, 1 a single dependent
+// chain per thread (a = fma(a, b, c)).
+__global__ void __launch_bounds__(1024) probe_fp64_ex_kernel(double* out, int iters, int active, int chains) {
+    const int lane = threadIdx.x & 31;
+    double r = 0.0;
+    if (lane < active) {
+        if (chains == 0) {
+            double a[4], b[4], acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                a[i] = 0.999999 + threadIdx.x * 1e-9 + i * 1e-7;
+                b[i] = 1.0 - i * 1e-8 - blockIdx.x * 1e-12;
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+            }
+            for (int it = 0; it < iters; it++) {
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) r += acc[i][j];
+        } else {
+            double a = threadIdx.x * 1e-3, b = 0.999999 - blockIdx.x * 1e-12, c = 0.5;
+            for (int it = 0; it < iters; it++) {
+#pragma unroll
+                for (int u = 0; u < 16; u++) a = fma(a, b, c);
+            }
+            r = a;
+        }
+    }
+    out[blockIdx.x * (long long)blockDim.x + threadIdx.x] = r;
+}
+
 }  // namespace bf
+
+extern "C" int bf_probe_fp64_ex(int blocks, int threads, int iters, int active, int chains, double* out,
+                                bf_stream_t stream) {
+    if (blocks <= 0) return -1;
+    if (threads <= 0 || threads > 1024 || threads % 32) return -2;
+    if (iters <= 0) return -3;
+    if (active < 0 || active > 32) return -4;
+    if (chains < 0 || chains > 1) return -5;
+    if (!out) return -6;
+    bf::probe_fp64_ex_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(out, iters, active, chains);
+    bf::count_launch();
+    return cudaGetLastError() == cudaSuccess ? BF_SUCCESS : BF_ERR_CUDA;
+}
 
 extern "C" unsigned long long bf_launch_count(void) {
     return bf::g_launches.load(std::memory_order_relaxed);

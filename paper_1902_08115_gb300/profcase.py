@@ -1,0 +1,51 @@
+"""One routine on a batch larger than L2 (256-384 MiB of operands), run three times: a
+small, self-contained case for kernel profilers.
+
+    python -m paper_1902_08115_gb300.profcase {potrf|gemm|trsm} N [PAD]
+"""
+from __future__ import annotations
+
+import os
+import sys
+
+if __package__ in (None, ""):
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main(argv):
+    import torch
+
+    import bfsynth
+    import paper_1902_08115_gb300 as bf
+    which, n = argv[0], int(argv[1])
+    pad = int(argv[2]) if len(argv) > 2 else 0
+    ld, dev = n + pad, "cuda"
+    if which == "potrf":
+        b = max(1, (256 << 20) // (ld * n * 8))
+        S0 = bfsynth.spd_batch(b, n, ld, 1, device=dev)
+        S = S0.clone()
+        for _ in range(3):
+            S.copy_(S0)
+            info = bf.dpotrf(S, n=n)
+        torch.cuda.synchronize()
+        assert int(info.abs().max()) == 0
+    elif which == "gemm":
+        b = max(1, (384 << 20) // (3 * ld * n * 8))
+        A, B, C = (bfsynth.randn_batch(b, n, n, ld, s, device=dev) for s in (1, 2, 3))
+        for _ in range(3):
+            bf.dgemm("N", "T", 1.0, A, B, 1.0, C, m=n, n=n, k=n)
+    elif which == "trsm":
+        b = max(1, (256 << 20) // (2 * ld * n * 8))
+        L = bfsynth.spd_batch(b, n, ld, 1, device=dev)
+        bf.dpotrf(L, n=n)
+        X = bfsynth.randn_batch(b, n, n, ld, 2, device=dev)
+        for _ in range(3):
+            bf.dtrsm("R", "L", "T", "U", 1.0, L, X, m=n, n=n)
+    else:
+        raise SystemExit("routine must be potrf, gemm or trsm")
+    torch.cuda.synchronize()
+    print("ok", which, n, pad, b)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])

@@ -153,3 +153,21 @@ def test_tune_table(lib):
             lib.tune_set(7, 0, 1, 2, 0)
     finally:
         lib.reset_table()
+
+
+def test_dsposv_and_backward_arguments(lib):
+    f = lib.bf_dsposv_strided_batched
+    assert f(b"X", 4, 1, 1, 4, 16, 1, 4, 4, 1, 4, 4, None, None, 1e-12, 30, 1, None) == -1
+    assert f(b"L", 4, 1, 1, 3, 16, 1, 4, 4, 1, 4, 4, None, None, 1e-12, 30, 1, None) == -5
+    assert f(b"L", 4, 1, 1, 4, 16, 1, 4, 4, 1, 4, 4, None, None, -1.0, 30, 1, None) == -15
+    assert f(b"L", 300, 1, 1, 300, 0, 1, 300, 0, 1, 300, 0, None, None, 1e-12, 30, 1, None) == \
+        lib.ERR_NOT_SUPPORTED
+    assert f(b"L", 0, 1, None, 1, 0, None, 1, 0, None, 1, 0, None, None, 1e-12, 30, 1, None) == 0
+    g = lib.bf_dpotrf_backward_strided_batched
+    assert g(b"L", 4, 1, 3, 16, 1, 4, 16, 1, 4, 16, 1, None) == -4
+    assert g(b"U", 4, 1, 4, 16, 1, 4, 16, 1, 4, 16, 1, None) == lib.ERR_NOT_SUPPORTED
+    h = lib.bf_dtrsm_backward_strided_batched
+    assert h(b"R", b"L", b"T", b"N", 4, 4, 0.0, 1, 4, 16, 1, 4, 16, 1, 4, 16, None, 4, 0, 1, None) == -7
+    k = lib.bf_dgemm_backward_strided_batched
+    assert k(b"N", b"N", 4, 4, 4, 1.0, 1, 3, 16, 1, 4, 16, 1.0, 1, 4, 16, None, 4, 0, None, 4, 0, None, 4, 0,
+             1, None) == -8
