@@ -5,11 +5,12 @@
 // Work items come from a device queue (one atomic counter, no waiting between
 // CTAs), ordered by decreasing cost so the largest problems start first:
 //   BIG items  (n_b > lane_max): one problem per CTA.  The lower triangle is
-//     held packed in shared memory and factored right-looking with 8-column
-//     panels: the panel column by column with all threads over its rows
-//     (pivots via rsqrt), the trailing update by all threads on 4x4 register
-//     tiles (section 3.2.1's dgemm loop + edge structure at CTA scale); then a
-//     blocked forward/backward substitution.
+//     held packed in shared memory and factored right-looking with 16-column
+//     panels: the panel's diagonal block by one warp (pivots via rsqrt), the
+//     rows below it by all threads (one row's triangular solve each), the
+//     trailing update by all threads on 4x4 register tiles (section 3.2.1's
+//     dgemm loop + edge structure at CTA scale); three barriers per panel.
+//     Then a blocked forward/backward substitution.
 //   LANE items (n_b <= lane_max): blockDim problems per CTA, one per thread,
 //     sorted so a warp's problems have (nearly) equal order, using the same
 //     lane Cholesky as the uniform path.
@@ -42,6 +43,8 @@ struct RaggedParams {
 __device__ __forceinline__ int pcol(int j, int n) { return j * n - (j * (j - 1)) / 2; }  // packed column start
 
 // --------------------------------------------------------------------------- BIG: one problem per CTA
+#define BF_BIG_NB 16
+
 __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
     const int n = p.n[q];
     const int tid = threadIdx.x, T = blockDim.x, warp = tid >> 5, lane = tid & 31;
@@ -51,41 +54,66 @@ __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
     __shared__ int s_fail;
     double* S = p.S + p.offS[q];
     double* Bq = p.B + p.offB[q];
-    for (int j = 0; j < n; j++)
-        for (int i = j + tid; i < n; i += T) P[pcol(j, n) + i - j] = S[i + (long long)j * n];
+    // flat, independent loads of the lower triangle (many in flight per thread)
+    const int nn = n * n;
+#pragma unroll 4
+    for (int e = tid; e < nn; e += T) {
+        const int j = e / n, i = e - j * n;
+        if (i >= j) P[pcol(j, n) + i - j] = S[e];
+    }
     for (int e = tid; e < n * p.nrhs; e += T) X[e] = Bq[e];
     if (tid == 0) s_fail = 0;
     __syncthreads();
 
-    for (int J = 0; J < n; J += 8) {
-        const int nb = imin(8, n - J);
-        // panel J..J+nb-1: pivot, column scaling and the rank-1 updates inside the panel, with
-        // every thread of the CTA over the rows (two barriers per column)
-        for (int c = 0; c < nb; c++) {
-            const int j = J + c;
-            const double d = P[pcol(j, n)];
-            if (!(d > 0.0)) {  // every thread sees the same value
-                if (tid == 0) s_fail = j + 1;
-                break;
+    for (int J = 0; J < n; J += BF_BIG_NB) {
+        const int nb = imin(BF_BIG_NB, n - J);
+        // (1) Cholesky of the nb x nb diagonal block, warp-synchronous in warp 0
+        if (warp == 0) {
+            for (int c = 0; c < nb; c++) {
+                const int j = J + c;
+                const double d = P[pcol(j, n)];
+                if (!(d > 0.0)) {  // the same value in every lane
+                    if (lane == 0) s_fail = j + 1;
+                    break;
+                }
+                const double rs = rsqrt(d);
+                __syncwarp();
+                if (lane == 0) {
+                    P[pcol(j, n)] = d * rs;
+                    rinv[j] = rs;
+                }
+                if (lane < nb - c - 1) P[pcol(j, n) + 1 + lane] *= rs;
+                __syncwarp();
+                const int w = nb - c - 1;  // trailing block columns/rows right of c
+                for (int e = lane; e < w * w; e += 32) {
+                    const int kk = e / w, rr = e - kk * w;
+                    if (rr >= kk) {
+                        const int i = j + 1 + rr, k = j + 1 + kk;
+                        P[pcol(k, n) + i - k] = fma(-P[pcol(j, n) + i - j], P[pcol(j, n) + k - j], P[pcol(k, n) + i - k]);
+                    }
+                }
+                __syncwarp();
             }
-            const double rs = rsqrt(d);
-            __syncthreads();
-            if (tid == 0) {
-                P[pcol(j, n)] = d * rs;
-                rinv[j] = rs;
-            }
-            for (int i = j + 1 + tid; i < n; i += T) P[pcol(j, n) + i - j] *= rs;
-            __syncthreads();
-            const int w = J + nb - j - 1;  // panel columns right of j
-            const int h = n - j - 1;       // rows below j
-            for (int e = tid; e < w * h; e += T) {
-                const int k = j + 1 + e / h, i = j + 1 + e % h;
-                if (i >= k) P[pcol(k, n) + i - k] = fma(-P[pcol(j, n) + i - j], P[pcol(j, n) + k - j], P[pcol(k, n) + i - k]);
-            }
-            __syncthreads();
         }
-        __syncthreads();  // s_fail is written by thread 0 after a failed pivot
+        __syncthreads();
         if (s_fail) break;
+        // (2) the panel rows below: L(i, J:J+nb) = A(i, J:J+nb) L_JJ^{-T}, one row per thread
+        for (int i = J + nb + tid; i < n; i += T) {
+            double x[BF_BIG_NB];
+#pragma unroll
+            for (int c = 0; c < BF_BIG_NB; c++) x[c] = (c < nb) ? P[pcol(J + c, n) + i - (J + c)] : 0.0;
+#pragma unroll
+            for (int c = 0; c < BF_BIG_NB; c++) {
+                if (c < nb) {
+#pragma unroll
+                    for (int c2 = 0; c2 < c; c2++) x[c] = fma(-x[c2], P[pcol(J + c2, n) + c - c2], x[c]);
+                    x[c] *= rinv[J + c];
+                    P[pcol(J + c, n) + i - (J + c)] = x[c];
+                }
+            }
+        }
+        __syncthreads();
+        // (3) trailing update L22 -= L21 L21^T, rank nb, on lower 4x4 tiles
         const int R = J + nb, m = n - R;
         if (m > 0) {
             const int tb = (m + 3) / 4;
@@ -180,8 +208,10 @@ __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
             }
             __syncthreads();
         }
-        for (int j = 0; j < n; j++)
-            for (int i = j + tid; i < n; i += T) S[i + (long long)j * n] = P[pcol(j, n) + i - j];
+        for (int e = tid; e < nn; e += T) {
+            const int j = e / n, i = e - j * n;
+            if (i >= j) S[e] = P[pcol(j, n) + i - j];
+        }
         for (int e = tid; e < n * p.nrhs; e += T) Bq[e] = X[e];
     }
     if (tid == 0 && p.info) p.info[p.orig[q]] = fail;
