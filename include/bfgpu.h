@@ -39,6 +39,7 @@ typedef struct CUstream_st* bf_stream_t; /* identical to cudaStream_t */
 #define BF_SUCCESS 0
 #define BF_ERR_CUDA 1001
 #define BF_ERR_NOT_SUPPORTED 1002
+#define BF_ERR_NOALLOC_LIMIT 1003
 
 #define BF_ROUTINE_DGEMM 0
 #define BF_ROUTINE_DTRSM 1
@@ -218,6 +219,33 @@ int bf_ragged_potrf_potrs_plan_create(int batch, const int* n_host, int nrhs, do
 int bf_ragged_plan_launch(bf_ragged_plan_t plan, bf_stream_t stream);
 int bf_ragged_plan_info(bf_ragged_plan_t plan, int* out);
 int bf_ragged_plan_destroy(bf_ragged_plan_t plan);
+
+/* ------------------------------------------------------------------------ */
+/* Allocation-free ragged solve (the paper has no counterpart).  For callers */
+/* that cannot allocate device memory when they solve -- a controller whose */
+/* memory is sized once at start-up and whose control loop may not allocate, */
+/* or code that cannot hand the library a workspace -- this call runs the    */
+/* same persistent kernel as the plan above, without a CUDA graph and        */
+/* without any workspace: its queue lives in a file-scope device array of    */
+/* BF_RAGGED_NOALLOC_MAX problems (about 0.77 MB), which every GPU that loads */
+/* the library holds until the process exits.  Arguments are those of the    */
+/* plan (no workspace); the call allocates nothing, on the device or on the  */
+/* host.                                                                     */
+/*  - batch > BF_RAGGED_NOALLOC_MAX returns BF_ERR_NOALLOC_LIMIT (nothing is */
+/*    launched).                                                             */
+/*  - The first call on a device looks up the array's device address (set-  */
+/*    up); make that first call before any stream capture.                   */
+/*  - Every call shares the one array and overwrites it (the queue counter   */
+/*    is cleared each call): calls that overlap on the GPU -- on different   */
+/*    streams, or from different host threads -- race; serialise them, e.g. */
+/*    on one stream.                                                         */
+/* ------------------------------------------------------------------------ */
+#define BF_RAGGED_NOALLOC_MAX 32768
+
+int bf_ragged_potrf_potrs_noalloc(int batch, const int* n_host, int nrhs, double* S,
+                                  const long long* offS_host, double* B,
+                                  const long long* offB_host, int* info, int lane_max,
+                                  int threads, bf_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* The size switch (section 2.4: the switch point between variants depends  */

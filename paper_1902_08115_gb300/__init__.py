@@ -66,6 +66,7 @@ _SIGS = {
     "bf_ragged_plan_launch": [_vp, _vp],
     "bf_ragged_plan_info": [_vp, _ip],
     "bf_ragged_plan_destroy": [_vp],
+    "bf_ragged_potrf_potrs_noalloc": [_i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _i, _i, _vp],
     "bf_launch_count": [],
     "bf_probe_fp64": [_i, _i, _vp, _vp],
     "bf_probe_fp64_ex": [_i, _i, _i, _i, _i, _vp, _vp],
@@ -81,7 +82,8 @@ for _name, _args in _SIGS.items():
 
 ROUTINE_DGEMM, ROUTINE_DTRSM, ROUTINE_DPOTRF = 0, 1, 2
 VARIANT_DIRECT, VARIANT_PACKED, VARIANT_BLOCKED = 0, 1, 2
-ERR_CUDA, ERR_NOT_SUPPORTED = 1001, 1002
+ERR_CUDA, ERR_NOT_SUPPORTED, ERR_NOALLOC_LIMIT = 1001, 1002, 1003
+RAGGED_NOALLOC_MAX = 32768
 
 
 class BFError(RuntimeError):

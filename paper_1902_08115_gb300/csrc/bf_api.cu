@@ -235,6 +235,8 @@ const char* bf_status_string(int s) {
     if (s == BF_SUCCESS) return "success";
     if (s == BF_ERR_CUDA) return "a CUDA launch failed";
     if (s == BF_ERR_NOT_SUPPORTED) return "option not supported by this library";
+    if (s == BF_ERR_NOALLOC_LIMIT)
+        return "problem count exceeds the allocation-free scratch limit (BF_RAGGED_NOALLOC_MAX)";
     if (s < 0) return "illegal argument (the value is minus its 1-based position)";
     return "unknown status";
 }

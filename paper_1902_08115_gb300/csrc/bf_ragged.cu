@@ -420,3 +420,119 @@ extern "C" int bf_ragged_plan_info(bf_ragged_plan_t plan, int* out) {
     out[4] = (int)plan->smem;
     return BF_SUCCESS;
 }
+
+// ----------------------------------------------------------------------------- allocation-free entry point
+// Some callers cannot allocate device memory when they solve: code running under a fixed
+// memory budget (an embedded or real-time controller that sizes all memory at start-up and
+// forbids allocation in its control loop, the setting the paper's routines are written for),
+// and code that hands the library no workspace because another allocator owns the device.
+// bf_ragged_potrf_potrs_noalloc serves them: the persistent kernel's queue lives in the
+// file-scope array below, which every GPU that loads this library holds until the process
+// exits, and the call allocates nothing (no cudaMalloc/cudaFree, no host heap).
+#include <mutex>
+
+#define BF_NOALLOC_ALIGN(x) (((x) + 255) / 256 * 256)
+
+static constexpr size_t kNoallocCounter = 256;
+static constexpr size_t kNoallocInts = BF_NOALLOC_ALIGN(sizeof(int) * (size_t)BF_RAGGED_NOALLOC_MAX);
+static constexpr size_t kNoallocLongs = BF_NOALLOC_ALIGN(sizeof(long long) * (size_t)BF_RAGGED_NOALLOC_MAX);
+static constexpr size_t kNoallocBytes = kNoallocCounter + 2 * kNoallocInts + 2 * kNoallocLongs;
+
+static __device__ __align__(256) unsigned char g_ragged_noalloc_scratch[kNoallocBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256];  // device address of the scratch array, per device ordinal
+// host-side queue construction, reused by every call (guarded by g_noalloc_mu)
+int h_order[BF_RAGGED_NOALLOC_MAX];
+int h_n[BF_RAGGED_NOALLOC_MAX];
+int h_orig[BF_RAGGED_NOALLOC_MAX];
+long long h_offS[BF_RAGGED_NOALLOC_MAX];
+long long h_offB[BF_RAGGED_NOALLOC_MAX];
+}  // namespace
+
+extern "C" int bf_ragged_potrf_potrs_noalloc(int batch, const int* n_host, int nrhs, double* S,
+                                             const long long* offS_host, double* B, const long long* offB_host,
+                                             int* info, int lane_max, int threads, bf_stream_t stream) {
+    if (batch < 0) return -1;
+    if (batch > 0 && !n_host) return -2;
+    if (nrhs < 0 || nrhs > 64) return -3;
+    if (batch > 0 && !S) return -4;
+    if (batch > 0 && !offS_host) return -5;
+    if (batch > 0 && nrhs > 0 && !B) return -6;
+    if (batch > 0 && nrhs > 0 && !offB_host) return -7;
+    if (lane_max < 0) return -9;
+    if (threads != 128 && threads != 256 && threads != 512) return -10;
+    if (batch > BF_RAGGED_NOALLOC_MAX) return BF_ERR_NOALLOC_LIMIT;
+    if (batch == 0) return BF_SUCCESS;
+    int nmax = 0;
+    for (int b = 0; b < batch; b++) {
+        if (n_host[b] < 0) return -2;
+        nmax = std::max(nmax, n_host[b]);
+    }
+    const size_t smem = bf::ragged_smem_bytes(nmax > lane_max ? nmax : 0, nrhs);
+    if (smem > 227 * 1024) return BF_ERR_NOT_SUPPORTED;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return BF_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    // set-up, once per device, with that device current
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_ragged_noalloc_scratch) != cudaSuccess || !ptr) return BF_ERR_CUDA;
+        g_noalloc_ptr[dev] = ptr;
+    }
+    char* w = (char*)g_noalloc_ptr[dev];
+    unsigned int* counter = (unsigned int*)w;
+    int* dn = (int*)(w + kNoallocCounter);
+    int* dorig = (int*)(w + kNoallocCounter + kNoallocInts);
+    long long* doS = (long long*)(w + kNoallocCounter + 2 * kNoallocInts);
+    long long* doB = (long long*)(w + kNoallocCounter + 2 * kNoallocInts + kNoallocLongs);
+    // queue order: decreasing order n, ties by index (in place, no allocation)
+    for (int i = 0; i < batch; i++) h_order[i] = i;
+    std::sort(h_order, h_order + batch, [&](int a, int b) {
+        return n_host[a] > n_host[b] || (n_host[a] == n_host[b] && a < b);
+    });
+    int nbig = 0;
+    while (nbig < batch && n_host[h_order[nbig]] > lane_max) nbig++;
+    for (int i = 0; i < batch; i++) {
+        const int b = h_order[i];
+        h_n[i] = n_host[b];
+        h_orig[i] = b;
+        h_offS[i] = offS_host[b];
+        h_offB[i] = nrhs ? offB_host[b] : 0;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // pageable copies are staged before cudaMemcpyAsync returns, so the host arrays may be reused
+    if (cudaMemcpyAsync(dn, h_n, sizeof(int) * batch, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dorig, h_orig, sizeof(int) * batch, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(doS, h_offS, sizeof(long long) * batch, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(doB, h_offB, sizeof(long long) * batch, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(counter, 0, sizeof(unsigned int), s) != cudaSuccess)  // the queue starts empty
+        return BF_ERR_CUDA;
+    bf::RaggedParams p;
+    p.n = dn;
+    p.offS = doS;
+    p.offB = doB;
+    p.orig = dorig;
+    p.S = S;
+    p.B = B;
+    p.info = info;
+    p.nrhs = nrhs;
+    p.nbig = nbig;
+    p.nprob = batch;
+    p.nitems = nbig + (batch - nbig + threads - 1) / threads;
+    p.counter = counter;
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(bf::ragged_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+        return BF_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bf::ragged_persistent_kernel, threads, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return BF_ERR_CUDA;
+    bf::ragged_persistent_kernel<<<sms * per_sm, threads, smem, s>>>(p);
+    bf::count_launch();
+    return cudaGetLastError() == cudaSuccess ? BF_SUCCESS : BF_ERR_CUDA;
+}
