@@ -2,6 +2,8 @@
 small, self-contained case for kernel profilers.
 
     python -m paper_1902_08115_gb300.profcase {potrf|gemm|trsm} N [PAD]
+    python -m paper_1902_08115_gb300.profcase dsposv      (2048 SPD systems of order 128)
+    python -m paper_1902_08115_gb300.profcase ragged      (3000 orders in [100, 200], 4 RHS)
 """
 from __future__ import annotations
 
@@ -17,7 +19,28 @@ def main(argv):
 
     import bfsynth
     import paper_1902_08115_gb300 as bf
-    which, n = argv[0], int(argv[1])
+    which = argv[0]
+    if which == "dsposv":
+        A = bfsynth.spd_batch(2048, 128, 128, 3, device="cuda")
+        b = torch.randn(2048, 1, 128, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            bf.dsposv(A, b)
+        torch.cuda.synchronize()
+        print("ok dsposv")
+        return
+    if which == "ragged":
+        ns = bfsynth.ragged_orders(3000, 100, 200, 5)
+        S0, offS, B0, offB = bfsynth.ragged_spd(ns, 4, 6, device="cuda")
+        S, B = S0.clone(), B0.clone()
+        plan = bf.RaggedPlan(ns.numpy(), S, offS.numpy(), B, offB.numpy(), 4, lane_max=48, threads=256)
+        for _ in range(3):
+            S.copy_(S0)
+            B.copy_(B0)
+            plan.launch()
+        torch.cuda.synchronize()
+        print("ok ragged")
+        return
+    n = int(argv[1])
     pad = int(argv[2]) if len(argv) > 2 else 0
     ld, dev = n + pad, "cuda"
     if which == "potrf":
