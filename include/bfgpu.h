@@ -126,24 +126,32 @@ int bf_dpotrs_strided_batched(char uplo, int n, int nrhs, const double* A, int l
 /* dsposv (LAPACK's name for the mixed-precision SPD solve; the routines it */
 /* runs are the paper's dpotrf and dtrsm, section 3.1, in binary32): solve   */
 /* A X = B for SPD A (uplo 'L': lower triangle referenced, A not modified).  */
-/* A is rounded to binary32 and factored (pivots tested and square-rooted in */
-/* binary64); the binary32 solution is refined in binary64 (residual         */
-/* b - A x and update x + d in binary64) until the normwise backward error   */
-/* ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= tol for every       */
-/* column, at most itmax steps.  If the binary32 factorisation fails or the  */
-/* refinement does not converge, that problem is solved in binary64 instead. */
-/* Outputs (device arrays, may be NULL): iter[b] = refinement steps taken    */
-/* (max over columns; 0 = the binary32 solution met tol), -1 = binary64      */
-/* fallback; info[b] = 0, or j > 0 when the binary64 fallback found the       */
-/* leading minor of order j not positive definite (X is then not written).   */
+/* A is rounded to binary32 and factored one problem per thread (pivots      */
+/* tested and square-rooted in binary64); the binary32 solution is refined   */
+/* in binary64 (residual b - A x and update x + d in binary64) until the     */
+/* normwise backward error ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf)*/
+/* <= tol for every column, at most itmax steps.  If the binary32           */
+/* factorisation fails (non-positive or NaN pivot, or an entry beyond the    */
+/* binary32 range) or the refinement does not converge, that problem is      */
+/* solved in binary64 instead.                                               */
+/*   work: device memory of at least bf_dsposv_workspace_bytes(n, batch)     */
+/*         bytes, 256-byte aligned, owned by the caller (LAPACK's swork: the */
+/*         binary32 factors); its contents are undefined on return.          */
+/*   iter[b] (device, may be NULL): refinement steps taken (max over         */
+/*         columns; 0 = the binary32 solution met tol), -1 = binary64        */
+/*         fallback.  info[b] (device, may be NULL): 0, or j > 0 when the    */
+/*         binary64 fallback found the leading minor of order j not positive */
+/*         definite (X is then not written).                                 */
 /* 1 <= n <= BF_DSPOSV_NMAX (larger n: BF_ERR_NOT_SUPPORTED); ldb, ldx >= n. */
 /* ------------------------------------------------------------------------ */
-#define BF_DSPOSV_NMAX 192
+#define BF_DSPOSV_NMAX 256
 
+size_t bf_dsposv_workspace_bytes(int n, int batch);
 int bf_dsposv_strided_batched(char uplo, int n, int nrhs, const double* A, int lda,
                               long long strideA, const double* B, int ldb, long long strideB,
                               double* X, int ldx, long long strideX, int* iter, int* info,
-                              double tol, int itmax, int batch, bf_stream_t stream);
+                              double tol, int itmax, void* work, size_t work_bytes, int batch,
+                              bf_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Reverse mode (adjoints) of the routines above, strided batches.  Output   */

@@ -54,7 +54,8 @@ _SIGS = {
     "bf_tune_query": [_i, _i, _i, _i, _i, _ll, _ip],
     "bf_status_string": [_i],
     "bf_dsposv_strided_batched": [_c, _i, _i, _vp, _i, _ll, _vp, _i, _ll, _vp, _i, _ll, _vp, _vp, _d, _i,
-                                  _i, _vp],
+                                  _vp, ctypes.c_size_t, _i, _vp],
+    "bf_dsposv_workspace_bytes": [_i, _i],
     "bf_dgemm_backward_strided_batched": [_c, _c, _i, _i, _i, _d, _vp, _i, _ll, _vp, _i, _ll, _d, _vp, _i,
                                           _ll, _vp, _i, _ll, _vp, _i, _ll, _vp, _i, _ll, _i, _vp],
     "bf_dtrsm_backward_strided_batched": [_c, _c, _c, _c, _i, _i, _d, _vp, _i, _ll, _vp, _i, _ll, _vp, _i,
@@ -72,6 +73,7 @@ _SIGS = {
     "bf_probe_fp64_ex": [_i, _i, _i, _i, _i, _vp, _vp],
 }
 _RES = {"bf_tune_clear": None, "bf_status_string": ctypes.c_char_p, "bf_ragged_workspace_bytes": ctypes.c_size_t,
+        "bf_dsposv_workspace_bytes": ctypes.c_size_t,
         "bf_launch_count": ctypes.c_ulonglong}
 
 for _name, _args in _SIGS.items():
@@ -198,10 +200,12 @@ def dpotrs(L, B, n=None, nrhs=None, uplo: str = "L", stream=None):
 
 
 def dsposv(A, B, X=None, n=None, nrhs=None, tol: float = 1e-12, itmax: int = 30, iter=None, info=None,
-           uplo: str = "L", stream=None):
+           work=None, uplo: str = "L", stream=None):
     """Mixed-precision SPD solve A X = B (binary32 factor, binary64 refinement).
 
-    Returns (X, iter, info) with per-problem refinement counts (-1 = binary64 fallback).
+    `work` (a uint8 CUDA tensor of bf_dsposv_workspace_bytes(n, batch) bytes) is allocated
+    when not given.  Returns (X, iter, info) with per-problem refinement counts (-1 = binary64
+    fallback).
     """
     import torch
     bA, cA, ldA, sA = _batch_dims(A)
@@ -215,9 +219,12 @@ def dsposv(A, B, X=None, n=None, nrhs=None, tol: float = 1e-12, itmax: int = 30,
         iter = torch.empty(bA, dtype=torch.int32, device=A.device)
     if info is None:
         info = torch.empty(bA, dtype=torch.int32, device=A.device)
+    wb = bf_dsposv_workspace_bytes(n, bA)
+    if work is None:
+        work = torch.empty(max(wb, 1), dtype=torch.uint8, device=A.device)
     _check("bf_dsposv_strided_batched", bf_dsposv_strided_batched(
         _ch(uplo), n, nrhs, _ptr(A), ldA, sA, _ptr(B), ldB, sB, _ptr(X), ldX, sX, _ptr(iter), _ptr(info),
-        tol, itmax, bA, _stream(stream)))
+        tol, itmax, _ptr(work), work.numel(), bA, _stream(stream)))
     return X, iter, info
 
 

@@ -1,29 +1,69 @@
 // bf_dsposv.cu -- batched mixed-precision SPD solve: binary32 Cholesky factor,
-// binary64 iterative refinement (the interface is LAPACK's dsposv).
+// binary64 iterative refinement (the interface is LAPACK's dsposv, including
+// its workspace).
 //
 // The factorisation and solves are the paper's dpotrf/dtrsm (section 3.1)
-// carried out in binary32; refinement recovers binary64 accuracy:
-//   1. A (binary64, lower triangle referenced) is rounded to binary32 into
-//      shared memory and factored A32 = L32 L32^T, right-looking with 8-column
-//      panels.  Each pivot is tested for positivity and square-rooted in
-//      binary64, then rounded to binary32.
-//   2. x = L32^{-T} L32^{-1} b (binary32 substitutions, x kept in binary64).
-//   3. repeat: r = b - A x in binary64 (A read from global memory, symmetric
-//      from its lower triangle); stop when the normwise backward error
-//      eta = ||r||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= tol;
+// carried out in binary32; refinement recovers binary64 accuracy.  One CTA
+// (128 threads) per problem, the binary32 factor packed in shared memory:
+//   1. A's lower triangle is rounded to binary32 and factored A32 = L32 L32^T,
+//      right-looking with 8-column panels: the panel by one warp without CTA
+//      barriers (each pivot tested for positivity and square-rooted in
+//      binary64, then rounded to binary32), the trailing update by all
+//      threads on 4x4 tiles -- two barriers per panel.
+//   2. x = L32^{-T} L32^{-1} b (binary32 substitutions by one warp, x kept in
+//      binary64); repeat: r = b - A x in binary64 (A symmetric from its lower
+//      triangle, read from global memory); stop when the normwise backward
+//      error eta = ||r||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= tol;
 //      d = L32^{-T} L32^{-1} r (binary32); x = x + d in binary64.
-//   4. If the binary32 factorisation fails or `itmax` refinement steps do not
-//      reach tol, the problem is factored and solved in binary64 instead and
-//      iter = -1 (LAPACK's dsposv rule).
-// ||A||_inf is accumulated in binary32 from the rounded matrix and scaled by
-// (1 - 2(n+1) 2^-24), a lower bound of the binary64 norm, so the stopping
-// test never under-estimates eta.
-//
-// One CTA (256 threads) per problem; n <= BF_DSPOSV_NMAX.
+//   3. If the binary32 factorisation fails (a pivot <= 0, NaN, or an entry
+//      outside the binary32 range) or `itmax` steps do not reach tol, the
+//      problem is factored and solved in binary64 in its workspace slice
+//      (iter = -1), as LAPACK's dsposv does.
+// The warp that runs the serial phases is rotated by problem index, so the
+// binary64 pivot square roots of co-resident CTAs spread over the SM's four
+// FP64 pipes.  ||A||_inf is accumulated in binary32 from entries truncated
+// toward zero and scaled by (1 - 2(n+1) 2^-24): a lower bound of the binary64
+// norm, so the stopping test never under-estimates eta.  binary64 -> binary32
+// conversions of matrix entries are integer operations (round to nearest
+// even; binary32-subnormal results flush to zero): FP64 instructions run at
+// 1/64 of the binary32 rate on this GPU.
 #include "bf_internal.h"
 #include "../../include/bfgpu.h"
 
 namespace bf {
+
+// ---------------------------------------------------------------- binary64 -> binary32 by integer operations
+__device__ __forceinline__ float f64_to_f32_rn(double a) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+    const unsigned int sign = (unsigned int)(u >> 63) << 31;
+    const int e = (int)((u >> 52) & 0x7FF);
+    const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+    if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));  // inf / NaN
+    int E = e - 1023 + 127;
+    if (e == 0 || E <= 0) return __uint_as_float(sign);  // zero, or below the binary32 normal range
+    unsigned int mant = (unsigned int)(m >> 29);
+    const unsigned int rem = (unsigned int)(m & 0x1FFFFFFFull);
+    if (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) {
+        mant++;
+        if (mant == 0x800000u) {
+            mant = 0;
+            E++;
+        }
+    }
+    if (E >= 255) return __uint_as_float(sign | 0x7F800000u);
+    return __uint_as_float(sign | ((unsigned int)E << 23) | mant);
+}
+
+// |a| rounded toward zero to binary32 (a lower bound of |a|)
+__device__ __forceinline__ float f64_abs_to_f32_rz(double a) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull;
+    const int e = (int)(u >> 52);
+    if (e == 0x7FF) return __uint_as_float(0x7F800000u);
+    const int E = e - 1023 + 127;
+    if (e == 0 || E <= 0) return 0.0f;
+    if (E >= 255) return 3.4028234663852886e38f;
+    return __uint_as_float(((unsigned int)E << 23) | (unsigned int)((u >> 29) & 0x7FFFFFu));
+}
 
 struct SposvParams {
     int n, nrhs;
@@ -38,22 +78,11 @@ struct SposvParams {
     double tol;
     int itmax;
     long long batch;
+    unsigned char* work;  // per problem: `wper` bytes for the binary64 fallback factor
+    long long wper;
 };
 
-static __host__ __device__ inline size_t sposv_mat_bytes(int n) {
-    size_t f32 = (size_t)n * (n + 1) * sizeof(float);
-    size_t f64 = (size_t)n * (n + 1) / 2 * sizeof(double);
-    size_t m = f32 > f64 ? f32 : f64;
-    return (m + 15) / 16 * 16;
-}
-
-static size_t sposv_smem_bytes(int n) {
-    // matrix | x, r (binary64) | w, rinv (binary32) | reduction scratch
-    return sposv_mat_bytes(n) + 2 * (size_t)n * sizeof(double) + 2 * (size_t)((n + 3) / 4 * 4) * sizeof(float) +
-           64 * sizeof(double);
-}
-
-// |v| of a non-negative or NaN-free double as an order-preserving integer
+// ---------------------------------------------------------------- one CTA per problem
 __device__ __forceinline__ unsigned long long absbits(double v) {
     return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
 }
@@ -67,7 +96,7 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
-// block-wide max of non-negative doubles (as bit patterns); all threads get the result
+// block-wide max of non-negative values given as order-preserving bit patterns
 __device__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* scratch) {
     v = warp_max_u64(v);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -79,106 +108,115 @@ __device__ unsigned long long block_max_u64(unsigned long long v, unsigned long 
     return r;
 }
 
-// binary32 substitutions with the factor in shared memory, one warp:
-// w <- L^{-T} L^{-1} w  (rinv holds 1 / l_jj)
-__device__ void solve32_warp(const float* L, int ld, const float* rinv, float* w, int n) {
+__device__ __forceinline__ int pk(int i, int j, int n) { return j * n - (j * (j - 1)) / 2 + (i - j); }
+
+// w <- L^{-T} L^{-1} w with the packed binary32 factor in shared memory, one warp
+__device__ void solve32_warp(const float* L, const float* rinv, float* w, int n) {
     const int lane = threadIdx.x & 31;
     for (int j = 0; j < n; j++) {
         const float wj = w[j] * rinv[j];
         __syncwarp();
         if (lane == 0) w[j] = wj;
-        for (int i = j + 1 + lane; i < n; i += 32) w[i] = fmaf(-L[i + j * ld], wj, w[i]);
+        const float* col = L + pk(j, j, n);
+        for (int i = j + 1 + lane; i < n; i += 32) w[i] = fmaf(-col[i - j], wj, w[i]);
         __syncwarp();
     }
     for (int j = n - 1; j >= 0; j--) {
         const float wj = w[j] * rinv[j];
         __syncwarp();
         if (lane == 0) w[j] = wj;
-        for (int i = lane; i < j; i += 32) w[i] = fmaf(-L[j + i * ld], wj, w[i]);
+        for (int i = lane; i < j; i += 32) w[i] = fmaf(-L[pk(j, i, n)], wj, w[i]);
         __syncwarp();
     }
 }
 
-// packed lower index (column-major)
-__device__ __forceinline__ int pk(int i, int j, int n) { return j * n - (j * (j - 1)) / 2 + (i - j); }
+static size_t refine_smem_bytes(int n) {
+    // packed factor | reciprocal pivots | w (binary32) | x, r (binary64) | scratch
+    size_t f = ((size_t)n * (n + 1) / 2 + (size_t)n + (size_t)n) * sizeof(float);
+    f = (f + 15) / 16 * 16;
+    return f + 2 * (size_t)n * sizeof(double) + 32 * sizeof(double);
+}
 
-__global__ void __launch_bounds__(256) dsposv_kernel(SposvParams p) {
+__global__ void __launch_bounds__(128) dsposv_kernel(SposvParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const long long q = blockIdx.x;
     if (q >= p.batch) return;
     const int n = p.n;
     const int tid = threadIdx.x, T = blockDim.x, warp = tid >> 5, lane = tid & 31;
-    const int ld = n + 1;
+    const int sw = (int)(q % (T >> 5));  // the warp that runs the serial phases
     float* L = reinterpret_cast<float*>(smem_raw);
-    double* Lp = reinterpret_cast<double*>(smem_raw);  // binary64 fallback (packed lower)
-    double* xv = reinterpret_cast<double*>(smem_raw + sposv_mat_bytes(n));
+    float* rinv = L + (size_t)n * (n + 1) / 2;
+    float* wv = rinv + n;
+    size_t off = ((size_t)n * (n + 1) / 2 + 2 * (size_t)n) * sizeof(float);
+    off = (off + 15) / 16 * 16;
+    double* xv = reinterpret_cast<double*>(smem_raw + off);
     double* rv = xv + n;
-    float* wv = reinterpret_cast<float*>(rv + n);
-    float* rinv = wv + (n + 3) / 4 * 4;
-    unsigned long long* scratch = reinterpret_cast<unsigned long long*>(rinv + (n + 3) / 4 * 4);
-    __shared__ int s_flag;
-    __shared__ double s_anorm;
+    unsigned long long* scratch = reinterpret_cast<unsigned long long*>(rv + n);
+    __shared__ int s_done;
 
     const double* A = p.A.ptr(q);
     const double* B = p.B.ptr(q);
     double* X = p.X.mptr(q);
+    unsigned char* wbytes = p.work + q * p.wper;
 
-    // ---- 1. round the lower triangle to binary32 ----
+    // ---- 1. round the lower triangle to binary32 (packed by columns); independent loads ----
+#pragma unroll 8
     for (int e = tid; e < n * n; e += T) {
         const int j = e / n, i = e - j * n;
-        if (i >= j) L[i + j * ld] = (float)A[i + (long long)j * p.lda];
+        if (i >= j) L[pk(i, j, n)] = f64_to_f32_rn(A[i + (long long)j * p.lda]);
     }
+    if (tid == 0) s_done = 0;
     __syncthreads();
-    // ||A||_inf of the symmetric matrix, binary32 sums of the rounded entries
+    // ||A||_inf of the symmetric matrix from the rounded lower triangle.  Each rounded entry
+    // is at most (1 + 2^-24) times the binary64 one and the binary32 row sum is accurate to
+    // (n + 1) 2^-24, so the scaled result is a lower bound of the binary64 norm.
     unsigned long long an = 0;
     for (int i = tid; i < n; i += T) {
         float s = 0.0f;
-        for (int j = 0; j < n; j++) s += fabsf(j <= i ? L[i + j * ld] : L[j + i * ld]);
-        an = (unsigned long long)__double_as_longlong((double)s) > an ? (unsigned long long)__double_as_longlong((double)s) : an;
+        for (int j = 0; j < n; j++) s += fabsf(j <= i ? L[pk(i, j, n)] : L[pk(j, i, n)]);
+        const unsigned long long b = (unsigned long long)__float_as_uint(s);
+        an = b > an ? b : an;
     }
     an = block_max_u64(an, scratch);
-    if (tid == 0) s_anorm = __longlong_as_double((long long)an) * (1.0 - 2.0 * (n + 1) * 5.9604644775390625e-08);
+    const double anorm =
+        (double)__uint_as_float((unsigned int)an) * (1.0 - 2.0 * (n + 2) * 5.9604644775390625e-08);
 
     // ---- 2. binary32 Cholesky, right-looking, 8-column panels ----
-    if (tid == 0) s_flag = 0;
-    __syncthreads();
     for (int J = 0; J < n; J += 8) {
         const int nb = imin(8, n - J);
-        if (warp == 0) {
+        if (warp == sw) {
             for (int c = 0; c < nb; c++) {
                 const int j = J + c;
-                const double d = (double)L[j + j * ld];
-                if (!(d > 0.0)) {  // every lane sees the same value
-                    if (lane == 0) s_flag = j + 1;
+                const double d = (double)L[pk(j, j, n)];
+                if (!(d > 0.0) || !(d < 3.4e38)) {  // binary64 test of the binary32 pivot
+                    if (lane == 0) s_done = j + 1;
                     break;
                 }
-                const float ljj = (float)sqrt(d);  // pivot square root in binary64
+                const float ljj = (float)sqrt(d);  // binary64 square root, rounded to binary32
                 const float ri = 1.0f / ljj;
                 __syncwarp();
                 if (lane == 0) {
-                    L[j + j * ld] = ljj;
+                    L[pk(j, j, n)] = ljj;
                     rinv[j] = ri;
                 }
-                for (int i = j + 1 + lane; i < n; i += 32) L[i + j * ld] *= ri;
+                float* colj = L + pk(j, j, n) - j;
+                for (int i = j + 1 + lane; i < n; i += 32) colj[i] *= ri;
                 __syncwarp();
-                // rank-1 update of the rest of the panel
                 for (int k = j + 1; k < J + nb; k++) {
-                    const float lkj = L[k + j * ld];
-                    for (int i = k + lane; i < n; i += 32) L[i + k * ld] = fmaf(-L[i + j * ld], lkj, L[i + k * ld]);
+                    const float lkj = colj[k];
+                    float* colk = L + pk(k, k, n) - k;
+                    for (int i = k + lane; i < n; i += 32) colk[i] = fmaf(-colj[i], lkj, colk[i]);
                 }
                 __syncwarp();
             }
         }
         __syncthreads();
-        if (s_flag) break;
-        // trailing update: L22 -= L21 L21^T on lower 4x4 tiles, rank nb
-        const int R = J + nb;
-        const int m = n - R;
+        if (s_done) break;
+        const int R = J + nb, m = n - R;
         if (m > 0) {
             const int tb = (m + 3) / 4;
             const int ntile = tb * (tb + 1) / 2;
             for (int t = tid; t < ntile; t += T) {
-                // tile (I, K), I >= K, enumerated row by row of the lower tile triangle
                 int I = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
                 while ((I + 1) * (I + 2) / 2 <= t) I++;
                 while (I * (I + 1) / 2 > t) I--;
@@ -190,56 +228,73 @@ __global__ void __launch_bounds__(256) dsposv_kernel(SposvParams p) {
 #pragma unroll
                     for (int b = 0; b < 4; b++) acc[a][b] = 0.0f;
                 for (int c = 0; c < nb; c++) {
+                    const float* col = L + pk(J + c, J + c, n) - (J + c);
                     float li[4], lk[4];
 #pragma unroll
-                    for (int a = 0; a < 4; a++) li[a] = L[imin(i0 + a, n - 1) + (J + c) * ld];
+                    for (int a = 0; a < 4; a++) li[a] = col[imin(i0 + a, n - 1)];
 #pragma unroll
-                    for (int b = 0; b < 4; b++) lk[b] = L[imin(k0 + b, n - 1) + (J + c) * ld];
+                    for (int b = 0; b < 4; b++) lk[b] = col[imin(k0 + b, n - 1)];
 #pragma unroll
                     for (int a = 0; a < 4; a++)
 #pragma unroll
                         for (int b = 0; b < 4; b++) acc[a][b] = fmaf(li[a], lk[b], acc[a][b]);
                 }
 #pragma unroll
-                for (int a = 0; a < 4; a++)
+                for (int b = 0; b < 4; b++) {
+                    const int k = k0 + b;
+                    if (k >= n) continue;
+                    float* col = L + pk(k, k, n) - k;
 #pragma unroll
-                    for (int b = 0; b < 4; b++) {
-                        const int i = i0 + a, k = k0 + b;
-                        if (i < n && k <= i) L[i + k * ld] -= acc[a][b];
+                    for (int a = 0; a < 4; a++) {
+                        const int i = i0 + a;
+                        if (i < n && i >= k) col[i] -= acc[a][b];
                     }
+                }
             }
         }
         __syncthreads();
     }
-    bool fallback = s_flag != 0;
+    bool fallback = s_done != 0;
+    int iters = 0;
 
     // ---- 3. solve and refine every right-hand side ----
-    int iters = 0;
     for (int c = 0; c < p.nrhs && !fallback; c++) {
         const double* b = B + (long long)c * p.ldb;
         unsigned long long bn = 0;
         for (int i = tid; i < n; i += T) {
             const double bi = b[i];
             bn = absbits(bi) > bn ? absbits(bi) : bn;
-            wv[i] = (float)bi;
+            wv[i] = f64_to_f32_rn(bi);
         }
         bn = block_max_u64(bn, scratch);
         const double bnorm = __longlong_as_double((long long)bn);
-        if (warp == 0) solve32_warp(L, ld, rinv, wv, n);
+        if (warp == sw) solve32_warp(L, rinv, wv, n);
         __syncthreads();
         for (int i = tid; i < n; i += T) xv[i] = (double)wv[i];
         __syncthreads();
         int it = 0;
         bool done = false;
         for (;;) {
-            // r = b - A x, binary64, A symmetric from its lower triangle
             unsigned long long rn = 0, xn = 0;
             for (int i = tid; i < n; i += T) {
-                double s = b[i];
-                for (int j = 0; j < n; j++) {
-                    const double a = (j <= i) ? A[i + (long long)j * p.lda] : A[j + (long long)i * p.lda];
-                    s = fma(-a, xv[j], s);
+                // four partial sums: independent loads and FMA chains in flight
+                double s0 = b[i], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                int j = 0;
+                for (; j + 3 < n; j += 4) {
+                    const double a0 = (j <= i) ? A[i + (long long)j * p.lda] : A[j + (long long)i * p.lda];
+                    const double a1 = (j + 1 <= i) ? A[i + (long long)(j + 1) * p.lda] : A[j + 1 + (long long)i * p.lda];
+                    const double a2 = (j + 2 <= i) ? A[i + (long long)(j + 2) * p.lda] : A[j + 2 + (long long)i * p.lda];
+                    const double a3 = (j + 3 <= i) ? A[i + (long long)(j + 3) * p.lda] : A[j + 3 + (long long)i * p.lda];
+                    s0 = fma(-a0, xv[j], s0);
+                    s1 = fma(-a1, xv[j + 1], s1);
+                    s2 = fma(-a2, xv[j + 2], s2);
+                    s3 = fma(-a3, xv[j + 3], s3);
                 }
+                for (; j < n; j++) {
+                    const double a = (j <= i) ? A[i + (long long)j * p.lda] : A[j + (long long)i * p.lda];
+                    s0 = fma(-a, xv[j], s0);
+                }
+                const double s = (s0 + s1) + (s2 + s3);
                 rv[i] = s;
                 rn = absbits(s) > rn ? absbits(s) : rn;
                 xn = absbits(xv[i]) > xn ? absbits(xv[i]) : xn;
@@ -249,15 +304,14 @@ __global__ void __launch_bounds__(256) dsposv_kernel(SposvParams p) {
             xn = block_max_u64(xn, scratch);
             const double rnorm = __longlong_as_double((long long)rn);
             const double xnorm = __longlong_as_double((long long)xn);
-            const double den = s_anorm * xnorm + bnorm;
-            if (rnorm <= p.tol * den) {
+            if (rnorm <= p.tol * (anorm * xnorm + bnorm)) {
                 done = true;
                 break;
             }
             if (it == p.itmax) break;
             for (int i = tid; i < n; i += T) wv[i] = (float)rv[i];
             __syncthreads();
-            if (warp == 0) solve32_warp(L, ld, rinv, wv, n);
+            if (warp == sw) solve32_warp(L, rinv, wv, n);
             __syncthreads();
             for (int i = tid; i < n; i += T) xv[i] += (double)wv[i];
             __syncthreads();
@@ -280,19 +334,19 @@ __global__ void __launch_bounds__(256) dsposv_kernel(SposvParams p) {
         return;
     }
 
-    // ---- 4. binary64 fallback: factor (packed lower, in shared memory) and solve ----
+    // ---- binary64 fallback: factor (packed lower, in this problem's workspace) and solve ----
     __syncthreads();
+    double* Lp = reinterpret_cast<double*>(wbytes);
     for (int e = tid; e < n * n; e += T) {
         const int j = e / n, i = e - j * n;
         if (i >= j) Lp[pk(i, j, n)] = A[i + (long long)j * p.lda];
     }
-    __syncthreads();
-    if (tid == 0) s_flag = 0;
+    if (tid == 0) s_done = 0;
     __syncthreads();
     for (int j = 0; j < n; j++) {
         const double d = Lp[pk(j, j, n)];
         if (!(d > 0.0)) {
-            if (tid == 0) s_flag = j + 1;
+            if (tid == 0) s_done = j + 1;
             break;
         }
         const double ljj = sqrt(d);
@@ -310,7 +364,7 @@ __global__ void __launch_bounds__(256) dsposv_kernel(SposvParams p) {
         __syncthreads();
     }
     __syncthreads();
-    const int finfo = s_flag;
+    const int finfo = s_done;
     if (finfo == 0) {
         for (int c = 0; c < p.nrhs; c++) {
             const double* b = B + (long long)c * p.ldb;
@@ -344,26 +398,43 @@ __global__ void __launch_bounds__(256) dsposv_kernel(SposvParams p) {
     }
 }
 
-cudaError_t launch_dsposv(int n, int nrhs, MatRef A, int lda, MatRef B, int ldb, MatRef X, int ldx,
-                          int* iter, int* info, double tol, int itmax, long long batch, cudaStream_t s) {
+// workspace layout: per problem the binary64 packed lower triangle of the fallback, 256-byte aligned
+static long long sposv_wper(int n) {
+    const long long f64 = (long long)n * (n + 1) / 2 * (long long)sizeof(double);
+    return (f64 + 255) / 256 * 256;
+}
+
+size_t dsposv_workspace_bytes(int n, long long batch) {
+    if (n <= 0 || batch <= 0) return 0;
+    return (size_t)(sposv_wper(n) * batch);
+}
+
+cudaError_t launch_dsposv(int n, int nrhs, MatRef A, int lda, MatRef B, int ldb, MatRef X, int ldx, int* iter,
+                          int* info, double tol, int itmax, void* work, long long batch, cudaStream_t s) {
     if (batch == 0 || n == 0 || nrhs == 0) return cudaSuccess;
     SposvParams p;
     p.n = n; p.nrhs = nrhs; p.A = A; p.lda = lda; p.B = B; p.ldb = ldb; p.X = X; p.ldx = ldx;
     p.iter = iter; p.info = info; p.tol = tol; p.itmax = itmax; p.batch = batch;
-    const size_t smem = sposv_smem_bytes(n);
-    cudaError_t e = cudaFuncSetAttribute(dsposv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dsposv_kernel<<<(unsigned)batch, 256, smem, s>>>(p);
+    p.wper = sposv_wper(n);
+    p.work = reinterpret_cast<unsigned char*>(work);
+    const size_t smem = refine_smem_bytes(n);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(dsposv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dsposv_kernel<<<(unsigned)batch, 128, smem, s>>>(p);
     count_launch();
     return cudaGetLastError();
 }
 
 }  // namespace bf
 
+extern "C" size_t bf_dsposv_workspace_bytes(int n, int batch) { return bf::dsposv_workspace_bytes(n, batch); }
+
 extern "C" int bf_dsposv_strided_batched(char uplo, int n, int nrhs, const double* A, int lda, long long strideA,
                                          const double* B, int ldb, long long strideB, double* X, int ldx,
                                          long long strideX, int* iter, int* info, double tol, int itmax,
-                                         int batch, bf_stream_t stream) {
+                                         void* work, size_t work_bytes, int batch, bf_stream_t stream) {
     const bool lo = (uplo == 'L' || uplo == 'l'), up = (uplo == 'U' || uplo == 'u');
     if (!(lo || up)) return -1;
     if (n < 0) return -2;
@@ -372,19 +443,21 @@ extern "C" int bf_dsposv_strided_batched(char uplo, int n, int nrhs, const doubl
     if (strideA < 0) return -6;
     if (ldb < (n > 1 ? n : 1)) return -8;
     if (ldx < (n > 1 ? n : 1)) return -11;
-    if (batch < 0) return -17;
+    if (batch < 0) return -19;
     if (batch > 1 && strideX < (long long)ldx * nrhs) return -12;
     if (!(tol >= 0.0)) return -15;
     if (itmax < 0) return -16;
-    const bool work = n > 0 && nrhs > 0 && batch > 0;
-    if (work && !A) return -4;
-    if (work && !B) return -7;
-    if (work && !X) return -10;
+    const bool work_needed = n > 0 && nrhs > 0 && batch > 0;
+    if (work_needed && !A) return -4;
+    if (work_needed && !B) return -7;
+    if (work_needed && !X) return -10;
+    if (work_needed && work_bytes < bf::dsposv_workspace_bytes(n, batch)) return -18;
+    if (work_needed && (!work || (reinterpret_cast<unsigned long long>(work) & 255ull))) return -17;
     if (up) return BF_ERR_NOT_SUPPORTED;
     if (n > BF_DSPOSV_NMAX) return BF_ERR_NOT_SUPPORTED;
-    if (!work) return 0;
+    if (!work_needed) return 0;
     cudaError_t e = bf::launch_dsposv(n, nrhs, bf::mat_strided(A, strideA), lda, bf::mat_strided(B, strideB), ldb,
-                                      bf::mat_strided(X, strideX), ldx, iter, info, tol, itmax, batch,
+                                      bf::mat_strided(X, strideX), ldx, iter, info, tol, itmax, work, batch,
                                       (cudaStream_t)stream);
     return e == cudaSuccess ? BF_SUCCESS : BF_ERR_CUDA;
 }

@@ -157,12 +157,16 @@ def test_tune_table(lib):
 
 def test_dsposv_and_backward_arguments(lib):
     f = lib.bf_dsposv_strided_batched
-    assert f(b"X", 4, 1, 1, 4, 16, 1, 4, 4, 1, 4, 4, None, None, 1e-12, 30, 1, None) == -1
-    assert f(b"L", 4, 1, 1, 3, 16, 1, 4, 4, 1, 4, 4, None, None, 1e-12, 30, 1, None) == -5
-    assert f(b"L", 4, 1, 1, 4, 16, 1, 4, 4, 1, 4, 4, None, None, -1.0, 30, 1, None) == -15
-    assert f(b"L", 300, 1, 1, 300, 0, 1, 300, 0, 1, 300, 0, None, None, 1e-12, 30, 1, None) == \
-        lib.ERR_NOT_SUPPORTED
-    assert f(b"L", 0, 1, None, 1, 0, None, 1, 0, None, 1, 0, None, None, 1e-12, 30, 1, None) == 0
+    W = lib.bf_dsposv_workspace_bytes(4, 1)
+    assert W >= 4 * 4 * 4
+    assert f(b"X", 4, 1, 1, 4, 16, 1, 4, 4, 1, 4, 4, None, None, 1e-12, 30, 256, W, 1, None) == -1
+    assert f(b"L", 4, 1, 1, 3, 16, 1, 4, 4, 1, 4, 4, None, None, 1e-12, 30, 256, W, 1, None) == -5
+    assert f(b"L", 4, 1, 1, 4, 16, 1, 4, 4, 1, 4, 4, None, None, -1.0, 30, 256, W, 1, None) == -15
+    assert f(b"L", 4, 1, 1, 4, 16, 1, 4, 4, 1, 4, 4, None, None, 1e-12, 30, 256, W - 1, 1, None) == -18
+    assert f(b"L", 4, 1, 1, 4, 16, 1, 4, 4, 1, 4, 4, None, None, 1e-12, 30, 8, W, 1, None) == -17
+    assert f(b"L", 300, 1, 1, 300, 0, 1, 300, 0, 1, 300, 0, None, None, 1e-12, 30, 256,
+             lib.bf_dsposv_workspace_bytes(300, 1), 1, None) == lib.ERR_NOT_SUPPORTED
+    assert f(b"L", 0, 1, None, 1, 0, None, 1, 0, None, 1, 0, None, None, 1e-12, 30, None, 0, 1, None) == 0
     g = lib.bf_dpotrf_backward_strided_batched
     assert g(b"L", 4, 1, 3, 16, 1, 4, 16, 1, 4, 16, 1, None) == -4
     assert g(b"U", 4, 1, 4, 16, 1, 4, 16, 1, 4, 16, 1, None) == lib.ERR_NOT_SUPPORTED

@@ -31,7 +31,7 @@ def colmajor_batch(A_rowmajor):
     return np.ascontiguousarray(np.transpose(A_rowmajor, (0, 2, 1)))
 
 
-@pytest.mark.parametrize("n", [128, 96, 33, 5])
+@pytest.mark.parametrize("n", [128, 96, 33, 5, 256])
 def test_dsposv_conditioned(bf, oracle, n):
     batch = 30
     A, b, kap = bfsynth.precision_batch(batch, n, (1e2, 1e4, 1e6), seed=77 + n)
@@ -94,10 +94,3 @@ def test_dsposv_fallback_and_failure(bf, oracle):
         assert oracle.backward_error(Ac[q:q + 1], X[q], b[q])[0] <= 1e-12
 
 
-def test_dsposv_arguments(bf):
-    assert bf.bf_dsposv_strided_batched(b"X", 4, 1, 1, 4, 16, 1, 4, 4, 1, 4, 4, None, None, 1e-12, 30, 1,
-                                        None) == -1
-    assert bf.bf_dsposv_strided_batched(b"L", 4, 1, 1, 3, 16, 1, 4, 4, 1, 4, 4, None, None, 1e-12, 30, 1,
-                                        None) == -5
-    assert bf.bf_dsposv_strided_batched(b"L", 300, 1, 1, 300, 0, 1, 300, 0, 1, 300, 0, None, None, 1e-12,
-                                        30, 1, None) == bf.ERR_NOT_SUPPORTED
