@@ -88,6 +88,23 @@ def hbm_peak():
         return HBM_FALLBACK_GBS, "fallback (profiling recipe)"
 
 
+# ---------------------------------------------------------------------------- ranks
+def reduce_max_ms(ms: float, world: int, device=None) -> float:
+    """Max of a per-rank time over all ranks (one all-reduce; replicas share nothing else)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gflops(flops_per_rank: float, world: int, ms_step: float) -> float:
+    """Units all ranks processed / the slowest rank's time (weak scaling: fixed work per rank)."""
+    return flops_per_rank * world / (ms_step * 1e-3) / 1e9
+
+
 # ---------------------------------------------------------------------------- clocks
 class Clocks:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -218,11 +235,28 @@ def fp64_peak(bf, torch, dev):
 
 
 # ---------------------------------------------------------------------------- CPU oracle baseline
-def oracle_sample(budget_s: float, steps: int = 1):
-    """Time the CPU oracle on a bounded sample of every sweep point; returns (GFLOP/s, desc, cores)."""
-    import numpy as np
+_SAMPLES = {}
 
-    import bfsynth
+
+def _oracle_inputs(r, n, ld, k, seed):
+    """Seeded CPU inputs of one sampled sweep point, built once and reused across steps."""
+    key = (r, n, ld, k)
+    if key not in _SAMPLES:
+        import bfsynth
+        if r.startswith("dgemm"):
+            _SAMPLES[key] = tuple(bfsynth.randn_batch(k, n, n, ld, seed + t).numpy() for t in range(3))
+        elif r.startswith("dtrsm"):
+            _SAMPLES[key] = (bfsynth.unit_lower_batch(k, n, ld, seed, unit=(r[-1] == "u")).numpy(),
+                             bfsynth.randn_batch(k, n, n, ld, seed + 1).numpy())
+        else:
+            _SAMPLES[key] = (bfsynth.spd_batch(k, n, ld, seed).numpy(),)
+    return _SAMPLES[key]
+
+
+def oracle_sample(budget_s: float, steps: int = 1):
+    """Time the CPU oracle on a bounded sample of every sweep point; returns (GFLOP/s, desc, cores).
+
+    Only the oracle calls are timed; the sample inputs are generated once per process."""
     import oracle
     oracle.build()
     cores = oracle.num_threads()
@@ -236,27 +270,20 @@ def oracle_sample(budget_s: float, steps: int = 1):
                 for r in ROUTINES:
                     full = batch_of(r, n, ld)
                     k = int(max(16, min(full, 65536, per_call * est_rate / flops(r, n))))
-                    seed = 7 * n + pad
+                    ins = _oracle_inputs(r, n, ld, k, 7 * n + pad)
+                    t0 = time.perf_counter()
                     if r.startswith("dgemm"):
-                        A = bfsynth.randn_batch(k, n, n, ld, seed).numpy()
-                        B = bfsynth.randn_batch(k, n, n, ld, seed + 1).numpy()
-                        C = bfsynth.randn_batch(k, n, n, ld, seed + 2).numpy()
-                        t0 = time.perf_counter()
-                        oracle.dgemm(r[-2].upper(), r[-1].upper(), n, n, n, 1.0, A, B, 1.0, C)
+                        oracle.dgemm(r[-2].upper(), r[-1].upper(), n, n, n, 1.0, ins[0], ins[1], 1.0, ins[2])
                     elif r.startswith("dtrsm"):
-                        Lm = bfsynth.unit_lower_batch(k, n, ld, seed, unit=(r[-1] == "u")).numpy()
-                        X = bfsynth.randn_batch(k, n, n, ld, seed + 1).numpy()
-                        t0 = time.perf_counter()
-                        oracle.dtrsm("R", "L", "T", r[-1].upper(), n, n, 1.0, Lm, X)
+                        oracle.dtrsm("R", "L", "T", r[-1].upper(), n, n, 1.0, ins[0], ins[1])
                     else:
-                        S = bfsynth.spd_batch(k, n, ld, seed).numpy()
-                        t0 = time.perf_counter()
-                        oracle.dpotrf_l(S)
+                        oracle.dpotrf_l(ins[0])
                     tot_time += time.perf_counter() - t0
                     tot_flops += k * flops(r, n)
                     nprob += k
     desc = (f"oracle (plain C, binary64, OpenMP over problems) on {nprob} problems: a bounded "
-            f"sample of every sweep point and routine, ~{budget_s:.0f} s of CPU work per step")
+            f"sample of every sweep point and routine, ~{budget_s:.0f} s of CPU work per step "
+            f"(inputs built once, outside the timing)")
     return tot_flops / tot_time / 1e9, desc, cores
 
 
@@ -339,13 +366,9 @@ def main():
     bad = sum(int((p.info != 0).sum()) for p in points)
     if bad:
         raise RuntimeError(f"{bad} dpotrf problems failed during the timed steps")
-    ms_total = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = reduce_max_ms(t0.elapsed_time(t1), world, dev)
     ms_step = ms_total / args.steps
-    value = step_flops * world / (ms_step * 1e-3) / 1e9  # GFLOP/s, all ranks
+    value = whole_job_gflops(step_flops, world, ms_step)  # GFLOP/s, all ranks
 
     # ---- per-call figures and the roofline
     # FP64 roof from unit counts and the clock measured during the timed steps: every SM issues
