@@ -261,11 +261,13 @@ int bf_ragged_potrf_potrs_noalloc(int batch, const int* n_host, int nrhs, double
 /* bf_tune_set adds a table entry, consulted before the built-in defaults:    */
 /*   routine  BF_ROUTINE_*                                                    */
 /*   code     dgemm: 2*transA + transB; dtrsm: 8*right + 4*upper + 2*trans +  */
-/*            unit; dpotrf: 0.  -1 matches every code.                        */
+/*            unit; dpotrf: lda & 1 (even / odd leading dimension).        */
+/*            -1 matches every code.                                        */
 /*   [n_lo, n_hi]  matrix order range (dgemm: max(m, n); dtrsm: order of A)   */
 /*   variant  BF_VARIANT_*                                                    */
 /*   p0..p3   dgemm: TM, TN, KC, P (super-tile rows/cols, k-slice, problems   */
-/*            per CTA; 0 = default); dtrsm: MR (4/8), P; dpotrf: T, NB.       */
+/*            per CTA; 0 = default); dtrsm: MR (4/8), P; dpotrf: T, NB,     */
+/*            lane row-block height (4/8), lane k-loop unroll (1/2).        */
 /* Later entries take precedence.  bf_tune_clear removes all entries.         */
 /* bf_tune_query writes the configuration a call would use into out[5]:       */
 /* {variant, p0, p1, p2, p3} in the order above (dgemm: variant,TM,TN,KC,P).  */

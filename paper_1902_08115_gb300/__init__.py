@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libbfgpu.so")
 if not os.path.exists(LIB_PATH):
     raise ImportError(
         f"{LIB_PATH} is missing: build the CUDA library first "
-        "(python -m paper_1902_08115_gb300.build); there is no CPU fallback")
+        "(python paper_1902_08115_gb300/build.py); there is no CPU fallback")
 
 _lib = ctypes.CDLL(LIB_PATH)
 

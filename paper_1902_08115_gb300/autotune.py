@@ -125,33 +125,35 @@ def tune(quick=False, out=None, log=print):
                                 p=[best[1][1], best[1][2], 0, 0], gflops=round(fl / best[0] / 1e6, 1), n=n))
             log(f"dtrsm {''.join(args)} n={n}: {best[1]} {fl / best[0] / 1e6:.0f} GFLOP/s")
         del L, X
-        # ---- dpotrf
-        b = max(1, min(bfsynth.sweep_batch(n, n, 1), BUDGET // (n * n * 8)))
-        S0 = bfsynth.spd_batch(b, n, n, 6, device=dev)
-        S = S0.clone()
-        best = None
-        cands = [(0, T, 0) for T in (64, 128, 256)]
-        if n <= 16:
-            cands += [(1, T, 0) for T in (32, 64, 128)]
-        if n >= 16:
-            cands += [(2, 128, NB) for NB in (8, 16, 32, 64) if NB < n]
-        for variant, T, NB in cands:
-            bf.tune_clear()
-            bf.tune_set(bf.ROUTINE_DPOTRF, 0, 0, 1 << 30, variant, T, NB)
-
-            def run():
-                S.copy_(S0)
-                bf.dpotrf(S, n=n)
-
+        # ---- dpotrf, per leading-dimension parity (table code lda & 1)
+        for code, ld in ((0, n + (n & 1)), (1, n + 1 - (n & 1))):
+            b = max(1, min(bfsynth.sweep_batch(n, ld, 1), BUDGET // (ld * n * 8)))
+            S0 = bfsynth.spd_batch(b, n, ld, 6, device=dev)
+            S = S0.clone()
+            best = None
+            cands = [(0, T, 0, R, 2) for T in (64, 128, 256) for R in (4, 8) if R == 4 or n >= 8]
+            cands += [(0, 64, 0, R, 1) for R in (4, 8) if R == 4 or n >= 8]
+            if n <= 16:
+                cands += [(1, T, 0, 0, 0) for T in (32, 64, 128)]
+            if n >= 16:
+                cands += [(2, 128, NB, 0, 0) for NB in (8, 16, 32, 64) if NB < n]
             ms_copy = _time(torch, lambda: S.copy_(S0))
-            ms = _time(torch, run) - ms_copy
-            if best is None or ms < best[0]:
-                best = (max(ms, 1e-6), (variant, T, NB))
-        fl = b * (n ** 3 / 3 + n ** 2 / 2 + n / 6)
-        entries.append(dict(routine=bf.ROUTINE_DPOTRF, code=0, lo=lo, hi=hi, variant=best[1][0],
-                            p=[best[1][1], best[1][2], 0, 0], gflops=round(fl / best[0] / 1e6, 1), n=n))
-        log(f"dpotrf n={n}: {best[1]} {fl / best[0] / 1e6:.0f} GFLOP/s")
-        del S, S0
+            for variant, T, NB, R, U in cands:
+                bf.tune_clear()
+                bf.tune_set(bf.ROUTINE_DPOTRF, code, 0, 1 << 30, variant, T, NB, R, U)
+
+                def run():
+                    S.copy_(S0)
+                    bf.dpotrf(S, n=n)
+
+                ms = _time(torch, run) - ms_copy
+                if best is None or ms < best[0]:
+                    best = (max(ms, 1e-6), (variant, T, NB, R, U))
+            fl = b * (n ** 3 / 3 + n ** 2 / 2 + n / 6)
+            entries.append(dict(routine=bf.ROUTINE_DPOTRF, code=code, lo=lo, hi=hi, variant=best[1][0],
+                                p=list(best[1][1:]), gflops=round(fl / best[0] / 1e6, 1), n=n, lda=ld))
+            log(f"dpotrf n={n} lda={ld}: {best[1]} {fl / best[0] / 1e6:.0f} GFLOP/s")
+            del S, S0
         torch.cuda.empty_cache()
     bf.tune_clear()
     ragged = tune_ragged(torch, bf, dev, log, count=20000 if quick else 50000)

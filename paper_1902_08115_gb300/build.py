@@ -3,7 +3,7 @@
 Every translation unit under csrc/ is compiled for sm_103a only, in parallel,
 then linked into one shared library with the C ABI of include/bfgpu.h.
 
-    python -m paper_1902_08115_gb300.build [--force] [-v]
+    python paper_1902_08115_gb300/build.py [--force] [-v]
 """
 from __future__ import annotations
 

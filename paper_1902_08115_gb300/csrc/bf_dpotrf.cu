@@ -29,12 +29,12 @@
 
 namespace bf {
 
+template <int R, int U>
 __global__ void __launch_bounds__(256) dpotrf_lane_direct_kernel(PotrfParams p) {
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= p.batch) return;
     if (p.skip && p.skip[q] != 0) return;
-    double* a = p.A.mptr(q);
-    const int info = strips_aligned(a, p.lda) ? potrf_lane(GAccV{a, p.lda}, p.n) : potrf_lane(GAcc{a, p.lda}, p.n);
+    const int info = potrf_lane_global<R, U>(p.A.mptr(q), p.lda, p.n);
     if (info && p.info) p.info[q] = info + p.info_off;
 }
 
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) dpotrf_lane_packed_kernel(PotrfParams p) 
     bool active = q < p.batch && !(p.skip && p.skip[q] != 0);
     if (active) {
         SAcc M{smem + threadIdx.x, n, T};
-        info = potrf_lane(M, n);
+        info = potrf_lane<4, 2>(M, n);
         if (info && p.info) p.info[q] = info + p.info_off;
     }
     __syncthreads();
@@ -96,8 +96,20 @@ cudaError_t launch_dpotrf_lane(int n, MatRef A, int lda, long long batch, int* i
         return cudaGetLastError();
     }
     const int T = cfg.T > 0 ? cfg.T : 128;
-    long long blocks = (batch + T - 1) / T;
-    dpotrf_lane_direct_kernel<<<(unsigned)blocks, T, 0, s>>>(p);
+    const unsigned blocks = (unsigned)((batch + T - 1) / T);
+    if (cfg.rows == 8) {
+        if (cfg.unroll == 2) {
+            dpotrf_lane_direct_kernel<8, 2><<<blocks, T, 0, s>>>(p);
+        } else {
+            dpotrf_lane_direct_kernel<8, 1><<<blocks, T, 0, s>>>(p);
+        }
+    } else {
+        if (cfg.unroll == 1) {
+            dpotrf_lane_direct_kernel<4, 1><<<blocks, T, 0, s>>>(p);
+        } else {
+            dpotrf_lane_direct_kernel<4, 2><<<blocks, T, 0, s>>>(p);
+        }
+    }
     count_launch();
     return cudaGetLastError();
 }
@@ -113,7 +125,8 @@ cudaError_t launch_dpotrf(int n, MatRef A, int lda, long long batch, int* info,
     if (cfg.variant != VAR_BLOCKED) return launch_dpotrf_lane(n, A, lda, batch, info, 0, nullptr, cfg, s);
     // right-looking blocked factorisation built from the library's kernels
     const int NB = cfg.NB;
-    PotrfConfig lane{VAR_DIRECT, 128, 0};
+    PotrfConfig lane = choose_potrf(NB, lda, batch);
+    lane.variant = VAR_DIRECT;
     for (int J = 0; J < n; J += NB) {
         const int jb = (n - J < NB) ? (n - J) : NB;
         cudaError_t e = launch_dpotrf_lane(jb, mat_sub(A, J, J, lda), lda, batch, info, J, info, lane, s);

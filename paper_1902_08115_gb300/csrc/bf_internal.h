@@ -64,6 +64,8 @@ struct PotrfConfig {
                   // shared memory), VAR_BLOCKED (right-looking sequence of kernels)
     int T;        // threads (= problems) per CTA for the lane kernels
     int NB;       // block size of the blocked variant
+    int rows;     // lane kernels: row-block height, 4 or 8
+    int unroll;   // lane kernels: unroll of the k loops, 1 or 2
 };
 
 struct PotrfParams {

@@ -1,68 +1,138 @@
 // bf_lane.cuh -- the lane Cholesky: one thread factors one whole problem.
 //
 // Left-looking by 4-column blocks, in the structure of the paper's
-// kernel_dpotrf_nt_l (section 3.2.1): for the diagonal block a dgemm loop
-// (D = A_JJ - L_J L_J^T), then a 4x4 Cholesky edge in registers; for every
-// 4-row block below it a dgemm loop, then the triangular edge with the
-// reciprocal pivots.  Shared by the uniform (bf_dpotrf.cu) and ragged
-// (bf_ragged.cu) kernels.
+// kernel_dpotrf_nt_l (section 3.2.1): the rows J..n-1 of block column J are
+// computed as "dgemm_nt loop over the factored columns, then an edge".  Two
+// row-block heights R:
 //
-// Operands are reached through an accessor.  ld4/st4 move a strip of four
-// consecutive rows of one column (rows clamped to n - 1 on loads at the end
-// of the matrix); the aligned global accessor does it with two 16-byte
-// accesses, which halves the L1 requests of these uncoalesced per-lane
-// streams (the lane kernels are bound by L1 request throughput, not DRAM).
+//  * R = 4: the 4x4 diagonal block (Cholesky edge in registers), then 4x4
+//    blocks below it (triangular edge with the reciprocal pivots).  Each k
+//    step of a block moves 8 words for 16 fused multiply-adds.
+//  * R = 8: the first row block holds the diagonal block and the 4 rows under
+//    it, like the paper's 8x4 dpotrf kernel; the rows below follow as 8x4
+//    blocks and a 4x4 tail.  Each k step of an 8x4 block moves 12 words for
+//    32 fused multiply-adds, at the price of more registers per thread.
+//
+// Shared by the uniform (bf_dpotrf.cu) and ragged (bf_ragged.cu) kernels.
+//
+// Operands are reached through an accessor whose strip<R> loads move R
+// consecutive rows of one column (rows clamped to n - 1 at the end of the
+// matrix).  The lanes of a warp hold different problems, so every access is
+// uncoalesced and these kernels are bound by L1 request throughput; the
+// global accessors differ in how many requests a strip takes.
 #pragma once
 
 #include "bf_common.cuh"
 
 namespace bf {
 
-struct GAcc {  // a problem in global memory
+// Global memory, one 8-byte access per element.
+struct GAccS {
     double* a;
     int lda;
     __device__ __forceinline__ double ld(int i, int j) const { return a[i + (long long)j * lda]; }
     __device__ __forceinline__ void st(int i, int j, double v) const { a[i + (long long)j * lda] = v; }
-    __device__ __forceinline__ void ld4(int i, int j, int n, double* o) const {
+    template <int R>
+    __device__ __forceinline__ void strip(int i, int j, int n, double* o) const {
 #pragma unroll
-        for (int r = 0; r < 4; r++) o[r] = ld(imin(i + r, n - 1), j);
+        for (int r = 0; r < R; r++) o[r] = ld(imin(i + r, n - 1), j);
     }
-    __device__ __forceinline__ void st4(int i, int j, int cnt, const double* v) const {
+    template <int R>
+    __device__ __forceinline__ void put(int i, int j, int cnt, const double* v) const {
 #pragma unroll
-        for (int r = 0; r < 4; r++)
+        for (int r = 0; r < R; r++)
             if (r < cnt) st(i + r, j, v[r]);
     }
 };
 
-// Global memory, base 16-byte aligned and lda even: a strip starting at a row
-// multiple of 4 is 16-byte aligned.
+// Global memory, base 16-byte aligned and lda even: every strip that starts at
+// an even row is 16-byte aligned and moves as R/2 16-byte accesses.
 struct GAccV {
     double* a;
     int lda;
     __device__ __forceinline__ double ld(int i, int j) const { return a[i + (long long)j * lda]; }
     __device__ __forceinline__ void st(int i, int j, double v) const { a[i + (long long)j * lda] = v; }
-    __device__ __forceinline__ void ld4(int i, int j, int n, double* o) const {
-        if (i + 3 < n) {
+    template <int R>
+    __device__ __forceinline__ void strip(int i, int j, int n, double* o) const {
+        if (i + R <= n) {
             const double2* p = reinterpret_cast<const double2*>(a + i + (long long)j * lda);
-            const double2 x = p[0], y = p[1];
-            o[0] = x.x;
-            o[1] = x.y;
-            o[2] = y.x;
-            o[3] = y.y;
+#pragma unroll
+            for (int k = 0; k < R / 2; k++) {
+                const double2 x = p[k];
+                o[2 * k] = x.x;
+                o[2 * k + 1] = x.y;
+            }
         } else {
 #pragma unroll
-            for (int r = 0; r < 4; r++) o[r] = ld(imin(i + r, n - 1), j);
+            for (int r = 0; r < R; r++) o[r] = ld(imin(i + r, n - 1), j);
         }
     }
-    __device__ __forceinline__ void st4(int i, int j, int cnt, const double* v) const {
-        if (cnt == 4) {
+    template <int R>
+    __device__ __forceinline__ void put(int i, int j, int cnt, const double* v) const {
+        if (cnt == R) {
             double2* p = reinterpret_cast<double2*>(a + i + (long long)j * lda);
-            p[0] = make_double2(v[0], v[1]);
-            p[1] = make_double2(v[2], v[3]);
+#pragma unroll
+            for (int k = 0; k < R / 2; k++) p[k] = make_double2(v[2 * k], v[2 * k + 1]);
         } else {
 #pragma unroll
-            for (int r = 0; r < 4; r++)
+            for (int r = 0; r < R; r++)
                 if (r < cnt) st(i + r, j, v[r]);
+        }
+    }
+};
+
+// Global memory, any lda: a strip moves as 16-byte pieces from its first
+// 16-byte boundary on -- R/2 accesses when it starts on a boundary, R/2 + 1
+// (a single word at each end) when it starts 8 bytes past one.
+struct GAccP {
+    double* a;
+    int lda;
+    __device__ __forceinline__ double ld(int i, int j) const { return a[i + (long long)j * lda]; }
+    __device__ __forceinline__ void st(int i, int j, double v) const { a[i + (long long)j * lda] = v; }
+    template <int R>
+    __device__ __forceinline__ void strip(int i, int j, int n, double* o) const {
+        const double* p = a + i + (long long)j * lda;
+        if (i + R <= n) {
+            if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
+#pragma unroll
+                for (int k = 0; k < R / 2; k++) {
+                    const double2 x = reinterpret_cast<const double2*>(p)[k];
+                    o[2 * k] = x.x;
+                    o[2 * k + 1] = x.y;
+                }
+            } else {
+                o[0] = p[0];
+#pragma unroll
+                for (int k = 0; k < R / 2 - 1; k++) {
+                    const double2 x = reinterpret_cast<const double2*>(p + 1)[k];
+                    o[1 + 2 * k] = x.x;
+                    o[2 + 2 * k] = x.y;
+                }
+                o[R - 1] = p[R - 1];
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; r++) o[r] = ld(imin(i + r, n - 1), j);
+        }
+    }
+    template <int R>
+    __device__ __forceinline__ void put(int i, int j, int cnt, const double* v) const {
+        double* p = a + i + (long long)j * lda;
+        if (cnt == R) {
+            if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
+#pragma unroll
+                for (int k = 0; k < R / 2; k++) reinterpret_cast<double2*>(p)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+            } else {
+                p[0] = v[0];
+#pragma unroll
+                for (int k = 0; k < R / 2 - 1; k++)
+                    reinterpret_cast<double2*>(p + 1)[k] = make_double2(v[1 + 2 * k], v[2 + 2 * k]);
+                p[R - 1] = v[R - 1];
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; r++)
+                if (r < cnt) p[r] = v[r];
         }
     }
 };
@@ -72,121 +142,211 @@ struct SAcc {  // a problem in shared memory, interleaved with the CTA's other p
     int n, T;
     __device__ __forceinline__ double ld(int i, int j) const { return s[(i + j * n) * T]; }
     __device__ __forceinline__ void st(int i, int j, double v) const { s[(i + j * n) * T] = v; }
-    __device__ __forceinline__ void ld4(int i, int j, int nn, double* o) const {
+    template <int R>
+    __device__ __forceinline__ void strip(int i, int j, int nn, double* o) const {
 #pragma unroll
-        for (int r = 0; r < 4; r++) o[r] = ld(imin(i + r, nn - 1), j);
+        for (int r = 0; r < R; r++) o[r] = ld(imin(i + r, nn - 1), j);
     }
-    __device__ __forceinline__ void st4(int i, int j, int cnt, const double* v) const {
+    template <int R>
+    __device__ __forceinline__ void put(int i, int j, int cnt, const double* v) const {
 #pragma unroll
-        for (int r = 0; r < 4; r++)
+        for (int r = 0; r < R; r++)
             if (r < cnt) st(i + r, j, v[r]);
     }
 };
 
-// Factor one problem in place through the accessor.  Returns info (0 or 1-based column).
-template <class Acc>
+// acc (R x 4) <- acc L_JJ^{-T}: forward substitution against the factored
+// diagonal block d (lower, diagonal replaced by its reciprocal rinv).
+template <int R>
+__device__ __forceinline__ void trsm_edge(double (&acc)[R][4], const double (&d)[4][4], const double (&rinv)[4]) {
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+#pragma unroll
+        for (int c2 = 0; c2 < c; c2++)
+#pragma unroll
+            for (int r = 0; r < R; r++) acc[r][c] = fma(-acc[r][c2], d[c][c2], acc[r][c]);
+#pragma unroll
+        for (int r = 0; r < R; r++) acc[r][c] *= rinv[c];
+    }
+}
+
+// Rows I..I+R-1 of block column J: acc = A(I:I+R, J:J+4) - L(I:I+R, 0:J) L(J:J+4, 0:J)^T,
+// then acc L_JJ^{-T}, stored for the rows that exist.  U = unroll of the k loop.
+template <int R, int U, class Acc>
+__device__ __forceinline__ void lane_block(const Acc& M, int n, int I, int J, int jb, const int (&jr)[4],
+                                           const double (&d)[4][4], const double (&rinv)[4]) {
+    double acc[R][4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        double col[R];
+        M.template strip<R>(I, jr[c], n, col);
+#pragma unroll
+        for (int r = 0; r < R; r++) acc[r][c] = col[r];
+    }
+#pragma unroll U
+    for (int pp = 0; pp < J; pp++) {
+        double a[R], b[4];
+        M.template strip<R>(I, pp, n, a);
+        M.template strip<4>(J, pp, n, b);
+#pragma unroll
+        for (int r = 0; r < R; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[r][c] = fma(-a[r], b[c], acc[r][c]);
+    }
+    trsm_edge<R>(acc, d, rinv);
+    const int ib = imin(R, n - I);
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        if (c < jb) {
+            double col[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) col[r] = acc[r][c];
+            M.template put<R>(I, J + c, ib, col);
+        }
+    }
+}
+
+// D = A_JJ - L_J L_J^T (lower part) for the 4 rows J..J+3 alone.
+template <int U, class Acc>
+__device__ __forceinline__ void lane_diag(const Acc& M, int n, int J, const int (&jr)[4], double (&d)[4][4]) {
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        double col[4];
+        M.template strip<4>(J, jr[c], n, col);  // rows above c are read but not used
+#pragma unroll
+        for (int r = c; r < 4; r++) d[r][c] = col[r];
+    }
+#pragma unroll U
+    for (int pp = 0; pp < J; pp++) {
+        double l[4];
+        M.template strip<4>(J, pp, n, l);
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c <= r; c++) d[r][c] = fma(-l[r], l[c], d[r][c]);
+    }
+}
+
+// Rows J..J+7 in one pass: D as above and E = A(J+4:J+8, J:J+4) - L(J+4:J+8, 0:J) L_J^T,
+// both from one 8-row strip per k step.
+template <int U, class Acc>
+__device__ __forceinline__ void lane_diag_under(const Acc& M, int n, int J, const int (&jr)[4], double (&d)[4][4],
+                                                double (&e)[4][4]) {
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        double col[8];
+        M.template strip<8>(J, jr[c], n, col);  // rows above c are read but not used
+#pragma unroll
+        for (int r = c; r < 4; r++) d[r][c] = col[r];
+#pragma unroll
+        for (int r = 0; r < 4; r++) e[r][c] = col[4 + r];
+    }
+#pragma unroll U
+    for (int pp = 0; pp < J; pp++) {
+        double l[8];
+        M.template strip<8>(J, pp, n, l);
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c <= r; c++) d[r][c] = fma(-l[r], l[c], d[r][c]);
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) e[r][c] = fma(-l[4 + r], l[c], e[r][c]);
+    }
+}
+
+// 4x4 Cholesky edge in registers (rows past jb padded with the identity): d becomes L_JJ
+// and rinv its reciprocal diagonal.  Returns 0, or the 1-based column (within the block)
+// whose pivot is not positive.
+__device__ __forceinline__ int chol_edge(double (&d)[4][4], double (&rinv)[4], int jb) {
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        if (r >= jb) {
+#pragma unroll
+            for (int c = 0; c < r; c++) d[r][c] = 0.0;
+            d[r][r] = 1.0;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const double piv = d[c][c];
+        if (!(piv > 0.0)) return c + 1;
+        const double rs = rsqrt(piv);
+        rinv[c] = rs;
+        d[c][c] = piv * rs;
+#pragma unroll
+        for (int r = c + 1; r < 4; r++) d[r][c] *= rs;
+#pragma unroll
+        for (int r = c + 1; r < 4; r++)
+#pragma unroll
+            for (int c2 = c + 1; c2 <= r; c2++) d[r][c2] = fma(-d[r][c], d[c2][c], d[r][c2]);
+    }
+    return 0;
+}
+
+// Factor one problem in place through the accessor, with row blocks of R (4 or 8) and the
+// k loops unrolled U times.  Returns info (0 or 1-based column).
+template <int R, int U, class Acc>
 __device__ __forceinline__ int potrf_lane(const Acc& M, int n) {
     for (int J = 0; J < n; J += 4) {
         const int jb = imin(4, n - J);
+        const bool under = R == 8 && J + 4 < n;  // the 8-row first block applies
         int jr[4];
 #pragma unroll
         for (int r = 0; r < 4; r++) jr[r] = imin(J + r, n - 1);
-        // ---- diagonal block: D = A_JJ - sum_p L(J:J+4, p) L(J:J+4, p)^T (lower part) ----
-        double d[4][4];
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-            double col[4];
-            M.ld4(J, jr[c], n, col);  // rows above c are read but not used (strict upper triangle)
-#pragma unroll
-            for (int r = c; r < 4; r++) d[r][c] = col[r];
+        double d[4][4], e[4][4], rinv[4];
+        if (under) {
+            lane_diag_under<U>(M, n, J, jr, d, e);
+        } else {
+            lane_diag<U>(M, n, J, jr, d);
         }
-#pragma unroll 2
-        for (int pp = 0; pp < J; pp++) {
-            double l[4];
-            M.ld4(J, pp, n, l);
-#pragma unroll
-            for (int r = 0; r < 4; r++)
-#pragma unroll
-                for (int c = 0; c <= r; c++) d[r][c] = fma(-l[r], l[c], d[r][c]);
-        }
-        // pad the block beyond n with the identity
-#pragma unroll
-        for (int r = 0; r < 4; r++) {
-            if (r >= jb) {
-#pragma unroll
-                for (int c = 0; c < r; c++) d[r][c] = 0.0;
-                d[r][r] = 1.0;
-            }
-        }
-        // ---- 4x4 Cholesky edge in registers ----
-        double rinv[4];
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-            const double piv = d[c][c];
-            if (!(piv > 0.0)) return J + c + 1;
-            const double rs = rsqrt(piv);
-            rinv[c] = rs;
-            d[c][c] = piv * rs;
-#pragma unroll
-            for (int r = c + 1; r < 4; r++) d[r][c] *= rs;
-#pragma unroll
-            for (int r = c + 1; r < 4; r++)
-#pragma unroll
-                for (int c2 = c + 1; c2 <= r; c2++) d[r][c2] = fma(-d[r][c], d[c2][c], d[r][c2]);
-        }
+        const int f = chol_edge(d, rinv, jb);
+        if (f) return J + f;
         // lower part of the diagonal block only (the strict upper triangle is never written)
 #pragma unroll
         for (int r = 0; r < 4; r++)
 #pragma unroll
             for (int c = 0; c <= r; c++)
                 if (r < jb) M.st(J + r, J + c, d[r][c]);
-        // ---- 4-row blocks below: acc = A_IJ - L_I L_J^T, then acc L_JJ^{-T} ----
-        for (int I = J + 4; I < n; I += 4) {
+        int I = J + 4;
+        if (under) {  // the 4 rows under the diagonal block, accumulated with it
+            trsm_edge<4>(e, d, rinv);
             const int ib = imin(4, n - I);
-            double acc[4][4];
 #pragma unroll
             for (int c = 0; c < 4; c++) {
                 double col[4];
-                M.ld4(I, jr[c], n, col);
 #pragma unroll
-                for (int r = 0; r < 4; r++) acc[r][c] = col[r];
+                for (int r = 0; r < 4; r++) col[r] = e[r][c];
+                M.template put<4>(I, J + c, ib, col);
             }
-#pragma unroll 2
-            for (int pp = 0; pp < J; pp++) {
-                double a[4], b[4];
-                M.ld4(I, pp, n, a);
-                M.ld4(J, pp, n, b);
-#pragma unroll
-                for (int r = 0; r < 4; r++)
-#pragma unroll
-                    for (int c = 0; c < 4; c++) acc[r][c] = fma(-a[r], b[c], acc[r][c]);
-            }
-#pragma unroll
-            for (int c = 0; c < 4; c++) {
-#pragma unroll
-                for (int c2 = 0; c2 < c; c2++)
-#pragma unroll
-                    for (int r = 0; r < 4; r++) acc[r][c] = fma(-acc[r][c2], d[c][c2], acc[r][c]);
-#pragma unroll
-                for (int r = 0; r < 4; r++) acc[r][c] *= rinv[c];
-            }
-#pragma unroll
-            for (int c = 0; c < 4; c++) {
-                if (c < jb) {
-                    double col[4];
-#pragma unroll
-                    for (int r = 0; r < 4; r++) col[r] = acc[r][c];
-                    M.st4(I, J + c, ib, col);
-                }
-            }
+            I += 4;
         }
+        if (R == 8) {  // R-row blocks while more than 4 rows remain, then a 4-row tail
+            for (; I + 4 < n; I += R) lane_block<R, U>(M, n, I, J, jb, jr, d, rinv);
+        }
+        for (; I < n; I += 4) lane_block<4, U>(M, n, I, J, jb, jr, d, rinv);
     }
     return 0;
 }
 
-// 16-byte alignment of every 4-row strip: base aligned and lda even
+#ifndef BF_LANE8_MISALIGNED
+#define BF_LANE8_MISALIGNED GAccP
+#endif
+
+// 16-byte alignment of every strip that starts at an even row: base aligned and lda even
 __device__ __forceinline__ bool strips_aligned(const double* a, int lda) {
     return ((reinterpret_cast<unsigned long long>(a) & 15ull) == 0) && ((lda & 1) == 0);
+}
+
+// Factor one problem stored in global memory (any leading dimension).  Aligned problems
+// take 16-byte strips; otherwise the 4-row form reads single words and the 8-row form
+// 16-byte pieces from each strip's first boundary.
+template <int R, int U>
+__device__ __forceinline__ int potrf_lane_global(double* a, int lda, int n) {
+    if (strips_aligned(a, lda)) return potrf_lane<R, U>(GAccV{a, lda}, n);
+    if (R == 8) return potrf_lane<R, U>(BF_LANE8_MISALIGNED{a, lda}, n);
+    return potrf_lane<R, U>(GAccS{a, lda}, n);
 }
 
 }  // namespace bf

@@ -223,7 +223,7 @@ __device__ void lane_problem(const RaggedParams& p, int q) {
     const int n = p.n[q];
     double* S = p.S + p.offS[q];
     double* Bq = p.B + p.offB[q];
-    const int info = strips_aligned(S, n) ? potrf_lane(GAccV{S, n}, n) : potrf_lane(GAcc{S, n}, n);
+    const int info = potrf_lane_global<4, 2>(S, n, n);
     if (info == 0) {
         for (int c = 0; c < p.nrhs; c++) {
             double* b = Bq + (long long)c * n;

@@ -132,27 +132,40 @@ TrsmConfig choose_trsm(int side, int uplo, int trans, int unit, int m, int n, lo
 }
 
 PotrfConfig choose_potrf(int n, int lda, long long batch) {
-    (void)lda;
+    // Table code 0 holds even leading dimensions, code 1 odd ones (an odd lda leaves
+    // every other column's strips off the 16-byte boundary, which changes the best
+    // lane kernel).
+    const int code = lda & 1;
     PotrfConfig c;
     c.NB = 32;
-    c.T = 128;
+    c.T = 64;
+    // one problem per thread needs tens of thousands of problems to fill the GPU;
+    // below that, larger orders go to the blocked sequence
     if (n <= 8) {
         c.variant = VAR_PACKED;
-    } else if (n <= 64 || batch >= 40000) {
+    } else if (n <= 64 || batch >= 20000) {
         c.variant = VAR_DIRECT;
     } else {
         c.variant = VAR_BLOCKED;
     }
+    // lane kernels: 8-row blocks (fewer requests per multiply-add, more registers)
+    // once the k loops are long enough; sooner when strips are misaligned
+    c.rows = (code ? n >= 16 : n >= 24) ? 8 : 4;
+    c.unroll = 2;
     TuneEntry e;
-    if (lookup(BF_ROUTINE_DPOTRF, 0, n, &e)) {
+    if (lookup(BF_ROUTINE_DPOTRF, code, n, &e)) {
         c.variant = e.variant;
         if (e.p0 > 0) c.T = e.p0;
         if (e.p1 > 0) c.NB = e.p1;
+        if (e.p2 > 0) c.rows = e.p2;
+        if (e.p3 > 0) c.unroll = e.p3;
     }
     if (c.T < 32) c.T = 32;
     if (c.T > 256) c.T = 256;
     c.T = c.T / 32 * 32;
     if (c.NB < 4) c.NB = 4;
+    c.rows = c.rows == 8 ? 8 : 4;
+    c.unroll = c.unroll == 1 ? 1 : 2;
     if (c.variant == VAR_PACKED) {
         while (c.T > 32 && (size_t)c.T * n * n * sizeof(double) > kSmemBudget) c.T -= 32;
         if ((size_t)c.T * n * n * sizeof(double) > kSmemBudget) c.variant = VAR_DIRECT;
@@ -191,8 +204,8 @@ extern "C" int bf_tune_query(int routine, int code, int m, int n, int k, long lo
         return 0;
     }
     if (routine == BF_ROUTINE_DPOTRF) {
-        bf::PotrfConfig c = bf::choose_potrf(n, n, batch);
-        out[0] = c.variant; out[1] = c.T; out[2] = c.NB; out[3] = 0; out[4] = 0;
+        bf::PotrfConfig c = bf::choose_potrf(n, code == 1 ? n + 1 : n, batch);
+        out[0] = c.variant; out[1] = c.T; out[2] = c.NB; out[3] = c.rows; out[4] = c.unroll;
         return 0;
     }
     return -1;

@@ -149,6 +149,15 @@ def test_tune_table(lib):
         assert lib.tune_query(lib.ROUTINE_DGEMM, 1, 40, 40, 40, 1000)[1] == 40
         lib.tune_set(lib.ROUTINE_DPOTRF, 0, 1, 300, lib.VARIANT_BLOCKED, 128, 16)
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 100, 100, 0, 10)[:3] == [lib.VARIANT_BLOCKED, 128, 16]
+        # dpotrf codes are the leading-dimension parity: an odd-lda entry leaves even lda alone
+        lib.tune_set(lib.ROUTINE_DPOTRF, 1, 1, 300, lib.VARIANT_DIRECT, 64, 0, 8, 1)
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10) == [lib.VARIANT_DIRECT, 64, 32, 8, 1]
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 100, 100, 0, 10)[:3] == [lib.VARIANT_BLOCKED, 128, 16]
+        # defaults of the lane kernel: 8-row blocks for odd lda from n = 16, for even lda from n = 24
+        lib.tune_clear()
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 16, 16, 0, 10 ** 5)[3:] == [4, 2]
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 16, 16, 0, 10 ** 5)[3:] == [8, 2]
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 24, 24, 0, 10 ** 5)[3:] == [8, 2]
         with pytest.raises(lib.BFError):
             lib.tune_set(7, 0, 1, 2, 0)
     finally:

@@ -197,13 +197,16 @@ def spd_upper_nan(batch, n, ld, seed):
     return S
 
 
-POTRF_VARIANTS = [("direct", 0, 0, 0), ("packed", 1, 128, 0), ("blocked8", 2, 0, 8),
-                  ("blocked32", 2, 0, 32)]
+# (name, variant, T, NB, lane row-block height, lane k-loop unroll); forced for both
+# leading-dimension parities (table code -1)
+POTRF_VARIANTS = [("direct4u2", 0, 0, 0, 4, 2), ("direct4u1", 0, 64, 0, 4, 1), ("direct8u1", 0, 0, 0, 8, 1),
+                  ("direct8u2", 0, 256, 0, 8, 2), ("packed", 1, 128, 0, 0, 0), ("blocked8", 2, 0, 8, 0, 0),
+                  ("blocked32", 2, 0, 32, 0, 0)]
 
 
-@pytest.mark.parametrize("vname,variant,T,NB", POTRF_VARIANTS, ids=[v[0] for v in POTRF_VARIANTS])
+@pytest.mark.parametrize("vname,variant,T,NB,R,U", POTRF_VARIANTS, ids=[v[0] for v in POTRF_VARIANTS])
 @pytest.mark.parametrize("n", SMALL_N)
-def test_dpotrf(bf, oracle, vname, variant, T, NB, n):
+def test_dpotrf(bf, oracle, vname, variant, T, NB, R, U, n):
     if variant == 1 and n > 16:
         pytest.skip("packed lane Cholesky holds whole problems in shared memory (small n)")
     for pad in (0, 3):
@@ -212,7 +215,7 @@ def test_dpotrf(bf, oracle, vname, variant, T, NB, n):
         L, info = oracle.dpotrf_l(S)
         assert (info == 0).all()
         Sg = gpu(S)
-        with forced(bf, bf.ROUTINE_DPOTRF, 0, variant, T, NB):
+        with forced(bf, bf.ROUTINE_DPOTRF, -1, variant, T, NB, R, U):
             ig = bf.dpotrf(Sg, n=n)
         out = host(Sg)
         assert (host(ig) == 0).all()
@@ -222,9 +225,9 @@ def test_dpotrf(bf, oracle, vname, variant, T, NB, n):
         assert np.isnan(out[:, :, n:]).all()
 
 
-@pytest.mark.parametrize("vname,variant,T,NB", POTRF_VARIANTS, ids=[v[0] for v in POTRF_VARIANTS])
-def test_dpotrf_failures(bf, oracle, vname, variant, T, NB):
-    for n in (5, 12, 40, 100):
+@pytest.mark.parametrize("vname,variant,T,NB,R,U", POTRF_VARIANTS, ids=[v[0] for v in POTRF_VARIANTS])
+def test_dpotrf_failures(bf, oracle, vname, variant, T, NB, R, U):
+    for n in (5, 12, 40, 41, 100):
         if variant == 1 and n > 16:
             continue
         batch = 9
@@ -235,7 +238,7 @@ def test_dpotrf_failures(bf, oracle, vname, variant, T, NB):
         S[7, 0, 0] = 0.0
         L, info = oracle.dpotrf_l(S)
         Sg = gpu(S)
-        with forced(bf, bf.ROUTINE_DPOTRF, 0, variant, T, NB):
+        with forced(bf, bf.ROUTINE_DPOTRF, -1, variant, T, NB, R, U):
             ig = bf.dpotrf(Sg, n=n)
         gi = host(ig)
         np.testing.assert_array_equal(gi, info)
