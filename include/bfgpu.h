@@ -206,14 +206,14 @@ int bf_dpotrf_backward_strided_batched(char uplo, int n, const double* L, int ld
 /*   workspace      device memory of bf_ragged_workspace_bytes(batch) bytes, */
 /*                  owned by the caller, kept for the plan's lifetime        */
 /*   lane_max       orders <= lane_max are factored one problem per thread,  */
-/*                  larger ones one problem per CTA in shared memory         */
-/*   threads        CTA size: 128, 256 or 512                                */
+/*                  larger ones (at most 256) one problem per CTA            */
+/*   threads        CTA size: 64, 128, 256 or 512                            */
 /* Plan creation sorts the problems (largest first), copies the queue into   */
 /* the workspace on `stream` (synchronously) and instantiates the graph; the */
 /* device pointers and offsets are fixed in the plan.  bf_ragged_plan_launch */
-/* enqueues the graph on `stream`.  Orders above the shared-memory limit     */
-/* (lower triangle of the largest order + its right-hand sides > 227 KB)     */
-/* return BF_ERR_NOT_SUPPORTED.  bf_ragged_plan_info writes {BIG problems,   */
+/* enqueues the graph on `stream`.  A batch with an order above both        */
+/* lane_max and 256 returns BF_ERR_NOT_SUPPORTED (nothing is launched).      */
+/* bf_ragged_plan_info writes {BIG problems,                                 */
 /* queue items, CTAs, threads, shared bytes} into out[5].                    */
 /* ------------------------------------------------------------------------ */
 typedef struct bf_ragged_plan_st* bf_ragged_plan_t;

@@ -236,9 +236,11 @@ class RaggedPlan:
     The workspace and info tensors are owned by the plan object.
     """
 
-    def __init__(self, ns, S, offS, B, offB, nrhs, lane_max=48, threads=256, stream=None):
+    def __init__(self, ns, S, offS, B, offB, nrhs, lane_max=None, threads=None, stream=None):
         import numpy as np
         import torch
+        lane_max = _ragged_cfg["lane_max"] if lane_max is None else lane_max
+        threads = _ragged_cfg["threads"] if threads is None else threads
         self.ns = np.ascontiguousarray(ns, dtype=np.int32)
         self.offS = np.ascontiguousarray(offS, dtype=np.int64)
         self.offB = np.ascontiguousarray(offB, dtype=np.int64)
@@ -281,7 +283,7 @@ def tune_clear():
     bf_tune_clear()
 
 
-_RAGGED_DEFAULT = {"lane_max": 48, "threads": 256}
+_RAGGED_DEFAULT = {"lane_max": 32, "threads": 128}
 _ragged_cfg = dict(_RAGGED_DEFAULT)
 
 

@@ -127,7 +127,7 @@ def tune(quick=False, out=None, log=print):
         del L, X
         # ---- dpotrf, per leading-dimension parity (table code lda & 1)
         for code, ld in ((0, n + (n & 1)), (1, n + 1 - (n & 1))):
-            b = max(1, min(bfsynth.sweep_batch(n, ld, 1), BUDGET // (ld * n * 8)))
+            b = bfsynth.sweep_batch(n, ld, 1)  # the lane/blocked switch depends on the batch: tune at 2 GiB
             S0 = bfsynth.spd_batch(b, n, ld, 6, device=dev)
             S = S0.clone()
             best = None
@@ -156,7 +156,7 @@ def tune(quick=False, out=None, log=print):
             del S, S0
         torch.cuda.empty_cache()
     bf.tune_clear()
-    ragged = tune_ragged(torch, bf, dev, log, count=20000 if quick else 50000)
+    ragged = tune_ragged(torch, bf, dev, log, count=50000 if quick else 200000)
     doc = {"gpu": name, "ragged": ragged, "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
            "seconds": round(time.time() - t_start, 1), "entries": entries}
     path = out or table_path(name)
@@ -167,7 +167,7 @@ def tune(quick=False, out=None, log=print):
     return path
 
 
-def tune_ragged(torch, bf, dev, log, count=50000, nrhs=4):
+def tune_ragged(torch, bf, dev, log, count=200000, nrhs=4):
     """Threshold between the per-thread and per-CTA ragged forms, and the CTA size."""
     import numpy as np
 
@@ -176,8 +176,8 @@ def tune_ragged(torch, bf, dev, log, count=50000, nrhs=4):
     S0, offS, B0, offB = bfsynth.ragged_spd(ns_t, nrhs, 100, device=dev)
     S, B = S0.clone(), B0.clone()
     best = None
-    for lane_max in (16, 24, 32, 48, 64, 96):
-        for threads in (256, 512):
+    for lane_max in (16, 24, 32, 48, 64):
+        for threads in (64, 128, 256):
             plan = bf.RaggedPlan(ns_t.numpy(), S, offS.numpy(), B, offB.numpy(), nrhs, lane_max=lane_max,
                                  threads=threads)
             ts = []

@@ -4,13 +4,13 @@
 //
 // Work items come from a device queue (one atomic counter, no waiting between
 // CTAs), ordered by decreasing cost so the largest problems start first:
-//   BIG items  (n_b > lane_max): one problem per CTA.  The lower triangle is
-//     held packed in shared memory and factored right-looking with 16-column
-//     panels: the panel's diagonal block by one warp (pivots via rsqrt), the
-//     rows below it by all threads (one row's triangular solve each), the
-//     trailing update by all threads on 4x4 register tiles (section 3.2.1's
-//     dgemm loop + edge structure at CTA scale); three barriers per panel.
-//     Then a blocked forward/backward substitution.
+//   BIG items  (n_b > lane_max, n_b <= 256): one problem per CTA, left-looking by
+//     16-column panels: the panel is updated with the factored columns (read back from
+//     the matrix through L1/L2) on 4x4 register tiles, its diagonal block is factored by
+//     one warp (pivots via rsqrt), the rows below by all threads; the right-hand sides
+//     follow panel by panel (forward substitution), then a warp-per-right-hand-side
+//     backward substitution.  Only the panel lives in shared memory, so several
+//     problems share an SM and cover each other's serial phases.
 //   LANE items (n_b <= lane_max): blockDim problems per CTA, one per thread,
 //     sorted so a warp's problems have (nearly) equal order, using the same
 //     lane Cholesky as the uniform path.
@@ -40,179 +40,203 @@ struct RaggedParams {
     unsigned int* counter;
 };
 
-__device__ __forceinline__ int pcol(int j, int n) { return j * n - (j * (j - 1)) / 2; }  // packed column start
-
 // --------------------------------------------------------------------------- BIG: one problem per CTA
 #define BF_BIG_NB 16
+#define BF_BIG_NMAX 256  // backward substitution keeps x in 8 registers per lane
 
+// Four consecutive rows i..i+3 of column k of a problem in global memory (rows clamped to
+// n - 1): two 16-byte loads when the strip starts on a 16-byte boundary, one 16-byte load
+// between two single words when it starts 8 bytes past one.
+__device__ __forceinline__ void big_strip4(const double* S, int n, int i, int k, double* o) {
+    const double* p = S + i + (long long)k * n;
+    if (i + 4 <= n) {
+        if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
+            const double2 x = reinterpret_cast<const double2*>(p)[0], y = reinterpret_cast<const double2*>(p)[1];
+            o[0] = x.x; o[1] = x.y; o[2] = y.x; o[3] = y.y;
+        } else {
+            const double2 x = reinterpret_cast<const double2*>(p + 1)[0];
+            o[0] = p[0]; o[1] = x.x; o[2] = x.y; o[3] = p[3];
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 4; a++) o[a] = S[imin(i + a, n - 1) + (long long)k * n];
+    }
+}
+
+// Left-looking Cholesky by 16-column panels with the panel in shared memory and the
+// factored columns in global memory (read back through L1/L2), so a CTA holds about
+// 17 n doubles and several problems share an SM, each filling the FP64 pipes while
+// another is in a serial phase.  Per panel J (section 3.2.1's dgemm loop + edges, at
+// CTA scale):
+//   (1) W = A(J:n, J:J+nb) - L(J:n, 0:J) L(J:J+nb, 0:J)^T on 4x4 register tiles
+//       (lower tiles only), and the right-hand-side rows J..J+nb minus L(J:J+nb, 0:J) Y(0:J);
+//   (2) one warp factors W's diagonal block (pivots via rsqrt);
+//   (3) every thread: one row of the panel below, L(i,:) = W(i,:) L_JJ^{-T}, written to the
+//       matrix, and the diagonal block written back; the last nrhs threads solve
+//       Y(J:J+nb) = L_JJ^{-1} (rows J..J+nb) -- the forward substitution, panel by panel.
+// Then the backward substitution L^T X = Y, one warp per right-hand side.
 __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
     const int n = p.n[q];
+    const int r = p.nrhs;
     const int tid = threadIdx.x, T = blockDim.x, warp = tid >> 5, lane = tid & 31;
-    double* P = sm;                                   // packed lower triangle
-    double* X = sm + (size_t)n * (n + 1) / 2;         // n x nrhs right-hand sides
-    double* rinv = X + (size_t)n * p.nrhs;            // reciprocal pivots
+    double* W = sm;                            // panel: W[i + c n], i = row - J, c < 16
+    double* X = sm + (size_t)BF_BIG_NB * n;    // n x nrhs right-hand sides
+    double* rinv = X + (size_t)n * r;          // reciprocal pivots
     __shared__ int s_fail;
     double* S = p.S + p.offS[q];
     double* Bq = p.B + p.offB[q];
-    // flat, independent loads of the lower triangle (many in flight per thread)
-    const int nn = n * n;
-#pragma unroll 4
-    for (int e = tid; e < nn; e += T) {
-        const int j = e / n, i = e - j * n;
-        if (i >= j) P[pcol(j, n) + i - j] = S[e];
-    }
-    for (int e = tid; e < n * p.nrhs; e += T) X[e] = Bq[e];
+    for (int e = tid; e < n * r; e += T) X[e] = Bq[e];
     if (tid == 0) s_fail = 0;
     __syncthreads();
 
     for (int J = 0; J < n; J += BF_BIG_NB) {
-        const int nb = imin(BF_BIG_NB, n - J);
-        // (1) Cholesky of the nb x nb diagonal block, warp-synchronous in warp 0
+        const int nb = imin(BF_BIG_NB, n - J), m = n - J;
+        // (1) panel update: tile (I, K) covers rows J+4I.., columns J+4K..; consecutive
+        //     threads take consecutive row blocks of one column block (the L(J+4K.., k)
+        //     operand is then the same for the whole warp)
+        {
+            const int nI = (m + 3) / 4, nK = (nb + 3) / 4;
+            for (int t = tid; t < nI * nK; t += T) {
+                const int K = t / nI, I = t - K * nI;
+                if (I < K) continue;  // strictly above the diagonal block
+                const int i0 = J + 4 * I, k0 = J + 4 * K;
+                double acc[4][4];
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    double col[4];
+                    big_strip4(S, n, i0, imin(k0 + b, n - 1), col);  // upper entries unused
+#pragma unroll
+                    for (int a = 0; a < 4; a++) acc[a][b] = col[a];
+                }
+#pragma unroll 2
+                for (int k = 0; k < J; k++) {
+                    double li[4], lk[4];
+                    big_strip4(S, n, i0, k, li);
+#pragma unroll
+                    for (int b = 0; b < 4; b++) lk[b] = S[imin(k0 + b, n - 1) + (long long)k * n];
+#pragma unroll
+                    for (int a = 0; a < 4; a++)
+#pragma unroll
+                        for (int b = 0; b < 4; b++) acc[a][b] = fma(-li[a], lk[b], acc[a][b]);
+                }
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    const int c = 4 * K + b;
+                    if (c >= nb) continue;
+#pragma unroll
+                    for (int a = 0; a < 4; a++)
+                        if (4 * I + a < m) W[4 * I + a + c * n] = acc[a][b];
+                }
+            }
+            for (int e = T - 1 - tid; e < nb * r; e += T) {  // the last threads, fewest tiles
+                const int c = e % nb, rr = e / nb;
+                double s = X[J + c + (size_t)rr * n];
+                for (int k = 0; k < J; k++) s = fma(-S[J + c + (long long)k * n], X[k + (size_t)rr * n], s);
+                X[J + c + (size_t)rr * n] = s;
+            }
+        }
+        __syncthreads();
+        // (2) the diagonal block, warp-synchronous in warp 0
         if (warp == 0) {
             for (int c = 0; c < nb; c++) {
-                const int j = J + c;
-                const double d = P[pcol(j, n)];
+                const double d = W[c + c * n];
                 if (!(d > 0.0)) {  // the same value in every lane
-                    if (lane == 0) s_fail = j + 1;
+                    if (lane == 0) s_fail = J + c + 1;
                     break;
                 }
                 const double rs = rsqrt(d);
                 __syncwarp();
                 if (lane == 0) {
-                    P[pcol(j, n)] = d * rs;
-                    rinv[j] = rs;
+                    W[c + c * n] = d * rs;
+                    rinv[J + c] = rs;
                 }
-                if (lane < nb - c - 1) P[pcol(j, n) + 1 + lane] *= rs;
+                if (lane > c && lane < nb) W[lane + c * n] *= rs;
                 __syncwarp();
-                const int w = nb - c - 1;  // trailing block columns/rows right of c
+                const int w = nb - c - 1;
                 for (int e = lane; e < w * w; e += 32) {
-                    const int kk = e / w, rr = e - kk * w;
-                    if (rr >= kk) {
-                        const int i = j + 1 + rr, k = j + 1 + kk;
-                        P[pcol(k, n) + i - k] = fma(-P[pcol(j, n) + i - j], P[pcol(j, n) + k - j], P[pcol(k, n) + i - k]);
+                    const int kk = e / w, ii = e - kk * w;
+                    if (ii >= kk) {
+                        const int i = c + 1 + ii, k = c + 1 + kk;
+                        W[i + k * n] = fma(-W[i + c * n], W[k + c * n], W[i + k * n]);
                     }
                 }
                 __syncwarp();
             }
         }
         __syncthreads();
-        if (s_fail) break;
-        // (2) the panel rows below: L(i, J:J+nb) = A(i, J:J+nb) L_JJ^{-T}, one row per thread
-        for (int i = J + nb + tid; i < n; i += T) {
+        if (s_fail) break;  // written before the barrier: the same in every thread
+        // (3) rows below the diagonal block, the diagonal block itself, and Y of the block's rows
+        for (int i = nb + tid; i < m; i += T) {
             double x[BF_BIG_NB];
 #pragma unroll
-            for (int c = 0; c < BF_BIG_NB; c++) x[c] = (c < nb) ? P[pcol(J + c, n) + i - (J + c)] : 0.0;
+            for (int c = 0; c < BF_BIG_NB; c++) x[c] = (c < nb) ? W[i + c * n] : 0.0;
 #pragma unroll
             for (int c = 0; c < BF_BIG_NB; c++) {
                 if (c < nb) {
 #pragma unroll
-                    for (int c2 = 0; c2 < c; c2++) x[c] = fma(-x[c2], P[pcol(J + c2, n) + c - c2], x[c]);
+                    for (int c2 = 0; c2 < c; c2++) x[c] = fma(-x[c2], W[c + c2 * n], x[c]);
                     x[c] *= rinv[J + c];
-                    P[pcol(J + c, n) + i - (J + c)] = x[c];
+                    S[J + i + (long long)(J + c) * n] = x[c];
                 }
             }
         }
-        __syncthreads();
-        // (3) trailing update L22 -= L21 L21^T, rank nb, on lower 4x4 tiles
-        const int R = J + nb, m = n - R;
-        if (m > 0) {
-            const int tb = (m + 3) / 4;
-            const int ntile = tb * (tb + 1) / 2;
-            for (int t = tid; t < ntile; t += T) {
-                int I = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
-                while ((I + 1) * (I + 2) / 2 <= t) I++;
-                while (I * (I + 1) / 2 > t) I--;
-                const int K = t - I * (I + 1) / 2;
-                const int i0 = R + 4 * I, k0 = R + 4 * K;
-                double acc[4][4];
-#pragma unroll
-                for (int a = 0; a < 4; a++)
-#pragma unroll
-                    for (int b = 0; b < 4; b++) acc[a][b] = 0.0;
+        for (int e = tid; e < nb * nb; e += T) {
+            const int c = e / nb, i = e - c * nb;
+            if (i >= c) S[J + i + (long long)(J + c) * n] = W[i + c * n];
+        }
+        {
+            const int rr = T - 1 - tid;
+            if (rr < r) {
+                double* y = X + (size_t)rr * n;
                 for (int c = 0; c < nb; c++) {
-                    const int col = pcol(J + c, n) - (J + c);
-                    double li[4], lk[4];
-#pragma unroll
-                    for (int a = 0; a < 4; a++) li[a] = P[col + imin(i0 + a, n - 1)];
-#pragma unroll
-                    for (int b = 0; b < 4; b++) lk[b] = P[col + imin(k0 + b, n - 1)];
-#pragma unroll
-                    for (int a = 0; a < 4; a++)
-#pragma unroll
-                        for (int b = 0; b < 4; b++) acc[a][b] = fma(li[a], lk[b], acc[a][b]);
-                }
-#pragma unroll
-                for (int b = 0; b < 4; b++) {
-                    const int k = k0 + b;
-                    if (k >= n) continue;
-                    const int col = pcol(k, n) - k;
-#pragma unroll
-                    for (int a = 0; a < 4; a++) {
-                        const int i = i0 + a;
-                        if (i < n && i >= k) P[col + i] -= acc[a][b];
-                    }
+                    double s = y[J + c];
+                    for (int c2 = 0; c2 < c; c2++) s = fma(-W[c + c2 * n], y[J + c2], s);
+                    y[J + c] = s * rinv[J + c];
                 }
             }
         }
-        __syncthreads();
+        __syncthreads();  // the panel's columns of L (global) and Y (shared) are complete
     }
     const int fail = s_fail;
     if (fail == 0) {
-        // forward substitution L Y = B, 8-row blocks: the block triangle by warp 0, the rest by all
-        const int r = p.nrhs;
-        for (int J = 0; J < n; J += 8) {
-            const int nb = imin(8, n - J);
-            if (warp == 0) {
-                for (int c = 0; c < nb; c++) {
-                    const int j = J + c;
-                    for (int e = lane; e < r; e += 32) X[j + e * n] *= rinv[j];
-                    __syncwarp();
-                    for (int e = lane; e < (nb - c - 1) * r; e += 32) {
-                        const int i = j + 1 + e % (nb - c - 1), rr = e / (nb - c - 1);
-                        X[i + rr * n] = fma(-P[pcol(j, n) + i - j], X[j + rr * n], X[i + rr * n]);
+        // backward substitution L^T x = y, one warp per right-hand side: lane l holds x_i for
+        // i = l, l + 32, ...; x_j is broadcast from its lane, then every lane updates its
+        // x_i, i < j, with L(j, i); the next step's L(j - 1, i) is loaded a step ahead
+        constexpr int NS = BF_BIG_NMAX / 32;
+        for (int rr = warp; rr < r; rr += T >> 5) {
+            double* y = X + (size_t)rr * n;
+            double xr[NS], ln[NS];
+#pragma unroll
+            for (int s = 0; s < NS; s++) {
+                const int i = lane + 32 * s;
+                xr[s] = (i < n) ? y[i] : 0.0;
+                ln[s] = (i < n - 1) ? S[n - 1 + (long long)i * n] : 0.0;
+            }
+#pragma unroll
+            for (int s = NS - 1; s >= 0; s--) {
+                if (32 * s >= n) continue;
+                for (int lj = imin(31, n - 1 - 32 * s); lj >= 0; lj--) {
+                    const int j = 32 * s + lj;
+                    double lc[NS];
+#pragma unroll
+                    for (int s2 = 0; s2 <= s; s2++) {
+                        const int i = lane + 32 * s2;
+                        lc[s2] = ln[s2];
+                        ln[s2] = (i < j - 1) ? S[j - 1 + (long long)i * n] : 0.0;
                     }
-                    __syncwarp();
+                    const double xj = __shfl_sync(0xffffffffu, xr[s], lj) * rinv[j];
+                    if (lane == lj) xr[s] = xj;
+#pragma unroll
+                    for (int s2 = 0; s2 <= s; s2++) {
+                        const int i = lane + 32 * s2;
+                        if (i < j) xr[s2] = fma(-lc[s2], xj, xr[s2]);
+                    }
                 }
             }
-            __syncthreads();
-            const int m = n - J - nb;
-            for (int e = tid; e < m * r; e += T) {
-                const int i = J + nb + e % m, rr = e / m;
-                double s = X[i + rr * n];
-                for (int c = 0; c < nb; c++) s = fma(-P[pcol(J + c, n) + i - (J + c)], X[J + c + rr * n], s);
-                X[i + rr * n] = s;
-            }
-            __syncthreads();
+#pragma unroll
+            for (int s = 0; s < NS; s++)
+                if (lane + 32 * s < n) Bq[lane + 32 * s + (size_t)rr * n] = xr[s];
         }
-        // backward substitution L^T X = Y
-        for (int J = ((n - 1) / 8) * 8; J >= 0; J -= 8) {
-            const int nb = imin(8, n - J);
-            if (warp == 0) {
-                for (int c = nb - 1; c >= 0; c--) {
-                    const int j = J + c;
-                    for (int e = lane; e < r; e += 32) X[j + e * n] *= rinv[j];
-                    __syncwarp();
-                    for (int e = lane; e < c * r; e += 32) {
-                        const int i = J + e % c, rr = e / c;
-                        X[i + rr * n] = fma(-P[pcol(i, n) + j - i], X[j + rr * n], X[i + rr * n]);
-                    }
-                    __syncwarp();
-                }
-            }
-            __syncthreads();
-            for (int e = tid; e < J * r; e += T) {
-                const int i = e % J, rr = e / J;
-                double s = X[i + rr * n];
-                for (int c = 0; c < nb; c++) s = fma(-P[pcol(i, n) + J + c - i], X[J + c + rr * n], s);
-                X[i + rr * n] = s;
-            }
-            __syncthreads();
-        }
-        for (int e = tid; e < nn; e += T) {
-            const int j = e / n, i = e - j * n;
-            if (i >= j) S[e] = P[pcol(j, n) + i - j];
-        }
-        for (int e = tid; e < n * p.nrhs; e += T) Bq[e] = X[e];
     }
     if (tid == 0 && p.info) p.info[p.orig[q]] = fail;
     __syncthreads();
@@ -261,7 +285,8 @@ __global__ void __launch_bounds__(512) ragged_persistent_kernel(RaggedParams p) 
 }
 
 size_t ragged_smem_bytes(int nmax, int nrhs) {
-    return sizeof(double) * ((size_t)nmax * (nmax + 1) / 2 + (size_t)nmax * nrhs + nmax);
+    // BIG items: a 16-column panel, the right-hand sides and the reciprocal pivots
+    return sizeof(double) * ((size_t)BF_BIG_NB * nmax + (size_t)nmax * nrhs + nmax);
 }
 
 }  // namespace bf
@@ -295,7 +320,7 @@ extern "C" int bf_ragged_potrf_potrs_plan_create(int batch, const int* n_host, i
     if (workspace_bytes < bf_ragged_workspace_bytes(batch)) return -10;
     if (batch > 0 && !workspace) return -9;
     if (lane_max < 0) return -11;
-    if (threads != 128 && threads != 256 && threads != 512) return -12;
+    if (threads != 64 && threads != 128 && threads != 256 && threads != 512) return -12;
     if (!plan) return -14;
     int nmax = 0;
     for (int b = 0; b < batch; b++) {
@@ -303,7 +328,7 @@ extern "C" int bf_ragged_potrf_potrs_plan_create(int batch, const int* n_host, i
         nmax = std::max(nmax, n_host[b]);
     }
     const size_t smem = bf::ragged_smem_bytes(nmax > lane_max ? nmax : 0, nrhs);
-    if (smem > 227 * 1024) return BF_ERR_NOT_SUPPORTED;
+    if (smem > 227 * 1024 || (nmax > lane_max && nmax > BF_BIG_NMAX)) return BF_ERR_NOT_SUPPORTED;
     // queue order: BIG problems by decreasing order, then LANE problems by decreasing order
     std::vector<int> order(batch);
     std::iota(order.begin(), order.end(), 0);
@@ -462,7 +487,7 @@ extern "C" int bf_ragged_potrf_potrs_noalloc(int batch, const int* n_host, int n
     if (batch > 0 && nrhs > 0 && !B) return -6;
     if (batch > 0 && nrhs > 0 && !offB_host) return -7;
     if (lane_max < 0) return -9;
-    if (threads != 128 && threads != 256 && threads != 512) return -10;
+    if (threads != 64 && threads != 128 && threads != 256 && threads != 512) return -10;
     if (batch > BF_RAGGED_NOALLOC_MAX) return BF_ERR_NOALLOC_LIMIT;
     if (batch == 0) return BF_SUCCESS;
     int nmax = 0;
@@ -471,7 +496,7 @@ extern "C" int bf_ragged_potrf_potrs_noalloc(int batch, const int* n_host, int n
         nmax = std::max(nmax, n_host[b]);
     }
     const size_t smem = bf::ragged_smem_bytes(nmax > lane_max ? nmax : 0, nrhs);
-    if (smem > 227 * 1024) return BF_ERR_NOT_SUPPORTED;
+    if (smem > 227 * 1024 || (nmax > lane_max && nmax > BF_BIG_NMAX)) return BF_ERR_NOT_SUPPORTED;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return BF_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);

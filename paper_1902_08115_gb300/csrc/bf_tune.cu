@@ -160,6 +160,9 @@ PotrfConfig choose_potrf(int n, int lda, long long batch) {
         if (e.p2 > 0) c.rows = e.p2;
         if (e.p3 > 0) c.unroll = e.p3;
     }
+    // the table is measured on 2 GiB batches; a lane kernel on far fewer problems than
+    // that leaves most of the GPU idle, so small batches of larger orders stay blocked
+    if (c.variant != VAR_BLOCKED && n > 64 && batch < 20000) c.variant = VAR_BLOCKED;
     if (c.T < 32) c.T = 32;
     if (c.T > 256) c.T = 256;
     c.T = c.T / 32 * 32;

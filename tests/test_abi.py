@@ -151,7 +151,9 @@ def test_tune_table(lib):
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 100, 100, 0, 10)[:3] == [lib.VARIANT_BLOCKED, 128, 16]
         # dpotrf codes are the leading-dimension parity: an odd-lda entry leaves even lda alone
         lib.tune_set(lib.ROUTINE_DPOTRF, 1, 1, 300, lib.VARIANT_DIRECT, 64, 0, 8, 1)
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10) == [lib.VARIANT_DIRECT, 64, 32, 8, 1]
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10 ** 5) == [lib.VARIANT_DIRECT, 64, 32, 8, 1]
+        # a lane kernel needs tens of thousands of problems: small batches of larger orders stay blocked
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10)[0] == lib.VARIANT_BLOCKED
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 100, 100, 0, 10)[:3] == [lib.VARIANT_BLOCKED, 128, 16]
         # defaults of the lane kernel: 8-row blocks for odd lda from n = 16, for even lda from n = 24
         lib.tune_clear()

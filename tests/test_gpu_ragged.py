@@ -55,7 +55,7 @@ def check(ns, S, offS, B, offB, nrhs, Sg, Bg, info_g, oracle, bad=()):
     assert worst_l <= TOL and worst_x <= TOL, (worst_l, worst_x)
 
 
-@pytest.mark.parametrize("lane_max,threads", [(48, 256), (0, 256), (200, 128), (24, 512), (64, 128)])
+@pytest.mark.parametrize("lane_max,threads", [(48, 256), (0, 256), (200, 128), (24, 512), (64, 128), (32, 64)])
 def test_ragged_matches_oracle(bf, oracle, lane_max, threads):
     nrhs = 4
     bad = (3, 17, 1000)
@@ -77,8 +77,8 @@ def test_ragged_matches_oracle(bf, oracle, lane_max, threads):
 
 
 def test_ragged_edge_cases(bf, oracle):
-    # orders 1..3 and a single large problem; nrhs = 1
-    ns = np.array([1, 2, 3, 1, 150], dtype=np.int32)
+    # orders 1..3, a large problem, and the largest order of the per-CTA form (256); nrhs = 1
+    ns = np.array([1, 2, 3, 1, 150, 256], dtype=np.int32)
     S, offS, B, offB = bfsynth.ragged_spd(torch.as_tensor(ns), 1, 5)
     S, offS, B, offB = S.numpy(), offS.numpy(), B.numpy(), offB.numpy()
     Sg, Bg = torch.as_tensor(S).cuda(), torch.as_tensor(B).cuda()
@@ -98,6 +98,7 @@ def test_ragged_arguments(bf):
     assert f(-1, nsp, 1, 1, op, 1, op, None, 1, 10 ** 6, 8, 256, None, ctypes.byref(out)) == -1
     assert f(2, nsp, 1, 1, op, 1, op, None, 1, 8, 8, 256, None, ctypes.byref(out)) == -10
     assert f(2, nsp, 1, 1, op, 1, op, None, 1, 10 ** 6, 8, 100, None, ctypes.byref(out)) == -12
-    big = np.array([400], dtype=np.int32)
-    assert f(1, big.ctypes.data_as(ctypes.c_void_p), 1, 1, op, 1, op, None, 1, 10 ** 6, 8, 256, None,
-             ctypes.byref(out)) == bf.ERR_NOT_SUPPORTED
+    for nbig in (257, 400):  # above the per-CTA form's largest order and above lane_max
+        big = np.array([nbig], dtype=np.int32)
+        assert f(1, big.ctypes.data_as(ctypes.c_void_p), 1, 1, op, 1, op, None, 1, 10 ** 6, 8, 256, None,
+                 ctypes.byref(out)) == bf.ERR_NOT_SUPPORTED
