@@ -63,6 +63,17 @@ __device__ __forceinline__ void big_strip4(const double* S, int n, int i, int k,
     }
 }
 
+// Tile t of a panel's lower tiles, column block by column block: column block K holds the
+// row blocks I = K .. nI-1 (consecutive t: consecutive row blocks of one column block).
+__device__ __forceinline__ void big_tile_index(int t, int nI, int& K, int& I) {
+    K = 0;
+    while (t >= nI - K) {
+        t -= nI - K;
+        K++;
+    }
+    I = K + t;
+}
+
 // Left-looking Cholesky by 16-column panels with the panel in shared memory and the
 // factored columns in global memory (read back through L1/L2), so a CTA holds about
 // 17 n doubles and several problems share an SM, each filling the FP64 pipes while
@@ -93,23 +104,38 @@ __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
         const int nb = imin(BF_BIG_NB, n - J), m = n - J;
         // (1) panel update: tile (I, K) covers rows J+4I.., columns J+4K..; consecutive
         //     threads take consecutive row blocks of one column block (the L(J+4K.., k)
-        //     operand is then the same for the whole warp)
+        //     operand is then the same for the whole warp).  When the tiles fill less than
+        //     half the CTA (the late panels: few rows, long k loops), the k range is split
+        //     sp ways and the partial sums are added in a fixed order, so the idle lanes of
+        //     a mostly empty warp turn into work and the result is reproducible.
         {
             const int nI = (m + 3) / 4, nK = (nb + 3) / 4;
-            for (int t = tid; t < nI * nK; t += T) {
-                const int K = t / nI, I = t - K * nI;
-                if (I < K) continue;  // strictly above the diagonal block
+            const int tiles = nI * nK - nK * (nK - 1) / 2;  // tiles on or below the diagonal block
+            const int sp = imax(1, imin(T / tiles, J / 8));
+            double* part = rinv + n;  // [sp][16][tiles] partial sums, only when sp > 1
+            for (int u = tid; u < tiles * sp; u += T) {
+                const int z = u / tiles, t = u - z * tiles;
+                int K, I;
+                big_tile_index(t, nI, K, I);
                 const int i0 = J + 4 * I, k0 = J + 4 * K;
+                const int klo = (J * z) / sp, khi = (J * (z + 1)) / sp;
                 double acc[4][4];
+                if (z == 0) {
 #pragma unroll
-                for (int b = 0; b < 4; b++) {
-                    double col[4];
-                    big_strip4(S, n, i0, imin(k0 + b, n - 1), col);  // upper entries unused
+                    for (int b = 0; b < 4; b++) {
+                        double col[4];
+                        big_strip4(S, n, i0, imin(k0 + b, n - 1), col);  // upper entries unused
 #pragma unroll
-                    for (int a = 0; a < 4; a++) acc[a][b] = col[a];
+                        for (int a = 0; a < 4; a++) acc[a][b] = col[a];
+                    }
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 4; a++)
+#pragma unroll
+                        for (int b = 0; b < 4; b++) acc[a][b] = 0.0;
                 }
 #pragma unroll 2
-                for (int k = 0; k < J; k++) {
+                for (int k = klo; k < khi; k++) {
                     double li[4], lk[4];
                     big_strip4(S, n, i0, k, li);
 #pragma unroll
@@ -119,13 +145,20 @@ __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
 #pragma unroll
                         for (int b = 0; b < 4; b++) acc[a][b] = fma(-li[a], lk[b], acc[a][b]);
                 }
+                if (sp == 1) {
 #pragma unroll
-                for (int b = 0; b < 4; b++) {
-                    const int c = 4 * K + b;
-                    if (c >= nb) continue;
+                    for (int b = 0; b < 4; b++) {
+                        const int c = 4 * K + b;
+                        if (c >= nb) continue;
+#pragma unroll
+                        for (int a = 0; a < 4; a++)
+                            if (4 * I + a < m) W[4 * I + a + c * n] = acc[a][b];
+                    }
+                } else {
 #pragma unroll
                     for (int a = 0; a < 4; a++)
-                        if (4 * I + a < m) W[4 * I + a + c * n] = acc[a][b];
+#pragma unroll
+                        for (int b = 0; b < 4; b++) part[(z * 16 + a * 4 + b) * tiles + t] = acc[a][b];
                 }
             }
             for (int e = T - 1 - tid; e < nb * r; e += T) {  // the last threads, fewest tiles
@@ -133,6 +166,19 @@ __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
                 double s = X[J + c + (size_t)rr * n];
                 for (int k = 0; k < J; k++) s = fma(-S[J + c + (long long)k * n], X[k + (size_t)rr * n], s);
                 X[J + c + (size_t)rr * n] = s;
+            }
+            if (sp > 1) {
+                __syncthreads();
+                for (int e = tid; e < 16 * tiles; e += T) {
+                    const int ab = e / tiles, t = e - ab * tiles;
+                    int K, I;
+                    big_tile_index(t, nI, K, I);
+                    const int c = 4 * K + (ab & 3), i = 4 * I + (ab >> 2);
+                    if (c >= nb || i >= m) continue;
+                    double v = part[ab * tiles + t];
+                    for (int z = 1; z < sp; z++) v += part[(z * 16 + ab) * tiles + t];
+                    W[i + c * n] = v;
+                }
             }
         }
         __syncthreads();
@@ -284,9 +330,11 @@ __global__ void __launch_bounds__(512) ragged_persistent_kernel(RaggedParams p) 
     }
 }
 
-size_t ragged_smem_bytes(int nmax, int nrhs) {
-    // BIG items: a 16-column panel, the right-hand sides and the reciprocal pivots
-    return sizeof(double) * ((size_t)BF_BIG_NB * nmax + (size_t)nmax * nrhs + nmax);
+size_t ragged_smem_bytes(int nmax, int nrhs, int threads) {
+    // BIG items: a 16-column panel, the right-hand sides, the reciprocal pivots and the
+    // split-k partial sums (at most 16 per thread)
+    if (nmax == 0) return 0;
+    return sizeof(double) * ((size_t)BF_BIG_NB * nmax + (size_t)nmax * nrhs + nmax + 16 * (size_t)threads);
 }
 
 }  // namespace bf
@@ -327,7 +375,7 @@ extern "C" int bf_ragged_potrf_potrs_plan_create(int batch, const int* n_host, i
         if (n_host[b] < 0) return -2;
         nmax = std::max(nmax, n_host[b]);
     }
-    const size_t smem = bf::ragged_smem_bytes(nmax > lane_max ? nmax : 0, nrhs);
+    const size_t smem = bf::ragged_smem_bytes(nmax > lane_max ? nmax : 0, nrhs, threads);
     if (smem > 227 * 1024 || (nmax > lane_max && nmax > BF_BIG_NMAX)) return BF_ERR_NOT_SUPPORTED;
     // queue order: BIG problems by decreasing order, then LANE problems by decreasing order
     std::vector<int> order(batch);
@@ -495,7 +543,7 @@ extern "C" int bf_ragged_potrf_potrs_noalloc(int batch, const int* n_host, int n
         if (n_host[b] < 0) return -2;
         nmax = std::max(nmax, n_host[b]);
     }
-    const size_t smem = bf::ragged_smem_bytes(nmax > lane_max ? nmax : 0, nrhs);
+    const size_t smem = bf::ragged_smem_bytes(nmax > lane_max ? nmax : 0, nrhs, threads);
     if (smem > 227 * 1024 || (nmax > lane_max && nmax > BF_BIG_NMAX)) return BF_ERR_NOT_SUPPORTED;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return BF_ERR_CUDA;

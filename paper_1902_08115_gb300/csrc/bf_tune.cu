@@ -141,9 +141,7 @@ PotrfConfig choose_potrf(int n, int lda, long long batch) {
     c.T = 64;
     // one problem per thread needs tens of thousands of problems to fill the GPU;
     // below that, larger orders go to the blocked sequence
-    if (n <= 8) {
-        c.variant = VAR_PACKED;
-    } else if (n <= 64 || batch >= 20000) {
+    if (n <= 64 || batch >= 20000) {
         c.variant = VAR_DIRECT;
     } else {
         c.variant = VAR_BLOCKED;
