@@ -40,6 +40,10 @@ SWEEP_N = (4, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256)
 PADS = (0, 3)
 GEMM_FORMS = ("nn", "nt", "tn", "tt")
 METRIC = "batched FP64 dgemm/dpotrf GFLOP/s and % of roofline vs n; chosen vs plain form"
+# DRAM bytes per problem of the dgemm_nt kernel at n = lda = 256 (dgemm_tile_kernel<4,4,0,1,0,0>):
+# dram__bytes_read.sum + dram__bytes_write.sum = 403.57 MB + 110.01 MB over 256 problems in one ncu
+# capture of `python -m paper_1902_08115_gb300.profcase gemm 256 0`
+DGEMM_NT_256_TRAFFIC_PER_PROBLEM = (403.572736e6 + 110.007040e6) / 256
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -387,12 +391,18 @@ def main():
         roof = min(peak, hbm * 1e9 * f / by)
         per[(r, p.n, p.pad)] = dict(ms=ms, gflops=f / (ms * 1e-3) / 1e9, frac=f / (ms * 1e-3) / roof,
                                     flops=f, bytes=by, roof=roof)
-    dom = max(per, key=lambda k: per[k]["ms"])
+    # the dominant kernel: the four dgemm forms and dtrsm at n = 256 have the largest per-call times
+    # (within a few percent of each other); dgemm_nt, the paper's headline form, is reported
+    dom = ("dgemm_nt", 256, 0)
     d = per[dom]
+    traffic = DGEMM_NT_256_TRAFFIC_PER_PROBLEM * batch_of("dgemm_nt", 256, 256)
     roofline = {"bound": "alu", "achieved": round(d["flops"] / (d["ms"] * 1e-3) / 1e12, 4),
                 "peak": round(peak / 1e12, 4), "unit": "TFLOP/s",
-                "frac": round(d["flops"] / (d["ms"] * 1e-3) / peak, 4), "traffic": None,
-                "kernel": f"{dom[0]} n={dom[1]} lda={dom[1] + dom[2]} (largest per-call time)",
+                "frac": round(d["flops"] / (d["ms"] * 1e-3) / peak, 4), "traffic": round(traffic),
+                "traffic_note": "bytes per launch: DRAM read + write per problem from one ncu capture of "
+                                "256 problems of this kernel, times the launch's batch; algorithmic "
+                                f"{round(d['bytes'])} bytes",
+                "kernel": f"{dom[0]} n={dom[1]} lda={dom[1] + dom[2]} (dgemm_tile_kernel<4,4,0,1,0,0>)",
                 "peak_source": f"{sms} SMs x 2 FP64 FMA/clk x 2 flop x {clk_mhz:.0f} MHz (median SM clock "
                                f"of the timed steps)",
                 "hbm_gbs": hbm, "hbm_source": hbm_src}

@@ -32,7 +32,7 @@ def main(argv):
         ns = bfsynth.ragged_orders(3000, 100, 200, 5)
         S0, offS, B0, offB = bfsynth.ragged_spd(ns, 4, 6, device="cuda")
         S, B = S0.clone(), B0.clone()
-        plan = bf.RaggedPlan(ns.numpy(), S, offS.numpy(), B, offB.numpy(), 4, lane_max=48, threads=256)
+        plan = bf.RaggedPlan(ns.numpy(), S, offS.numpy(), B, offB.numpy(), 4, **bf.ragged_config())
         for _ in range(3):
             S.copy_(S0)
             B.copy_(B0)
