@@ -83,7 +83,7 @@ __device__ __forceinline__ void big_tile_index(int t, int nI, int& K, int& I) {
 //       (lower tiles only), and the right-hand-side rows J..J+nb minus L(J:J+nb, 0:J) Y(0:J);
 //   (2) one warp factors W's diagonal block (pivots via rsqrt);
 //   (3) every thread: one row of the panel below, L(i,:) = W(i,:) L_JJ^{-T}, written to the
-//       matrix, and the diagonal block written back; the last nrhs threads solve
+//       matrix, and the diagonal block written back; the last warp solves
 //       Y(J:J+nb) = L_JJ^{-1} (rows J..J+nb) -- the forward substitution, panel by panel.
 // Then the backward substitution L^T X = Y, one warp per right-hand side.
 __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
@@ -104,21 +104,28 @@ __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
         const int nb = imin(BF_BIG_NB, n - J), m = n - J;
         // (1) panel update: tile (I, K) covers rows J+4I.., columns J+4K..; consecutive
         //     threads take consecutive row blocks of one column block (the L(J+4K.., k)
-        //     operand is then the same for the whole warp).  When the tiles fill less than
-        //     half the CTA (the late panels: few rows, long k loops), the k range is split
-        //     sp ways and the partial sums are added in a fixed order, so the idle lanes of
-        //     a mostly empty warp turn into work and the result is reproducible.
+        //     operand is then the same for the whole warp).  The tiles go out in rounds of
+        //     T; the rem tiles of the last, partial round (all of them in the late panels:
+        //     few rows, long k loops) have their k range split sp ways, so the idle lanes of
+        //     a mostly empty round turn into work; the partial sums are added in a fixed
+        //     order, so the result is reproducible.
         {
             const int nI = (m + 3) / 4, nK = (nb + 3) / 4;
             const int tiles = nI * nK - nK * (nK - 1) / 2;  // tiles on or below the diagonal block
-            const int sp = imax(1, imin(T / tiles, J / 8));
-            double* part = rinv + n;  // [sp][16][tiles] partial sums, only when sp > 1
-            for (int u = tid; u < tiles * sp; u += T) {
-                const int z = u / tiles, t = u - z * tiles;
+            const int full = tiles / T * T, rem = tiles - full;
+            const int sp = rem ? imax(1, imin(T / rem, J / 8)) : 1;
+            double* part = rinv + n;  // [sp][16][rem] partial sums, only when sp > 1
+            for (int u = tid; u < full + rem * sp; u += T) {
+                int t = u, z = 0;
+                if (u >= full) {
+                    z = (u - full) / rem;
+                    t = u - z * rem;
+                }
+                const bool split = u >= full && sp > 1;
                 int K, I;
                 big_tile_index(t, nI, K, I);
                 const int i0 = J + 4 * I, k0 = J + 4 * K;
-                const int klo = (J * z) / sp, khi = (J * (z + 1)) / sp;
+                const int klo = split ? (J * z) / sp : 0, khi = split ? (J * (z + 1)) / sp : J;
                 double acc[4][4];
                 if (z == 0) {
 #pragma unroll
@@ -145,7 +152,7 @@ __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
 #pragma unroll
                         for (int b = 0; b < 4; b++) acc[a][b] = fma(-li[a], lk[b], acc[a][b]);
                 }
-                if (sp == 1) {
+                if (!split) {
 #pragma unroll
                     for (int b = 0; b < 4; b++) {
                         const int c = 4 * K + b;
@@ -158,7 +165,7 @@ __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
 #pragma unroll
                     for (int a = 0; a < 4; a++)
 #pragma unroll
-                        for (int b = 0; b < 4; b++) part[(z * 16 + a * 4 + b) * tiles + t] = acc[a][b];
+                        for (int b = 0; b < 4; b++) part[(z * 16 + a * 4 + b) * rem + (t - full)] = acc[a][b];
                 }
             }
             for (int e = T - 1 - tid; e < nb * r; e += T) {  // the last threads, fewest tiles
@@ -169,14 +176,14 @@ __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
             }
             if (sp > 1) {
                 __syncthreads();
-                for (int e = tid; e < 16 * tiles; e += T) {
-                    const int ab = e / tiles, t = e - ab * tiles;
+                for (int e = tid; e < 16 * rem; e += T) {
+                    const int ab = e / rem, tt = e - ab * rem;
                     int K, I;
-                    big_tile_index(t, nI, K, I);
+                    big_tile_index(full + tt, nI, K, I);
                     const int c = 4 * K + (ab & 3), i = 4 * I + (ab >> 2);
                     if (c >= nb || i >= m) continue;
-                    double v = part[ab * tiles + t];
-                    for (int z = 1; z < sp; z++) v += part[(z * 16 + ab) * tiles + t];
+                    double v = part[ab * rem + tt];
+                    for (int z = 1; z < sp; z++) v += part[(z * 16 + ab) * rem + tt];
                     W[i + c * n] = v;
                 }
             }
@@ -230,15 +237,18 @@ __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
             const int c = e / nb, i = e - c * nb;
             if (i >= c) S[J + i + (long long)(J + c) * n] = W[i + c * n];
         }
-        {
-            const int rr = T - 1 - tid;
-            if (rr < r) {
-                double* y = X + (size_t)rr * n;
-                for (int c = 0; c < nb; c++) {
-                    double s = y[J + c];
-                    for (int c2 = 0; c2 < c; c2++) s = fma(-W[c + c2 * n], y[J + c2], s);
-                    y[J + c] = s * rinv[J + c];
+        if (warp == (T >> 5) - 1) {
+            // Y(J:J+nb, :) = L_JJ^{-1} (rows J..J+nb), column-oriented by the last warp: step c
+            // scales row J+c of every right-hand side, then its lanes update the rows below
+            for (int c = 0; c < nb; c++) {
+                for (int e = lane; e < r; e += 32) X[J + c + (size_t)e * n] *= rinv[J + c];
+                __syncwarp();
+                const int w = nb - c - 1;
+                for (int e = lane; e < w * r; e += 32) {
+                    const int i = c + 1 + e % w, rr = e / w;
+                    X[J + i + (size_t)rr * n] = fma(-W[i + c * n], X[J + c + (size_t)rr * n], X[J + i + (size_t)rr * n]);
                 }
+                __syncwarp();
             }
         }
         __syncthreads();  // the panel's columns of L (global) and Y (shared) are complete
