@@ -24,6 +24,12 @@ Functions and the passage each follows:
 ``dsposv``                 binary32 factor + binary64 iterative refinement
 ``dpotrf_l_adjoint``       reverse mode of the unblocked Cholesky loop
 ``spd_solve_loss_grad``    closed-form gradient of sum(A^{-1}B .* W)
+``dsyrk``                  section 3.1 "dsyrk", C <= alpha op(A) op(A)^T + beta C
+``dsyrk_dpotrf_l``         dsyrk then dpotrf: chol(C + A A^T) (section 5)
+``dtrmm``                  section 3.1 "dtrmm", all side/uplo/trans/diag cases
+``dpotrf_u``               upper Cholesky A = U^T U (appendix routine table)
+``dgetrf`` / ``dgetrs``    section 3.1 "dgetrf", LU with partial pivoting + solve
+``riccati``                section 5 "Riccati recursion", square-root form
 =========================  ===================================================
 """
 from __future__ import annotations
@@ -89,6 +95,15 @@ def _load():
             "bfo_dpotrf_l_adjoint": ([_i, _dp, _i, _dp, _i, _dp, _i], None),
             "bfo_spd_solve_loss_grad_sb": ([_i, _i, _i, _i, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
                                             _dp, _dp, _dp, _ip], None),
+            "bfo_dsyrk": ([_c, _c, _i, _i, _d, _dp, _i, _d, _dp, _i], _i),
+            "bfo_dsyrk_sb": ([_c, _c, _i, _i, _d, _dp, _i, _ll, _d, _dp, _i, _ll, _i], None),
+            "bfo_dsyrk_dpotrf_l_sb": ([_i, _i, _dp, _i, _ll, _dp, _i, _ll, _i, _ip], None),
+            "bfo_dtrmm": ([_c, _c, _c, _c, _i, _i, _d, _dp, _i, _dp, _i], _i),
+            "bfo_dtrmm_sb": ([_c, _c, _c, _c, _i, _i, _d, _dp, _i, _ll, _dp, _i, _ll, _i], None),
+            "bfo_dpotrf_u_sb": ([_i, _dp, _i, _ll, _i, _ip], None),
+            "bfo_dgetrf_sb": ([_i, _i, _dp, _i, _ll, _ip, _i, _ip], None),
+            "bfo_dgetrs_sb": ([_c, _i, _i, _dp, _i, _ll, _ip, _dp, _i, _ll, _i], None),
+            "bfo_riccati_sb": ([_i, _i, _i, _dp, _dp, _dp, _dp, _i, _ip], None),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -245,3 +260,90 @@ def spd_solve_loss_grad(Qd: np.ndarray, J: np.ndarray, B: np.ndarray, W: np.ndar
                                        _p(loss), _p(Jbar), _p(Qbar), _p(Bbar), _p(Wbar),
                                        info.ctypes.data_as(_ip))
     return dict(X=X, loss=loss, Jbar=Jbar, Qbar=Qbar, Bbar=Bbar, Wbar=Wbar, info=info)
+
+
+def dsyrk(uplo: str, trans: str, n: int, k: int, alpha: float, A: np.ndarray, beta: float,
+          C: np.ndarray) -> np.ndarray:
+    """Batched C <= alpha op(A) op(A)^T + beta C on the uplo triangle (section 3.1 "dsyrk")."""
+    A, C = _f64(_batch3(A)), _f64(_batch3(C))
+    out = C.copy()
+    _load().bfo_dsyrk_sb(_ch(uplo), _ch(trans), n, k, alpha, _p(A), A.shape[2], A[0].size, beta,
+                         _p(out), out.shape[2], out[0].size, out.shape[0])
+    return out
+
+
+def dsyrk_dpotrf_l(n: int, k: int, A: np.ndarray, C: np.ndarray):
+    """Batched chol(C + A A^T), lower (dsyrk_ln then dpotrf_l); returns (factor, info)."""
+    A, C = _f64(_batch3(A)), _f64(_batch3(C))
+    out = C.copy()
+    info = np.zeros(out.shape[0], dtype=np.int32)
+    _load().bfo_dsyrk_dpotrf_l_sb(n, k, _p(A), A.shape[2], A[0].size, _p(out), out.shape[2], out[0].size,
+                                  out.shape[0], info.ctypes.data_as(_ip))
+    return out, info
+
+
+def dtrmm(side: str, uplo: str, ta: str, diag: str, m: int, n: int, alpha: float, A: np.ndarray,
+          B: np.ndarray) -> np.ndarray:
+    """Batched triangular multiply (section 3.1 "dtrmm"); returns the new B."""
+    A, B = _f64(_batch3(A)), _f64(_batch3(B))
+    out = B.copy()
+    _load().bfo_dtrmm_sb(_ch(side), _ch(uplo), _ch(ta), _ch(diag), m, n, alpha, _p(A), A.shape[2],
+                         A[0].size, _p(out), out.shape[2], out[0].size, out.shape[0])
+    return out
+
+
+def dpotrf_u(A: np.ndarray, n: int | None = None):
+    """Batched upper Cholesky A = U^T U; returns (factor, info)."""
+    A = _f64(_batch3(A))
+    out = A.copy()
+    batch, ncols, lda = out.shape
+    n = ncols if n is None else n
+    info = np.zeros(batch, dtype=np.int32)
+    _load().bfo_dpotrf_u_sb(n, _p(out), lda, out[0].size, batch, info.ctypes.data_as(_ip))
+    return out, info
+
+
+def dgetrf(A: np.ndarray, m: int | None = None, n: int | None = None):
+    """Batched LU with partial pivoting (section 3.1 "dgetrf"); returns (LU, ipiv, info).
+
+    ipiv is (batch, min(m, n)) int32, 1-based as in LAPACK.
+    """
+    A = _f64(_batch3(A))
+    out = A.copy()
+    batch, ncols, lda = out.shape
+    m = lda if m is None else m
+    n = ncols if n is None else n
+    ipiv = np.zeros((batch, min(m, n)), dtype=np.int32)
+    info = np.zeros(batch, dtype=np.int32)
+    _load().bfo_dgetrf_sb(m, n, _p(out), lda, out[0].size, ipiv.ctypes.data_as(_ip), batch,
+                          info.ctypes.data_as(_ip))
+    return out, ipiv, info
+
+
+def dgetrs(trans: str, LU: np.ndarray, ipiv: np.ndarray, B: np.ndarray, n: int, nrhs: int) -> np.ndarray:
+    """Batched solve op(A) X = B with dgetrf's factors; returns X."""
+    LU, B = _f64(_batch3(LU)), _f64(_batch3(B))
+    ipiv = np.ascontiguousarray(ipiv, dtype=np.int32).reshape(LU.shape[0], -1)
+    out = B.copy()
+    _load().bfo_dgetrs_sb(_ch(trans), n, nrhs, _p(LU), LU.shape[2], LU[0].size, ipiv.ctypes.data_as(_ip),
+                          _p(out), out.shape[2], out[0].size, out.shape[0])
+    return out
+
+
+def riccati(BAt: np.ndarray, RSQ: np.ndarray, QN: np.ndarray, nx: int, nu: int):
+    """Square-root Riccati recursion (section 5), batched.
+
+    BAt (batch, N, nx, nu+nx): [B^T; A^T] per stage, column-major (nx columns);
+    RSQ (batch, N, nu+nx, nu+nx): [R S; S^T Q] per stage; QN (batch, nx, nx).
+    Returns (F, info): F (batch, N+1, nu+nx, nu+nx) holds every stage's Cholesky factor
+    (lower triangle; stage N: chol(Q_N) in its top-left nx x nx block).
+    """
+    BAt = np.ascontiguousarray(BAt, dtype=np.float64)
+    RSQ = np.ascontiguousarray(RSQ, dtype=np.float64)
+    QN = np.ascontiguousarray(QN, dtype=np.float64)
+    batch, N = BAt.shape[0], BAt.shape[1]
+    m = nx + nu
+    F = np.zeros((batch, N + 1, m, m), dtype=np.float64)
+    info = np.zeros(batch, dtype=np.int32)
+    _load().bfo_riccati_sb(N, nx, nu, _p(BAt), _p(RSQ), _p(QN), _p(F), batch, info.ctypes.data_as(_ip))
+    return F, info

@@ -462,3 +462,318 @@ void bfo_spd_solve_loss_grad_sb(int n, int q, int r, int batch, const double* Qd
                                           Qbar + (size_t)p * n, Bbar + p * nr, Wbar + p * nr);
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* dsyrk -- section 3.1 ("dsyrk": dgemm whose A and B coincide):            */
+/*   C <= alpha * op(A) * op(A)^T + beta * C,  C n x n symmetric,            */
+/* op(A) = A (n x k) for trans 'N', A^T (A stored k x n) for 'T'.  Only the  */
+/* uplo triangle of C is read and written.  BLAS semantics: beta == 0       */
+/* writes without reading C; alpha == 0 does not read A.                     */
+/* ------------------------------------------------------------------------ */
+static double opa(const double* A, int lda, int tr, int i, int p) {
+    return tr ? A[IDX(p, i, lda)] : A[IDX(i, p, lda)];
+}
+
+int bfo_dsyrk(char uplo, char trans, int n, int k, double alpha, const double* A, int lda,
+              double beta, double* C, int ldc) {
+    if (!(is_l(uplo) || is_u(uplo))) return -1;
+    if (!(is_n(trans) || is_t(trans))) return -2;
+    if (n < 0) return -3;
+    if (k < 0) return -4;
+    const int tr = is_t(trans);
+    if (lda < ((tr ? k : n) > 1 ? (tr ? k : n) : 1)) return -7;
+    if (ldc < (n > 1 ? n : 1)) return -10;
+    if (n == 0 || ((alpha == 0.0 || k == 0) && beta == 1.0)) return 0;
+    const int low = is_l(uplo);
+    for (int j = 0; j < n; j++) {
+        const int i0 = low ? j : 0, i1 = low ? n : j + 1;
+        for (int i = i0; i < i1; i++) {
+            double s = 0.0;
+            if (alpha != 0.0)
+                for (int p = 0; p < k; p++) s += opa(A, lda, tr, i, p) * opa(A, lda, tr, j, p);
+            C[IDX(i, j, ldc)] = (beta == 0.0) ? alpha * s : alpha * s + beta * C[IDX(i, j, ldc)];
+        }
+    }
+    return 0;
+}
+
+void bfo_dsyrk_sb(char uplo, char trans, int n, int k, double alpha, const double* A, int lda,
+                  long long sA, double beta, double* C, int ldc, long long sC, int batch) {
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int b = 0; b < batch; b++)
+        bfo_dsyrk(uplo, trans, n, k, alpha, A + (size_t)b * sA, lda, beta, C + (size_t)b * sC, ldc);
+}
+
+/* ------------------------------------------------------------------------ */
+/* dsyrk followed by dpotrf, lower: C <= chol(C + A * A^T), A n x k -- the  */
+/* fused routine of the paper's own API that section 5 credits for part of  */
+/* the Riccati recursion's speed-up.  Defined as the two calls in sequence;  */
+/* returns dpotrf's info.                                                    */
+/* ------------------------------------------------------------------------ */
+int bfo_dsyrk_dpotrf_l(int n, int k, const double* A, int lda, double* C, int ldc) {
+    bfo_dsyrk('L', 'N', n, k, 1.0, A, lda, 1.0, C, ldc);
+    return bfo_dpotrf_l(n, C, ldc);
+}
+
+void bfo_dsyrk_dpotrf_l_sb(int n, int k, const double* A, int lda, long long sA, double* C, int ldc,
+                           long long sC, int batch, int* info) {
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int b = 0; b < batch; b++)
+        info[b] = bfo_dsyrk_dpotrf_l(n, k, A + (size_t)b * sA, lda, C + (size_t)b * sC, ldc);
+}
+
+/* ------------------------------------------------------------------------ */
+/* dtrmm -- section 3.1 ("dtrmm", treated like dtrsm) and the Riccati        */
+/* recursion of section 5 (dtrmm_rlnn): B <= alpha * op(A) * B (side 'L', A  */
+/* m x m) or B <= alpha * B * op(A) (side 'R', A n x n).  uplo: the stored   */
+/* triangle of A; diag 'U': unit diagonal, not read.  Written from the       */
+/* definition: T = op(A) is made explicit (zero outside its triangle), the   */
+/* product is formed in a temporary with plain loops, then scaled into B.    */
+/* alpha == 0 sets B to zero without reading A or B (BLAS).                  */
+/* ------------------------------------------------------------------------ */
+int bfo_dtrmm(char side, char uplo, char ta, char diag, int m, int n, double alpha,
+              const double* A, int lda, double* B, int ldb) {
+    if (!(is_l(side) || is_r(side))) return -1;
+    if (!(is_l(uplo) || is_u(uplo))) return -2;
+    if (!(is_n(ta) || is_t(ta))) return -3;
+    if (!(is_u(diag) || is_n(diag))) return -4;
+    if (m < 0) return -5;
+    if (n < 0) return -6;
+    if (m == 0 || n == 0) return 0;
+    if (alpha == 0.0) {
+        for (int j = 0; j < n; j++)
+            for (int i = 0; i < m; i++) B[IDX(i, j, ldb)] = 0.0;
+        return 0;
+    }
+    const int left = is_l(side), trans = is_t(ta), unit = is_u(diag);
+    const int k = left ? m : n;
+    const int t_lower = (is_l(uplo) && !trans) || (is_u(uplo) && trans);
+    double* T = (double*)calloc((size_t)k * k, sizeof(double));
+    double* R = (double*)malloc(sizeof(double) * (size_t)m * n);
+    for (int j = 0; j < k; j++)
+        for (int i = 0; i < k; i++) {
+            if (i == j) T[IDX(i, j, k)] = unit ? 1.0 : tri_elem(A, lda, trans, i, i);
+            else if (t_lower ? (i > j) : (i < j)) T[IDX(i, j, k)] = tri_elem(A, lda, trans, i, j);
+        }
+    for (int j = 0; j < n; j++)
+        for (int i = 0; i < m; i++) {
+            double s = 0.0;
+            if (left)
+                for (int p = 0; p < m; p++) s += T[IDX(i, p, k)] * B[IDX(p, j, ldb)];
+            else
+                for (int p = 0; p < n; p++) s += B[IDX(i, p, ldb)] * T[IDX(p, j, k)];
+            R[IDX(i, j, m)] = s;
+        }
+    for (int j = 0; j < n; j++)
+        for (int i = 0; i < m; i++) B[IDX(i, j, ldb)] = alpha * R[IDX(i, j, m)];
+    free(T);
+    free(R);
+    return 0;
+}
+
+void bfo_dtrmm_sb(char side, char uplo, char ta, char diag, int m, int n, double alpha,
+                  const double* A, int lda, long long sA, double* B, int ldb, long long sB,
+                  int batch) {
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int b = 0; b < batch; b++)
+        bfo_dtrmm(side, uplo, ta, diag, m, n, alpha, A + (size_t)b * sA, lda, B + (size_t)b * sB, ldb);
+}
+
+/* ------------------------------------------------------------------------ */
+/* dpotrf, upper -- appendix table of LAPACK routines (dpotrf_u, chol(Q,    */
+/* 'upper')): A = U^T U with U upper triangular, positive diagonal.          */
+/* Unblocked recurrence on the upper triangle, for j = 0..n-1:               */
+/*   d     = a_jj - sum_{p<j} u_pj^2,  u_jj = sqrt(d)  (fails: d <= 0 / NaN)   */
+/*   u_ji  = (a_ji - sum_{p<j} u_pj u_pi) / u_jj     for i > j               */
+/* Only the upper triangle is read and written.  LAPACK info as dpotrf_l.    */
+/* ------------------------------------------------------------------------ */
+int bfo_dpotrf_u(int n, double* A, int lda) {
+    for (int j = 0; j < n; j++) {
+        double d = A[IDX(j, j, lda)];
+        for (int p = 0; p < j; p++) d -= A[IDX(p, j, lda)] * A[IDX(p, j, lda)];
+        if (!(d > 0.0)) return j + 1;
+        const double ujj = sqrt(d);
+        A[IDX(j, j, lda)] = ujj;
+        for (int i = j + 1; i < n; i++) {
+            double s = A[IDX(j, i, lda)];
+            for (int p = 0; p < j; p++) s -= A[IDX(p, j, lda)] * A[IDX(p, i, lda)];
+            A[IDX(j, i, lda)] = s / ujj;
+        }
+    }
+    return 0;
+}
+
+void bfo_dpotrf_u_sb(int n, double* A, int lda, long long sA, int batch, int* info) {
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int b = 0; b < batch; b++) info[b] = bfo_dpotrf_u(n, A + (size_t)b * sA, lda);
+}
+
+/* ------------------------------------------------------------------------ */
+/* dgetrf -- section 3.1 ("dgetrf"): LU factorisation with partial (row)     */
+/* pivoting, P A = L U, A m x n, L unit lower (stored below the diagonal),   */
+/* U upper.  Unblocked, column by column, for j = 0..min(m,n)-1:             */
+/*   p = the first row index i >= j of the largest |a_ij| (a NaN never      */
+/*       counts as larger);  ipiv[j] = p + 1 (1-based, as LAPACK);           */
+/*   if a_pj != 0: swap rows j and p across all n columns, then              */
+/*       l_ij = a_ij / a_jj for i > j;                                       */
+/*   else: info = j + 1 if it is the first zero pivot (the column is left);  */
+/*   a_ik -= l_ij a_jk for i > j, k > j.                                     */
+/* Returns info (0, or the 1-based column of the first exactly zero pivot:   */
+/* U is then singular; the factorisation is still completed).                */
+/* ------------------------------------------------------------------------ */
+int bfo_dgetrf(int m, int n, double* A, int lda, int* ipiv) {
+    int info = 0;
+    const int mn = m < n ? m : n;
+    for (int j = 0; j < mn; j++) {
+        int p = j;
+        double best = fabs(A[IDX(j, j, lda)]);
+        for (int i = j + 1; i < m; i++) {
+            const double v = fabs(A[IDX(i, j, lda)]);
+            if (v > best) {
+                best = v;
+                p = i;
+            }
+        }
+        ipiv[j] = p + 1;
+        if (A[IDX(p, j, lda)] != 0.0) {
+            if (p != j)
+                for (int c = 0; c < n; c++) {
+                    const double t = A[IDX(j, c, lda)];
+                    A[IDX(j, c, lda)] = A[IDX(p, c, lda)];
+                    A[IDX(p, c, lda)] = t;
+                }
+            for (int i = j + 1; i < m; i++) A[IDX(i, j, lda)] = A[IDX(i, j, lda)] / A[IDX(j, j, lda)];
+        } else if (info == 0) {
+            info = j + 1;
+        }
+        for (int c = j + 1; c < n; c++)
+            for (int i = j + 1; i < m; i++) A[IDX(i, c, lda)] -= A[IDX(i, j, lda)] * A[IDX(j, c, lda)];
+    }
+    return info;
+}
+
+void bfo_dgetrf_sb(int m, int n, double* A, int lda, long long sA, int* ipiv, int batch, int* info) {
+    const int mn = m < n ? m : n;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int b = 0; b < batch; b++) info[b] = bfo_dgetrf(m, n, A + (size_t)b * sA, lda, ipiv + (size_t)b * mn);
+}
+
+/* ------------------------------------------------------------------------ */
+/* dgetrs -- solve op(A) X = B with the factors of dgetrf (n x n):           */
+/*   'N': B <- P B (the row swaps j <-> ipiv[j]-1, j ascending), then        */
+/*        L Y = B (unit lower, forward), U X = Y (backward);                 */
+/*   'T': U^T Y = B (forward), L^T Z = Y (unit, backward), then the swaps    */
+/*        in descending order.                                              */
+/* ------------------------------------------------------------------------ */
+int bfo_dgetrs(char trans, int n, int nrhs, const double* A, int lda, const int* ipiv, double* B, int ldb) {
+    if (!(is_n(trans) || is_t(trans))) return -1;
+    for (int c = 0; c < nrhs; c++) {
+        double* b = B + (size_t)c * ldb;
+        if (is_n(trans)) {
+            for (int j = 0; j < n; j++) {
+                const int p = ipiv[j] - 1;
+                if (p != j) {
+                    const double t = b[j];
+                    b[j] = b[p];
+                    b[p] = t;
+                }
+            }
+            for (int i = 0; i < n; i++) {
+                double s = b[i];
+                for (int p = 0; p < i; p++) s -= A[IDX(i, p, lda)] * b[p];
+                b[i] = s;
+            }
+            for (int i = n - 1; i >= 0; i--) {
+                double s = b[i];
+                for (int p = i + 1; p < n; p++) s -= A[IDX(i, p, lda)] * b[p];
+                b[i] = s / A[IDX(i, i, lda)];
+            }
+        } else {
+            for (int i = 0; i < n; i++) {
+                double s = b[i];
+                for (int p = 0; p < i; p++) s -= A[IDX(p, i, lda)] * b[p];
+                b[i] = s / A[IDX(i, i, lda)];
+            }
+            for (int i = n - 1; i >= 0; i--) {
+                double s = b[i];
+                for (int p = i + 1; p < n; p++) s -= A[IDX(p, i, lda)] * b[p];
+                b[i] = s;
+            }
+            for (int j = n - 1; j >= 0; j--) {
+                const int p = ipiv[j] - 1;
+                if (p != j) {
+                    const double t = b[j];
+                    b[j] = b[p];
+                    b[p] = t;
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+void bfo_dgetrs_sb(char trans, int n, int nrhs, const double* A, int lda, long long sA, const int* ipiv,
+                   double* B, int ldb, long long sB, int batch) {
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int b = 0; b < batch; b++)
+        bfo_dgetrs(trans, n, nrhs, A + (size_t)b * sA, lda, ipiv + (size_t)b * n, B + (size_t)b * sB, ldb);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Riccati recursion, square-root form (section 5, "Riccati recursion"):    */
+/* N stages, n_x states, n_u controls.  Inputs per stage s = 0..N-1:        */
+/*   BAt_s = [B_s^T; A_s^T]  ((n_u+n_x) x n_x, column-major),               */
+/*   RSQ_s = [R_s S_s; S_s^T Q_s]  ((n_u+n_x) square, SPD, lower read),      */
+/* and the terminal Q_N (n_x x n_x, SPD).  With Lc_N = chol(Q_N), for        */
+/* s = N-1 down to 0:                                                        */
+/*   C   = BAt_s * Lc_{s+1}                      (dtrmm_rlnn)                */
+/*   F_s = chol(RSQ_s + C C^T)                   (dsyrk_ln, then dpotrf_l)    */
+/*   Lc_s = the trailing n_x x n_x block of F_s                              */
+/* F (N+1 factors: F_s for s < N, then chol(Q_N) in the top-left n_x block   */
+/* of F_N) receives every factor; returns 0 or the first failing stage's     */
+/* dpotrf info + 1000 * stage.                                               */
+/* ------------------------------------------------------------------------ */
+int bfo_riccati(int N, int nx, int nu, const double* BAt, const double* RSQ, const double* QN, double* F) {
+    const int m = nx + nu;
+    const size_t fsz = (size_t)m * m;
+    double* C = (double*)malloc(sizeof(double) * (size_t)m * nx);
+    double* FN = F + (size_t)N * fsz;
+    for (size_t e = 0; e < fsz; e++) FN[e] = 0.0;
+    for (int j = 0; j < nx; j++)
+        for (int i = 0; i < nx; i++) FN[IDX(i, j, m)] = QN[IDX(i, j, nx)];
+    int info = bfo_dpotrf_l(nx, FN, m);
+    if (info) {
+        free(C);
+        return info + 1000 * N;
+    }
+    const double* Lc = FN;  /* leading dimension m; chol(Q_N) sits at offset 0 */
+    for (int s = N - 1; s >= 0; s--) {
+        const double* Bs = BAt + (size_t)s * m * nx;
+        double* Fs = F + (size_t)s * fsz;
+        memcpy(C, Bs, sizeof(double) * (size_t)m * nx);
+        /* dtrmm_rlnn on a copy of Lc with leading dimension nx */
+        double* L = (double*)malloc(sizeof(double) * (size_t)nx * nx);
+        for (int j = 0; j < nx; j++)
+            for (int i = 0; i < nx; i++) L[IDX(i, j, nx)] = (i >= j) ? Lc[IDX(i, j, m)] : 0.0;
+        bfo_dtrmm('R', 'L', 'N', 'N', m, nx, 1.0, L, nx, C, m);
+        free(L);
+        memcpy(Fs, RSQ + (size_t)s * fsz, sizeof(double) * fsz);
+        info = bfo_dsyrk_dpotrf_l(m, nx, C, m, Fs, m);
+        if (info) {
+            free(C);
+            return info + 1000 * s;
+        }
+        Lc = Fs + IDX(nu, nu, m);
+    }
+    free(C);
+    return 0;
+}
+
+void bfo_riccati_sb(int N, int nx, int nu, const double* BAt, const double* RSQ, const double* QN, double* F,
+                    int batch, int* info) {
+    const int m = nx + nu;
+    const size_t sB = (size_t)N * m * nx, sR = (size_t)N * m * m, sQ = (size_t)nx * nx, sF = (size_t)(N + 1) * m * m;
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int b = 0; b < batch; b++)
+        info[b] = bfo_riccati(N, nx, nu, BAt + b * sB, RSQ + b * sR, QN + b * sQ, F + b * sF);
+}
