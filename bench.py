@@ -442,6 +442,8 @@ def main():
         torch.cuda.empty_cache()
         result["precision"] = precision_form(bf, torch, dev, rank)
         torch.cuda.empty_cache()
+        result["next_rows"] = next_rows(bf, torch, dev, peak)
+        torch.cuda.empty_cache()
         if rank == 0:
             v, desc, cores = oracle_sample(args.cpu_budget)
             result["cpu_baseline"] = {"value": round(v, 3), "unit": "GFLOP/s", "cores": cores,
@@ -700,6 +702,81 @@ def precision_form(bf, torch, dev, rank, batch=16384, n=128):
     return {"batch": batch, "n": n, "mixed_ms": round(t_mixed, 3), "fp64_ms": round(t_fp64, 3),
             "speedup": round(t_fp64 / t_mixed, 3), "eta_max": float(eta.max()),
             "all_info_zero": int((info != 0).sum()) == 0, "per_kappa": per}
+
+
+def next_rows(bf, torch, dev, peak):
+    """The routines beyond the sweep: dsyrk (ln, ut), dtrmm (rlnn, llnn), dpotrf 'U', the fused
+    dsyrk + dpotrf against its two calls, and the square-root Riccati recursion (section 5) with the
+    fused routine against dsyrk + dpotrf; GFLOP/s and the fraction of the FP64 peak."""
+    import bfsynth
+
+    def rate(fl, ms):
+        return {"ms": round(ms, 3), "gflops": round(fl / ms / 1e6, 1), "frac": round(fl / (ms * 1e-3) / peak, 4)}
+
+    out = {"peak_tflops": round(peak / 1e12, 4)}
+    for n in (16, 64, 256):
+        b = bfsynth.sweep_batch(n, n, 2)
+        A = bfsynth.randn_batch(b, n, n, n, 31, device=dev)
+        C = bfsynth.randn_batch(b, n, n, n, 32, device=dev)
+        fl = b * n * (n + 1) * n
+        row = {"batch": b}
+        for uplo, tr in (("L", "N"), ("U", "T")):
+            row[f"dsyrk_{uplo.lower()}{tr.lower()}"] = rate(fl, _events_ms(
+                torch, lambda: bf.dsyrk(uplo, tr, 1.0, A, 1.0, C, n=n, k=n)))
+        L = bfsynth.spd_batch(b, n, n, 33, device=dev)
+        bf.dpotrf(L)
+        for side in "RL":
+            row[f"dtrmm_{side.lower()}lnn"] = rate(b * n * n * (n + 1), _events_ms(
+                torch, lambda: bf.dtrmm(side, "L", "N", "N", 1.0, L, C)))
+        del A, C, L
+        b1 = bfsynth.sweep_batch(n, n, 1)
+        S0 = bfsynth.spd_batch(b1, n, n, 34, device=dev)
+        S = S0.clone()
+        ms = _events_ms(torch, lambda: bf.dpotrf(S, uplo="U"), before=lambda: S.copy_(S0))
+        row["dpotrf_u"] = rate(b1 * (n ** 3 / 3 + n ** 2 / 2 + n / 6), ms)
+        del S, S0
+        torch.cuda.empty_cache()
+        out[f"n{n}"] = row
+    for n in (8, 32):
+        b = bfsynth.sweep_batch(n, n, 1) // 2
+        k = n // 2
+        Y = bfsynth.randn_batch(b, n, k, n, 35, device=dev)
+        S0 = bfsynth.spd_batch(b, n, n, 36, device=dev)
+        S = S0.clone()
+        fl = b * (n * (n + 1) * k + n ** 3 / 3 + n ** 2 / 2 + n / 6)
+
+        def two_calls():
+            bf.dsyrk("L", "N", 1.0, Y, 1.0, S, n=n, k=k)
+            bf.dpotrf(S)
+
+        out[f"dsyrk_dpotrf_n{n}"] = {
+            "batch": b, "k": k,
+            "fused_routine": rate(fl, _events_ms(torch, lambda: bf.dsyrk_dpotrf(Y, S, n=n, k=k),
+                                                 before=lambda: S.copy_(S0))),
+            "dsyrk_then_dpotrf": rate(fl, _events_ms(torch, two_calls, before=lambda: S.copy_(S0)))}
+        del Y, S, S0
+    # Riccati recursion, N = 10 stages; batches of ~16 GB of stage data (up to 64k problems)
+    N = 10
+    for nx, nu in ((8, 4), (24, 12), (40, 20), (64, 32)):
+        m = nx + nu
+        per = 8 * (N * m * nx + 2 * (N + 1) * m * m + nx * nx)
+        batch = int(min(65536, 16e9 // per))
+        BAt, RSQ, QN = bfsynth.riccati_batch(batch, N, nx, nu, 37 + nx, device=dev)
+        F = torch.empty(batch, N + 1, m, m, dtype=torch.float64, device=dev)
+        info = torch.empty(batch, dtype=torch.int32, device=dev)
+        work = torch.empty(bf.bf_riccati_workspace_bytes(nx, nu, batch), dtype=torch.uint8, device=dev)
+        fl = batch * (nx ** 3 / 3 + N * (m * nx * (nx + 1) + m * (m + 1) * nx + m ** 3 / 3 + m ** 2 / 2 + m / 6))
+        row = {"batch": batch, "N": N}
+        for fused in (True, False):
+            ms = _events_ms(torch, lambda: bf.riccati(BAt, RSQ, QN, nx, nu, F=F, info=info, fused=fused, work=work))
+            r = rate(fl, ms)
+            r["us_per_recursion"] = round(ms * 1e3 / batch, 4)
+            row["fused_routine" if fused else "dsyrk_then_dpotrf"] = r
+        row["all_info_zero"] = int((info != 0).sum()) == 0
+        out[f"riccati_nx{nx}_nu{nu}"] = row
+        del BAt, RSQ, QN, F, work
+        torch.cuda.empty_cache()
+    return out
 
 
 def reference_arm(args, rank, world):

@@ -235,3 +235,25 @@ SWEEP_BYTES = 2 ** 31
 def sweep_batch(n: int, ld: int, operands: int) -> int:
     """Problems per sweep point: floor(2 GiB / (operands * ld * n * 8 bytes))."""
     return SWEEP_BYTES // (operands * ld * n * 8)
+
+
+def riccati_batch(batch: int, N: int, nx: int, nu: int, seed: int, device="cpu"):
+    """Inputs of the square-root Riccati recursion (section 5), m = nu + nx, per problem:
+    N stages of BAt = [B^T; A^T] (m x nx) with A ~ N(0, 1/nx) (nx x nx) and B ~ N(0, 1/nx)
+    (nx x nu), and of RSQ = [R S; S^T Q] = G G^T + m I with G ~ N(0, 1) (m x m); the terminal
+    Q_N = H H^T + nx I, H ~ N(0, 1).  Column-major layouts: BAt (batch, N, nx, m), RSQ
+    (batch, N, m, m), QN (batch, nx, nx)."""
+    g = _gen(seed, device)
+    m = nx + nu
+    f = dict(generator=g, dtype=torch.float64, device=device)
+    A = torch.randn(batch, N, nx, nx, **f) / nx ** 0.5
+    B = torch.randn(batch, N, nx, nu, **f) / nx ** 0.5
+    BAt = torch.cat([B.transpose(-1, -2), A.transpose(-1, -2)], dim=-2).transpose(-1, -2).contiguous()
+    del A, B
+    G = torch.randn(batch, N, m, m, **f)
+    RSQ = G @ G.transpose(-1, -2)
+    del G
+    RSQ = 0.5 * (RSQ + RSQ.transpose(-1, -2)) + m * torch.eye(m, dtype=torch.float64, device=device)
+    H = torch.randn(batch, nx, nx, **f)
+    QN = H @ H.transpose(-1, -2) + nx * torch.eye(nx, dtype=torch.float64, device=device)
+    return BAt, RSQ.contiguous(), QN.contiguous()

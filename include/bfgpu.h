@@ -99,8 +99,9 @@ int bf_dtrsm_batched(char side, char uplo, char transa, char diag, int m, int n,
 /* the strict upper triangle and the padding rows (lda > n) are not touched. */
 /* info (device, one int per problem): 0 on success, j > 0 when the leading  */
 /* minor of order j is not positive definite (or NaN); that problem's        */
-/* factorisation stops at column j.  info may be NULL.  uplo 'U' returns     */
-/* BF_ERR_NOT_SUPPORTED.                                                      */
+/* factorisation stops at column j.  info may be NULL.  uplo 'U' (the        */
+/* appendix's dpotrf_u, chol(Q, 'upper')): A = U^T U from the upper triangle, */
+/* which U overwrites; the strict lower triangle is not touched.             */
 /* ------------------------------------------------------------------------ */
 int bf_dpotrf(char uplo, int n, double* A, int lda, int* info, bf_stream_t stream);
 
@@ -111,9 +112,85 @@ int bf_dpotrf_batched(char uplo, int n, double* const* Aarray, int lda, int* inf
                       bf_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
-/* dpotrs: solve A X = B with the factor from bf_dpotrf ('L'): the forward  */
-/* solve L Y = B then the backward solve L^T X = Y (section 3.1 "dtrsm"       */
-/* left variants).  B (n x nrhs, ldb >= max(1, n)) is overwritten by X.       */
+/* dsyrk (section 3.1 "dsyrk": dgemm whose A and B coincide):               */
+/*   C <= alpha op(A) op(A)^T + beta C   on the uplo triangle of C           */
+/* C n x n (ldc >= max(1, n)); op(A) = A (n x k, lda >= max(1, n)) for trans */
+/* 'N', A^T (A stored k x n, lda >= max(1, k)) for 'T'.  The other triangle  */
+/* of C is not written.  beta == 0: C is not read; alpha == 0 or k == 0:     */
+/* C <= beta C on the triangle (A not read).                                 */
+/* ------------------------------------------------------------------------ */
+int bf_dsyrk(char uplo, char trans, int n, int k, double alpha, const double* A, int lda, double beta,
+             double* C, int ldc, bf_stream_t stream);
+
+int bf_dsyrk_strided_batched(char uplo, char trans, int n, int k, double alpha, const double* A, int lda,
+                             long long strideA, double beta, double* C, int ldc, long long strideC,
+                             int batch, bf_stream_t stream);
+
+int bf_dsyrk_batched(char uplo, char trans, int n, int k, double alpha, const double* const* Aarray,
+                     int lda, double beta, double* const* Carray, int ldc, int batch, bf_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* dsyrk + dpotrf, lower, fused (the routine of the paper's own API that     */
+/* section 5 credits in the Riccati recursion): C <= chol(C + A A^T), A n x k */
+/* (lda >= max(1, n)), C n x n with its lower triangle read and overwritten  */
+/* by the factor (ldc >= max(1, n)); A A^T is added inside the Cholesky's    */
+/* own register tiles and never stored.  info (device, may be NULL) as       */
+/* bf_dpotrf.                                                                */
+/* ------------------------------------------------------------------------ */
+int bf_dsyrk_dpotrf(int n, int k, const double* A, int lda, double* C, int ldc, int* info,
+                    bf_stream_t stream);
+
+int bf_dsyrk_dpotrf_strided_batched(int n, int k, const double* A, int lda, long long strideA, double* C,
+                                    int ldc, long long strideC, int* info, int batch, bf_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* dtrmm (section 3.1 "dtrmm", built like dtrsm): B <= alpha op(A) B (side   */
+/* 'L', A m x m) or B <= alpha B op(A) (side 'R', A n x n); B m x n, ldb >=  */
+/* max(1, m).  uplo: the stored triangle of A; diag 'U': unit diagonal, not  */
+/* read.  alpha == 0: B <= 0 (A not read).                                   */
+/* ------------------------------------------------------------------------ */
+int bf_dtrmm(char side, char uplo, char transa, char diag, int m, int n, double alpha, const double* A,
+             int lda, double* B, int ldb, bf_stream_t stream);
+
+int bf_dtrmm_strided_batched(char side, char uplo, char transa, char diag, int m, int n, double alpha,
+                             const double* A, int lda, long long strideA, double* B, int ldb,
+                             long long strideB, int batch, bf_stream_t stream);
+
+int bf_dtrmm_batched(char side, char uplo, char transa, char diag, int m, int n, double alpha,
+                     const double* const* Aarray, int lda, double* const* Barray, int ldb, int batch,
+                     bf_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Riccati recursion, square-root form (section 5 "Riccati recursion"), for   */
+/* a batch of independent problems of N stages, nx states, nu controls,      */
+/* m = nu + nx.  Per problem (column-major, all leading dimensions m except  */
+/* Q_N's, nx):                                                               */
+/*   BAt   stage s at BAt + s m nx: [B_s^T; A_s^T], m x nx                    */
+/*   RSQ   stage s at RSQ + s m m:  [R_s S_s; S_s^T Q_s], m x m, lower read   */
+/*   QN    nx x nx, lower read                                              */
+/*   F     stage s at F + s m m, s = 0..N: receives chol(RSQ_s + C_s C_s^T)   */
+/*         with C_s = [B_s^T; A_s^T] Lc_{s+1} (dtrmm_rlnn), Lc_s its trailing */
+/*         nx x nx block; F_N holds chol(Q_N) in its top-left block, zeros    */
+/*         elsewhere.  Only lower triangles of F are meaningful.             */
+/*   info  (device) 0, or 1000 s + j for the first stage s (N: the terminal  */
+/*         factorisation) whose dpotrf failed at column j                    */
+/*   fused 1: the fused dsyrk + dpotrf; 0: dsyrk then dpotrf (BLAS/LAPACK)   */
+/*   work  caller-owned device memory of bf_riccati_workspace_bytes(nx, nu,  */
+/*         batch) bytes                                                      */
+/* The stages run as a sequence of batched launches on `stream`.            */
+/* ------------------------------------------------------------------------ */
+size_t bf_riccati_workspace_bytes(int nx, int nu, int batch);
+
+int bf_riccati_strided_batched(int N, int nx, int nu, const double* BAt, long long strideBAt,
+                               const double* RSQ, long long strideRSQ, const double* QN,
+                               long long strideQN, double* F, long long strideF, int* info, int fused,
+                               void* work, size_t work_bytes, int batch, bf_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* dpotrs: solve A X = B with the factor from bf_dpotrf: 'L' the forward    */
+/* solve L Y = B then the backward solve L^T X = Y, 'U' U^T Y = B then       */
+/* U X = Y (section 3.1 "dtrsm" left variants).  B (n x nrhs, ldb >=         */
+/* max(1, n)) is overwritten by X.                                           */
 /* ------------------------------------------------------------------------ */
 int bf_dpotrs(char uplo, int n, int nrhs, const double* A, int lda, double* B, int ldb,
               bf_stream_t stream);

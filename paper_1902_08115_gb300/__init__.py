@@ -68,12 +68,23 @@ _SIGS = {
     "bf_ragged_plan_info": [_vp, _ip],
     "bf_ragged_plan_destroy": [_vp],
     "bf_ragged_potrf_potrs_noalloc": [_i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _i, _i, _vp],
+    "bf_dsyrk": [_c, _c, _i, _i, _d, _vp, _i, _d, _vp, _i, _vp],
+    "bf_dsyrk_strided_batched": [_c, _c, _i, _i, _d, _vp, _i, _ll, _d, _vp, _i, _ll, _i, _vp],
+    "bf_dsyrk_batched": [_c, _c, _i, _i, _d, _vp, _i, _d, _vp, _i, _i, _vp],
+    "bf_dsyrk_dpotrf": [_i, _i, _vp, _i, _vp, _i, _vp, _vp],
+    "bf_dsyrk_dpotrf_strided_batched": [_i, _i, _vp, _i, _ll, _vp, _i, _ll, _vp, _i, _vp],
+    "bf_dtrmm": [_c, _c, _c, _c, _i, _i, _d, _vp, _i, _vp, _i, _vp],
+    "bf_dtrmm_strided_batched": [_c, _c, _c, _c, _i, _i, _d, _vp, _i, _ll, _vp, _i, _ll, _i, _vp],
+    "bf_dtrmm_batched": [_c, _c, _c, _c, _i, _i, _d, _vp, _i, _vp, _i, _i, _vp],
+    "bf_riccati_workspace_bytes": [_i, _i, _i],
+    "bf_riccati_strided_batched": [_i, _i, _i, _vp, _ll, _vp, _ll, _vp, _ll, _vp, _ll, _vp, _i, _vp,
+                                   ctypes.c_size_t, _i, _vp],
     "bf_launch_count": [],
     "bf_probe_fp64": [_i, _i, _vp, _vp],
     "bf_probe_fp64_ex": [_i, _i, _i, _i, _i, _vp, _vp],
 }
 _RES = {"bf_tune_clear": None, "bf_status_string": ctypes.c_char_p, "bf_ragged_workspace_bytes": ctypes.c_size_t,
-        "bf_dsposv_workspace_bytes": ctypes.c_size_t,
+        "bf_dsposv_workspace_bytes": ctypes.c_size_t, "bf_riccati_workspace_bytes": ctypes.c_size_t,
         "bf_launch_count": ctypes.c_ulonglong}
 
 for _name, _args in _SIGS.items():
@@ -177,7 +188,7 @@ def dtrsm(side: str, uplo: str, transa: str, diag: str, alpha: float, A, B, m=No
 
 
 def dpotrf(A, n=None, info=None, uplo: str = "L", stream=None):
-    """Cholesky of every problem in place (lower); returns the device int32 info tensor."""
+    """Cholesky of every problem in place (uplo 'L': A = L L^T, 'U': A = U^T U); returns info."""
     import torch
     bA, cA, ldA, sA = _batch_dims(A)
     n = cA if n is None else n
@@ -197,6 +208,82 @@ def dpotrs(L, B, n=None, nrhs=None, uplo: str = "L", stream=None):
     _check("bf_dpotrs_strided_batched", bf_dpotrs_strided_batched(
         _ch(uplo), n, nrhs, _ptr(L), ldL, sL, _ptr(B), ldB, sB, bB, _stream(stream)))
     return B
+
+
+def dsyrk(uplo: str, trans: str, alpha: float, A, beta: float, C, n=None, k=None, stream=None):
+    """C <= alpha op(A) op(A)^T + beta C on the uplo triangle, every problem (in place on C).
+
+    Defaults: n = C's number of columns; k = A's number of columns for trans 'N', A's leading
+    dimension for 'T' (pass k when that A is padded).
+    """
+    bA, cA, ldA, sA = _batch_dims(A)
+    bC, cC, ldC, sC = _batch_dims(C)
+    n = cC if n is None else n
+    if k is None:
+        k = cA if trans.upper() == "N" else ldA
+    _check("bf_dsyrk_strided_batched", bf_dsyrk_strided_batched(
+        _ch(uplo), _ch(trans), n, k, alpha, _ptr(A), ldA, sA if bA > 1 else 0, beta, _ptr(C), ldC, sC, bC,
+        _stream(stream)))
+    return C
+
+
+def dsyrk_dpotrf(A, C, n=None, k=None, info=None, stream=None):
+    """C <= chol(C + A A^T) (lower) in one kernel, every problem; returns the info tensor."""
+    import torch
+    bA, cA, ldA, sA = _batch_dims(A)
+    bC, cC, ldC, sC = _batch_dims(C)
+    n = cC if n is None else n
+    k = cA if k is None else k
+    if info is None:
+        info = torch.empty(bC, dtype=torch.int32, device=C.device)
+    _check("bf_dsyrk_dpotrf_strided_batched", bf_dsyrk_dpotrf_strided_batched(
+        n, k, _ptr(A), ldA, sA if bA > 1 else 0, _ptr(C), ldC, sC, _ptr(info), bC, _stream(stream)))
+    return info
+
+
+def dtrmm(side: str, uplo: str, transa: str, diag: str, alpha: float, A, B, m=None, n=None, stream=None):
+    """B <= alpha op(A) B (side 'L') or alpha B op(A) (side 'R'), every problem (in place on B).
+
+    m, n may be omitted only for unpadded square batches of one order.
+    """
+    bA, cA, ldA, sA = _batch_dims(A)
+    bB, cB, ldB, sB = _batch_dims(B)
+    if m is None or n is None:
+        sq = _square(A, B)
+        if sq is None:
+            raise ValueError("pass m, n explicitly for padded or non-square operands")
+        m = sq if m is None else m
+        n = sq if n is None else n
+    _check("bf_dtrmm_strided_batched", bf_dtrmm_strided_batched(
+        _ch(side), _ch(uplo), _ch(transa), _ch(diag), m, n, alpha, _ptr(A), ldA, sA if bA > 1 else 0,
+        _ptr(B), ldB, sB, bB, _stream(stream)))
+    return B
+
+
+def riccati(BAt, RSQ, QN, nx: int, nu: int, F=None, info=None, fused: bool = True, work=None, stream=None):
+    """Square-root Riccati recursion (section 5) for a batch of independent problems.
+
+    BAt (batch, N, nx, m): per stage [B^T; A^T] (m x nx, column-major); RSQ (batch, N, m, m):
+    [R S; S^T Q]; QN (batch, nx, nx); m = nu + nx.  Returns (F, info) with F (batch, N+1, m, m)
+    the stage factors (see bf_riccati_strided_batched).
+    """
+    import torch
+    batch, N = BAt.shape[0], BAt.shape[1]
+    m = nx + nu
+    if F is None:
+        F = torch.empty(batch, N + 1, m, m, dtype=torch.float64, device=BAt.device)
+    if info is None:
+        info = torch.empty(batch, dtype=torch.int32, device=BAt.device)
+    wb = bf_riccati_workspace_bytes(nx, nu, batch)
+    if work is None:
+        work = torch.empty(max(wb, 1), dtype=torch.uint8, device=BAt.device)
+    for t in (BAt, RSQ, QN, F):
+        if not t.is_contiguous():
+            raise ValueError("riccati operands must be contiguous")
+    _check("bf_riccati_strided_batched", bf_riccati_strided_batched(
+        N, nx, nu, _ptr(BAt), N * m * nx, _ptr(RSQ), N * m * m, _ptr(QN), nx * nx, _ptr(F), (N + 1) * m * m,
+        _ptr(info), 1 if fused else 0, _ptr(work), work.numel(), batch, _stream(stream)))
+    return F, info
 
 
 def dsposv(A, B, X=None, n=None, nrhs=None, tol: float = 1e-12, itmax: int = 30, iter=None, info=None,

@@ -101,13 +101,12 @@ int check_potrf(char uplo, int n, const void* A, int lda, int batch, long long s
     if (pos_batch && batch < 0) return -pos_batch;
     if (strided && batch > 1 && strideA < (long long)lda * n) return -pos_sA;
     if (n > 0 && batch != 0 && !A) return -pos_A;
-    if (is_u(uplo)) return BF_ERR_NOT_SUPPORTED;
     return 0;
 }
 
-int run_potrf(int n, MatRef A, int lda, int* info, long long batch, cudaStream_t s) {
+int run_potrf(char uplo, int n, MatRef A, int lda, int* info, long long batch, cudaStream_t s) {
     PotrfConfig cfg = choose_potrf(n, lda, batch);
-    return status(launch_dpotrf(n, A, lda, batch, info, cfg, s));
+    return status(launch_dpotrf(n, A, lda, batch, info, cfg, s, is_u(uplo) ? 1 : 0));
 }
 
 }  // namespace
@@ -180,21 +179,21 @@ int bf_dtrsm_batched(char side, char uplo, char transa, char diag, int m, int n,
 int bf_dpotrf(char uplo, int n, double* A, int lda, int* info, bf_stream_t stream) {
     int r = check_potrf(uplo, n, A, lda, 1, 0, false, 1, 2, 3, 4, 0, 0);
     if (r) return r;
-    return run_potrf(n, mat_strided(A, 0), lda, info, 1, (cudaStream_t)stream);
+    return run_potrf(uplo, n, mat_strided(A, 0), lda, info, 1, (cudaStream_t)stream);
 }
 
 int bf_dpotrf_strided_batched(char uplo, int n, double* A, int lda, long long strideA, int* info,
                               int batch, bf_stream_t stream) {
     int r = check_potrf(uplo, n, A, lda, batch, strideA, true, 1, 2, 3, 4, 5, 7);
     if (r) return r;
-    return run_potrf(n, mat_strided(A, strideA), lda, info, batch, (cudaStream_t)stream);
+    return run_potrf(uplo, n, mat_strided(A, strideA), lda, info, batch, (cudaStream_t)stream);
 }
 
 int bf_dpotrf_batched(char uplo, int n, double* const* Aarray, int lda, int* info, int batch,
                       bf_stream_t stream) {
     int r = check_potrf(uplo, n, Aarray, lda, batch, 0, false, 1, 2, 3, 4, 0, 6);
     if (r) return r;
-    return run_potrf(n, mat_array((const double* const*)Aarray, 0), lda, info, batch, (cudaStream_t)stream);
+    return run_potrf(uplo, n, mat_array((const double* const*)Aarray, 0), lda, info, batch, (cudaStream_t)stream);
 }
 
 static int potrs_impl(char uplo, int n, int nrhs, const double* A, int lda, long long strideA, double* B,
@@ -210,13 +209,14 @@ static int potrs_impl(char uplo, int n, int nrhs, const double* A, int lda, long
     const bool work = n > 0 && nrhs > 0 && batch > 0;
     if (work && !A) return -pos[3];
     if (work && !B) return -pos[5];
-    if (is_u(uplo)) return BF_ERR_NOT_SUPPORTED;
     if (!work) return 0;
-    int r = run_trsm('L', 'L', 'N', 'N', n, nrhs, 1.0, mat_strided(A, strideA), lda, mat_strided(B, strideB),
-                     ldb, batch, (cudaStream_t)stream);
+    // 'L': L Y = B, L^T X = Y;  'U': U^T Y = B, U X = Y
+    const char u = is_u(uplo) ? 'U' : 'L';
+    int r = run_trsm('L', u, u == 'L' ? 'N' : 'T', 'N', n, nrhs, 1.0, mat_strided(A, strideA), lda,
+                     mat_strided(B, strideB), ldb, batch, (cudaStream_t)stream);
     if (r) return r;
-    return run_trsm('L', 'L', 'T', 'N', n, nrhs, 1.0, mat_strided(A, strideA), lda, mat_strided(B, strideB),
-                    ldb, batch, (cudaStream_t)stream);
+    return run_trsm('L', u, u == 'L' ? 'T' : 'N', 'N', n, nrhs, 1.0, mat_strided(A, strideA), lda,
+                    mat_strided(B, strideB), ldb, batch, (cudaStream_t)stream);
 }
 
 int bf_dpotrs(char uplo, int n, int nrhs, const double* A, int lda, double* B, int ldb, bf_stream_t stream) {
@@ -229,6 +229,136 @@ int bf_dpotrs_strided_batched(char uplo, int n, int nrhs, const double* A, int l
     static const int pos[9] = {1, 2, 3, 4, 5, 7, 8, 9, 10};
     if (strideA < 0) return -6;
     return potrs_impl(uplo, n, nrhs, A, lda, strideA, B, ldb, strideB, batch, stream, pos);
+}
+
+// ------------------------------------------------------------------------ dsyrk
+static int syrk_impl(char uplo, char trans, int n, int k, double alpha, MatRef A, const void* Ap, int lda,
+                     double beta, MatRef C, const void* Cp, int ldc, long long strideC, int batch, bool strided,
+                     bf_stream_t stream, const int* pos) {
+    // pos: uplo, trans, n, k, A, lda, C, ldc, strideC, batch
+    if (!(is_l(uplo) || is_u(uplo))) return -pos[0];
+    if (!(is_n(trans) || is_t(trans))) return -pos[1];
+    if (n < 0) return -pos[2];
+    if (k < 0) return -pos[3];
+    if (lda < imax1(is_n(trans) ? n : k)) return -pos[5];
+    if (ldc < imax1(n)) return -pos[7];
+    if (pos[9] && batch < 0) return -pos[9];
+    if (strided && batch > 1 && strideC < (long long)ldc * n) return -pos[8];
+    const bool work = n > 0 && batch > 0;
+    if (work && k > 0 && alpha != 0.0 && !Ap) return -pos[4];
+    if (work && !Cp) return -pos[6];
+    if (!work) return 0;
+    return status(launch_dsyrk(is_u(uplo) ? 1 : 0, is_t(trans) ? 1 : 0, n, k, alpha, A, lda, beta, C, ldc, batch,
+                               (cudaStream_t)stream));
+}
+
+int bf_dsyrk(char uplo, char trans, int n, int k, double alpha, const double* A, int lda, double beta, double* C,
+             int ldc, bf_stream_t stream) {
+    static const int pos[10] = {1, 2, 3, 4, 6, 7, 9, 10, 0, 0};
+    return syrk_impl(uplo, trans, n, k, alpha, mat_strided(A, 0), A, lda, beta, mat_strided(C, 0), C, ldc, 0, 1,
+                     false, stream, pos);
+}
+
+int bf_dsyrk_strided_batched(char uplo, char trans, int n, int k, double alpha, const double* A, int lda,
+                             long long strideA, double beta, double* C, int ldc, long long strideC, int batch,
+                             bf_stream_t stream) {
+    static const int pos[10] = {1, 2, 3, 4, 6, 7, 10, 11, 12, 13};
+    if (strideA < 0) return -8;
+    return syrk_impl(uplo, trans, n, k, alpha, mat_strided(A, strideA), A, lda, beta, mat_strided(C, strideC), C,
+                     ldc, strideC, batch, true, stream, pos);
+}
+
+int bf_dsyrk_batched(char uplo, char trans, int n, int k, double alpha, const double* const* Aarray, int lda,
+                     double beta, double* const* Carray, int ldc, int batch, bf_stream_t stream) {
+    static const int pos[10] = {1, 2, 3, 4, 6, 7, 9, 10, 0, 11};
+    return syrk_impl(uplo, trans, n, k, alpha, mat_array(Aarray, 0), Aarray, lda, beta,
+                     mat_array((const double* const*)Carray, 0), Carray, ldc, 0, batch, false, stream, pos);
+}
+
+// ------------------------------------------------------------------------ dsyrk + dpotrf
+static int syrk_potrf_impl(int n, int k, MatRef A, const void* Ap, int lda, MatRef C, const void* Cp, int ldc,
+                           long long strideC, int* info, int batch, bool strided, bf_stream_t stream,
+                           const int* pos) {
+    // pos: n, k, A, lda, C, ldc, strideC, batch
+    if (n < 0) return -pos[0];
+    if (k < 0) return -pos[1];
+    if (lda < imax1(n)) return -pos[3];
+    if (ldc < imax1(n)) return -pos[5];
+    if (pos[7] && batch < 0) return -pos[7];
+    if (strided && batch > 1 && strideC < (long long)ldc * n) return -pos[6];
+    const bool work = n > 0 && batch > 0;
+    if (work && k > 0 && !Ap) return -pos[2];
+    if (work && !Cp) return -pos[4];
+    if (batch <= 0) return 0;
+    return status(launch_dsyrk_dpotrf(n, k, A, lda, C, ldc, batch, info, (cudaStream_t)stream));
+}
+
+int bf_dsyrk_dpotrf(int n, int k, const double* A, int lda, double* C, int ldc, int* info, bf_stream_t stream) {
+    static const int pos[8] = {1, 2, 3, 4, 5, 6, 0, 0};
+    return syrk_potrf_impl(n, k, mat_strided(A, 0), A, lda, mat_strided(C, 0), C, ldc, 0, info, 1, false, stream,
+                           pos);
+}
+
+int bf_dsyrk_dpotrf_strided_batched(int n, int k, const double* A, int lda, long long strideA, double* C, int ldc,
+                                    long long strideC, int* info, int batch, bf_stream_t stream) {
+    static const int pos[8] = {1, 2, 3, 4, 6, 7, 8, 10};
+    if (strideA < 0) return -5;
+    return syrk_potrf_impl(n, k, mat_strided(A, strideA), A, lda, mat_strided(C, strideC), C, ldc, strideC, info,
+                           batch, true, stream, pos);
+}
+
+// ------------------------------------------------------------------------ dtrmm
+static int trmm_impl(char side, char uplo, char ta, char diag, int m, int n, double alpha, MatRef A, const void* Ap,
+                     int lda, MatRef B, const void* Bp, int ldb, long long strideB, int batch, bool strided,
+                     bf_stream_t stream, const int* pos) {
+    // pos: side, uplo, ta, diag, m, n, A, lda, B, ldb, strideB, batch
+    if (!(is_l(side) || is_r(side))) return -pos[0];
+    if (!(is_l(uplo) || is_u(uplo))) return -pos[1];
+    if (!(is_n(ta) || is_t(ta))) return -pos[2];
+    if (!(is_u(diag) || is_n(diag))) return -pos[3];
+    if (m < 0) return -pos[4];
+    if (n < 0) return -pos[5];
+    if (lda < imax1(is_l(side) ? m : n)) return -pos[7];
+    if (ldb < imax1(m)) return -pos[9];
+    if (pos[11] && batch < 0) return -pos[11];
+    if (strided && batch > 1 && strideB < (long long)ldb * n) return -pos[10];
+    const bool work = m > 0 && n > 0 && batch > 0;
+    if (work && alpha != 0.0 && !Ap) return -pos[6];
+    if (work && !Bp) return -pos[8];
+    if (!work) return 0;
+    if (alpha == 0.0) {  // B <= 0 without reading A or B
+        GemmConfig dummy{VAR_DIRECT, 4, 4, 1, 1};
+        return status(launch_dgemm(false, false, m, n, 0, 0.0, B, ldb, B, ldb, 0.0, B, ldb, batch, dummy, 0, nullptr,
+                                   (cudaStream_t)stream));
+    }
+    const int right = is_r(side) ? 1 : 0;
+    const int rows = right ? m : n;  // independent rows of the right-side form
+    return status(launch_dtrmm(right, is_u(uplo) ? 1 : 0, is_t(ta) ? 1 : 0, is_u(diag) ? 1 : 0, m, n, alpha, A, lda,
+                               B, ldb, batch, rows >= 256 ? 8 : 4, (cudaStream_t)stream));
+}
+
+int bf_dtrmm(char side, char uplo, char transa, char diag, int m, int n, double alpha, const double* A, int lda,
+             double* B, int ldb, bf_stream_t stream) {
+    static const int pos[12] = {1, 2, 3, 4, 5, 6, 8, 9, 10, 11, 0, 0};
+    return trmm_impl(side, uplo, transa, diag, m, n, alpha, mat_strided(A, 0), A, lda, mat_strided(B, 0), B, ldb, 0,
+                     1, false, stream, pos);
+}
+
+int bf_dtrmm_strided_batched(char side, char uplo, char transa, char diag, int m, int n, double alpha,
+                             const double* A, int lda, long long strideA, double* B, int ldb, long long strideB,
+                             int batch, bf_stream_t stream) {
+    static const int pos[12] = {1, 2, 3, 4, 5, 6, 8, 9, 11, 12, 13, 14};
+    if (strideA < 0) return -10;
+    return trmm_impl(side, uplo, transa, diag, m, n, alpha, mat_strided(A, strideA), A, lda, mat_strided(B, strideB),
+                     B, ldb, strideB, batch, true, stream, pos);
+}
+
+int bf_dtrmm_batched(char side, char uplo, char transa, char diag, int m, int n, double alpha,
+                     const double* const* Aarray, int lda, double* const* Barray, int ldb, int batch,
+                     bf_stream_t stream) {
+    static const int pos[12] = {1, 2, 3, 4, 5, 6, 8, 9, 10, 11, 0, 12};
+    return trmm_impl(side, uplo, transa, diag, m, n, alpha, mat_array(Aarray, 0), Aarray, lda,
+                     mat_array((const double* const*)Barray, 0), Barray, ldb, 0, batch, false, stream, pos);
 }
 
 const char* bf_status_string(int s) {

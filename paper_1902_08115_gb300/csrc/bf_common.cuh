@@ -91,5 +91,7 @@ __device__ __forceinline__ int imax(int a, int b) { return a > b ? a : b; }
 // Read-only global load through the non-coherent path (operands that the
 // kernel never writes).
 __device__ __forceinline__ double ldg(const double* p) { return __ldg(p); }
+// two consecutive doubles from a 16-byte-aligned address, read-only path
+__device__ __forceinline__ double2 ldg2(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
 
 }  // namespace bf

@@ -29,12 +29,13 @@
 
 namespace bf {
 
-template <int R, int U>
+template <int R, int U, bool UP>
 __global__ void __launch_bounds__(256) dpotrf_lane_direct_kernel(PotrfParams p) {
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= p.batch) return;
     if (p.skip && p.skip[q] != 0) return;
-    const int info = potrf_lane_global<R, U>(p.A.mptr(q), p.lda, p.n);
+    const int info = UP ? potrf_lane<R, U>(GAccT{p.A.mptr(q), p.lda}, p.n)
+                        : potrf_lane_global<R, U>(p.A.mptr(q), p.lda, p.n);
     if (info && p.info) p.info[q] = info + p.info_off;
 }
 
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(256) dpotrf_lane_packed_kernel(PotrfParams p) 
         const int j = rem / n, i = rem - j * n;
         const long long qg = q0 + qq;
         double v = 0.0;
-        if (qg < p.batch && i >= j) v = p.A.ptr(qg)[i + (long long)j * p.lda];
+        if (qg < p.batch && i >= j) v = p.upper ? p.A.ptr(qg)[j + (long long)i * p.lda] : p.A.ptr(qg)[i + (long long)j * p.lda];
         smem[(i + j * n) * T + qq] = v;
     }
     __syncthreads();
@@ -73,15 +74,34 @@ __global__ void __launch_bounds__(256) dpotrf_lane_packed_kernel(PotrfParams p) 
         if (qg < p.batch && i >= j) {
             if (p.skip && p.skip[qg] != 0) continue;
             if (p.info && p.info[qg] != 0) continue;
-            p.A.mptr(qg)[i + (long long)j * p.lda] = smem[(i + j * n) * T + qq];
+            const long long at = p.upper ? j + (long long)i * p.lda : i + (long long)j * p.lda;
+            p.A.mptr(qg)[at] = smem[(i + j * n) * T + qq];
+        }
+    }
+}
+
+template <bool UP>
+static void launch_direct(const PotrfParams& p, const PotrfConfig& cfg, unsigned blocks, int T, cudaStream_t s) {
+    if (cfg.rows == 8) {
+        if (cfg.unroll == 2) {
+            dpotrf_lane_direct_kernel<8, 2, UP><<<blocks, T, 0, s>>>(p);
+        } else {
+            dpotrf_lane_direct_kernel<8, 1, UP><<<blocks, T, 0, s>>>(p);
+        }
+    } else {
+        if (cfg.unroll == 1) {
+            dpotrf_lane_direct_kernel<4, 1, UP><<<blocks, T, 0, s>>>(p);
+        } else {
+            dpotrf_lane_direct_kernel<4, 2, UP><<<blocks, T, 0, s>>>(p);
         }
     }
 }
 
 cudaError_t launch_dpotrf_lane(int n, MatRef A, int lda, long long batch, int* info, int info_off,
-                               const int* skip, const PotrfConfig& cfg, cudaStream_t s) {
+                               const int* skip, const PotrfConfig& cfg, cudaStream_t s, int upper) {
     PotrfParams p;
     p.n = n; p.A = A; p.lda = lda; p.batch = batch; p.info = info; p.info_off = info_off; p.skip = skip;
+    p.upper = upper;
     if (cfg.variant == VAR_PACKED) {
         const int T = cfg.T;
         size_t smem = sizeof(double) * (size_t)T * n * n;
@@ -97,42 +117,48 @@ cudaError_t launch_dpotrf_lane(int n, MatRef A, int lda, long long batch, int* i
     }
     const int T = cfg.T > 0 ? cfg.T : 128;
     const unsigned blocks = (unsigned)((batch + T - 1) / T);
-    if (cfg.rows == 8) {
-        if (cfg.unroll == 2) {
-            dpotrf_lane_direct_kernel<8, 2><<<blocks, T, 0, s>>>(p);
-        } else {
-            dpotrf_lane_direct_kernel<8, 1><<<blocks, T, 0, s>>>(p);
-        }
+    if (upper) {
+        launch_direct<true>(p, cfg, blocks, T, s);
     } else {
-        if (cfg.unroll == 1) {
-            dpotrf_lane_direct_kernel<4, 1><<<blocks, T, 0, s>>>(p);
-        } else {
-            dpotrf_lane_direct_kernel<4, 2><<<blocks, T, 0, s>>>(p);
-        }
+        launch_direct<false>(p, cfg, blocks, T, s);
     }
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_dpotrf(int n, MatRef A, int lda, long long batch, int* info,
-                          const PotrfConfig& cfg, cudaStream_t s) {
+                          const PotrfConfig& cfg, cudaStream_t s, int upper) {
     if (batch == 0) return cudaSuccess;
     if (info) {
         cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int) * (size_t)batch, s);
         if (e != cudaSuccess) return e;
     }
     if (n == 0) return cudaSuccess;
-    if (cfg.variant != VAR_BLOCKED) return launch_dpotrf_lane(n, A, lda, batch, info, 0, nullptr, cfg, s);
+    if (cfg.variant != VAR_BLOCKED) return launch_dpotrf_lane(n, A, lda, batch, info, 0, nullptr, cfg, s, upper);
     // right-looking blocked factorisation built from the library's kernels
     const int NB = cfg.NB;
     PotrfConfig lane = choose_potrf(NB, lda, batch);
     lane.variant = VAR_DIRECT;
     for (int J = 0; J < n; J += NB) {
         const int jb = (n - J < NB) ? (n - J) : NB;
-        cudaError_t e = launch_dpotrf_lane(jb, mat_sub(A, J, J, lda), lda, batch, info, J, info, lane, s);
+        cudaError_t e = launch_dpotrf_lane(jb, mat_sub(A, J, J, lda), lda, batch, info, J, info, lane, s, upper);
         if (e != cudaSuccess) return e;
         const int rest = n - J - jb;
         if (rest <= 0) break;
+        if (upper) {
+            // panel: U(J:J+jb, J+jb:n) = U_JJ^{-T} A(J:J+jb, J+jb:n)
+            TrsmConfig tc = choose_trsm(0, 1, 1, 0, jb, rest, batch);
+            e = launch_dtrsm(0, 1, 1, 0, jb, rest, 1.0, mat_sub(A, J, J, lda), lda,
+                             mat_sub(A, J, J + jb, lda), lda, batch, tc, info, s);
+            if (e != cudaSuccess) return e;
+            // trailing update (upper part only): A22 -= U12^T U12
+            MatRef P = mat_sub(A, J, J + jb, lda);
+            GemmConfig gc = choose_gemm(true, false, rest, rest, jb, lda, batch);
+            e = launch_dgemm(true, false, rest, rest, jb, -1.0, P, lda, P, lda, 1.0,
+                             mat_sub(A, J + jb, J + jb, lda), lda, batch, gc, TRI_UPPER, info, s);
+            if (e != cudaSuccess) return e;
+            continue;
+        }
         // panel: L(J+jb:n, J:J+jb) = A(J+jb:n, J:J+jb) L_JJ^{-T}
         TrsmConfig tc = choose_trsm(1, 0, 1, 0, rest, jb, batch);
         e = launch_dtrsm(1, 0, 1, 0, rest, jb, 1.0, mat_sub(A, J, J, lda), lda,

@@ -76,6 +76,7 @@ struct PotrfParams {
     int* info;      // per-problem LAPACK info (device), may be null
     int info_off;   // added to a failing column (blocked use on a sub-matrix)
     const int* skip;
+    int upper;      // 1: A = U^T U from the upper triangle (the lower factor of the transposed view)
 };
 
 // Increments the library's kernel-launch counter (bf_launch_count).
@@ -93,10 +94,20 @@ cudaError_t launch_dtrsm(int side, int uplo, int trans, int unit, int m, int n, 
                          const TrsmConfig& cfg, const int* skip, cudaStream_t s);
 
 cudaError_t launch_dpotrf_lane(int n, MatRef A, int lda, long long batch, int* info, int info_off,
-                               const int* skip, const PotrfConfig& cfg, cudaStream_t s);
+                               const int* skip, const PotrfConfig& cfg, cudaStream_t s, int upper = 0);
 
 cudaError_t launch_dpotrf(int n, MatRef A, int lda, long long batch, int* info,
-                          const PotrfConfig& cfg, cudaStream_t s);
+                          const PotrfConfig& cfg, cudaStream_t s, int upper = 0);
+
+// dsyrk (upper: 0/1, trans: 0/1) and the fused chol(C + A A^T), lower (bf_dsyrk.cu)
+cudaError_t launch_dsyrk(int upper, int trans, int n, int k, double alpha, MatRef A, int lda, double beta,
+                         MatRef C, int ldc, long long batch, cudaStream_t s);
+cudaError_t launch_dsyrk_dpotrf(int n, int k, MatRef A, int lda, MatRef C, int ldc, long long batch, int* info,
+                                cudaStream_t s);
+
+// dtrmm, row-parallel like dtrsm (bf_dtrmm.cu); side: 0 = left, 1 = right
+cudaError_t launch_dtrmm(int side, int uplo, int trans, int unit, int m, int n, double alpha, MatRef A, int lda,
+                         MatRef B, int ldb, long long batch, int MR, cudaStream_t s);
 
 // Configuration choice (the size switch), in bf_tune.cu.
 GemmConfig choose_gemm(bool ta, bool tb, int m, int n, int k, int lda, long long batch);

@@ -13,7 +13,8 @@
 //    blocks and a 4x4 tail.  Each k step of an 8x4 block moves 12 words for
 //    32 fused multiply-adds, at the price of more registers per thread.
 //
-// Shared by the uniform (bf_dpotrf.cu) and ragged (bf_ragged.cu) kernels.
+// Shared by the uniform (bf_dpotrf.cu), ragged (bf_ragged.cu) and fused dsyrk + dpotrf
+// (bf_dsyrk.cu) kernels.
 //
 // Operands are reached through an accessor whose strip<R> loads move R
 // consecutive rows of one column (rows clamped to n - 1 at the end of the
@@ -155,6 +156,47 @@ struct SAcc {  // a problem in shared memory, interleaved with the CTA's other p
     }
 };
 
+// Global memory, transposed view: element (i, j) of the view is a[j + i lda], so the lower
+// Cholesky of the view reads and writes the upper triangle of the stored matrix (A = U^T U,
+// U = the view's L transposed).  A strip runs along a row of the stored matrix: single words.
+struct GAccT {
+    double* a;
+    int lda;
+    __device__ __forceinline__ double ld(int i, int j) const { return a[j + (long long)i * lda]; }
+    __device__ __forceinline__ void st(int i, int j, double v) const { a[j + (long long)i * lda] = v; }
+    template <int R>
+    __device__ __forceinline__ void strip(int i, int j, int n, double* o) const {
+#pragma unroll
+        for (int r = 0; r < R; r++) o[r] = ld(imin(i + r, n - 1), j);
+    }
+    template <int R>
+    __device__ __forceinline__ void put(int i, int j, int cnt, const double* v) const {
+#pragma unroll
+        for (int r = 0; r < R; r++)
+            if (r < cnt) st(i + r, j, v[r]);
+    }
+};
+
+// The optional rank-k operand of the fused dsyrk + dpotrf: the factorisation then acts on
+// C + Y Y^T, the product accumulated in the same register tiles as the Cholesky updates
+// (the paper's fused dsyrk_dpotrf routine, section 5).  NoSyrk: plain dpotrf.
+struct NoSyrk {
+    static constexpr bool active = false;
+    template <int R>
+    __device__ __forceinline__ void strip(int, int, int, double* o) const {
+#pragma unroll
+        for (int r = 0; r < R; r++) o[r] = 0.0;
+    }
+};
+
+template <class G>
+struct SyrkOp {  // Y (n x k) in global memory through accessor G
+    static constexpr bool active = true;
+    G g;
+    template <int R>
+    __device__ __forceinline__ void strip(int i, int j, int n, double* o) const { g.template strip<R>(i, j, n, o); }
+};
+
 // acc (R x 4) <- acc L_JJ^{-T}: forward substitution against the factored
 // diagonal block d (lower, diagonal replaced by its reciprocal rinv).
 template <int R>
@@ -172,9 +214,10 @@ __device__ __forceinline__ void trsm_edge(double (&acc)[R][4], const double (&d)
 
 // Rows I..I+R-1 of block column J: acc = A(I:I+R, J:J+4) - L(I:I+R, 0:J) L(J:J+4, 0:J)^T,
 // then acc L_JJ^{-T}, stored for the rows that exist.  U = unroll of the k loop.
-template <int R, int U, class Acc>
+template <int R, int U, class Acc, class Y>
 __device__ __forceinline__ void lane_block(const Acc& M, int n, int I, int J, int jb, const int (&jr)[4],
-                                           const double (&d)[4][4], const double (&rinv)[4]) {
+                                           const double (&d)[4][4], const double (&rinv)[4], const Y& ysk,
+                                           int k) {
     double acc[R][4];
 #pragma unroll
     for (int c = 0; c < 4; c++) {
@@ -182,6 +225,18 @@ __device__ __forceinline__ void lane_block(const Acc& M, int n, int I, int J, in
         M.template strip<R>(I, jr[c], n, col);
 #pragma unroll
         for (int r = 0; r < R; r++) acc[r][c] = col[r];
+    }
+    if (Y::active) {
+#pragma unroll U
+        for (int p = 0; p < k; p++) {
+            double a[R], b[4];
+            ysk.template strip<R>(I, p, n, a);
+            ysk.template strip<4>(J, p, n, b);
+#pragma unroll
+            for (int r = 0; r < R; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
     }
 #pragma unroll U
     for (int pp = 0; pp < J; pp++) {
@@ -207,14 +262,26 @@ __device__ __forceinline__ void lane_block(const Acc& M, int n, int I, int J, in
 }
 
 // D = A_JJ - L_J L_J^T (lower part) for the 4 rows J..J+3 alone.
-template <int U, class Acc>
-__device__ __forceinline__ void lane_diag(const Acc& M, int n, int J, const int (&jr)[4], double (&d)[4][4]) {
+template <int U, class Acc, class Y>
+__device__ __forceinline__ void lane_diag(const Acc& M, int n, int J, const int (&jr)[4], double (&d)[4][4],
+                                          const Y& ysk, int k) {
 #pragma unroll
     for (int c = 0; c < 4; c++) {
         double col[4];
         M.template strip<4>(J, jr[c], n, col);  // rows above c are read but not used
 #pragma unroll
         for (int r = c; r < 4; r++) d[r][c] = col[r];
+    }
+    if (Y::active) {
+#pragma unroll U
+        for (int p = 0; p < k; p++) {
+            double l[4];
+            ysk.template strip<4>(J, p, n, l);
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c <= r; c++) d[r][c] = fma(l[r], l[c], d[r][c]);
+        }
     }
 #pragma unroll U
     for (int pp = 0; pp < J; pp++) {
@@ -229,9 +296,9 @@ __device__ __forceinline__ void lane_diag(const Acc& M, int n, int J, const int 
 
 // Rows J..J+7 in one pass: D as above and E = A(J+4:J+8, J:J+4) - L(J+4:J+8, 0:J) L_J^T,
 // both from one 8-row strip per k step.
-template <int U, class Acc>
+template <int U, class Acc, class Y>
 __device__ __forceinline__ void lane_diag_under(const Acc& M, int n, int J, const int (&jr)[4], double (&d)[4][4],
-                                                double (&e)[4][4]) {
+                                                double (&e)[4][4], const Y& ysk, int k) {
 #pragma unroll
     for (int c = 0; c < 4; c++) {
         double col[8];
@@ -240,6 +307,21 @@ __device__ __forceinline__ void lane_diag_under(const Acc& M, int n, int J, cons
         for (int r = c; r < 4; r++) d[r][c] = col[r];
 #pragma unroll
         for (int r = 0; r < 4; r++) e[r][c] = col[4 + r];
+    }
+    if (Y::active) {
+#pragma unroll U
+        for (int p = 0; p < k; p++) {
+            double l[8];
+            ysk.template strip<8>(J, p, n, l);
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c <= r; c++) d[r][c] = fma(l[r], l[c], d[r][c]);
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) e[r][c] = fma(l[4 + r], l[c], e[r][c]);
+        }
     }
 #pragma unroll U
     for (int pp = 0; pp < J; pp++) {
@@ -287,8 +369,8 @@ __device__ __forceinline__ int chol_edge(double (&d)[4][4], double (&rinv)[4], i
 
 // Factor one problem in place through the accessor, with row blocks of R (4 or 8) and the
 // k loops unrolled U times.  Returns info (0 or 1-based column).
-template <int R, int U, class Acc>
-__device__ __forceinline__ int potrf_lane(const Acc& M, int n) {
+template <int R, int U, class Acc, class Y = NoSyrk>
+__device__ __forceinline__ int potrf_lane(const Acc& M, int n, const Y& ysk = Y(), int k = 0) {
     for (int J = 0; J < n; J += 4) {
         const int jb = imin(4, n - J);
         const bool under = R == 8 && J + 4 < n;  // the 8-row first block applies
@@ -297,9 +379,9 @@ __device__ __forceinline__ int potrf_lane(const Acc& M, int n) {
         for (int r = 0; r < 4; r++) jr[r] = imin(J + r, n - 1);
         double d[4][4], e[4][4], rinv[4];
         if (under) {
-            lane_diag_under<U>(M, n, J, jr, d, e);
+            lane_diag_under<U>(M, n, J, jr, d, e, ysk, k);
         } else {
-            lane_diag<U>(M, n, J, jr, d);
+            lane_diag<U>(M, n, J, jr, d, ysk, k);
         }
         const int f = chol_edge(d, rinv, jb);
         if (f) return J + f;
@@ -323,9 +405,9 @@ __device__ __forceinline__ int potrf_lane(const Acc& M, int n) {
             I += 4;
         }
         if (R == 8) {  // R-row blocks while more than 4 rows remain, then a 4-row tail
-            for (; I + 4 < n; I += R) lane_block<R, U>(M, n, I, J, jb, jr, d, rinv);
+            for (; I + 4 < n; I += R) lane_block<R, U>(M, n, I, J, jb, jr, d, rinv, ysk, k);
         }
-        for (; I < n; I += 4) lane_block<4, U>(M, n, I, J, jb, jr, d, rinv);
+        for (; I < n; I += 4) lane_block<4, U>(M, n, I, J, jb, jr, d, rinv, ysk, k);
     }
     return 0;
 }

@@ -122,7 +122,8 @@ def test_dpotrf_and_dpotrs_arguments(lib):
     assert lib.bf_dpotrf(b"L", -1, 1, 4, NULL, NULL) == -2
     assert lib.bf_dpotrf(b"L", 4, NULL, 4, NULL, NULL) == -3
     assert lib.bf_dpotrf(b"L", 4, 1, 3, NULL, NULL) == -4
-    assert lib.bf_dpotrf(b"U", 4, 1, 4, NULL, NULL) == lib.ERR_NOT_SUPPORTED
+    assert lib.bf_dpotrf(b"U", 4, 1, 3, NULL, NULL) == -4  # uplo 'U' is checked like 'L'
+    assert lib.bf_dpotrf(b"U", 0, NULL, 1, NULL, NULL) == 0   # n = 0: nothing launched
     assert lib.bf_dpotrf_strided_batched(b"L", 4, 1, 4, 15, NULL, 2, NULL) == -5
     assert lib.bf_dpotrf_strided_batched(b"L", 4, 1, 4, 16, NULL, -1, NULL) == -7
     assert lib.bf_dpotrf_strided_batched(b"L", 0, NULL, 1, 0, NULL, 5, NULL) == 0  # n = 0, no info

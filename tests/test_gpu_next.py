@@ -1,0 +1,266 @@
+"""GPU parity of dsyrk, the fused dsyrk + dpotrf, dtrmm, upper dpotrf / dpotrs and the
+square-root Riccati recursion against the CPU oracle.
+
+Every case runs the CUDA library through its C ABI (via the thin Python binding) on seeded
+inputs and compares with the oracle on the same bytes.  Tolerance: normwise relative error
+per problem <= 1e-13 for one routine call (the bar of the other FP64 tests); the Riccati
+recursion chains 10 dependent stages of dtrmm + dsyrk + dpotrf, each within 1e-13, so its
+factors are held to 1e-12.  Integer-valued inputs (dsyrk, dtrmm) must match bit for bit.
+Sentinels: padding rows and the triangles a routine must not touch hold NaN and must come
+back untouched.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import bfsynth
+from bfhelp import forced, gpu, host, lower_part, normwise
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-13
+TOL_RICCATI = 1e-12
+
+
+@pytest.fixture(scope="module")
+def bf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from bfhelp import build_lib
+    m = build_lib()
+    m.reset_table()
+    return m
+
+
+def batch_for(n):
+    return 3 if n >= 128 else (9 if n >= 48 else 37)
+
+
+def tri_mask(n, uplo):
+    """(ncols, ld) mask of the stored triangle of an n x n matrix."""
+    M = np.tril(np.ones((n, n), bool)) if uplo == "L" else np.triu(np.ones((n, n), bool))
+    return M.T  # element (i, j) lives at [j, i]
+
+
+def rnd(shape, seed, integer=False):
+    g = np.random.default_rng(seed)
+    return g.integers(-3, 4, size=shape).astype(np.float64) if integer else g.standard_normal(shape)
+
+
+# ----------------------------------------------------------------------------- dsyrk
+@pytest.mark.parametrize("uplo,trans", list(itertools.product("LU", "NT")))
+@pytest.mark.parametrize("n", [1, 3, 4, 5, 13, 24, 33, 64, 100, 130])
+def test_dsyrk(bf, oracle, uplo, trans, n):
+    k = max(1, (n * 2) // 3)
+    batch = batch_for(n)
+    rows, cols = (n, k) if trans == "N" else (k, n)
+    A = np.full((batch, cols, rows + 2), np.nan)
+    A[:, :, :rows] = rnd((batch, cols, rows), 10 + n)
+    mask = tri_mask(n, uplo)
+    C = np.full((batch, n, n + 3), np.nan)
+    C[:, :, :n] = np.where(mask, rnd((batch, n, n), 20 + n), np.nan)  # other triangle: sentinel
+    for alpha, beta in ((1.0, 1.0), (-0.5, 2.0), (1.0, 0.0), (2.0, 1.0)):
+        Cin = C.copy()
+        if beta == 0.0:
+            Cin[:, :, :n] = np.nan  # beta = 0: C is not read
+        ref = oracle.dsyrk(uplo, trans, n, k, alpha, A, beta, Cin)
+        Cg = gpu(Cin)
+        bf.dsyrk(uplo, trans, alpha, gpu(A), beta, Cg, n=n, k=k)
+        out = host(Cg)
+        got, want = np.where(mask, out[:, :, :n], 0.0), np.where(mask, ref[:, :, :n], 0.0)
+        assert normwise(got, want, n) <= TOL, (alpha, beta)
+        assert np.isnan(out[:, :, :n][:, ~mask]).all() and np.isnan(out[:, :, n:]).all()
+
+
+@pytest.mark.parametrize("uplo,trans", list(itertools.product("LU", "NT")))
+def test_dsyrk_integer_bit_exact_and_alpha_zero(bf, oracle, uplo, trans):
+    n, k, batch = 21, 10, 5
+    rows, cols = (n, k) if trans == "N" else (k, n)
+    A = rnd((batch, cols, rows), 3, integer=True)
+    C = rnd((batch, n, n), 4, integer=True)
+    ref = oracle.dsyrk(uplo, trans, n, k, 1.0, A, 1.0, C)
+    Cg = gpu(C)
+    bf.dsyrk(uplo, trans, 1.0, gpu(A), 1.0, Cg, n=n, k=k)
+    mask = tri_mask(n, uplo)
+    np.testing.assert_array_equal(host(Cg)[:, mask], ref[:, mask])
+    Cg = gpu(C)
+    bf.dsyrk(uplo, trans, 0.0, gpu(np.full_like(A, np.nan)), 3.0, Cg, n=n, k=k)  # A not read
+    np.testing.assert_array_equal(host(Cg)[:, mask], 3.0 * C[:, mask])
+
+
+# ----------------------------------------------------------------------------- dsyrk + dpotrf
+SP_VARIANTS = [("lane4", 0, 64, 0, 4, 2), ("lane8", 0, 64, 0, 8, 2), ("lane8u1", 0, 128, 0, 8, 1),
+               ("blocked16", 2, 0, 16, 0, 0)]
+
+
+@pytest.mark.parametrize("vname,variant,T,NB,R,U", SP_VARIANTS, ids=[v[0] for v in SP_VARIANTS])
+@pytest.mark.parametrize("n", [1, 5, 12, 16, 24, 33, 48, 64, 96, 130])
+def test_dsyrk_dpotrf(bf, oracle, vname, variant, T, NB, R, U, n):
+    batch = batch_for(n)
+    k = max(1, n // 2)
+    for pad in (0, 3):
+        A = np.full((batch, k, n + 1), np.nan)
+        A[:, :, :n] = rnd((batch, k, n), 30 + n + pad)
+        S = bfsynth.spd_batch(batch, n, n + pad, 40 + n + pad).numpy()
+        for j in range(n):
+            S[:, j, :j] = np.nan  # strict upper triangle: never read, never written
+        F, info = oracle.dsyrk_dpotrf_l(n, k, A, S)
+        assert (info == 0).all()
+        Sg = gpu(S)
+        with forced(bf, bf.ROUTINE_DPOTRF, -1, variant, T, NB, R, U):
+            ig = bf.dsyrk_dpotrf(gpu(A), Sg, n=n, k=k)
+        out = host(Sg)
+        assert (host(ig) == 0).all()
+        assert normwise(lower_part(out, n), lower_part(F, n), n) <= TOL
+        for j in range(n):
+            assert np.isnan(out[:, j, :j]).all()
+        assert np.isnan(out[:, :, n:]).all()
+
+
+def test_dsyrk_dpotrf_failures(bf, oracle):
+    for n in (5, 40):
+        batch, k = 7, 3
+        A = rnd((batch, k, n), 50 + n)
+        S = bfsynth.spd_batch(batch, n, n, 60 + n).numpy()
+        S[2, 2, 2] = -1e3 * n  # problem 2 fails at column 3 despite the A A^T term
+        S[5, n - 1, n - 1] = np.nan
+        F, info = oracle.dsyrk_dpotrf_l(n, k, A, S)
+        Sg = gpu(S)
+        ig = host(bf.dsyrk_dpotrf(gpu(A), Sg, n=n, k=k))
+        np.testing.assert_array_equal(ig, info)
+        ok = info == 0
+        assert normwise(lower_part(host(Sg)[ok], n), lower_part(F[ok], n), n) <= TOL
+
+
+# ----------------------------------------------------------------------------- dtrmm
+@pytest.mark.parametrize("side,uplo,trans,diag", list(itertools.product("LR", "LU", "NT", "NU")))
+def test_dtrmm_all_cases(bf, oracle, side, uplo, trans, diag):
+    for m, n in ((1, 1), (5, 3), (13, 17), (33, 24), (64, 40)):
+        k = m if side == "L" else n
+        batch = 11
+        A = np.full((batch, k, k + 1), np.nan)
+        A[:, :, :k] = rnd((batch, k, k), 70 + m + n)
+        mask = tri_mask(k, uplo)
+        A[:, :, :k] = np.where(mask, A[:, :, :k], np.nan)  # the other triangle is never read
+        if diag == "U":
+            for j in range(k):
+                A[:, j, j] = np.nan  # nor the unit diagonal
+        B = np.full((batch, n, m + 2), np.nan)
+        B[:, :, :m] = rnd((batch, n, m), 80 + m + n)
+        ref = oracle.dtrmm(side, uplo, trans, diag, m, n, 1.5, A, B)
+        Bg = gpu(B)
+        bf.dtrmm(side, uplo, trans, diag, 1.5, gpu(A), Bg, m=m, n=n)
+        out = host(Bg)
+        assert normwise(out, ref, m) <= TOL, (m, n)
+        assert np.isnan(out[:, :, m:]).all()
+
+
+@pytest.mark.parametrize("side", "LR")
+def test_dtrmm_integer_bit_exact_and_alpha_zero(bf, oracle, side):
+    m, n, batch = 19, 14, 6
+    k = m if side == "L" else n
+    A = rnd((batch, k, k), 90, integer=True)
+    B = rnd((batch, n, m), 91, integer=True)
+    for uplo, trans in itertools.product("LU", "NT"):
+        ref = oracle.dtrmm(side, uplo, trans, "N", m, n, 1.0, A, B)
+        Bg = gpu(B)
+        bf.dtrmm(side, uplo, trans, "N", 1.0, gpu(A), Bg, m=m, n=n)
+        np.testing.assert_array_equal(host(Bg), ref)
+    Bg = gpu(B)
+    bf.dtrmm(side, "L", "N", "N", 0.0, gpu(np.full_like(A, np.nan)), Bg, m=m, n=n)
+    np.testing.assert_array_equal(host(Bg), np.zeros_like(B))
+
+
+# ----------------------------------------------------------------------------- dpotrf / dpotrs upper
+POTRF_U = [("direct4", 0, 64, 0, 4, 2), ("direct8", 0, 64, 0, 8, 2), ("packed", 1, 64, 0, 0, 0),
+           ("blocked8", 2, 0, 8, 0, 0), ("blocked32", 2, 0, 32, 0, 0)]
+
+
+@pytest.mark.parametrize("vname,variant,T,NB,R,U", POTRF_U, ids=[v[0] for v in POTRF_U])
+@pytest.mark.parametrize("n", [1, 3, 4, 7, 12, 16, 24, 33, 64, 100])
+def test_dpotrf_upper(bf, oracle, vname, variant, T, NB, R, U, n):
+    if variant == 1 and n > 16:
+        pytest.skip("packed lane Cholesky holds whole problems in shared memory (small n)")
+    batch = batch_for(n)
+    for pad in (0, 3):
+        S = bfsynth.spd_batch(batch, n, n + pad, 100 + n + pad).numpy()
+        for j in range(n):
+            S[:, j, j + 1:n] = np.nan  # strict lower triangle: never read, never written
+        Uo, info = oracle.dpotrf_u(S, n=n)
+        assert (info == 0).all()
+        Sg = gpu(S)
+        with forced(bf, bf.ROUTINE_DPOTRF, -1, variant, T, NB, R, U):
+            ig = bf.dpotrf(Sg, n=n, uplo="U")
+        out = host(Sg)
+        assert (host(ig) == 0).all()
+        up = tri_mask(n, "U")
+        assert normwise(np.where(up, out[:, :, :n], 0), np.where(up, Uo[:, :, :n], 0), n) <= TOL
+        for j in range(n):
+            assert np.isnan(out[:, j, j + 1:n]).all()
+        assert np.isnan(out[:, :, n:]).all()
+
+
+def test_dpotrf_upper_failures_and_dpotrs(bf, oracle):
+    n, batch = 30, 8
+    S = bfsynth.spd_batch(batch, n, n, 123).numpy()
+    S[3, 4, 4] = -50.0 * n
+    Uo, info = oracle.dpotrf_u(S)
+    Sg = gpu(S)
+    np.testing.assert_array_equal(host(bf.dpotrf(Sg, uplo="U")), info)
+    # solve with the upper factor: U^T U X = B
+    good = np.nonzero(info == 0)[0]
+    Sg = gpu(S[good].copy())
+    bf.dpotrf(Sg, uplo="U")
+    B = rnd((len(good), 3, n), 124)
+    Xg = gpu(B)
+    bf.dpotrs(Sg, Xg, n=n, nrhs=3, uplo="U")
+    L, _ = oracle.dpotrf_l(np.ascontiguousarray(np.transpose(S[good], (0, 2, 1))))  # A symmetric: lower = upper^T
+    Xo = oracle.dpotrs_l(L, B, n, 3)
+    assert normwise(host(Xg), Xo, n) <= TOL
+
+
+# ----------------------------------------------------------------------------- Riccati
+def riccati_inputs(batch, N, nx, nu, seed):
+    g = np.random.default_rng(seed)
+    m = nx + nu
+    A = g.standard_normal((batch, N, nx, nx)) / np.sqrt(nx)
+    B = g.standard_normal((batch, N, nx, nu)) / np.sqrt(nx)
+    G = g.standard_normal((batch, N, m, m))
+    RSQ = G @ np.swapaxes(G, -1, -2) + m * np.eye(m)
+    H = g.standard_normal((batch, nx, nx))
+    QN = H @ np.swapaxes(H, -1, -2) + nx * np.eye(nx)
+    BAt = np.concatenate([np.swapaxes(B, -1, -2), np.swapaxes(A, -1, -2)], axis=-2)  # (batch, N, m, nx)
+    # column-major (ncols, ld) layouts
+    return (np.ascontiguousarray(np.swapaxes(BAt, -1, -2)), np.ascontiguousarray(np.swapaxes(RSQ, -1, -2)),
+            np.ascontiguousarray(np.swapaxes(QN, -1, -2)))
+
+
+@pytest.mark.parametrize("fused", [True, False], ids=["fused", "blas"])
+@pytest.mark.parametrize("nx,nu", [(8, 4), (24, 12), (40, 20)])
+def test_riccati(bf, oracle, fused, nx, nu):
+    N, batch = 10, 24
+    BAt, RSQ, QN = riccati_inputs(batch, N, nx, nu, 7 * nx + nu)
+    Fo, info_o = oracle.riccati(BAt, RSQ, QN, nx, nu)
+    assert (info_o == 0).all()
+    Fg, ig = bf.riccati(gpu(BAt), gpu(RSQ), gpu(QN), nx, nu, fused=fused)
+    Fg, ig = host(Fg), host(ig)
+    assert (ig == 0).all()
+    m = nx + nu
+    for s in range(N + 1):
+        size = nx if s == N else m
+        got, want = lower_part(Fg[:, s], size), lower_part(Fo[:, s], size)
+        assert normwise(got, want, size) <= TOL_RICCATI, s
+
+
+def test_riccati_failure_stage(bf, oracle):
+    N, nx, nu, batch = 6, 8, 4, 5
+    BAt, RSQ, QN = riccati_inputs(batch, N, nx, nu, 99)
+    RSQ[2, 3, 1, 1] = -1e4  # problem 2 fails at stage 3, column 2
+    QN[4, 0, 0] = -1.0      # problem 4 fails in the terminal factorisation, column 1
+    Fo, info_o = oracle.riccati(BAt, RSQ, QN, nx, nu)
+    assert info_o[2] == 3002 and info_o[4] == 1000 * N + 1
+    for fused in (True, False):
+        _, ig = bf.riccati(gpu(BAt), gpu(RSQ), gpu(QN), nx, nu, fused=fused)
+        np.testing.assert_array_equal(host(ig), info_o)
