@@ -705,7 +705,8 @@ def precision_form(bf, torch, dev, rank, batch=16384, n=128):
 
 
 def next_rows(bf, torch, dev, peak):
-    """The routines beyond the sweep: dsyrk (ln, ut), dtrmm (rlnn, llnn), dpotrf 'U', the fused
+    """The routines beyond the sweep: dsyrk (ln, ut), dtrmm (rlnn, llnn), dpotrf 'U', dgetrf, skinny
+    dgemm_nt, the fused
     dsyrk + dpotrf against its two calls, and the square-root Riccati recursion (section 5) with the
     fused routine against dsyrk + dpotrf; GFLOP/s and the fraction of the FP64 peak."""
     import bfsynth
@@ -734,9 +735,24 @@ def next_rows(bf, torch, dev, peak):
         S = S0.clone()
         ms = _events_ms(torch, lambda: bf.dpotrf(S, uplo="U"), before=lambda: S.copy_(S0))
         row["dpotrf_u"] = rate(b1 * (n ** 3 / 3 + n ** 2 / 2 + n / 6), ms)
+        if n <= 64:  # dgetrf on the same batch (LAPACK's flop count 2n^3/3 - n^2/2 + 5n/6)
+            ipiv = torch.empty(b1, n, dtype=torch.int32, device=dev)
+            info = torch.empty(b1, dtype=torch.int32, device=dev)
+            ms = _events_ms(torch, lambda: bf.dgetrf(S, ipiv=ipiv, info=info), before=lambda: S.copy_(S0))
+            row["dgetrf"] = rate(b1 * (2 * n ** 3 / 3 - n ** 2 / 2 + 5 * n / 6), ms)
+            del ipiv, info
         del S, S0
         torch.cuda.empty_cache()
         out[f"n{n}"] = row
+    # skinny dgemm_nt (one dimension 4): C (m x n) += A (m x k) B^T (B n x k), ~2 GiB of operands
+    for m, n, k in ((4, 256, 256), (256, 4, 256)):
+        b = (1 << 31) // (8 * (m * k + n * k + m * n))
+        A = bfsynth.randn_batch(b, m, k, m, 38, device=dev)
+        B = bfsynth.randn_batch(b, n, k, n, 39, device=dev)
+        C = bfsynth.randn_batch(b, m, n, m, 40, device=dev)
+        out[f"dgemm_nt_m{m}_n{n}_k{k}"] = dict(batch=b, **rate(2.0 * b * m * n * k, _events_ms(
+            torch, lambda: bf.dgemm("N", "T", 1.0, A, B, 1.0, C, m=m, n=n, k=k))))
+        del A, B, C
     for n in (8, 32):
         b = bfsynth.sweep_batch(n, n, 1) // 2
         k = n // 2

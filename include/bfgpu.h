@@ -161,6 +161,34 @@ int bf_dtrmm_batched(char side, char uplo, char transa, char diag, int m, int n,
                      bf_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* dgetrf (section 3.1 "dgetrf"): LU factorisation with partial (row)        */
+/* pivoting, P A = L U, of square matrices (m == n; m != n returns           */
+/* BF_ERR_NOT_SUPPORTED).  L (unit lower, below the diagonal) and U (upper)  */
+/* overwrite A.  ipiv (device, n ints per problem, stride strideIpiv):       */
+/* row j was interchanged with row ipiv[j] - 1 (1-based, as LAPACK); the     */
+/* pivot is the first row of largest magnitude.  info (device, may be        */
+/* NULL): 0, or j when U(j-1, j-1) is exactly zero (the factorisation still   */
+/* completes).                                                               */
+/* ------------------------------------------------------------------------ */
+int bf_dgetrf(int m, int n, double* A, int lda, int* ipiv, int* info, bf_stream_t stream);
+
+int bf_dgetrf_strided_batched(int m, int n, double* A, int lda, long long strideA, int* ipiv,
+                              long long strideIpiv, int* info, int batch, bf_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* dgetrs: solve op(A) X = B with the factors and pivots of bf_dgetrf:       */
+/* 'N': the interchanges, L Y = P B, U X = Y;  'T': U^T Y = B, L^T Z = Y,    */
+/* then the interchanges in reverse.  B (n x nrhs, ldb >= max(1, n)) is      */
+/* overwritten by X.                                                         */
+/* ------------------------------------------------------------------------ */
+int bf_dgetrs(char trans, int n, int nrhs, const double* A, int lda, const int* ipiv, double* B, int ldb,
+              bf_stream_t stream);
+
+int bf_dgetrs_strided_batched(char trans, int n, int nrhs, const double* A, int lda, long long strideA,
+                              const int* ipiv, long long strideIpiv, double* B, int ldb, long long strideB,
+                              int batch, bf_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Riccati recursion, square-root form (section 5 "Riccati recursion"), for   */
 /* a batch of independent problems of N stages, nx states, nu controls,      */
 /* m = nu + nx.  Per problem (column-major, all leading dimensions m except  */

@@ -76,6 +76,10 @@ _SIGS = {
     "bf_dtrmm": [_c, _c, _c, _c, _i, _i, _d, _vp, _i, _vp, _i, _vp],
     "bf_dtrmm_strided_batched": [_c, _c, _c, _c, _i, _i, _d, _vp, _i, _ll, _vp, _i, _ll, _i, _vp],
     "bf_dtrmm_batched": [_c, _c, _c, _c, _i, _i, _d, _vp, _i, _vp, _i, _i, _vp],
+    "bf_dgetrf": [_i, _i, _vp, _i, _vp, _vp, _vp],
+    "bf_dgetrf_strided_batched": [_i, _i, _vp, _i, _ll, _vp, _ll, _vp, _i, _vp],
+    "bf_dgetrs": [_c, _i, _i, _vp, _i, _vp, _vp, _i, _vp],
+    "bf_dgetrs_strided_batched": [_c, _i, _i, _vp, _i, _ll, _vp, _ll, _vp, _i, _ll, _i, _vp],
     "bf_riccati_workspace_bytes": [_i, _i, _i],
     "bf_riccati_strided_batched": [_i, _i, _i, _vp, _ll, _vp, _ll, _vp, _ll, _vp, _ll, _vp, _i, _vp,
                                    ctypes.c_size_t, _i, _vp],
@@ -257,6 +261,35 @@ def dtrmm(side: str, uplo: str, transa: str, diag: str, alpha: float, A, B, m=No
     _check("bf_dtrmm_strided_batched", bf_dtrmm_strided_batched(
         _ch(side), _ch(uplo), _ch(transa), _ch(diag), m, n, alpha, _ptr(A), ldA, sA if bA > 1 else 0,
         _ptr(B), ldB, sB, bB, _stream(stream)))
+    return B
+
+
+def dgetrf(A, n=None, ipiv=None, info=None, stream=None):
+    """LU with partial pivoting of every (square) problem in place; returns (ipiv, info).
+
+    ipiv: (batch, n) int32, 1-based row interchanges; info: (batch,) int32.
+    """
+    import torch
+    bA, cA, ldA, sA = _batch_dims(A)
+    n = cA if n is None else n
+    if ipiv is None:
+        ipiv = torch.empty(bA, max(n, 1), dtype=torch.int32, device=A.device)
+    if info is None:
+        info = torch.empty(bA, dtype=torch.int32, device=A.device)
+    _check("bf_dgetrf_strided_batched", bf_dgetrf_strided_batched(
+        n, n, _ptr(A), ldA, sA, _ptr(ipiv), ipiv.shape[-1], _ptr(info), bA, _stream(stream)))
+    return ipiv, info
+
+
+def dgetrs(trans: str, LU, ipiv, B, n=None, nrhs=None, stream=None):
+    """Solve op(A) X = B with dgetrf's factors and pivots (in place on B)."""
+    bL, cL, ldL, sL = _batch_dims(LU)
+    bB, cB, ldB, sB = _batch_dims(B)
+    n = cL if n is None else n
+    nrhs = cB if nrhs is None else nrhs
+    _check("bf_dgetrs_strided_batched", bf_dgetrs_strided_batched(
+        _ch(trans), n, nrhs, _ptr(LU), ldL, sL, _ptr(ipiv), ipiv.shape[-1], _ptr(B), ldB, sB, bB,
+        _stream(stream)))
     return B
 
 

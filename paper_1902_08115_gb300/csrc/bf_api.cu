@@ -361,6 +361,73 @@ int bf_dtrmm_batched(char side, char uplo, char transa, char diag, int m, int n,
                      mat_array((const double* const*)Barray, 0), Barray, ldb, 0, batch, false, stream, pos);
 }
 
+// ------------------------------------------------------------------------ dgetrf / dgetrs
+static int getrf_impl(int m, int n, double* A, int lda, long long strideA, int* ipiv, long long strideIpiv,
+                      int* info, int batch, bool strided, bf_stream_t stream, const int* pos) {
+    // pos: m, n, A, lda, strideA, ipiv, strideIpiv, batch
+    if (m < 0) return -pos[0];
+    if (n < 0) return -pos[1];
+    if (lda < imax1(m)) return -pos[3];
+    if (pos[7] && batch < 0) return -pos[7];
+    if (strided && batch > 1 && strideA < (long long)lda * n) return -pos[4];
+    const int mn = m < n ? m : n;
+    if (strided && batch > 1 && strideIpiv < mn) return -pos[6];
+    const bool work = mn > 0 && batch > 0;
+    if (work && !A) return -pos[2];
+    if (work && !ipiv) return -pos[5];
+    if (m != n) return BF_ERR_NOT_SUPPORTED;
+    if (batch <= 0) return 0;
+    return status(launch_dgetrf(n, mat_strided(A, strideA), lda, ipiv, strided ? strideIpiv : n, info, batch,
+                                (cudaStream_t)stream));
+}
+
+int bf_dgetrf(int m, int n, double* A, int lda, int* ipiv, int* info, bf_stream_t stream) {
+    static const int pos[8] = {1, 2, 3, 4, 0, 5, 0, 0};
+    return getrf_impl(m, n, A, lda, 0, ipiv, 0, info, 1, false, stream, pos);
+}
+
+int bf_dgetrf_strided_batched(int m, int n, double* A, int lda, long long strideA, int* ipiv, long long strideIpiv,
+                              int* info, int batch, bf_stream_t stream) {
+    static const int pos[8] = {1, 2, 3, 4, 5, 6, 7, 9};
+    if (strideA < 0) return -5;
+    return getrf_impl(m, n, A, lda, strideA, ipiv, strideIpiv, info, batch, true, stream, pos);
+}
+
+static int getrs_impl(char trans, int n, int nrhs, const double* A, int lda, long long strideA, const int* ipiv,
+                      long long strideIpiv, double* B, int ldb, long long strideB, int batch, bool strided,
+                      bf_stream_t stream, const int* pos) {
+    // pos: trans, n, nrhs, A, lda, ipiv, B, ldb, strideB, batch
+    if (!(is_n(trans) || is_t(trans))) return -pos[0];
+    if (n < 0) return -pos[1];
+    if (nrhs < 0) return -pos[2];
+    if (lda < imax1(n)) return -pos[4];
+    if (ldb < imax1(n)) return -pos[7];
+    if (pos[9] && batch < 0) return -pos[9];
+    if (strided && batch > 1 && strideB < (long long)ldb * nrhs) return -pos[8];
+    const bool work = n > 0 && nrhs > 0 && batch > 0;
+    if (work && !A) return -pos[3];
+    if (work && !ipiv) return -pos[5];
+    if (work && !B) return -pos[6];
+    if (!work) return 0;
+    return status(launch_dgetrs(is_t(trans) ? 1 : 0, n, nrhs, mat_strided(A, strideA), lda, ipiv,
+                                strided ? strideIpiv : n, mat_strided(B, strideB), ldb, batch, (cudaStream_t)stream));
+}
+
+int bf_dgetrs(char trans, int n, int nrhs, const double* A, int lda, const int* ipiv, double* B, int ldb,
+              bf_stream_t stream) {
+    static const int pos[10] = {1, 2, 3, 4, 5, 6, 7, 8, 0, 0};
+    return getrs_impl(trans, n, nrhs, A, lda, 0, ipiv, 0, B, ldb, 0, 1, false, stream, pos);
+}
+
+int bf_dgetrs_strided_batched(char trans, int n, int nrhs, const double* A, int lda, long long strideA,
+                              const int* ipiv, long long strideIpiv, double* B, int ldb, long long strideB, int batch,
+                              bf_stream_t stream) {
+    static const int pos[10] = {1, 2, 3, 4, 5, 7, 9, 10, 11, 12};
+    if (strideA < 0) return -6;
+    if (batch > 1 && strideIpiv < n) return -8;
+    return getrs_impl(trans, n, nrhs, A, lda, strideA, ipiv, strideIpiv, B, ldb, strideB, batch, true, stream, pos);
+}
+
 const char* bf_status_string(int s) {
     if (s == BF_SUCCESS) return "success";
     if (s == BF_ERR_CUDA) return "a CUDA launch failed";

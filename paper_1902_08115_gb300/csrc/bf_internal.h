@@ -109,6 +109,12 @@ cudaError_t launch_dsyrk_dpotrf(int n, int k, MatRef A, int lda, MatRef C, int l
 cudaError_t launch_dtrmm(int side, int uplo, int trans, int unit, int m, int n, double alpha, MatRef A, int lda,
                          MatRef B, int ldb, long long batch, int MR, cudaStream_t s);
 
+// LU with partial pivoting and its solve (bf_dgetrf.cu); ipiv: sipiv ints per problem, 1-based
+cudaError_t launch_dgetrf(int n, MatRef A, int lda, int* ipiv, long long sipiv, int* info, long long batch,
+                          cudaStream_t s);
+cudaError_t launch_dgetrs(int trans, int n, int nrhs, MatRef A, int lda, const int* ipiv, long long sipiv, MatRef B,
+                          int ldb, long long batch, cudaStream_t s);
+
 // Configuration choice (the size switch), in bf_tune.cu.
 GemmConfig choose_gemm(bool ta, bool tb, int m, int n, int k, int lda, long long batch);
 TrsmConfig choose_trsm(int side, int uplo, int trans, int unit, int m, int n, long long batch);

@@ -90,6 +90,30 @@ def test_dsyrk_integer_bit_exact_and_alpha_zero(bf, oracle, uplo, trans):
     np.testing.assert_array_equal(host(Cg)[:, mask], 3.0 * C[:, mask])
 
 
+# ----------------------------------------------------------------------------- skinny dgemm
+@pytest.mark.parametrize("variant", [0, 1], ids=["direct", "packed"])
+@pytest.mark.parametrize("ta,tb", list(itertools.product("NT", "NT")))
+def test_dgemm_rectangular_and_skinny(bf, oracle, variant, ta, tb):
+    code = (2 if ta == "T" else 0) + (1 if tb == "T" else 0)
+    for m, n, k in ((4, 256, 64), (256, 4, 64), (4, 4, 256), (128, 64, 4), (300, 4, 37), (1, 97, 5)):
+        batch = 4
+        rA, cA = (m, k) if ta == "N" else (k, m)
+        rB, cB = (k, n) if tb == "N" else (n, k)
+        A = np.full((batch, cA, rA + 1), np.nan)
+        A[:, :, :rA] = rnd((batch, cA, rA), m + n + k)
+        B = np.full((batch, cB, rB + 3), np.nan)
+        B[:, :, :rB] = rnd((batch, cB, rB), m + n + k + 1)
+        C = np.full((batch, n, m + 2), np.nan)
+        C[:, :, :m] = rnd((batch, n, m), m + n + k + 2)
+        ref = oracle.dgemm(ta, tb, m, n, k, -1.0, A, B, 1.0, C)
+        Cg = gpu(C)
+        with forced(bf, bf.ROUTINE_DGEMM, code, variant):
+            bf.dgemm(ta, tb, -1.0, gpu(A), gpu(B), 1.0, Cg, m=m, n=n, k=k)
+        out = host(Cg)
+        assert normwise(out, ref, m) <= TOL, (m, n, k)
+        assert np.isnan(out[:, :, m:]).all()
+
+
 # ----------------------------------------------------------------------------- dsyrk + dpotrf
 SP_VARIANTS = [("lane4", 0, 64, 0, 4, 2), ("lane8", 0, 64, 0, 8, 2), ("lane8u1", 0, 128, 0, 8, 1),
                ("blocked16", 2, 0, 16, 0, 0)]
@@ -219,6 +243,56 @@ def test_dpotrf_upper_failures_and_dpotrs(bf, oracle):
     L, _ = oracle.dpotrf_l(np.ascontiguousarray(np.transpose(S[good], (0, 2, 1))))  # A symmetric: lower = upper^T
     Xo = oracle.dpotrs_l(L, B, n, 3)
     assert normwise(host(Xg), Xo, n) <= TOL
+
+
+# ----------------------------------------------------------------------------- dgetrf / dgetrs
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 8, 13, 16, 24, 33, 48, 64, 96])
+def test_dgetrf(bf, oracle, n):
+    batch = batch_for(n)
+    for pad in (0, 3):
+        A = np.full((batch, n, n + pad), np.nan)
+        A[:, :, :n] = rnd((batch, n, n), 200 + n + pad)
+        LU, piv, info = oracle.dgetrf(A, m=n)
+        Ag = gpu(A)
+        pg, ig = bf.dgetrf(Ag, n=n)
+        pg, ig, out = host(pg), host(ig), host(Ag)
+        np.testing.assert_array_equal(ig, info)
+        np.testing.assert_array_equal(pg, piv)  # same pivots: generic matrices have no near ties
+        assert normwise(out, LU, n) <= TOL
+        assert np.isnan(out[:, :, n:]).all()
+
+
+def test_dgetrf_singular_and_permutation(bf, oracle):
+    n, batch = 9, 4
+    A = rnd((batch, n, n), 300)
+    A[1, 4, :] = 0.0                               # problem 1: column 4 zero -> info 5
+    A[2] = np.eye(n)[np.random.default_rng(1).permutation(n)]  # problem 2: a permutation matrix
+    A[3, :, :] = 0.0                               # problem 3: all zero -> info 1
+    LU, piv, info = oracle.dgetrf(A, m=n)
+    Ag = gpu(A)
+    pg, ig = bf.dgetrf(Ag)
+    np.testing.assert_array_equal(host(ig), info)
+    assert info[1] == 5 and info[3] == 1 and info[2] == 0
+    np.testing.assert_array_equal(host(pg), piv)
+    np.testing.assert_array_equal(host(Ag)[2], LU[2])  # integer-exact: no rounding happens
+
+
+@pytest.mark.parametrize("trans", "NT")
+@pytest.mark.parametrize("n", [1, 7, 32, 65])
+def test_dgetrs(bf, oracle, trans, n):
+    batch, r = 9, 3
+    A = rnd((batch, n, n), 400 + n) + 2 * np.eye(n)
+    B = np.full((batch, r, n + 1), np.nan)
+    B[:, :, :n] = rnd((batch, r, n), 500 + n)
+    LU, piv, info = oracle.dgetrf(A, m=n)
+    Xo = oracle.dgetrs(trans, LU, piv, B, n, r)
+    Ag = gpu(A)
+    pg, _ = bf.dgetrf(Ag)
+    Bg = gpu(B)
+    bf.dgetrs(trans, Ag, pg, Bg, n=n, nrhs=r)
+    out = host(Bg)
+    assert normwise(out, Xo, n) <= TOL
+    assert np.isnan(out[:, :, n:]).all()
 
 
 # ----------------------------------------------------------------------------- Riccati
