@@ -371,7 +371,8 @@ int bf_ragged_potrf_potrs_noalloc(int batch, const int* n_host, int nrhs, double
 /*   [n_lo, n_hi]  matrix order range (dgemm: max(m, n); dtrsm: order of A)   */
 /*   variant  BF_VARIANT_*                                                    */
 /*   p0..p3   dgemm: TM, TN, KC, P (super-tile rows/cols, k-slice, problems   */
-/*            per CTA; 0 = default); dtrsm: MR (4/8), P; dpotrf: T, NB,     */
+/*            per CTA; 0 = default); dtrsm: MR (4/8), P, CTAs per SM (1/2);  */
+/*            dpotrf: T, NB,                                                */
 /*            lane row-block height (4/8), lane k-loop unroll (1/2).        */
 /* Later entries take precedence.  bf_tune_clear removes all entries.         */
 /* bf_tune_query writes the configuration a call would use into out[5]:       */

@@ -48,6 +48,14 @@ def _time(torch, fn, reps=3):
     return best
 
 
+def _install(bf, entries):
+    """Replace the size-switch table by the given entries."""
+    bf.tune_clear()
+    for e in entries:
+        p = list(e["p"]) + [0] * (4 - len(e["p"]))
+        bf.tune_set(e["routine"], e["code"], e["lo"], e["hi"], e["variant"], *p[:4])
+
+
 def _gemm_candidates(n):
     cands = []
     tiles = [(0, 0)] if n <= 64 else [(0, 0), (32, 32), (48, 48), (64, 64), (n // 2 // 4 * 4, 64)]
@@ -83,7 +91,7 @@ def tune(quick=False, out=None, log=print):
         hi = orders[idx + 1] - 1 if idx + 1 < len(orders) else 1 << 20
         lo = n if idx else 1
         # ---- dgemm, four forms
-        b = max(1, min(bfsynth.sweep_batch(n, n, 3), BUDGET // (3 * n * n * 8)))
+        b = bfsynth.sweep_batch(n, n, 3)  # the sweep's batch (2 GiB of operands)
         A = bfsynth.randn_batch(b, n, n, n, 1, device=dev)
         B = bfsynth.randn_batch(b, n, n, n, 2, device=dev)
         C = bfsynth.randn_batch(b, n, n, n, 3, device=dev)
@@ -101,7 +109,7 @@ def tune(quick=False, out=None, log=print):
             log(f"dgemm {ta}{tb} n={n}: {best[1]} {gf:.0f} GFLOP/s")
         del A, B, C
         # ---- dtrsm: right-lower-T unit/non-unit, and the left-lower N/T of dpotrs
-        b = max(1, min(bfsynth.sweep_batch(n, n, 2), BUDGET // (2 * n * n * 8)))
+        b = bfsynth.sweep_batch(n, n, 2)  # wave quantization depends on the batch: tune at 2 GiB
         L = bfsynth.spd_batch(b, n, n, 4, device=dev)
         bf.tune_clear()
         bf.dpotrf(L, n=n)
@@ -111,18 +119,19 @@ def tune(quick=False, out=None, log=print):
             best = None
             for variant in (0, 1):
                 for MR in (4, 8):
-                    for P in ((0,) if variant == 0 else (0, 8, 16, 32)):
+                    for P, minb in (((0, 1), (0, 2)) if variant == 0 else ((0, 1), (8, 1), (16, 1), (32, 1))):
                         bf.tune_clear()
-                        bf.tune_set(bf.ROUTINE_DTRSM, code, 0, 1 << 30, variant, MR, P)
+                        bf.tune_set(bf.ROUTINE_DTRSM, code, 0, 1 << 30, variant, MR, P, minb)
                         cfg = bf.tune_query(bf.ROUTINE_DTRSM, code, n, n, 0, b)
                         if cfg[0] != variant:
                             continue  # not launchable in this form at this order
                         ms = _time(torch, lambda: bf.dtrsm(*args, 1.0, L, X, m=n, n=n))
                         if best is None or ms < best[0]:
-                            best = (ms, (variant, MR, P))
+                            best = (ms, (variant, MR, P, minb))
             fl = b * n ** 3
             entries.append(dict(routine=bf.ROUTINE_DTRSM, code=code, lo=lo, hi=hi, variant=best[1][0],
-                                p=[best[1][1], best[1][2], 0, 0], gflops=round(fl / best[0] / 1e6, 1), n=n))
+                                p=[best[1][1], best[1][2], best[1][3], 0], gflops=round(fl / best[0] / 1e6, 1),
+                                n=n))
             log(f"dtrsm {''.join(args)} n={n}: {best[1]} {fl / best[0] / 1e6:.0f} GFLOP/s")
         del L, X
         # ---- dpotrf, per leading-dimension parity (table code lda & 1)
@@ -139,7 +148,9 @@ def tune(quick=False, out=None, log=print):
                 cands += [(2, 128, NB, 0, 0) for NB in (8, 16, 32, 64) if NB < n]
             ms_copy = _time(torch, lambda: S.copy_(S0))
             for variant, T, NB, R, U in cands:
-                bf.tune_clear()
+                # the blocked form calls dtrsm and dgemm: time it with the entries measured so
+                # far installed, as every later call will run it
+                _install(bf, entries)
                 bf.tune_set(bf.ROUTINE_DPOTRF, code, 0, 1 << 30, variant, T, NB, R, U)
 
                 def run():

@@ -20,7 +20,7 @@
 //  * blocked (large n, small batches): right-looking with block NB, as a
 //    sequence of launches of the library's own kernels on sub-matrices --
 //    lane Cholesky of the NB x NB diagonal blocks, row-parallel trsm of the
-//    panel below, lower-only dgemm_nt trailing update.
+//    panel below, dsyrk trailing update on the triangle's tiles.
 //
 // info follows LAPACK: 0, or the 1-based column j whose pivot is not
 // positive (or NaN); the problem's factorisation stops there.
@@ -151,11 +151,9 @@ cudaError_t launch_dpotrf(int n, MatRef A, int lda, long long batch, int* info,
             e = launch_dtrsm(0, 1, 1, 0, jb, rest, 1.0, mat_sub(A, J, J, lda), lda,
                              mat_sub(A, J, J + jb, lda), lda, batch, tc, info, s);
             if (e != cudaSuccess) return e;
-            // trailing update (upper part only): A22 -= U12^T U12
-            MatRef P = mat_sub(A, J, J + jb, lda);
-            GemmConfig gc = choose_gemm(true, false, rest, rest, jb, lda, batch);
-            e = launch_dgemm(true, false, rest, rest, jb, -1.0, P, lda, P, lda, 1.0,
-                             mat_sub(A, J + jb, J + jb, lda), lda, batch, gc, TRI_UPPER, info, s);
+            // trailing update (upper triangle only, tiles of the triangle alone): A22 -= U12^T U12
+            e = launch_dsyrk(1, 1, rest, jb, -1.0, mat_sub(A, J, J + jb, lda), lda, 1.0,
+                             mat_sub(A, J + jb, J + jb, lda), lda, batch, s);
             if (e != cudaSuccess) return e;
             continue;
         }
@@ -164,11 +162,11 @@ cudaError_t launch_dpotrf(int n, MatRef A, int lda, long long batch, int* info,
         e = launch_dtrsm(1, 0, 1, 0, rest, jb, 1.0, mat_sub(A, J, J, lda), lda,
                          mat_sub(A, J + jb, J, lda), lda, batch, tc, info, s);
         if (e != cudaSuccess) return e;
-        // trailing update (lower part only): A22 -= L21 L21^T
-        MatRef P = mat_sub(A, J + jb, J, lda);
-        GemmConfig gc = choose_gemm(false, true, rest, rest, jb, lda, batch);
-        e = launch_dgemm(false, true, rest, rest, jb, -1.0, P, lda, P, lda, 1.0,
-                         mat_sub(A, J + jb, J + jb, lda), lda, batch, gc, 1, info, s);
+        // trailing update (lower triangle only, tiles of the triangle alone): A22 -= L21 L21^T;
+        // a problem that failed keeps being updated, harmlessly: its info is already set and
+        // its later columns are unspecified (LAPACK)
+        e = launch_dsyrk(0, 0, rest, jb, -1.0, mat_sub(A, J + jb, J, lda), lda, 1.0,
+                         mat_sub(A, J + jb, J + jb, lda), lda, batch, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

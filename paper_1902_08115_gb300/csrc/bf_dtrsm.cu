@@ -19,8 +19,10 @@
 
 namespace bf {
 
-template <int MR, bool PACKED>
-__global__ void __launch_bounds__(256)
+// MINB: CTAs of 256 threads the kernel is compiled to keep resident per SM (2 caps the
+// registers at 128).
+template <int MR, bool PACKED, bool UP, int MINB>
+__global__ void __launch_bounds__(256, MINB)
 dtrsm_rows_kernel(TrsmParams p) {
     extern __shared__ double smem[];
     const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -40,7 +42,7 @@ dtrsm_rows_kernel(TrsmParams p) {
             const int j = rem / n, i = rem - j * n;
             const long long qg = q0 + qq;
             double v = 0.0;
-            const bool inT = p.upper ? (i <= j) : (i >= j);
+            const bool inT = UP ? (i <= j) : (i >= j);
             if (qg < p.batch && inT && !(p.unit && i == j)) {
                 const double* Aq = p.A.ptr(qg);
                 v = p.et ? ldg(Aq + j + (long long)i * p.lda) : ldg(Aq + i + (long long)j * p.lda);
@@ -65,12 +67,12 @@ dtrsm_rows_kernel(TrsmParams p) {
     const double* Rs = PACKED ? (sR + (q - q0) * n) : nullptr;
 
     int rows[MR];
-    long long roff[MR];
+    int roff[MR];  // element offsets within the problem (a small matrix: 32 bits suffice)
 #pragma unroll
     for (int s = 0; s < MR; s++) {
         rows[s] = rr + p.tpp * s;
         const int rc = imin(rows[s], p.m - 1);
-        roff[s] = p.bt ? (long long)rc * p.ldb : rc;
+        roff[s] = p.bt ? rc * p.ldb : rc;
     }
     const long long cstep = p.bt ? 1 : p.ldb;  // R(r, j + 1) - R(r, j)
 
@@ -81,7 +83,7 @@ dtrsm_rows_kernel(TrsmParams p) {
 
     const int nblk = (n + 3) / 4;
     for (int bi = 0; bi < nblk; bi++) {
-        const int blk = p.upper ? bi : (nblk - 1 - bi);
+        const int blk = UP ? bi : (nblk - 1 - bi);
         const int J = blk * 4;
         const int jb = imin(4, n - J);
         double acc[MR][4];
@@ -98,8 +100,8 @@ dtrsm_rows_kernel(TrsmParams p) {
                 for (int c = 0; c < 4; c++) acc[s][c] *= p.alpha;
         }
         // dgemm loop over the already solved columns
-        const int pb = p.upper ? 0 : J + jb;
-        const int pe = p.upper ? J : n;
+        const int pb = UP ? 0 : J + jb;
+        const int pe = UP ? J : n;
 #pragma unroll 2
         for (int pp = pb; pp < pe; pp++) {
             double x[MR], tv[4];
@@ -118,7 +120,7 @@ dtrsm_rows_kernel(TrsmParams p) {
         for (int c = 0; c < 4; c++) {
 #pragma unroll
             for (int c2 = 0; c2 < 4; c2++) {
-                const bool need = p.upper ? (c2 < c) : (c2 > c);
+                const bool need = UP ? (c2 < c) : (c2 > c);
                 tb[c2][c] = (need && c < jb && c2 < jb) ? Tel(J + c2, J + c) : 0.0;
             }
             if (!p.unit) {
@@ -126,7 +128,7 @@ dtrsm_rows_kernel(TrsmParams p) {
                 else rinv[c] = (c < jb) ? 1.0 / Tel(J + c, J + c) : 1.0;
             }
         }
-        if (p.upper) {
+        if (UP) {
 #pragma unroll
             for (int c = 0; c < 4; c++) {
 #pragma unroll
@@ -160,10 +162,12 @@ dtrsm_rows_kernel(TrsmParams p) {
     }
 }
 
-template <int MR, bool PACKED>
-static cudaError_t launch_rows(const TrsmParams& p, long long threads, int block, size_t smem,
+template <int MR, bool PACKED, bool UP>
+static cudaError_t launch_rows3(const TrsmParams& p, long long threads, int block, size_t smem, int minb,
                                cudaStream_t s) {
-    auto kfn = dtrsm_rows_kernel<MR, PACKED>;
+    // the residency is a tuned choice: with few, large problems one more CTA per SM can
+    // decide whether the launch fits one wave (or how full its last wave is)
+    auto kfn = (!PACKED && minb == 2) ? dtrsm_rows_kernel<MR, PACKED, UP, 2> : dtrsm_rows_kernel<MR, PACKED, UP, 1>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -172,6 +176,13 @@ static cudaError_t launch_rows(const TrsmParams& p, long long threads, int block
     kfn<<<(unsigned)blocks, block, smem, s>>>(p);
     count_launch();
     return cudaGetLastError();
+}
+
+template <int MR, bool PACKED>
+static cudaError_t launch_rows(const TrsmParams& p, long long threads, int block, size_t smem, int minb,
+                               cudaStream_t s) {
+    return p.upper ? launch_rows3<MR, PACKED, true>(p, threads, block, smem, minb, s)
+                   : launch_rows3<MR, PACKED, false>(p, threads, block, smem, minb, s);
 }
 
 cudaError_t launch_dtrsm(int side, int uplo, int trans, int unit, int m, int n, double alpha,
@@ -200,12 +211,12 @@ cudaError_t launch_dtrsm(int side, int uplo, int trans, int unit, int m, int n, 
         int block = p.P * p.tpp;
         size_t smem = sizeof(double) * ((size_t)p.P * p.n * (p.n + 1) + (size_t)p.P * p.n);
         threads = ((batch + p.P - 1) / p.P) * (long long)block;
-        return MR == 8 ? launch_rows<8, true>(p, threads, block, smem, s)
-                       : launch_rows<4, true>(p, threads, block, smem, s);
+        return MR == 8 ? launch_rows<8, true>(p, threads, block, smem, 1, s)
+                       : launch_rows<4, true>(p, threads, block, smem, 1, s);
     }
     p.P = 1;
-    return MR == 8 ? launch_rows<8, false>(p, threads, 256, 0, s)
-                   : launch_rows<4, false>(p, threads, 256, 0, s);
+    return MR == 8 ? launch_rows<8, false>(p, threads, 256, 0, cfg.minb, s)
+                   : launch_rows<4, false>(p, threads, 256, 0, cfg.minb, s);
 }
 
 }  // namespace bf

@@ -41,6 +41,7 @@ struct TrsmConfig {
     int variant;  // VAR_DIRECT or VAR_PACKED
     int MR;       // rows of the right-hand side per thread (4 or 8)
     int P;        // problems per CTA (packed)
+    int minb;     // direct: 256-thread CTAs the kernel is compiled to keep per SM (1 or 2)
 };
 
 // Row-parallel triangular solve X T = alpha R (every row of R independent).

@@ -50,6 +50,10 @@ static void sanitize_gemm(GemmConfig& c, int m, int n, int k) {
     }
     const int tpp = (c.TM / 4) * (c.TN / 4);
     if (c.P < 1) c.P = 1;
+    // a table entry's P was measured on square tiles; a skinny problem's super-tile has far
+    // fewer threads, so keep at least 128 threads (whole warps) per CTA
+    while (c.P * tpp < 128 && (c.P + 1) * tpp <= 512) c.P++;
+    while ((c.P * tpp) % 32 != 0 && (c.P + 1) * tpp <= 512) c.P++;
     while (c.P > 1 && c.P * tpp > 512) c.P--;
     if (c.KC < 1 || c.KC > k) c.KC = k > 0 ? k : 1;
     if (c.variant == VAR_PACKED) {
@@ -110,11 +114,13 @@ TrsmConfig choose_trsm(int side, int uplo, int trans, int unit, int m, int n, lo
     c.variant = VAR_DIRECT;
     c.MR = rows >= 16 ? 8 : 4;
     c.P = 1;
+    c.minb = 1;
     TuneEntry e;
     if (lookup(BF_ROUTINE_DTRSM, code, order, &e)) {
         c.variant = e.variant == VAR_PACKED ? VAR_PACKED : VAR_DIRECT;
         if (e.p0 == 4 || e.p0 == 8) c.MR = e.p0;
         c.P = e.p1 > 0 ? e.p1 : 0;
+        if (e.p2 == 1 || e.p2 == 2) c.minb = e.p2;
     }
     if (c.variant == VAR_PACKED) {
         const int tpp = (rows + c.MR - 1) / c.MR;
@@ -201,7 +207,7 @@ extern "C" int bf_tune_query(int routine, int code, int m, int n, int k, long lo
     if (routine == BF_ROUTINE_DTRSM) {
         bf::TrsmConfig c = bf::choose_trsm((code >> 3) & 1, (code >> 2) & 1, (code >> 1) & 1, code & 1,
                                            m, n, batch);
-        out[0] = c.variant; out[1] = c.MR; out[2] = c.P; out[3] = 0; out[4] = 0;
+        out[0] = c.variant; out[1] = c.MR; out[2] = c.P; out[3] = c.minb; out[4] = 0;
         return 0;
     }
     if (routine == BF_ROUTINE_DPOTRF) {
