@@ -51,9 +51,11 @@ static void sanitize_gemm(GemmConfig& c, int m, int n, int k) {
     const int tpp = (c.TM / 4) * (c.TN / 4);
     if (c.P < 1) c.P = 1;
     // a table entry's P was measured on square tiles; a skinny problem's super-tile has far
-    // fewer threads, so keep at least 128 threads (whole warps) per CTA
-    while (c.P * tpp < 128 && (c.P + 1) * tpp <= 512) c.P++;
-    while ((c.P * tpp) % 32 != 0 && (c.P + 1) * tpp <= 512) c.P++;
+    // fewer threads, so a CTA below 96 threads is raised to at least 96 (whole warps)
+    if (c.P * tpp < 96) {
+        while (c.P * tpp < 96 && (c.P + 1) * tpp <= 512) c.P++;
+        while ((c.P * tpp) % 32 != 0 && (c.P + 1) * tpp <= 512) c.P++;
+    }
     while (c.P > 1 && c.P * tpp > 512) c.P--;
     if (c.KC < 1 || c.KC > k) c.KC = k > 0 ? k : 1;
     if (c.variant == VAR_PACKED) {

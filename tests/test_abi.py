@@ -144,7 +144,7 @@ def test_tune_table(lib):
         assert default[1] == 24 and default[2] == 24  # whole 24 x 24 problem per super-tile
         lib.tune_set(lib.ROUTINE_DGEMM, 1, 16, 32, lib.VARIANT_DIRECT, 12, 24, 8, 2)
         got = lib.tune_query(lib.ROUTINE_DGEMM, 1, 24, 24, 24, 1000)
-        # P = 2 of 18-thread super-tiles is raised to whole warps of at least 128 threads
+        # P = 2 of 18-thread super-tiles is raised to whole warps of at least 96 threads
         assert got == [lib.VARIANT_DIRECT, 12, 24, 8, 16]
         # other trans codes and sizes keep the default
         assert lib.tune_query(lib.ROUTINE_DGEMM, 0, 24, 24, 24, 1000) == default
