@@ -49,6 +49,8 @@ typedef struct CUstream_st* bf_stream_t; /* identical to cudaStream_t */
 #define BF_VARIANT_DIRECT 0  /* native column-major operands, no packing (algorithm 'D') */
 #define BF_VARIANT_PACKED 1  /* operands packed into shared-memory panels ('B'/'C')     */
 #define BF_VARIANT_BLOCKED 2 /* dpotrf only: right-looking sequence of the above kernels */
+#define BF_VARIANT_TINY 3    /* dgemm (m, n, k <= 4) and dtrsm (orders <= 8): one thread   */
+                             /* per problem, problems staged through shared memory       */
 
 /* ------------------------------------------------------------------------ */
 /* dgemm (section 2.1): C <= alpha * op(A) * op(B) + beta * C,               */

@@ -57,7 +57,7 @@ def _install(bf, entries):
 
 
 def _gemm_candidates(n):
-    cands = []
+    cands = [(3, 0, 0, 0, 0)] if n <= 4 else []  # tiny: one thread per problem via shared memory
     tiles = [(0, 0)] if n <= 64 else [(0, 0), (32, 32), (48, 48), (64, 64), (n // 2 // 4 * 4, 64)]
     for variant in (0, 1):
         for TM, TN in tiles:
@@ -117,9 +117,10 @@ def tune(quick=False, out=None, log=print):
         for code, args in ((11, ("R", "L", "T", "U")), (10, ("R", "L", "T", "N")),
                            (0, ("L", "L", "N", "N")), (2, ("L", "L", "T", "N"))):
             best = None
-            for variant in (0, 1):
-                for MR in (4, 8):
-                    for P, minb in (((0, 1), (0, 2)) if variant == 0 else ((0, 1), (8, 1), (16, 1), (32, 1))):
+            for variant in ((0, 1, 3) if n <= 8 else (0, 1)):
+                for MR in ((4,) if variant == 3 else (4, 8)):
+                    for P, minb in (((0, 1), (0, 2)) if variant == 0 else
+                                    (((0, 1),) if variant == 3 else ((0, 1), (8, 1), (16, 1), (32, 1)))):
                         bf.tune_clear()
                         bf.tune_set(bf.ROUTINE_DTRSM, code, 0, 1 << 30, variant, MR, P, minb)
                         cfg = bf.tune_query(bf.ROUTINE_DTRSM, code, n, n, 0, b)

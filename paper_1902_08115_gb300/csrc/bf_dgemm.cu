@@ -272,6 +272,7 @@ cudaError_t launch_dgemm(bool ta, bool tb, int m, int n, int k, double alpha, Ma
     p.lower = lower;
     p.skip = skip;
     const bool neg = (alpha == -1.0);
+    if (cfg.variant == VAR_TINY) return launch_dgemm_tiny(ta, tb, neg, p, s);
     const int tpp = (cfg.TM / 4) * (cfg.TN / 4);
     dim3 block(tpp * cfg.P);
     long long groups = (batch + cfg.P - 1) / cfg.P;

@@ -26,6 +26,7 @@
 // positive (or NaN); the problem's factorisation stops there.
 #include "bf_internal.h"
 #include "bf_lane.cuh"
+#include "bf_stage.cuh"
 
 namespace bf {
 
@@ -39,45 +40,27 @@ __global__ void __launch_bounds__(256) dpotrf_lane_direct_kernel(PotrfParams p) 
     if (info && p.info) p.info[q] = info + p.info_off;
 }
 
+// PACKED: the CTA's problems staged through shared memory (bf_stage.cuh: coalesced 16-byte
+// loads when they are one contiguous run, a padded problem-interleaved layout), factored
+// there one per thread, and written back the same way.
 __global__ void __launch_bounds__(256) dpotrf_lane_packed_kernel(PotrfParams p) {
     extern __shared__ double smem[];
-    const int T = blockDim.x;
+    const int T = blockDim.x, ST = T + 1;
     const long long q0 = blockIdx.x * (long long)T;
     const int n = p.n;
-    const int per = n * n;
-    // coalesced copy of the lower triangles of the CTA's problems into shared memory
-    for (int e = threadIdx.x; e < T * per; e += T) {
-        const int qq = e / per;
-        const int rem = e - qq * per;
-        const int j = rem / n, i = rem - j * n;
-        const long long qg = q0 + qq;
-        double v = 0.0;
-        if (qg < p.batch && i >= j) v = p.upper ? p.A.ptr(qg)[j + (long long)i * p.lda] : p.A.ptr(qg)[i + (long long)j * p.lda];
-        smem[(i + j * n) * T + qq] = v;
-    }
+    const int nq = (int)((p.batch - q0) < T ? (p.batch - q0) : T);
+    const bool up = p.upper != 0;
+    stage_in(p.A, n, n, p.lda, up, q0, nq, smem, ST);
     __syncthreads();
     const long long q = q0 + threadIdx.x;
-    int info = 0;
-    bool active = q < p.batch && !(p.skip && p.skip[q] != 0);
-    if (active) {
-        SAcc M{smem + threadIdx.x, n, T};
-        info = potrf_lane<4, 2>(M, n);
+    if ((int)threadIdx.x < nq && !(p.skip && p.skip[q] != 0)) {
+        const int info = potrf_lane<4, 2>(SAcc{smem + threadIdx.x, n, ST}, n);
         if (info && p.info) p.info[q] = info + p.info_off;
     }
     __syncthreads();
-    // write back the lower triangles of the problems that succeeded
-    for (int e = threadIdx.x; e < T * per; e += T) {
-        const int qq = e / per;
-        const int rem = e - qq * per;
-        const int j = rem / n, i = rem - j * n;
-        const long long qg = q0 + qq;
-        if (qg < p.batch && i >= j) {
-            if (p.skip && p.skip[qg] != 0) continue;
-            if (p.info && p.info[qg] != 0) continue;
-            const long long at = p.upper ? j + (long long)i * p.lda : i + (long long)j * p.lda;
-            p.A.mptr(qg)[at] = smem[(i + j * n) * T + qq];
-        }
-    }
+    // back: the stored triangle; a contiguous lower batch goes back whole, the other triangle
+    // with the very values it was read with
+    stage_out(p.A, n, n, p.lda, up, q0, nq, smem, ST, !up, [](int i, int j) { return i >= j; });
 }
 
 template <bool UP>
@@ -104,7 +87,7 @@ cudaError_t launch_dpotrf_lane(int n, MatRef A, int lda, long long batch, int* i
     p.upper = upper;
     if (cfg.variant == VAR_PACKED) {
         const int T = cfg.T;
-        size_t smem = sizeof(double) * (size_t)T * n * n;
+        size_t smem = sizeof(double) * (size_t)(T + 1) * n * n;
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(dpotrf_lane_packed_kernel,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

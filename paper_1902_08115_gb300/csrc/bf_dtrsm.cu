@@ -189,6 +189,8 @@ cudaError_t launch_dtrsm(int side, int uplo, int trans, int unit, int m, int n, 
                          MatRef A, int lda, MatRef B, int ldb, long long batch,
                          const TrsmConfig& cfg, const int* skip, cudaStream_t s) {
     if (m == 0 || n == 0 || batch == 0) return cudaSuccess;
+    if (cfg.variant == VAR_TINY) return launch_dtrsm_tiny(side, uplo, trans, unit, m, n, alpha, A, lda, B, ldb, batch,
+                                                          skip, s);
     TrsmParams p;
     const bool right = (side == 1);
     // rows of R: right -> rows of B (m x n, T is n x n); left -> columns of B (R = B^T, T is m x m)

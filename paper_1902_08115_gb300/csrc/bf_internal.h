@@ -11,7 +11,7 @@ namespace bf {
 
 // Kernel variants the size switch chooses between (section 2.4: direct 'D'
 // for very small sizes, packing variants for larger ones).
-enum Variant : int { VAR_DIRECT = 0, VAR_PACKED = 1, VAR_BLOCKED = 2 };
+enum Variant : int { VAR_DIRECT = 0, VAR_PACKED = 1, VAR_BLOCKED = 2, VAR_TINY = 3 };
 
 struct GemmConfig {
     int variant;  // VAR_DIRECT or VAR_PACKED
@@ -99,6 +99,13 @@ cudaError_t launch_dpotrf_lane(int n, MatRef A, int lda, long long batch, int* i
 
 cudaError_t launch_dpotrf(int n, MatRef A, int lda, long long batch, int* info,
                           const PotrfConfig& cfg, cudaStream_t s, int upper = 0);
+
+// tiny problems, one per thread through shared memory (bf_tiny.cu): dgemm with m, n, k <= 4,
+// dtrsm with both orders <= 8
+cudaError_t launch_dgemm_tiny(bool ta, bool tb, bool neg, const GemmParams& p, cudaStream_t s);
+size_t tiny_gemm_smem(int m, int n, int k, int T);
+cudaError_t launch_dtrsm_tiny(int side, int uplo, int trans, int unit, int m, int n, double alpha, MatRef A, int lda,
+                              MatRef B, int ldb, long long batch, const int* skip, cudaStream_t s);
 
 // dsyrk (upper: 0/1, trans: 0/1) and the fused chol(C + A A^T), lower (bf_dsyrk.cu)
 cudaError_t launch_dsyrk(int upper, int trans, int n, int k, double alpha, MatRef A, int lda, double beta,

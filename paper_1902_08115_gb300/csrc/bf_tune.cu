@@ -41,6 +41,8 @@ static const size_t kSmemBudget = 200 * 1024;  // per CTA, below the 227 KB opt-
 // than the (rounded) problem, at most 512 threads per CTA (the kernel's launch
 // bound), and the packed k-slice fits in shared memory.
 static void sanitize_gemm(GemmConfig& c, int m, int n, int k) {
+    if (c.variant == VAR_TINY && (m > 4 || n > 4 || k > 4)) c.variant = VAR_DIRECT;  // tiny: m, n, k <= 4
+    if (c.variant == VAR_TINY) return;
     if (c.variant != VAR_DIRECT && c.variant != VAR_PACKED) c.variant = VAR_PACKED;
     c.TM = ceil4(c.TM < ceil4(m) ? c.TM : ceil4(m));
     c.TN = ceil4(c.TN < ceil4(n) ? c.TN : ceil4(n));
@@ -119,11 +121,12 @@ TrsmConfig choose_trsm(int side, int uplo, int trans, int unit, int m, int n, lo
     c.minb = 1;
     TuneEntry e;
     if (lookup(BF_ROUTINE_DTRSM, code, order, &e)) {
-        c.variant = e.variant == VAR_PACKED ? VAR_PACKED : VAR_DIRECT;
+        c.variant = e.variant == VAR_PACKED ? VAR_PACKED : (e.variant == VAR_TINY ? VAR_TINY : VAR_DIRECT);
         if (e.p0 == 4 || e.p0 == 8) c.MR = e.p0;
         c.P = e.p1 > 0 ? e.p1 : 0;
         if (e.p2 == 1 || e.p2 == 2) c.minb = e.p2;
     }
+    if (c.variant == VAR_TINY && (m > 8 || n > 8)) c.variant = VAR_DIRECT;  // tiny: both orders <= 8
     if (c.variant == VAR_PACKED) {
         const int tpp = (rows + c.MR - 1) / c.MR;
         if (tpp > 256) {
@@ -176,8 +179,8 @@ PotrfConfig choose_potrf(int n, int lda, long long batch) {
     c.rows = c.rows == 8 ? 8 : 4;
     c.unroll = c.unroll == 1 ? 1 : 2;
     if (c.variant == VAR_PACKED) {
-        while (c.T > 32 && (size_t)c.T * n * n * sizeof(double) > kSmemBudget) c.T -= 32;
-        if ((size_t)c.T * n * n * sizeof(double) > kSmemBudget) c.variant = VAR_DIRECT;
+        while (c.T > 32 && (size_t)(c.T + 1) * n * n * sizeof(double) > kSmemBudget) c.T -= 32;
+        if ((size_t)(c.T + 1) * n * n * sizeof(double) > kSmemBudget) c.variant = VAR_DIRECT;
     }
     return c;
 }
@@ -188,7 +191,7 @@ extern "C" int bf_tune_set(int routine, int code, int n_lo, int n_hi, int varian
                            int p2, int p3) {
     if (routine < BF_ROUTINE_DGEMM || routine > BF_ROUTINE_DPOTRF) return -1;
     if (n_lo > n_hi) return -3;
-    if (variant < 0 || variant > 2) return -5;
+    if (variant < 0 || variant > 3) return -5;
     std::lock_guard<std::mutex> lk(bf::g_mu);
     bf::g_table.push_back(bf::TuneEntry{routine, code, n_lo, n_hi, variant, p0, p1, p2, p3});
     return 0;

@@ -114,6 +114,60 @@ def test_dgemm_rectangular_and_skinny(bf, oracle, variant, ta, tb):
         assert np.isnan(out[:, :, m:]).all()
 
 
+# ----------------------------------------------------------------------------- tiny problems
+@pytest.mark.parametrize("ta,tb", list(itertools.product("NT", "NT")))
+def test_dgemm_tiny(bf, oracle, ta, tb):
+    code = (2 if ta == "T" else 0) + (1 if tb == "T" else 0)
+    for (m, n, k) in ((4, 4, 4), (1, 1, 1), (3, 4, 2), (4, 1, 3), (2, 3, 4)):
+        for pad in (0, 1):  # contiguous batches (16-byte staging) and padded ones (word staging)
+            batch = 301
+            rA, cA = (m, k) if ta == "N" else (k, m)
+            rB, cB = (k, n) if tb == "N" else (n, k)
+            A = np.full((batch, cA, rA + pad), np.nan)
+            A[:, :, :rA] = rnd((batch, cA, rA), 600 + m + n + k, integer=True)
+            B = np.full((batch, cB, rB + pad), np.nan)
+            B[:, :, :rB] = rnd((batch, cB, rB), 601 + m + n + k, integer=True)
+            C = np.full((batch, n, m + pad), np.nan)
+            C[:, :, :m] = rnd((batch, n, m), 602 + m + n + k, integer=True)
+            for alpha, beta in ((1.0, 1.0), (-1.0, 1.0), (2.0, 0.0), (0.5, -3.0)):
+                Cin = C.copy()
+                if beta == 0.0:
+                    Cin[:, :, :m] = np.nan
+                ref = oracle.dgemm(ta, tb, m, n, k, alpha, A, B, beta, Cin)
+                Cg = gpu(Cin)
+                with forced(bf, bf.ROUTINE_DGEMM, code, bf.VARIANT_TINY):
+                    bf.dgemm(ta, tb, alpha, gpu(A), gpu(B), beta, Cg, m=m, n=n, k=k)
+                out = host(Cg)
+                np.testing.assert_array_equal(out[:, :, :m], ref[:, :, :m])  # integers: exact
+                assert np.isnan(out[:, :, m:]).all()
+
+
+@pytest.mark.parametrize("side,uplo,trans,diag", list(itertools.product("LR", "LU", "NT", "NU")))
+def test_dtrsm_tiny(bf, oracle, side, uplo, trans, diag):
+    code = (8 if side == "R" else 0) + (4 if uplo == "U" else 0) + (2 if trans == "T" else 0) + (1 if diag == "U" else 0)
+    for m, n in ((1, 1), (4, 4), (3, 7), (8, 8), (8, 5)):
+        for pad in (0, 1):
+            k = m if side == "L" else n
+            batch = 131
+            A = np.full((batch, k, k + pad), np.nan)
+            G = rnd((batch, k, k), 700 + m + n)
+            A[:, :, :k] = 0.25 * G + 2.0 * np.eye(k)  # well-conditioned triangles, unit or not
+            mask = tri_mask(k, uplo)
+            A[:, :, :k] = np.where(mask, A[:, :, :k], np.nan)
+            if diag == "U":
+                for j in range(k):
+                    A[:, j, j] = np.nan
+            B = np.full((batch, n, m + pad), np.nan)
+            B[:, :, :m] = rnd((batch, n, m), 800 + m + n)
+            ref = oracle.dtrsm(side, uplo, trans, diag, m, n, 0.75, A, B)
+            Bg = gpu(B)
+            with forced(bf, bf.ROUTINE_DTRSM, code, bf.VARIANT_TINY):
+                bf.dtrsm(side, uplo, trans, diag, 0.75, gpu(A), Bg, m=m, n=n)
+            out = host(Bg)
+            assert normwise(out, ref, m) <= TOL, (m, n, pad)
+            assert np.isnan(out[:, :, m:]).all()
+
+
 # ----------------------------------------------------------------------------- dsyrk + dpotrf
 SP_VARIANTS = [("lane4", 0, 64, 0, 4, 2), ("lane8", 0, 64, 0, 8, 2), ("lane8u1", 0, 128, 0, 8, 1),
                ("blocked16", 2, 0, 16, 0, 0)]
