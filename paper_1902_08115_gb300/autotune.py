@@ -129,7 +129,7 @@ def tune(quick=False, out=None, log=print):
                         ms = _time(torch, lambda: bf.dtrsm(*args, 1.0, L, X, m=n, n=n))
                         if best is None or ms < best[0]:
                             best = (ms, (variant, MR, P, minb))
-            fl = b * n ** 3
+            fl = b * n * n * (n - 1 if args[3] == "U" else n)  # unit diagonal: n^2 (n - 1)
             entries.append(dict(routine=bf.ROUTINE_DTRSM, code=code, lo=lo, hi=hi, variant=best[1][0],
                                 p=[best[1][1], best[1][2], best[1][3], 0], gflops=round(fl / best[0] / 1e6, 1),
                                 n=n))

@@ -67,7 +67,6 @@ static void sanitize_gemm(GemmConfig& c, int m, int n, int k) {
 }
 
 GemmConfig choose_gemm(bool ta, bool tb, int m, int n, int k, int lda, long long batch) {
-    (void)lda;
     (void)batch;
     GemmConfig c;
     const int size = m > n ? m : n;
@@ -89,6 +88,9 @@ GemmConfig choose_gemm(bool ta, bool tb, int m, int n, int k, int lda, long long
     c.KC = (m <= 64 && n <= 64) ? k : (k < 32 ? k : 32);
     TuneEntry e;
     if (lookup(BF_ROUTINE_DGEMM, (ta ? 2 : 0) + (tb ? 1 : 0), size, &e)) {
+        // the tiny form pays off when a CTA's problems are one contiguous run (16-byte staging);
+        // a padded A means padded problems, where the direct form reads them better
+        if (e.variant == VAR_TINY && lda != (ta ? k : m)) e.variant = VAR_DIRECT;
         c.variant = e.variant;
         if (e.p0 > 0) c.TM = e.p0;
         if (e.p1 > 0) c.TN = e.p1;
