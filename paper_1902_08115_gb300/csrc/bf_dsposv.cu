@@ -6,12 +6,12 @@
 // carried out in binary32; refinement recovers binary64 accuracy.  One CTA
 // (128 threads) per problem, the binary32 factor packed in shared memory:
 //   1. A's lower triangle is rounded to binary32 and factored A32 = L32 L32^T,
-//      right-looking with 8-column panels: the panel by one warp without CTA
-//      barriers (each pivot tested for positivity and square-rooted in
+//      right-looking with 8-column panels: the panel by one warp, in registers
+//      with shuffles (each pivot tested for positivity and square-rooted in
 //      binary64, then rounded to binary32), the trailing update by all
 //      threads on 4x4 tiles -- two barriers per panel.
-//   2. x = L32^{-T} L32^{-1} b (binary32 substitutions by one warp, x kept in
-//      binary64); repeat: r = b - A x in binary64 (A symmetric from its lower
+//   2. x = L32^{-T} L32^{-1} b (binary32 substitutions by one warp, the vector
+//      in registers, x kept in binary64); repeat: r = b - A x in binary64 (A symmetric from its lower
 //      triangle, read from global memory); stop when the normwise backward
 //      error eta = ||r||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= tol;
 //      d = L32^{-T} L32^{-1} r (binary32); x = x + d in binary64.
@@ -110,24 +110,105 @@ __device__ unsigned long long block_max_u64(unsigned long long v, unsigned long 
 
 __device__ __forceinline__ int pk(int i, int j, int n) { return j * n - (j * (j - 1)) / 2 + (i - j); }
 
-// w <- L^{-T} L^{-1} w with the packed binary32 factor in shared memory, one warp
+// w <- L^{-T} L^{-1} w with the packed binary32 factor in shared memory, by one warp with w in
+// registers: lane l holds w_i for i = l, l + 32, ...; each step broadcasts the solved entry
+// from its lane and every lane updates its own entries (a column of L for the forward solve,
+// contiguous in the packed layout; a row for the backward one).
+template <int NR>
 __device__ void solve32_warp(const float* L, const float* rinv, float* w, int n) {
     const int lane = threadIdx.x & 31;
-    for (int j = 0; j < n; j++) {
-        const float wj = w[j] * rinv[j];
-        __syncwarp();
-        if (lane == 0) w[j] = wj;
-        const float* col = L + pk(j, j, n);
-        for (int i = j + 1 + lane; i < n; i += 32) w[i] = fmaf(-col[i - j], wj, w[i]);
-        __syncwarp();
+    float x[NR];
+#pragma unroll
+    for (int r = 0; r < NR; r++) x[r] = (lane + 32 * r < n) ? w[lane + 32 * r] : 0.0f;
+#pragma unroll
+    for (int s = 0; s < NR; s++) {
+        if (32 * s >= n) continue;
+        for (int lj = 0; lj < 32 && 32 * s + lj < n; lj++) {
+            const int j = 32 * s + lj;
+            const float yj = __shfl_sync(0xffffffffu, x[s], lj) * rinv[j];
+            if (lane == lj) x[s] = yj;
+            const float* col = L + pk(j, j, n) - j;  // col[i] = L(i, j), i >= j
+#pragma unroll
+            for (int s2 = s; s2 < NR; s2++) {
+                const int i = lane + 32 * s2;
+                if (i > j && i < n) x[s2] = fmaf(-col[i], yj, x[s2]);
+            }
+        }
     }
-    for (int j = n - 1; j >= 0; j--) {
-        const float wj = w[j] * rinv[j];
-        __syncwarp();
-        if (lane == 0) w[j] = wj;
-        for (int i = lane; i < j; i += 32) w[i] = fmaf(-L[pk(j, i, n)], wj, w[i]);
-        __syncwarp();
+#pragma unroll
+    for (int s = NR - 1; s >= 0; s--) {
+        if (32 * s >= n) continue;
+        for (int lj = imin(31, n - 1 - 32 * s); lj >= 0; lj--) {
+            const int j = 32 * s + lj;
+            const float xj = __shfl_sync(0xffffffffu, x[s], lj) * rinv[j];
+            if (lane == lj) x[s] = xj;
+#pragma unroll
+            for (int s2 = 0; s2 <= s; s2++) {
+                const int i = lane + 32 * s2;
+                if (i < j) x[s2] = fmaf(-L[pk(j, i, n)], xj, x[s2]);
+            }
+        }
     }
+#pragma unroll
+    for (int r = 0; r < NR; r++)
+        if (lane + 32 * r < n) w[lane + 32 * r] = x[r];
+}
+
+// The panel J..J+nb (nb <= 8) of the packed binary32 factor, factored by one warp with the
+// panel in registers: lane l holds rows J + l + 32 r.  Each pivot (row J + c: lane c) is
+// broadcast, tested and square-rooted in binary64 and rounded to binary32; the multipliers of
+// the panel's later columns come by shuffle from the lanes that hold their rows.  Returns 0,
+// or the 1-based column whose pivot is not positive (or not finite).
+template <int NR>
+__device__ int panel32_warp(float* L, float* rinv, int n, int J, int nb) {
+    const int lane = threadIdx.x & 31;
+    float pnl[NR][8];
+#pragma unroll
+    for (int r = 0; r < NR; r++)
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            const int i = J + lane + 32 * r;
+            pnl[r][c] = (c < nb && i < n && i >= J + c) ? L[pk(i, J + c, n)] : 0.0f;
+        }
+    int fail = 0;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        if (c >= nb || fail) continue;  // (no break: keeps the loop unrolled, pnl in registers)
+        const int j = J + c;
+        const double d = (double)__shfl_sync(0xffffffffu, pnl[0][c], c);
+        if (!(d > 0.0) || !(d < 3.4e38)) {  // the same value in every lane
+            fail = j + 1;
+            continue;
+        }
+        const float ljj = (float)sqrt(d);  // binary64 square root, rounded to binary32
+        const float ri = 1.0f / ljj;
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+            const int i = J + lane + 32 * r;
+            if (i > j && i < n) pnl[r][c] *= ri;
+        }
+        if (lane == c) pnl[0][c] = ljj;
+        if (lane == 0) rinv[j] = ri;
+#pragma unroll
+        for (int c2 = c + 1; c2 < 8; c2++) {
+            if (c2 < nb) {
+                const float lk = __shfl_sync(0xffffffffu, pnl[0][c], c2);  // L(J + c2, j)
+#pragma unroll
+                for (int r = 0; r < NR; r++) {
+                    const int i = J + lane + 32 * r;
+                    if (i >= J + c2 && i < n) pnl[r][c2] = fmaf(-pnl[r][c], lk, pnl[r][c2]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; r++)
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            const int i = J + lane + 32 * r;
+            if (c < nb && i < n && i >= J + c) L[pk(i, J + c, n)] = pnl[r][c];
+        }
+    return fail;
 }
 
 static size_t refine_smem_bytes(int n) {
@@ -137,7 +218,9 @@ static size_t refine_smem_bytes(int n) {
     return f + 2 * (size_t)n * sizeof(double) + 32 * sizeof(double);
 }
 
-__global__ void __launch_bounds__(128) dsposv_kernel(SposvParams p) {
+// NR: rows per lane in the warp-register phases (n <= 32 NR); 4 keeps the panel in registers
+template <int NR>
+__global__ void __launch_bounds__(128, 6) dsposv_kernel(SposvParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const long long q = blockIdx.x;
     if (q >= p.batch) return;
@@ -185,30 +268,8 @@ __global__ void __launch_bounds__(128) dsposv_kernel(SposvParams p) {
     for (int J = 0; J < n; J += 8) {
         const int nb = imin(8, n - J);
         if (warp == sw) {
-            for (int c = 0; c < nb; c++) {
-                const int j = J + c;
-                const double d = (double)L[pk(j, j, n)];
-                if (!(d > 0.0) || !(d < 3.4e38)) {  // binary64 test of the binary32 pivot
-                    if (lane == 0) s_done = j + 1;
-                    break;
-                }
-                const float ljj = (float)sqrt(d);  // binary64 square root, rounded to binary32
-                const float ri = 1.0f / ljj;
-                __syncwarp();
-                if (lane == 0) {
-                    L[pk(j, j, n)] = ljj;
-                    rinv[j] = ri;
-                }
-                float* colj = L + pk(j, j, n) - j;
-                for (int i = j + 1 + lane; i < n; i += 32) colj[i] *= ri;
-                __syncwarp();
-                for (int k = j + 1; k < J + nb; k++) {
-                    const float lkj = colj[k];
-                    float* colk = L + pk(k, k, n) - k;
-                    for (int i = k + lane; i < n; i += 32) colk[i] = fmaf(-colj[i], lkj, colk[i]);
-                }
-                __syncwarp();
-            }
+            const int f = panel32_warp<NR>(L, rinv, n, J, nb);
+            if (f && lane == 0) s_done = f;
         }
         __syncthreads();
         if (s_done) break;
@@ -268,7 +329,7 @@ __global__ void __launch_bounds__(128) dsposv_kernel(SposvParams p) {
         }
         bn = block_max_u64(bn, scratch);
         const double bnorm = __longlong_as_double((long long)bn);
-        if (warp == sw) solve32_warp(L, rinv, wv, n);
+        if (warp == sw) solve32_warp<NR>(L, rinv, wv, n);
         __syncthreads();
         for (int i = tid; i < n; i += T) xv[i] = (double)wv[i];
         __syncthreads();
@@ -311,7 +372,7 @@ __global__ void __launch_bounds__(128) dsposv_kernel(SposvParams p) {
             if (it == p.itmax) break;
             for (int i = tid; i < n; i += T) wv[i] = (float)rv[i];
             __syncthreads();
-            if (warp == sw) solve32_warp(L, rinv, wv, n);
+            if (warp == sw) solve32_warp<NR>(L, rinv, wv, n);
             __syncthreads();
             for (int i = tid; i < n; i += T) xv[i] += (double)wv[i];
             __syncthreads();
@@ -418,11 +479,12 @@ cudaError_t launch_dsposv(int n, int nrhs, MatRef A, int lda, MatRef B, int ldb,
     p.wper = sposv_wper(n);
     p.work = reinterpret_cast<unsigned char*>(work);
     const size_t smem = refine_smem_bytes(n);
+    auto kfn = n <= 128 ? dsposv_kernel<4> : dsposv_kernel<BF_DSPOSV_NMAX / 32>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(dsposv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    dsposv_kernel<<<(unsigned)batch, 128, smem, s>>>(p);
+    kfn<<<(unsigned)batch, 128, smem, s>>>(p);
     count_launch();
     return cudaGetLastError();
 }
