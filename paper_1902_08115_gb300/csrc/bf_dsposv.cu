@@ -7,9 +7,9 @@
 // (128 threads) per problem, the binary32 factor packed in shared memory:
 //   1. A's lower triangle is rounded to binary32 and factored A32 = L32 L32^T,
 //      right-looking with 8-column panels: the panel by one warp, in registers
-//      with shuffles (each pivot tested for positivity and square-rooted in
-//      binary64, then rounded to binary32), the trailing update by all
-//      threads on 4x4 tiles -- two barriers per panel.
+//      with shuffles (each pivot tested for positivity; its binary64 square
+//      root rounded to binary32 is the correctly rounded binary32 one), the
+//      trailing update by all threads on 4x4 tiles -- two barriers per panel.
 //   2. x = L32^{-T} L32^{-1} b (binary32 substitutions by one warp, the vector
 //      in registers, x kept in binary64); repeat: r = b - A x in binary64 (A symmetric from its lower
 //      triangle, read from global memory); stop when the normwise backward
@@ -20,10 +20,10 @@
 //      problem is factored and solved in binary64 in its workspace slice
 //      (iter = -1), as LAPACK's dsposv does.
 // The warp that runs the serial phases is rotated by problem index, so the
-// binary64 pivot square roots of co-resident CTAs spread over the SM's four
-// FP64 pipes.  ||A||_inf is accumulated in binary32 from entries truncated
-// toward zero and scaled by (1 - 2(n+1) 2^-24): a lower bound of the binary64
-// norm, so the stopping test never under-estimates eta.  binary64 -> binary32
+// serial phases of co-resident CTAs spread over the SM's four sub-partitions.
+// ||A||_inf is accumulated in binary32 from the rounded entries and scaled by
+// (1 - 2(n+2) 2^-24): a lower bound of the binary64 norm, so the stopping
+// test never under-estimates eta.  binary64 -> binary32
 // conversions of matrix entries are integer operations (round to nearest
 // even; binary32-subnormal results flush to zero): FP64 instructions run at
 // 1/64 of the binary32 rate on this GPU.
@@ -52,17 +52,6 @@ __device__ __forceinline__ float f64_to_f32_rn(double a) {
     }
     if (E >= 255) return __uint_as_float(sign | 0x7F800000u);
     return __uint_as_float(sign | ((unsigned int)E << 23) | mant);
-}
-
-// |a| rounded toward zero to binary32 (a lower bound of |a|)
-__device__ __forceinline__ float f64_abs_to_f32_rz(double a) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull;
-    const int e = (int)(u >> 52);
-    if (e == 0x7FF) return __uint_as_float(0x7F800000u);
-    const int E = e - 1023 + 127;
-    if (e == 0 || E <= 0) return 0.0f;
-    if (E >= 255) return 3.4028234663852886e38f;
-    return __uint_as_float(((unsigned int)E << 23) | (unsigned int)((u >> 29) & 0x7FFFFFu));
 }
 
 struct SposvParams {
@@ -175,13 +164,16 @@ __device__ int panel32_warp(float* L, float* rinv, int n, int J, int nb) {
     for (int c = 0; c < 8; c++) {
         if (c >= nb || fail) continue;  // (no break: keeps the loop unrolled, pnl in registers)
         const int j = J + c;
-        const double d = (double)__shfl_sync(0xffffffffu, pnl[0][c], c);
-        if (!(d > 0.0) || !(d < 3.4e38)) {  // the same value in every lane
+        const float d = __shfl_sync(0xffffffffu, pnl[0][c], c);
+        if (!(d > 0.0f) || d == INFINITY) {  // the same value in every lane
             fail = j + 1;
             continue;
         }
-        const float ljj = (float)sqrt(d);  // binary64 square root, rounded to binary32
-        const float ri = 1.0f / ljj;
+        // sqrt(d) in binary64 rounded to binary32 equals the correctly rounded binary32 square
+        // root of d: double rounding of a square root is innocuous when the wider format has
+        // at least 2p + 2 significand bits (Figueroa, 1995; 53 >= 2 * 24 + 2).
+        const float ljj = __fsqrt_rn(d);
+        const float ri = __frcp_rn(ljj);
 #pragma unroll
         for (int r = 0; r < NR; r++) {
             const int i = J + lane + 32 * r;
@@ -242,22 +234,36 @@ __global__ void __launch_bounds__(128, 6) dsposv_kernel(SposvParams p) {
     double* X = p.X.mptr(q);
     unsigned char* wbytes = p.work + q * p.wper;
 
-    // ---- 1. round the lower triangle to binary32 (packed by columns); independent loads ----
-#pragma unroll 8
-    for (int e = tid; e < n * n; e += T) {
-        const int j = e / n, i = e - j * n;
-        if (i >= j) L[pk(i, j, n)] = f64_to_f32_rn(A[i + (long long)j * p.lda]);
+    // ---- 1. round the lower triangle to binary32 (packed by columns): warp w takes columns
+    //         w, w + 4, ...; its lanes read consecutive rows (coalesced) ----
+    const int nw = T >> 5;
+#pragma unroll 2
+    for (int j = warp; j < n; j += nw) {
+        const double* a = A + (long long)j * p.lda;
+        float* Lc = L + pk(j, j, n) - j;  // Lc[i] = L(i, j)
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+            const int i = j + lane + 32 * r;
+            if (i < n) Lc[i] = f64_to_f32_rn(a[i]);
+        }
     }
     if (tid == 0) s_done = 0;
     __syncthreads();
     // ||A||_inf of the symmetric matrix from the rounded lower triangle.  Each rounded entry
-    // is at most (1 + 2^-24) times the binary64 one and the binary32 row sum is accurate to
-    // (n + 1) 2^-24, so the scaled result is a lower bound of the binary64 norm.
+    // is at most (1 + 2^-24) times the binary64 one and a binary32 sum of n terms, in any
+    // order, is accurate to (n + 1) 2^-24, so the scaled result is a lower bound of the
+    // binary64 norm.  Row i: L(i, 0..i-1) along its row (packed offsets advance by n - 1 - j),
+    // then L(i..n-1, i) down its column (contiguous).
     unsigned long long an = 0;
     for (int i = tid; i < n; i += T) {
-        float s = 0.0f;
-        for (int j = 0; j < n; j++) s += fabsf(j <= i ? L[pk(i, j, n)] : L[pk(j, i, n)]);
-        const unsigned long long b = (unsigned long long)__float_as_uint(s);
+        float s0 = 0.0f, s1 = 0.0f;
+        int off = i;
+        for (int j = 0; j < i; j++) {
+            s0 += fabsf(L[off]);
+            off += n - 1 - j;
+        }
+        for (int k = 0; k < n - i; k++) s1 += fabsf(L[off + k]);
+        const unsigned long long b = (unsigned long long)__float_as_uint(s0 + s1);
         an = b > an ? b : an;
     }
     an = block_max_u64(an, scratch);

@@ -94,6 +94,26 @@ def test_dsposv_fallback_when_single_fails(oracle):
     assert oracle.backward_error(colmajor(A), x[0], b)[0] < 1e-14
 
 
+def test_pivot_sqrt_double_rounding_is_innocuous():
+    # The binary32 factorisation takes each pivot's square root in binary64 and rounds it to
+    # binary32; the kernel takes the correctly rounded binary32 square root instead.  The two
+    # agree for every positive binary32 d: sqrt(4^k d) = 2^k sqrt(d) exactly, so the mantissas
+    # of [1, 4) (both exponent parities) cover every case.  Checked exhaustively here.
+    lo = np.float32(1.0).view(np.uint32)
+    hi = np.float32(4.0).view(np.uint32)
+    for start in range(int(lo), int(hi), 1 << 22):
+        d = np.arange(start, min(start + (1 << 22), int(hi)), dtype=np.uint32).view(np.float32)
+        twice = np.sqrt(d.astype(np.float64)).astype(np.float32)
+        once = np.sqrt(d)
+        assert np.array_equal(twice.view(np.uint32), once.view(np.uint32))
+    # the scaling argument, spot-checked at the ends of the range (subnormal and huge pivots)
+    rng = np.random.default_rng(3)
+    bits = rng.integers(1, 0x7F800000, size=1 << 20, dtype=np.uint32)
+    d = bits.view(np.float32)
+    assert np.array_equal(np.sqrt(d.astype(np.float64)).astype(np.float32).view(np.uint32),
+                          np.sqrt(d).view(np.uint32))
+
+
 def _chol_loss(oracle, A, Lbar):
     L, info = oracle.dpotrf_l(colmajor(A))
     assert info[0] == 0
