@@ -236,15 +236,28 @@ __global__ void __launch_bounds__(128, 6) dsposv_kernel(SposvParams p) {
 
     // ---- 1. round the lower triangle to binary32 (packed by columns): warp w takes columns
     //         w, w + 4, ...; its lanes read consecutive rows (coalesced) ----
+    // Two columns per step, every load unconditional (rows clamped to n - 1, inside the
+    // column): all 2 NR loads are in flight before the first conversion.
     const int nw = T >> 5;
-#pragma unroll 2
-    for (int j = warp; j < n; j += nw) {
-        const double* a = A + (long long)j * p.lda;
-        float* Lc = L + pk(j, j, n) - j;  // Lc[i] = L(i, j)
+    for (int j0 = warp; j0 < n; j0 += 2 * nw) {
+        double v[2][NR];
 #pragma unroll
-        for (int r = 0; r < NR; r++) {
-            const int i = j + lane + 32 * r;
-            if (i < n) Lc[i] = f64_to_f32_rn(a[i]);
+        for (int h = 0; h < 2; h++) {
+            const int j = imin(j0 + h * nw, n - 1);
+            const double* a = A + (long long)j * p.lda;
+#pragma unroll
+            for (int r = 0; r < NR; r++) v[h][r] = a[imin(j + lane + 32 * r, n - 1)];
+        }
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int j = j0 + h * nw;
+            if (j >= n) continue;
+            float* Lc = L + pk(j, j, n) - j;  // Lc[i] = L(i, j)
+#pragma unroll
+            for (int r = 0; r < NR; r++) {
+                const int i = j + lane + 32 * r;
+                if (i < n) Lc[i] = f64_to_f32_rn(v[h][r]);
+            }
         }
     }
     if (tid == 0) s_done = 0;
@@ -256,14 +269,22 @@ __global__ void __launch_bounds__(128, 6) dsposv_kernel(SposvParams p) {
     // then L(i..n-1, i) down its column (contiguous).
     unsigned long long an = 0;
     for (int i = tid; i < n; i += T) {
-        float s0 = 0.0f, s1 = 0.0f;
+        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
         int off = i;
+#pragma unroll 4
         for (int j = 0; j < i; j++) {
             s0 += fabsf(L[off]);
             off += n - 1 - j;
         }
-        for (int k = 0; k < n - i; k++) s1 += fabsf(L[off + k]);
-        const unsigned long long b = (unsigned long long)__float_as_uint(s0 + s1);
+        int k = 0;
+        for (; k + 3 < n - i; k += 4) {
+            s1 += fabsf(L[off + k]);
+            s2 += fabsf(L[off + k + 1]);
+            s3 += fabsf(L[off + k + 2]);
+            s0 += fabsf(L[off + k + 3]);
+        }
+        for (; k < n - i; k++) s1 += fabsf(L[off + k]);
+        const unsigned long long b = (unsigned long long)__float_as_uint((s0 + s1) + (s2 + s3));
         an = b > an ? b : an;
     }
     an = block_max_u64(an, scratch);
@@ -294,7 +315,8 @@ __global__ void __launch_bounds__(128, 6) dsposv_kernel(SposvParams p) {
                 for (int a = 0; a < 4; a++)
 #pragma unroll
                     for (int b = 0; b < 4; b++) acc[a][b] = 0.0f;
-                for (int c = 0; c < nb; c++) {
+#pragma unroll
+                for (int c = 0; c < 8; c++) {  // nb == 8 whenever a trailing matrix remains
                     const float* col = L + pk(J + c, J + c, n) - (J + c);
                     float li[4], lk[4];
 #pragma unroll
