@@ -99,6 +99,16 @@ __device__ unsigned long long block_max_u64(unsigned long long v, unsigned long 
 
 __device__ __forceinline__ int pk(int i, int j, int n) { return j * n - (j * (j - 1)) / 2 + (i - j); }
 
+// Storage of the binary32 factor in shared memory: column j holds rows 4 floor(j/4) .. n4 - 1
+// (n4 = n rounded up to a multiple of 4), the columns one after another, so that
+// L(i, j) = L[cb(j, n4) + i] and four rows starting at a multiple of 4 are one aligned 16-byte
+// piece.  The rows above the diagonal inside a column's group of four, and the rows n .. n4 - 1,
+// are padding.  n4 * n4 / 2 + 2 n4 floats in all.
+__device__ __forceinline__ int cb(int j, int n4) {
+    const int g = j >> 2, r = j & 3;
+    return 4 * n4 * g - 8 * g * (g - 1) + r * (n4 - 4 * g) - 4 * g;
+}
+
 // w <- L^{-T} L^{-1} w with the packed binary32 factor in shared memory, by one warp with w in
 // registers: lane l holds w_i for i = l, l + 32, ...; each step broadcasts the solved entry
 // from its lane and every lane updates its own entries (a column of L for the forward solve,
@@ -106,6 +116,7 @@ __device__ __forceinline__ int pk(int i, int j, int n) { return j * n - (j * (j 
 template <int NR>
 __device__ void solve32_warp(const float* L, const float* rinv, float* w, int n) {
     const int lane = threadIdx.x & 31;
+    const int n4 = (n + 3) & ~3;
     float x[NR];
 #pragma unroll
     for (int r = 0; r < NR; r++) x[r] = (lane + 32 * r < n) ? w[lane + 32 * r] : 0.0f;
@@ -116,7 +127,7 @@ __device__ void solve32_warp(const float* L, const float* rinv, float* w, int n)
             const int j = 32 * s + lj;
             const float yj = __shfl_sync(0xffffffffu, x[s], lj) * rinv[j];
             if (lane == lj) x[s] = yj;
-            const float* col = L + pk(j, j, n) - j;  // col[i] = L(i, j), i >= j
+            const float* col = L + cb(j, n4);  // col[i] = L(i, j)
 #pragma unroll
             for (int s2 = s; s2 < NR; s2++) {
                 const int i = lane + 32 * s2;
@@ -124,6 +135,9 @@ __device__ void solve32_warp(const float* L, const float* rinv, float* w, int n)
             }
         }
     }
+    int base[NR];  // L(j, i) = L[base + j] for this lane's rows i
+#pragma unroll
+    for (int r = 0; r < NR; r++) base[r] = cb(imin(lane + 32 * r, n - 1), n4);
 #pragma unroll
     for (int s = NR - 1; s >= 0; s--) {
         if (32 * s >= n) continue;
@@ -134,7 +148,7 @@ __device__ void solve32_warp(const float* L, const float* rinv, float* w, int n)
 #pragma unroll
             for (int s2 = 0; s2 <= s; s2++) {
                 const int i = lane + 32 * s2;
-                if (i < j) x[s2] = fmaf(-L[pk(j, i, n)], xj, x[s2]);
+                if (i < j) x[s2] = fmaf(-L[base[s2] + j], xj, x[s2]);
             }
         }
     }
@@ -151,13 +165,14 @@ __device__ void solve32_warp(const float* L, const float* rinv, float* w, int n)
 template <int NR>
 __device__ int panel32_warp(float* L, float* rinv, int n, int J, int nb) {
     const int lane = threadIdx.x & 31;
+    const int n4 = (n + 3) & ~3;
     float pnl[NR][8];
 #pragma unroll
     for (int r = 0; r < NR; r++)
 #pragma unroll
         for (int c = 0; c < 8; c++) {
             const int i = J + lane + 32 * r;
-            pnl[r][c] = (c < nb && i < n && i >= J + c) ? L[pk(i, J + c, n)] : 0.0f;
+            pnl[r][c] = (c < nb && i < n && i >= J + c) ? L[cb(J + c, n4) + i] : 0.0f;
         }
     int fail = 0;
 #pragma unroll
@@ -198,14 +213,19 @@ __device__ int panel32_warp(float* L, float* rinv, int n, int J, int nb) {
 #pragma unroll
         for (int c = 0; c < 8; c++) {
             const int i = J + lane + 32 * r;
-            if (c < nb && i < n && i >= J + c) L[pk(i, J + c, n)] = pnl[r][c];
+            if (c < nb && i < n && i >= J + c) L[cb(J + c, n4) + i] = pnl[r][c];
         }
     return fail;
 }
 
+static size_t factor_floats(int n) {
+    const size_t n4 = (size_t)((n + 3) & ~3);
+    return n4 * n4 / 2 + 2 * n4;
+}
+
 static size_t refine_smem_bytes(int n) {
-    // packed factor | reciprocal pivots | w (binary32) | x, r (binary64) | scratch
-    size_t f = ((size_t)n * (n + 1) / 2 + (size_t)n + (size_t)n) * sizeof(float);
+    // factor | reciprocal pivots | w (binary32) | x, r (binary64) | scratch
+    size_t f = (factor_floats(n) + (size_t)n + (size_t)n) * sizeof(float);
     f = (f + 15) / 16 * 16;
     return f + 2 * (size_t)n * sizeof(double) + 32 * sizeof(double);
 }
@@ -220,9 +240,11 @@ __global__ void __launch_bounds__(128, 6) dsposv_kernel(SposvParams p) {
     const int tid = threadIdx.x, T = blockDim.x, warp = tid >> 5, lane = tid & 31;
     const int sw = (int)(q % (T >> 5));  // the warp that runs the serial phases
     float* L = reinterpret_cast<float*>(smem_raw);
-    float* rinv = L + (size_t)n * (n + 1) / 2;
+    const int n4 = (n + 3) & ~3;
+    const int nf = n4 * n4 / 2 + 2 * n4;  // factor_floats(n)
+    float* rinv = L + nf;
     float* wv = rinv + n;
-    size_t off = ((size_t)n * (n + 1) / 2 + 2 * (size_t)n) * sizeof(float);
+    size_t off = ((size_t)nf + 2 * (size_t)n) * sizeof(float);
     off = (off + 15) / 16 * 16;
     double* xv = reinterpret_cast<double*>(smem_raw + off);
     double* rv = xv + n;
@@ -234,10 +256,11 @@ __global__ void __launch_bounds__(128, 6) dsposv_kernel(SposvParams p) {
     double* X = p.X.mptr(q);
     unsigned char* wbytes = p.work + q * p.wper;
 
-    // ---- 1. round the lower triangle to binary32 (packed by columns): warp w takes columns
-    //         w, w + 4, ...; its lanes read consecutive rows (coalesced) ----
-    // Two columns per step, every load unconditional (rows clamped to n - 1, inside the
-    // column): all 2 NR loads are in flight before the first conversion.
+    // ---- 1. round the lower triangle to binary32: warp w takes columns w, w + 4, ...; its
+    //         lanes read consecutive rows (coalesced) and write the column's whole storage,
+    //         padding as zeros ----
+    // Two columns per step, every load unconditional (rows clamped into j .. n - 1): all 2 NR
+    // loads are in flight before the first conversion.
     const int nw = T >> 5;
     for (int j0 = warp; j0 < n; j0 += 2 * nw) {
         double v[2][NR];
@@ -246,17 +269,17 @@ __global__ void __launch_bounds__(128, 6) dsposv_kernel(SposvParams p) {
             const int j = imin(j0 + h * nw, n - 1);
             const double* a = A + (long long)j * p.lda;
 #pragma unroll
-            for (int r = 0; r < NR; r++) v[h][r] = a[imin(j + lane + 32 * r, n - 1)];
+            for (int r = 0; r < NR; r++) v[h][r] = a[imin(imax(4 * (j >> 2) + lane + 32 * r, j), n - 1)];
         }
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int j = j0 + h * nw;
             if (j >= n) continue;
-            float* Lc = L + pk(j, j, n) - j;  // Lc[i] = L(i, j)
+            float* Lc = L + cb(j, n4);  // Lc[i] = L(i, j)
 #pragma unroll
             for (int r = 0; r < NR; r++) {
-                const int i = j + lane + 32 * r;
-                if (i < n) Lc[i] = f64_to_f32_rn(v[h][r]);
+                const int i = 4 * (j >> 2) + lane + 32 * r;
+                if (i < n4) Lc[i] = (i >= j && i < n) ? f64_to_f32_rn(v[h][r]) : 0.0f;
             }
         }
     }
@@ -265,17 +288,13 @@ __global__ void __launch_bounds__(128, 6) dsposv_kernel(SposvParams p) {
     // ||A||_inf of the symmetric matrix from the rounded lower triangle.  Each rounded entry
     // is at most (1 + 2^-24) times the binary64 one and a binary32 sum of n terms, in any
     // order, is accurate to (n + 1) 2^-24, so the scaled result is a lower bound of the
-    // binary64 norm.  Row i: L(i, 0..i-1) along its row (packed offsets advance by n - 1 - j),
-    // then L(i..n-1, i) down its column (contiguous).
+    // binary64 norm.  Row i: L(i, 0..i-1) along its row, then L(i..n-1, i) down its column.
     unsigned long long an = 0;
     for (int i = tid; i < n; i += T) {
         float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-        int off = i;
 #pragma unroll 4
-        for (int j = 0; j < i; j++) {
-            s0 += fabsf(L[off]);
-            off += n - 1 - j;
-        }
+        for (int j = 0; j < i; j++) s0 += fabsf(L[cb(j, n4) + i]);
+        const int off = cb(i, n4) + i;
         int k = 0;
         for (; k + 3 < n - i; k += 4) {
             s1 += fabsf(L[off + k]);
@@ -317,27 +336,30 @@ __global__ void __launch_bounds__(128, 6) dsposv_kernel(SposvParams p) {
                     for (int b = 0; b < 4; b++) acc[a][b] = 0.0f;
 #pragma unroll
                 for (int c = 0; c < 8; c++) {  // nb == 8 whenever a trailing matrix remains
-                    const float* col = L + pk(J + c, J + c, n) - (J + c);
-                    float li[4], lk[4];
-#pragma unroll
-                    for (int a = 0; a < 4; a++) li[a] = col[imin(i0 + a, n - 1)];
-#pragma unroll
-                    for (int b = 0; b < 4; b++) lk[b] = col[imin(k0 + b, n - 1)];
+                    // rows i0.., k0.. (multiples of 4, below the panel) as aligned 16-byte pieces;
+                    // the zero padding rows n .. n4 - 1 only reach discarded tile entries
+                    const float* col = L + cb(J + c, n4);
+                    const float4 l4 = *reinterpret_cast<const float4*>(col + i0);
+                    const float4 k4 = *reinterpret_cast<const float4*>(col + k0);
+                    const float li[4] = {l4.x, l4.y, l4.z, l4.w}, lk[4] = {k4.x, k4.y, k4.z, k4.w};
 #pragma unroll
                     for (int a = 0; a < 4; a++)
 #pragma unroll
                         for (int b = 0; b < 4; b++) acc[a][b] = fmaf(li[a], lk[b], acc[a][b]);
                 }
+                // rows i0 .. i0 + 3 of columns k0 .. k0 + 3, whole pieces: on a diagonal tile the
+                // entries above the diagonal are padding, and padding rows receive zeros
 #pragma unroll
                 for (int b = 0; b < 4; b++) {
                     const int k = k0 + b;
                     if (k >= n) continue;
-                    float* col = L + pk(k, k, n) - k;
-#pragma unroll
-                    for (int a = 0; a < 4; a++) {
-                        const int i = i0 + a;
-                        if (i < n && i >= k) col[i] -= acc[a][b];
-                    }
+                    float4* cp = reinterpret_cast<float4*>(L + cb(k, n4) + i0);
+                    float4 v = *cp;
+                    v.x -= acc[0][b];
+                    v.y -= acc[1][b];
+                    v.z -= acc[2][b];
+                    v.w -= acc[3][b];
+                    *cp = v;
                 }
             }
         }
