@@ -33,7 +33,7 @@
 namespace bf {
 
 // ---------------------------------------------------------------- binary64 -> binary32 by integer operations
-__device__ __forceinline__ float f64_to_f32_rn(double a) {
+__device__ __noinline__ float f64_to_f32_rn(double a) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(a);
     const unsigned int sign = (unsigned int)(u >> 63) << 31;
     const int e = (int)((u >> 52) & 0x7FF);
@@ -114,7 +114,7 @@ __device__ __forceinline__ int cb(int j, int n4) {
 // from its lane and every lane updates its own entries (a column of L for the forward solve,
 // contiguous in the packed layout; a row for the backward one).
 template <int NR>
-__device__ void solve32_warp(const float* L, const float* rinv, float* w, int n) {
+__device__ __noinline__ void solve32_warp(const float* L, const float* rinv, float* w, int n) {
     const int lane = threadIdx.x & 31;
     const int n4 = (n + 3) & ~3;
     float x[NR];
@@ -157,11 +157,19 @@ __device__ void solve32_warp(const float* L, const float* rinv, float* w, int n)
         if (lane + 32 * r < n) w[lane + 32 * r] = x[r];
 }
 
-// The panel J..J+nb (nb <= 8) of the packed binary32 factor, factored by one warp with the
-// panel in registers: lane l holds rows J + l + 32 r.  Each pivot (row J + c: lane c) is
-// broadcast, tested and square-rooted in binary64 and rounded to binary32; the multipliers of
-// the panel's later columns come by shuffle from the lanes that hold their rows.  Returns 0,
-// or the 1-based column whose pivot is not positive (or not finite).
+// The panel J..J+nb (nb <= 8) of the binary32 factor, factored by one warp with the panel in
+// registers: lane l holds rows J + l + 32 r.  Per column j = J + c: the pivot d (row j: lane c)
+// is broadcast and tested; l_jj = sqrt(d) rounded to binary32, which equals the binary64 square
+// root rounded to binary32 (double rounding of a square root is innocuous when the wider format
+// has at least 2p + 2 significand bits: Figueroa, 1995; 53 >= 2 * 24 + 2); the column below is
+// scaled by 1 / l_jj, and the panel's later columns are updated with the scaled multipliers.
+// The code is straight-line (a failed or absent column continues with d = 1 and is reported),
+// so that the shuffles of the next multipliers are issued while the pivot is being rooted:
+// lane c2's scaled multiplier is its unscaled value times 1 / l_jj, formed here from a copy
+// fetched ahead -- the same product, bit for bit.  1 / l_jj comes from the hardware's
+// reciprocal square root of d refined by one Newton step y (3/2 - d y^2 / 2) (~1 ulp; the
+// refinement in binary64 removes the factor's rounding, whatever it is).  Returns 0, or the
+// 1-based column whose pivot is not positive (or not finite).
 template <int NR>
 __device__ int panel32_warp(float* L, float* rinv, int n, int J, int nb) {
     const int lane = threadIdx.x & 31;
@@ -177,35 +185,29 @@ __device__ int panel32_warp(float* L, float* rinv, int n, int J, int nb) {
     int fail = 0;
 #pragma unroll
     for (int c = 0; c < 8; c++) {
-        if (c >= nb || fail) continue;  // (no break: keeps the loop unrolled, pnl in registers)
         const int j = J + c;
-        const float d = __shfl_sync(0xffffffffu, pnl[0][c], c);
-        if (!(d > 0.0f) || d == INFINITY) {  // the same value in every lane
-            fail = j + 1;
-            continue;
-        }
-        // sqrt(d) in binary64 rounded to binary32 equals the correctly rounded binary32 square
-        // root of d: double rounding of a square root is innocuous when the wider format has
-        // at least 2p + 2 significand bits (Figueroa, 1995; 53 >= 2 * 24 + 2).
-        const float ljj = __fsqrt_rn(d);
-        const float ri = __frcp_rn(ljj);
+        float u[8];  // unscaled L(J + c2, j), c2 > c
 #pragma unroll
-        for (int r = 0; r < NR; r++) {
-            const int i = J + lane + 32 * r;
-            if (i > j && i < n) pnl[r][c] *= ri;
-        }
+        for (int c2 = c + 1; c2 < 8; c2++) u[c2] = __shfl_sync(0xffffffffu, pnl[0][c], c2);
+        float d = __shfl_sync(0xffffffffu, pnl[0][c], c);  // the same value in every lane
+        const bool bad = !(d > 0.0f) || d == INFINITY;
+        if (c < nb && bad && fail == 0) fail = j + 1;
+        if (c >= nb || bad) d = 1.0f;
+        const float y = rsqrtf(d);
+        const float t = 0.5f * d * y;
+        const float ri = fmaf(y, fmaf(-t, y, 0.5f), y);
+        const float ljj = __fsqrt_rn(d);
+        // unpredicated: entries on and above the diagonal and rows >= n are never stored
+        // back, rows >= n hold zeros, and every value read below comes from a row > j
+#pragma unroll
+        for (int r = 0; r < NR; r++) pnl[r][c] *= ri;
         if (lane == c) pnl[0][c] = ljj;
-        if (lane == 0) rinv[j] = ri;
+        if (lane == 0 && c < nb) rinv[j] = ri;
 #pragma unroll
         for (int c2 = c + 1; c2 < 8; c2++) {
-            if (c2 < nb) {
-                const float lk = __shfl_sync(0xffffffffu, pnl[0][c], c2);  // L(J + c2, j)
+            const float lk = u[c2] * ri;  // L(J + c2, j)
 #pragma unroll
-                for (int r = 0; r < NR; r++) {
-                    const int i = J + lane + 32 * r;
-                    if (i >= J + c2 && i < n) pnl[r][c2] = fmaf(-pnl[r][c], lk, pnl[r][c2]);
-                }
-            }
+            for (int r = 0; r < NR; r++) pnl[r][c2] = fmaf(-pnl[r][c], lk, pnl[r][c2]);
         }
     }
 #pragma unroll
@@ -259,20 +261,20 @@ __global__ void __launch_bounds__(128, 6) dsposv_kernel(SposvParams p) {
     // ---- 1. round the lower triangle to binary32: warp w takes columns w, w + 4, ...; its
     //         lanes read consecutive rows (coalesced) and write the column's whole storage,
     //         padding as zeros ----
-    // Two columns per step, every load unconditional (rows clamped into j .. n - 1): all 2 NR
+    // Four columns per step, every load unconditional (rows clamped into j .. n - 1): all 4 NR
     // loads are in flight before the first conversion.
     const int nw = T >> 5;
-    for (int j0 = warp; j0 < n; j0 += 2 * nw) {
-        double v[2][NR];
+    for (int j0 = warp; j0 < n; j0 += 4 * nw) {
+        double v[4][NR];
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
+        for (int h = 0; h < 4; h++) {
             const int j = imin(j0 + h * nw, n - 1);
             const double* a = A + (long long)j * p.lda;
 #pragma unroll
             for (int r = 0; r < NR; r++) v[h][r] = a[imin(imax(4 * (j >> 2) + lane + 32 * r, j), n - 1)];
         }
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
+        for (int h = 0; h < 4; h++) {
             const int j = j0 + h * nw;
             if (j >= n) continue;
             float* Lc = L + cb(j, n4);  // Lc[i] = L(i, j)
@@ -388,23 +390,33 @@ __global__ void __launch_bounds__(128, 6) dsposv_kernel(SposvParams p) {
         for (;;) {
             unsigned long long rn = 0, xn = 0;
             for (int i = tid; i < n; i += T) {
-                // four partial sums: independent loads and FMA chains in flight
+                // row i of the symmetric A: A(i, 0..i-1) along row i of the lower triangle
+                // (consecutive threads, consecutive rows: coalesced), then A(i..n-1, i) down
+                // column i (contiguous for the thread: 16-byte loads); four partial sums
                 double s0 = b[i], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                const double* ai = A + i;
                 int j = 0;
-                for (; j + 3 < n; j += 4) {
-                    const double a0 = (j <= i) ? A[i + (long long)j * p.lda] : A[j + (long long)i * p.lda];
-                    const double a1 = (j + 1 <= i) ? A[i + (long long)(j + 1) * p.lda] : A[j + 1 + (long long)i * p.lda];
-                    const double a2 = (j + 2 <= i) ? A[i + (long long)(j + 2) * p.lda] : A[j + 2 + (long long)i * p.lda];
-                    const double a3 = (j + 3 <= i) ? A[i + (long long)(j + 3) * p.lda] : A[j + 3 + (long long)i * p.lda];
-                    s0 = fma(-a0, xv[j], s0);
-                    s1 = fma(-a1, xv[j + 1], s1);
-                    s2 = fma(-a2, xv[j + 2], s2);
-                    s3 = fma(-a3, xv[j + 3], s3);
+                for (; j + 3 < i; j += 4) {
+                    s0 = fma(-ai[(long long)j * p.lda], xv[j], s0);
+                    s1 = fma(-ai[(long long)(j + 1) * p.lda], xv[j + 1], s1);
+                    s2 = fma(-ai[(long long)(j + 2) * p.lda], xv[j + 2], s2);
+                    s3 = fma(-ai[(long long)(j + 3) * p.lda], xv[j + 3], s3);
                 }
-                for (; j < n; j++) {
-                    const double a = (j <= i) ? A[i + (long long)j * p.lda] : A[j + (long long)i * p.lda];
-                    s0 = fma(-a, xv[j], s0);
+                for (; j < i; j++) s0 = fma(-ai[(long long)j * p.lda], xv[j], s0);
+                const double* ci = A + (long long)i * p.lda;
+                int k = i;
+                if ((reinterpret_cast<uintptr_t>(ci + k) & 15u) != 0) {
+                    s1 = fma(-ci[k], xv[k], s1);
+                    k++;
                 }
+                for (; k + 3 < n; k += 4) {
+                    const double2 u = ldg2(ci + k), v = ldg2(ci + k + 2);
+                    s0 = fma(-u.x, xv[k], s0);
+                    s1 = fma(-u.y, xv[k + 1], s1);
+                    s2 = fma(-v.x, xv[k + 2], s2);
+                    s3 = fma(-v.y, xv[k + 3], s3);
+                }
+                for (; k < n; k++) s2 = fma(-ci[k], xv[k], s2);
                 const double s = (s0 + s1) + (s2 + s3);
                 rv[i] = s;
                 rn = absbits(s) > rn ? absbits(s) : rn;
