@@ -433,6 +433,7 @@ def main():
 
     if not args.no_extras:
         result["forms"] = plain_forms(bf, torch, points, peak, hbm)
+        result["hot"] = hot_forms(bf, torch, points)
         result["e2e"] = end_to_end(bf, torch, dev, points)
         del points
         torch.cuda.empty_cache()
@@ -495,6 +496,83 @@ def plain_forms(bf, torch, points, peak, hbm):
             rows.append(row)
         forms[r] = rows
     return forms
+
+
+def _sub_ms(bf, torch, p, r, b, flush=None, reps=10):
+    """Median CUDA-event time of routine r on the first b problems of point p.  Before each
+    repetition the operand that the routine overwrites is restored from a saved copy (outside
+    the timed region; the copy itself leaves the operands in L2); with `flush`, a buffer larger
+    than L2 is then overwritten, so that the repetition starts cold."""
+    n = p.n
+    fam = r.split("_")[0]
+    if fam == "dgemm":
+        A, B, C = p.A[:b], p.B[:b], p.C[:b]
+        C0 = C.clone()
+        prep = lambda: C.copy_(C0)
+        run = lambda: bf.dgemm("N", "T", 1.0, A, B, 1.0, C, m=n, n=n, k=n)
+        keep = C0
+    elif fam == "dtrsm":
+        X, Lu = p.X[:b], p.Lu[:b]
+        X0 = X.clone()
+        prep = lambda: X.copy_(X0)
+        run = lambda: bf.dtrsm("R", "L", "T", "U", 1.0, Lu, X, m=n, n=n)
+        keep = X0
+    else:
+        p.restore_s()
+        S, info = p.S[:b], p.info[:b]
+        S0 = S.clone()
+        prep = lambda: S.copy_(S0)
+        run = lambda: bf.dpotrf(S, n=n, info=info)
+        keep = S0
+    ts = []
+    for rep in range(reps + 1):
+        prep()
+        if flush is not None:
+            flush.fill_(rep & 0x7F)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        e1.synchronize()
+        if rep:
+            ts.append(e0.elapsed_time(e1))
+    prep()
+    del keep
+    if fam == "dpotrf" and int(info.abs().max()) != 0:
+        raise RuntimeError("hot-cache dpotrf failed")
+    return statistics.median(ts)
+
+
+def hot_forms(bf, torch, points):
+    """Hot-cache figures, the paper's own setting (operands resident in cache across
+    repetitions): for every lda = n point, a sub-batch small enough to stay in the 126 MiB L2
+    (48 MiB of operands), timed back to back, median of 10.  Plus the 4096 x n = 24 workload
+    hot and cold (512 MiB overwritten between repetitions)."""
+    out = {}
+    budget = 48 << 20
+    for r, nops in (("dgemm_nt", 3), ("dtrsm_rltu", 2), ("dpotrf", 1)):
+        rows = []
+        for p in points:
+            if p.pad:
+                continue
+            b = max(1, min(p.nbatch(r), budget // (nops * p.n * p.ld * 8)))
+            ms = _sub_ms(bf, torch, p, r, b)
+            rows.append([p.n, b, round(b * flops(r, p.n) / (ms * 1e-3) / 1e9, 2)])
+        out[r] = rows
+    p24 = next(p for p in points if p.n == 24 and p.pad == 0)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=p24.A.device)
+    small = {}
+    for r in ("dgemm_nt", "dpotrf"):
+        hot = _sub_ms(bf, torch, p24, r, 4096)
+        cold = _sub_ms(bf, torch, p24, r, 4096, flush=flush)
+        f = 4096 * flops(r, 24)
+        small[r] = {"hot_gflops": round(f / (hot * 1e-3) / 1e9, 2), "hot_ms": round(hot, 4),
+                    "cold_gflops": round(f / (cold * 1e-3) / 1e9, 2), "cold_ms": round(cold, 4)}
+    del flush
+    out["n24_batch4096"] = small
+    out["columns"] = "[n, sub-batch, GFLOP/s]"
+    return out
 
 
 def end_to_end(bf, torch, dev, points, cap_bytes=32 << 20):
