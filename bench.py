@@ -459,7 +459,7 @@ def plain_forms(bf, torch, points, peak, hbm):
     """Chosen (size switch) vs each plain variant, lda = n, 2 timed repetitions each."""
     forms = {}
     variants = {"dgemm": [("direct", 0), ("packed", 1)], "dtrsm": [("direct", 0), ("packed", 1)],
-                "dpotrf": [("direct", 0), ("packed", 1), ("blocked", 2)]}
+                "dpotrf": [("direct", 0), ("packed", 1), ("blocked", 2), ("cta", 4)]}
     routine_id = {"dgemm": bf.ROUTINE_DGEMM, "dtrsm": bf.ROUTINE_DTRSM, "dpotrf": bf.ROUTINE_DPOTRF}
     for r in ("dgemm_nn", "dgemm_nt", "dgemm_tn", "dtrsm_rltu", "dpotrf"):
         fam = r.split("_")[0]
@@ -471,10 +471,12 @@ def plain_forms(bf, torch, points, peak, hbm):
             for name, var in [("chosen", None)] + variants[fam]:
                 if fam == "dpotrf" and name == "packed" and p.n > 16:
                     continue
+                if fam == "dpotrf" and name == "cta" and p.n < 16:
+                    continue
                 if var is not None:
                     code = {"dgemm": (2 if r[-2] == "t" else 0) + (1 if r[-1] == "t" else 0),
                             "dtrsm": 8 + 2 + 1, "dpotrf": 0}[fam]
-                    bf.tune_set(routine_id[fam], code, 0, 1 << 30, var)
+                    bf.tune_set(routine_id[fam], code, 0, 1 << 30, var | bf.TUNE_FORCE)
                 try:
                     ts = []
                     for rep in range(3):

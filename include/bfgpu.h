@@ -51,6 +51,13 @@ typedef struct CUstream_st* bf_stream_t; /* identical to cudaStream_t */
 #define BF_VARIANT_BLOCKED 2 /* dpotrf only: right-looking sequence of the above kernels */
 #define BF_VARIANT_TINY 3    /* dgemm (m, n, k <= 4) and dtrsm (orders <= 8): one thread   */
                              /* per problem, problems staged through shared memory       */
+#define BF_VARIANT_CTA 4     /* dpotrf 'L' only, n <= 256: one problem per CTA (left-      */
+                             /* looking by 16-column panels); batches too small to fill   */
+                             /* the GPU with one problem per thread                       */
+#define BF_TUNE_FORCE 0x100  /* or'ed into `variant`: the entry holds at every batch size; */
+                             /* without it, dpotrf batches too small to fill the GPU one  */
+                             /* problem per thread still switch to BF_VARIANT_CTA (or to  */
+                             /* BF_VARIANT_BLOCKED for n > 64, batch < 20000)             */
 
 /* ------------------------------------------------------------------------ */
 /* dgemm (section 2.1): C <= alpha * op(A) * op(B) + beta * C,               */
@@ -371,7 +378,7 @@ int bf_ragged_potrf_potrs_noalloc(int batch, const int* n_host, int nrhs, double
 /*            unit; dpotrf: lda & 1 (even / odd leading dimension).        */
 /*            -1 matches every code.                                        */
 /*   [n_lo, n_hi]  matrix order range (dgemm: max(m, n); dtrsm: order of A)   */
-/*   variant  BF_VARIANT_*                                                    */
+/*   variant  BF_VARIANT_*, optionally | BF_TUNE_FORCE                        */
 /*   p0..p3   dgemm: TM, TN, KC, P (super-tile rows/cols, k-slice, problems   */
 /*            per CTA; 0 = default); dtrsm: MR (4/8), P, CTAs per SM (1/2);  */
 /*            dpotrf: T, NB,                                                */

@@ -11,7 +11,7 @@ namespace bf {
 
 // Kernel variants the size switch chooses between (section 2.4: direct 'D'
 // for very small sizes, packing variants for larger ones).
-enum Variant : int { VAR_DIRECT = 0, VAR_PACKED = 1, VAR_BLOCKED = 2, VAR_TINY = 3 };
+enum Variant : int { VAR_DIRECT = 0, VAR_PACKED = 1, VAR_BLOCKED = 2, VAR_TINY = 3, VAR_CTA = 4 };
 
 struct GemmConfig {
     int variant;  // VAR_DIRECT or VAR_PACKED
@@ -62,7 +62,8 @@ struct TrsmParams {
 
 struct PotrfConfig {
     int variant;  // VAR_DIRECT (lane per problem, in place), VAR_PACKED (lane per problem,
-                  // shared memory), VAR_BLOCKED (right-looking sequence of kernels)
+                  // shared memory), VAR_BLOCKED (right-looking sequence of kernels),
+                  // VAR_CTA (problem per CTA, lower, n <= 256; small batches)
     int T;        // threads (= problems) per CTA for the lane kernels
     int NB;       // block size of the blocked variant
     int rows;     // lane kernels: row-block height, 4 or 8
@@ -127,5 +128,7 @@ cudaError_t launch_dgetrs(int trans, int n, int nrhs, MatRef A, int lda, const i
 GemmConfig choose_gemm(bool ta, bool tb, int m, int n, int k, int lda, long long batch);
 TrsmConfig choose_trsm(int side, int uplo, int trans, int unit, int m, int n, long long batch);
 PotrfConfig choose_potrf(int n, int lda, long long batch);
+// dpotrf (lower) with one problem per CTA, n <= 256 (bf_ragged.cu)
+cudaError_t launch_dpotrf_cta(int n, MatRef A, int lda, long long batch, int* info, cudaStream_t s);
 
 }  // namespace bf

@@ -44,11 +44,11 @@ struct RaggedParams {
 #define BF_BIG_NB 16
 #define BF_BIG_NMAX 256  // backward substitution keeps x in 8 registers per lane
 
-// Four consecutive rows i..i+3 of column k of a problem in global memory (rows clamped to
-// n - 1): two 16-byte loads when the strip starts on a 16-byte boundary, one 16-byte load
-// between two single words when it starts 8 bytes past one.
-__device__ __forceinline__ void big_strip4(const double* S, int n, int i, int k, double* o) {
-    const double* p = S + i + (long long)k * n;
+// Four consecutive rows i..i+3 of column k of a problem in global memory (leading dimension
+// ld, rows clamped to n - 1): two 16-byte loads when the strip starts on a 16-byte boundary,
+// one 16-byte load between two single words when it starts 8 bytes past one.
+__device__ __forceinline__ void big_strip4(const double* S, int ld, int n, int i, int k, double* o) {
+    const double* p = S + i + (long long)k * ld;
     if (i + 4 <= n) {
         if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
             const double2 x = reinterpret_cast<const double2*>(p)[0], y = reinterpret_cast<const double2*>(p)[1];
@@ -59,7 +59,7 @@ __device__ __forceinline__ void big_strip4(const double* S, int n, int i, int k,
         }
     } else {
 #pragma unroll
-        for (int a = 0; a < 4; a++) o[a] = S[imin(i + a, n - 1) + (long long)k * n];
+        for (int a = 0; a < 4; a++) o[a] = S[imin(i + a, n - 1) + (long long)k * ld];
     }
 }
 
@@ -85,17 +85,15 @@ __device__ __forceinline__ void big_tile_index(int t, int nI, int& K, int& I) {
 //   (3) every thread: one row of the panel below, L(i,:) = W(i,:) L_JJ^{-T}, written to the
 //       matrix, and the diagonal block written back; the last warp solves
 //       Y(J:J+nb) = L_JJ^{-1} (rows J..J+nb) -- the forward substitution, panel by panel.
-// Then the backward substitution L^T X = Y, one warp per right-hand side.
-__device__ void big_problem(const RaggedParams& p, int q, double* sm) {
-    const int n = p.n[q];
-    const int r = p.nrhs;
+// Then the backward substitution L^T X = Y, one warp per right-hand side.  The matrix S has
+// leading dimension lds, the r right-hand sides Bq leading dimension n; returns the LAPACK
+// info (every thread).  Shared memory: 8 (16 n + n r + n + 16 blockDim) bytes at sm.
+__device__ int big_core(int n, double* S, int lds, double* Bq, int r, double* sm) {
     const int tid = threadIdx.x, T = blockDim.x, warp = tid >> 5, lane = tid & 31;
     double* W = sm;                            // panel: W[i + c n], i = row - J, c < 16
     double* X = sm + (size_t)BF_BIG_NB * n;    // n x nrhs right-hand sides
     double* rinv = X + (size_t)n * r;          // reciprocal pivots
     __shared__ int s_fail;
-    double* S = p.S + p.offS[q];
-    double* Bq = p.B + p.offB[q];
     for (int e = tid; e < n * r; e += T) X[e] = Bq[e];
     if (tid == 0) s_fail = 0;
     __syncthreads();
@@ -131,7 +129,7 @@ __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
 #pragma unroll
                     for (int b = 0; b < 4; b++) {
                         double col[4];
-                        big_strip4(S, n, i0, imin(k0 + b, n - 1), col);  // upper entries unused
+                        big_strip4(S, lds, n, i0, imin(k0 + b, n - 1), col);  // upper entries unused
 #pragma unroll
                         for (int a = 0; a < 4; a++) acc[a][b] = col[a];
                     }
@@ -144,9 +142,9 @@ __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
 #pragma unroll 2
                 for (int k = klo; k < khi; k++) {
                     double li[4], lk[4];
-                    big_strip4(S, n, i0, k, li);
+                    big_strip4(S, lds, n, i0, k, li);
 #pragma unroll
-                    for (int b = 0; b < 4; b++) lk[b] = S[imin(k0 + b, n - 1) + (long long)k * n];
+                    for (int b = 0; b < 4; b++) lk[b] = S[imin(k0 + b, n - 1) + (long long)k * lds];
 #pragma unroll
                     for (int a = 0; a < 4; a++)
 #pragma unroll
@@ -171,7 +169,7 @@ __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
             for (int e = T - 1 - tid; e < nb * r; e += T) {  // the last threads, fewest tiles
                 const int c = e % nb, rr = e / nb;
                 double s = X[J + c + (size_t)rr * n];
-                for (int k = 0; k < J; k++) s = fma(-S[J + c + (long long)k * n], X[k + (size_t)rr * n], s);
+                for (int k = 0; k < J; k++) s = fma(-S[J + c + (long long)k * lds], X[k + (size_t)rr * n], s);
                 X[J + c + (size_t)rr * n] = s;
             }
             if (sp > 1) {
@@ -229,13 +227,13 @@ __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
 #pragma unroll
                     for (int c2 = 0; c2 < c; c2++) x[c] = fma(-x[c2], W[c + c2 * n], x[c]);
                     x[c] *= rinv[J + c];
-                    S[J + i + (long long)(J + c) * n] = x[c];
+                    S[J + i + (long long)(J + c) * lds] = x[c];
                 }
             }
         }
         for (int e = tid; e < nb * nb; e += T) {
             const int c = e / nb, i = e - c * nb;
-            if (i >= c) S[J + i + (long long)(J + c) * n] = W[i + c * n];
+            if (i >= c) S[J + i + (long long)(J + c) * lds] = W[i + c * n];
         }
         if (warp == (T >> 5) - 1) {
             // Y(J:J+nb, :) = L_JJ^{-1} (rows J..J+nb), column-oriented by the last warp: step c
@@ -266,7 +264,7 @@ __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
             for (int s = 0; s < NS; s++) {
                 const int i = lane + 32 * s;
                 xr[s] = (i < n) ? y[i] : 0.0;
-                ln[s] = (i < n - 1) ? S[n - 1 + (long long)i * n] : 0.0;
+                ln[s] = (i < n - 1) ? S[n - 1 + (long long)i * lds] : 0.0;
             }
 #pragma unroll
             for (int s = NS - 1; s >= 0; s--) {
@@ -278,7 +276,7 @@ __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
                     for (int s2 = 0; s2 <= s; s2++) {
                         const int i = lane + 32 * s2;
                         lc[s2] = ln[s2];
-                        ln[s2] = (i < j - 1) ? S[j - 1 + (long long)i * n] : 0.0;
+                        ln[s2] = (i < j - 1) ? S[j - 1 + (long long)i * lds] : 0.0;
                     }
                     const double xj = __shfl_sync(0xffffffffu, xr[s], lj) * rinv[j];
                     if (lane == lj) xr[s] = xj;
@@ -294,8 +292,14 @@ __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
                 if (lane + 32 * s < n) Bq[lane + 32 * s + (size_t)rr * n] = xr[s];
         }
     }
-    if (tid == 0 && p.info) p.info[p.orig[q]] = fail;
     __syncthreads();
+    return fail;
+}
+
+__device__ void big_problem(const RaggedParams& p, int q, double* sm) {
+    const int n = p.n[q];
+    const int fail = big_core(n, p.S + p.offS[q], n, p.B + p.offB[q], p.nrhs, sm);
+    if (threadIdx.x == 0 && p.info) p.info[p.orig[q]] = fail;
 }
 
 // --------------------------------------------------------------------------- LANE: one problem per thread
@@ -320,6 +324,33 @@ __device__ void lane_problem(const RaggedParams& p, int q) {
         }
     }
     if (p.info) p.info[p.orig[q]] = info;
+}
+
+// --------------------------------------------------------------------------- uniform batches, one problem per CTA
+// dpotrf of a uniform batch with too few problems to fill the GPU one problem per thread (a
+// warp issues one FP64 instruction every 64 cycles, so the lane kernels need ~20,000
+// problems): the BIG items' left-looking Cholesky, one problem per CTA, any leading
+// dimension, no right-hand sides.  CTAs stride over the batch.
+__global__ void __launch_bounds__(128) dpotrf_cta_kernel(int n, MatRef A, int lda, long long batch, int* info) {
+    extern __shared__ __align__(16) double sm_cta[];
+    for (long long q = blockIdx.x; q < batch; q += gridDim.x) {
+        const int fail = big_core(n, A.mptr(q), lda, nullptr, 0, sm_cta);
+        if (threadIdx.x == 0 && info) info[q] = fail;
+    }
+}
+
+cudaError_t launch_dpotrf_cta(int n, MatRef A, int lda, long long batch, int* info, cudaStream_t s) {
+    const int T = 128;
+    const size_t smem = sizeof(double) * ((size_t)(BF_BIG_NB + 1) * n + 16 * (size_t)T);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(dpotrf_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const long long cap = 152LL * 16;
+    const unsigned grid = (unsigned)(batch < cap ? batch : cap);
+    dpotrf_cta_kernel<<<grid, T, smem, s>>>(n, A, lda, batch, info);
+    count_launch();
+    return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(512) ragged_persistent_kernel(RaggedParams p) {

@@ -17,6 +17,7 @@ namespace bf {
 struct TuneEntry {
     int routine, code, lo, hi;
     int variant, p0, p1, p2, p3;
+    bool force;  // holds at every batch size (the small-batch switch is not applied)
 };
 
 static std::mutex g_mu;
@@ -144,6 +145,21 @@ TrsmConfig choose_trsm(int side, int uplo, int trans, int unit, int m, int n, lo
     return c;
 }
 
+// Largest batch for which one problem per CTA beats the table's choice, by order (measured
+// crossovers: n = 16: ~1,200; 24: ~1,800; 32: ~3,500; 64-128: ~5,000-6,000; 192: above the
+// sweep's 7,281 (995 against 970 GFLOP/s); 256: above 9,728).  0: never (n < 16, where a CTA
+// per problem idles most of its threads).
+static long long cta_batch_limit(int n) {
+    if (n < 16 || n > 256) return 0;
+    if (n < 24) return 1024;
+    if (n < 32) return 1536;
+    if (n < 48) return 3072;
+    if (n < 64) return 6144;
+    if (n < 96) return 4096;
+    if (n < 192) return 6144;
+    return 9728;
+}
+
 PotrfConfig choose_potrf(int n, int lda, long long batch) {
     // Table code 0 holds even leading dimensions, code 1 odd ones (an odd lda leaves
     // every other column's strips off the 16-byte boundary, which changes the best
@@ -164,7 +180,9 @@ PotrfConfig choose_potrf(int n, int lda, long long batch) {
     c.rows = (code ? n >= 16 : n >= 24) ? 8 : 4;
     c.unroll = 2;
     TuneEntry e;
+    bool force = false;
     if (lookup(BF_ROUTINE_DPOTRF, code, n, &e)) {
+        force = e.force;
         c.variant = e.variant;
         if (e.p0 > 0) c.T = e.p0;
         if (e.p1 > 0) c.NB = e.p1;
@@ -172,8 +190,13 @@ PotrfConfig choose_potrf(int n, int lda, long long batch) {
         if (e.p3 > 0) c.unroll = e.p3;
     }
     // the table is measured on 2 GiB batches; a lane kernel on far fewer problems than
-    // that leaves most of the GPU idle, so small batches of larger orders stay blocked
-    if (c.variant != VAR_BLOCKED && n > 64 && batch < 20000) c.variant = VAR_BLOCKED;
+    // that leaves most of the GPU idle (one warp issues an FP64 instruction every 64 cycles):
+    // small batches go to one problem per CTA, up to the crossover measured on GB300
+    // (e.g. n = 128: 818 against 196 GFLOP/s at 608 problems), and the rest of the small
+    // batches of larger orders to the blocked sequence
+    if (!force && batch <= cta_batch_limit(n)) c.variant = VAR_CTA;
+    if (!force && c.variant != VAR_BLOCKED && c.variant != VAR_CTA && n > 64 && batch < 20000)
+        c.variant = VAR_BLOCKED;
     if (c.T < 32) c.T = 32;
     if (c.T > 256) c.T = 256;
     c.T = c.T / 32 * 32;
@@ -193,9 +216,11 @@ extern "C" int bf_tune_set(int routine, int code, int n_lo, int n_hi, int varian
                            int p2, int p3) {
     if (routine < BF_ROUTINE_DGEMM || routine > BF_ROUTINE_DPOTRF) return -1;
     if (n_lo > n_hi) return -3;
-    if (variant < 0 || variant > 3) return -5;
+    const bool force = (variant & BF_TUNE_FORCE) != 0;
+    variant &= ~BF_TUNE_FORCE;
+    if (variant < 0 || variant > 4) return -5;
     std::lock_guard<std::mutex> lk(bf::g_mu);
-    bf::g_table.push_back(bf::TuneEntry{routine, code, n_lo, n_hi, variant, p0, p1, p2, p3});
+    bf::g_table.push_back(bf::TuneEntry{routine, code, n_lo, n_hi, variant, p0, p1, p2, p3, force});
     return 0;
 }
 

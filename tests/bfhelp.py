@@ -27,7 +27,8 @@ def lower_part(X, n):
 
 @contextlib.contextmanager
 def forced(bf, routine, code, variant, p0=0, p1=0, p2=0, p3=0):
-    bf.tune_set(routine, code, 0, 1 << 30, variant, p0, p1, p2, p3)
+    """The variant at every batch size (no small-batch switch), for the duration of a block."""
+    bf.tune_set(routine, code, 0, 1 << 30, variant | bf.TUNE_FORCE, p0, p1, p2, p3)
     try:
         yield
     finally:

@@ -150,13 +150,24 @@ def test_tune_table(lib):
         assert lib.tune_query(lib.ROUTINE_DGEMM, 0, 24, 24, 24, 1000) == default
         assert lib.tune_query(lib.ROUTINE_DGEMM, 1, 40, 40, 40, 1000)[1] == 40
         lib.tune_set(lib.ROUTINE_DPOTRF, 0, 1, 300, lib.VARIANT_BLOCKED, 128, 16)
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 100, 100, 0, 10)[:3] == [lib.VARIANT_BLOCKED, 128, 16]
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 100, 100, 0, 10 ** 4)[:3] == [lib.VARIANT_BLOCKED, 128, 16]
         # dpotrf codes are the leading-dimension parity: an odd-lda entry leaves even lda alone
         lib.tune_set(lib.ROUTINE_DPOTRF, 1, 1, 300, lib.VARIANT_DIRECT, 64, 0, 8, 1)
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10 ** 5) == [lib.VARIANT_DIRECT, 64, 32, 8, 1]
-        # a lane kernel needs tens of thousands of problems: small batches of larger orders stay blocked
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10)[0] == lib.VARIANT_BLOCKED
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 100, 100, 0, 10)[:3] == [lib.VARIANT_BLOCKED, 128, 16]
+        # a lane kernel needs tens of thousands of problems: batches too small to fill the GPU
+        # go to one problem per CTA (n >= 16), the rest of the small batches of n > 64 to the
+        # blocked sequence
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10)[0] == lib.VARIANT_CTA
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 100, 100, 0, 10)[0] == lib.VARIANT_CTA
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10 ** 4)[0] == lib.VARIANT_BLOCKED
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 2000)[0] == lib.VARIANT_CTA
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 10 ** 4)[0] == lib.VARIANT_DIRECT
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 8, 8, 0, 10)[0] == lib.VARIANT_DIRECT
+        # a forced entry holds at every batch size
+        lib.tune_set(lib.ROUTINE_DPOTRF, 1, 90, 110, lib.VARIANT_DIRECT | lib.TUNE_FORCE, 64, 0, 8, 1)
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10) == [lib.VARIANT_DIRECT, 64, 32, 8, 1]
+        with pytest.raises(lib.BFError):
+            lib.tune_set(lib.ROUTINE_DPOTRF, 1, 90, 110, 5)
         # defaults of the lane kernel: 8-row blocks for odd lda from n = 16, for even lda from n = 24
         lib.tune_clear()
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 16, 16, 0, 10 ** 5)[3:] == [4, 2]

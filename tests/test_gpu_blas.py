@@ -201,7 +201,7 @@ def spd_upper_nan(batch, n, ld, seed):
 # leading-dimension parities (table code -1)
 POTRF_VARIANTS = [("direct4u2", 0, 0, 0, 4, 2), ("direct4u1", 0, 64, 0, 4, 1), ("direct8u1", 0, 0, 0, 8, 1),
                   ("direct8u2", 0, 256, 0, 8, 2), ("packed", 1, 128, 0, 0, 0), ("blocked8", 2, 0, 8, 0, 0),
-                  ("blocked32", 2, 0, 32, 0, 0)]
+                  ("blocked32", 2, 0, 32, 0, 0), ("cta", 4, 0, 0, 0, 0)]
 
 
 @pytest.mark.parametrize("vname,variant,T,NB,R,U", POTRF_VARIANTS, ids=[v[0] for v in POTRF_VARIANTS])

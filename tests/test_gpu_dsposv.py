@@ -31,7 +31,7 @@ def colmajor_batch(A_rowmajor):
     return np.ascontiguousarray(np.transpose(A_rowmajor, (0, 2, 1)))
 
 
-@pytest.mark.parametrize("n", [128, 96, 33, 5, 256])
+@pytest.mark.parametrize("n", [128, 96, 33, 5, 256, 1, 2, 127, 129, 200])
 def test_dsposv_conditioned(bf, oracle, n):
     batch = 30
     A, b, kap = bfsynth.precision_batch(batch, n, (1e2, 1e4, 1e6), seed=77 + n)
