@@ -445,6 +445,8 @@ def main():
         torch.cuda.empty_cache()
         result["next_rows"] = next_rows(bf, torch, dev, peak)
         torch.cuda.empty_cache()
+        result["vbatched"] = vbatched_form(bf, torch, dev, peak)
+        torch.cuda.empty_cache()
         if rank == 0:
             v, desc, cores = oracle_sample(args.cpu_budget)
             result["cpu_baseline"] = {"value": round(v, 3), "unit": "GFLOP/s", "cores": cores,
@@ -788,6 +790,71 @@ def precision_form(bf, torch, dev, rank, batch=16384, n=128):
     return {"batch": batch, "n": n, "mixed_ms": round(t_mixed, 3), "fp64_ms": round(t_fp64, 3),
             "speedup": round(t_fp64 / t_mixed, 3), "eta_max": float(eta.max()),
             "all_info_zero": int((info != 0).sum()) == 0, "per_kappa": per}
+
+
+def vbatched_form(bf, torch, dev, peak):
+    """The variable-size entry points on mixed sizes: dpotrf on the ragged workload's 200,000
+    orders (log-uniform in [2, 200], factor only), dgemm_nn and dtrsm_rltu on 100,000 problems
+    with m, n, k uniform in [1, 64]; every problem's sizes and pointers in device arrays."""
+    import ctypes
+
+    import bfsynth
+    ip = lambda t: ctypes.c_void_p(t.data_ptr())
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    out = {}
+    ns = bfsynth.ragged_orders(200000, 2, 200, bfsynth.BASE_SEED + 3)
+    S0, offS, _, _ = bfsynth.ragged_spd(ns, 1, bfsynth.BASE_SEED + 4, device=dev)
+    S = S0.clone()
+    n_d = ns.to(dev)
+    ptr = (S.data_ptr() + 8 * offS.to(dev, torch.int64)).contiguous()
+    info = torch.empty(len(ns), dtype=torch.int32, device=dev)
+
+    def potrf():
+        _ok(bf.bf_dpotrf_vbatched(b"L", ip(n_d), ip(ptr), ip(n_d), ip(info), len(ns), 200, st))
+    ms = _events_ms(torch, potrf, before=lambda: S.copy_(S0))
+    nf = ns.to(torch.float64)
+    f = float((nf ** 3 / 3 + nf ** 2 / 2 + nf / 6).sum())
+    out["dpotrf_ragged_200k"] = {"ms": round(ms, 3), "gflops": round(f / ms / 1e6, 1),
+                                 "frac": round(f / ms * 1e3 / peak, 4), "all_info_zero": int(info.abs().max()) == 0}
+    del S0, S, ptr
+    g = torch.Generator().manual_seed(bfsynth.BASE_SEED + 7)
+    cnt = 100000
+    mm, nn, kk = (torch.randint(1, 65, (cnt,), generator=g) for _ in range(3))
+
+    def offsets(sz):
+        o = torch.zeros(cnt, dtype=torch.int64)
+        o[1:] = torch.cumsum(sz, 0)[:-1]
+        return o, int(sz.sum())
+    (oa, na), (ob, nb), (oc, nc), (ol, nl) = (offsets(x) for x in (mm * kk, kk * nn, mm * nn, nn * nn))
+    A = torch.randn(na, dtype=torch.float64, device=dev)
+    B = torch.randn(nb, dtype=torch.float64, device=dev)
+    C = torch.randn(nc, dtype=torch.float64, device=dev)
+    L = torch.randn(nl, dtype=torch.float64, device=dev) * 0.01  # unit lower: the strict part is read
+    m_d, n_d, k_d = (x.to(dev, torch.int32) for x in (mm, nn, kk))
+    pa, pb, pc, pl = ((X.data_ptr() + 8 * o).to(dev) for X, o in ((A, oa), (B, ob), (C, oc), (L, ol)))
+    dinfo = torch.empty(cnt, dtype=torch.int32, device=dev)
+
+    def gemm():
+        _ok(bf.bf_dgemm_vbatched(b"N", b"N", ip(m_d), ip(n_d), ip(k_d), 1.0, ip(pa), ip(m_d), ip(pb), ip(k_d), 1.0,
+                                 ip(pc), ip(m_d), cnt, 64, 64, 64, ip(dinfo), st))
+    ms = _events_ms(torch, gemm)
+    f = float((2 * mm * nn * kk).to(torch.float64).sum())
+    out["dgemm_nn_100k_mnk_1_64"] = {"ms": round(ms, 3), "gflops": round(f / ms / 1e6, 1),
+                                     "frac": round(f / ms * 1e3 / peak, 4), "dinfo_zero": int(dinfo.abs().max()) == 0}
+
+    def trsm():
+        _ok(bf.bf_dtrsm_vbatched(b"R", b"L", b"T", b"U", ip(m_d), ip(n_d), 1.0, ip(pl), ip(n_d), ip(pc), ip(m_d),
+                                 cnt, 64, 64, ip(dinfo), st))
+    ms = _events_ms(torch, trsm)
+    f = float((mm * nn * (nn - 1)).to(torch.float64).sum())
+    out["dtrsm_rltu_100k_mn_1_64"] = {"ms": round(ms, 3), "gflops": round(f / ms / 1e6, 1),
+                                      "frac": round(f / ms * 1e3 / peak, 4), "dinfo_zero": int(dinfo.abs().max()) == 0}
+    return out
+
+
+def _ok(status):
+    if status != 0:
+        raise RuntimeError(f"library call returned {status}")
 
 
 def next_rows(bf, torch, dev, peak):

@@ -83,6 +83,21 @@ int bf_dgemm_batched(char transa, char transb, int m, int n, int k, double alpha
                      const double* const* Aarray, int lda, const double* const* Barray, int ldb,
                      double beta, double* const* Carray, int ldc, int batch, bf_stream_t stream);
 
+/* Variable-size batches ("vbatched"; the paper's sizes are known only at run time, section */
+/* 1).  Problem q has its own sizes m[q], n[q], k[q], leading dimensions lda[q], ldb[q],     */
+/* ldc[q] and matrices Aarray[q], Barray[q], Carray[q]: all device arrays of `batch`        */
+/* entries.  max_m, max_n, max_k bound the sizes over the batch (they size the launch).     */
+/* A problem whose own arguments are illegal (a size < 0 or above its bound, a leading     */
+/* dimension too small, a null matrix that would be read or written) is skipped and         */
+/* dinfo[q] = minus that argument's position in this call (-3 m, -4 n, -5 k, -7 A, -8 lda,  */
+/* -9 B, -10 ldb, -12 C, -13 ldc); else dinfo[q] = 0.  dinfo (device) may be NULL.  The     */
+/* return value reports the call's own arguments (transa, transb, batch, max_*, and the     */
+/* device arrays themselves being non-null when batch > 0) as the uniform calls do.         */
+int bf_dgemm_vbatched(char transa, char transb, const int* m, const int* n, const int* k, double alpha,
+                      const double* const* Aarray, const int* lda, const double* const* Barray,
+                      const int* ldb, double beta, double* const* Carray, const int* ldc, int batch,
+                      int max_m, int max_n, int max_k, int* dinfo, bf_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* dtrsm (section 3.1 "dtrsm"): solve op(A) X = alpha B (side 'L') or         */
 /* X op(A) = alpha B (side 'R'); X overwrites B (m x n).  A is triangular    */
@@ -102,6 +117,12 @@ int bf_dtrsm_batched(char side, char uplo, char transa, char diag, int m, int n,
                      const double* const* Aarray, int lda, double* const* Barray, int ldb,
                      int batch, bf_stream_t stream);
 
+/* Variable-size dtrsm (see bf_dgemm_vbatched): per problem m[q], n[q], lda[q], ldb[q],    */
+/* Aarray[q], Barray[q]; dinfo[q] = 0 or -5 m, -6 n, -8 A, -9 lda, -10 B, -11 ldb.          */
+int bf_dtrsm_vbatched(char side, char uplo, char transa, char diag, const int* m, const int* n,
+                      double alpha, const double* const* Aarray, const int* lda, double* const* Barray,
+                      const int* ldb, int batch, int max_m, int max_n, int* dinfo, bf_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* dpotrf (section 3.1 "dpotrf"): Cholesky factorisation A = L L^T of SPD    */
 /* matrices, uplo 'L': the lower triangle of A is read and overwritten by L; */
@@ -119,6 +140,14 @@ int bf_dpotrf_strided_batched(char uplo, int n, double* A, int lda, long long st
 
 int bf_dpotrf_batched(char uplo, int n, double* const* Aarray, int lda, int* info, int batch,
                       bf_stream_t stream);
+
+/* Variable-size dpotrf (see bf_dgemm_vbatched): per problem n[q], lda[q], Aarray[q].      */
+/* info[q] = the LAPACK info (>= 0), or -2 (n[q] < 0 or above max_n) / -4 (lda[q] too      */
+/* small) for a skipped problem.  uplo 'U', or max_n above BF_VBATCHED_POTRF_NMAX, returns  */
+/* BF_ERR_NOT_SUPPORTED (nothing launched).                                                */
+#define BF_VBATCHED_POTRF_NMAX 1024
+int bf_dpotrf_vbatched(char uplo, const int* n, double* const* Aarray, const int* lda, int* info, int batch,
+                       int max_n, bf_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* dsyrk (section 3.1 "dsyrk": dgemm whose A and B coincide):               */

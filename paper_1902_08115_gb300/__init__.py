@@ -47,6 +47,10 @@ _SIGS = {
     "bf_dpotrf": [_c, _i, _vp, _i, _vp, _vp],
     "bf_dpotrf_strided_batched": [_c, _i, _vp, _i, _ll, _vp, _i, _vp],
     "bf_dpotrf_batched": [_c, _i, _vp, _i, _vp, _i, _vp],
+    "bf_dgemm_vbatched": [_c, _c, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _d, _vp, _vp, _i, _i, _i, _i, _vp,
+                          _vp],
+    "bf_dtrsm_vbatched": [_c, _c, _c, _c, _vp, _vp, _d, _vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp],
+    "bf_dpotrf_vbatched": [_c, _vp, _vp, _vp, _vp, _i, _i, _vp],
     "bf_dpotrs": [_c, _i, _i, _vp, _i, _vp, _i, _vp],
     "bf_dpotrs_strided_batched": [_c, _i, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _vp],
     "bf_tune_set": [_i, _i, _i, _i, _i, _i, _i, _i, _i],
@@ -213,6 +217,87 @@ def dpotrs(L, B, n=None, nrhs=None, uplo: str = "L", stream=None):
     _check("bf_dpotrs_strided_batched", bf_dpotrs_strided_batched(
         _ch(uplo), n, nrhs, _ptr(L), ldL, sL, _ptr(B), ldB, sB, bB, _stream(stream)))
     return B
+
+
+# ---------------------------------------------------------------------------- variable-size batches
+def _dims2(X):
+    """(ncols, ld) of one problem: a contiguous column-major (ncols, ld) float64 tensor."""
+    if X.dim() != 2 or X.stride(1) != 1 or X.stride(0) != X.shape[1] or X.dtype.itemsize != 8:
+        raise ValueError("each problem must be a contiguous column-major (ncols, ld) float64 tensor")
+    return X.shape[0], X.shape[1]
+
+
+class _DevArrays:
+    """Device copies of per-problem sizes and pointers, kept alive on the launch stream."""
+
+    def __init__(self, dev, stream):
+        self.dev, self.stream, self.keep = dev, stream, []
+
+    def ints(self, vals):
+        import torch
+        t = torch.tensor([int(v) for v in vals], dtype=torch.int32, device=self.dev)
+        self.keep.append(t)
+        return _ptr(t)
+
+    def ptrs(self, ts):
+        import torch
+        t = torch.tensor([x.data_ptr() for x in ts], dtype=torch.int64, device=self.dev)
+        self.keep.append(t)
+        return _ptr(t)
+
+    def done(self):
+        if self.stream is not None:
+            for t in self.keep:
+                t.record_stream(self.stream)
+
+
+def dgemm_vbatched(transa: str, transb: str, alpha: float, As, Bs, beta: float, Cs, ms, ns, ks, stream=None):
+    """C_q <= alpha op(A_q) op(B_q) + beta C_q for lists of problems of different sizes (m_q, n_q,
+    k_q), each matrix a column-major (ncols, ld) tensor.  Returns dinfo (per problem: 0, or
+    minus the position of an illegal argument of that problem, which was skipped)."""
+    import torch
+    batch = len(Cs)
+    dev = Cs[0].device
+    d = _DevArrays(dev, stream)
+    dinfo = torch.empty(batch, dtype=torch.int32, device=dev)
+    _check("bf_dgemm_vbatched", bf_dgemm_vbatched(
+        _ch(transa), _ch(transb), d.ints(ms), d.ints(ns), d.ints(ks), alpha, d.ptrs(As),
+        d.ints(_dims2(A)[1] for A in As), d.ptrs(Bs), d.ints(_dims2(B)[1] for B in Bs), beta, d.ptrs(Cs),
+        d.ints(_dims2(C)[1] for C in Cs), batch, max(ms, default=0), max(ns, default=0), max(ks, default=0),
+        _ptr(dinfo), _stream(stream)))
+    d.done()
+    return dinfo
+
+
+def dtrsm_vbatched(side: str, uplo: str, transa: str, diag: str, alpha: float, As, Bs, ms, ns, stream=None):
+    """op(A_q) X = alpha B_q (side 'L') or X op(A_q) = alpha B_q (side 'R') for lists of problems
+    of different sizes; X overwrites B_q.  Returns dinfo (see dgemm_vbatched)."""
+    import torch
+    batch = len(Bs)
+    dev = Bs[0].device
+    d = _DevArrays(dev, stream)
+    dinfo = torch.empty(batch, dtype=torch.int32, device=dev)
+    _check("bf_dtrsm_vbatched", bf_dtrsm_vbatched(
+        _ch(side), _ch(uplo), _ch(transa), _ch(diag), d.ints(ms), d.ints(ns), alpha, d.ptrs(As),
+        d.ints(_dims2(A)[1] for A in As), d.ptrs(Bs), d.ints(_dims2(B)[1] for B in Bs), batch,
+        max(ms, default=0), max(ns, default=0), _ptr(dinfo), _stream(stream)))
+    d.done()
+    return dinfo
+
+
+def dpotrf_vbatched(As, ns, uplo: str = "L", stream=None):
+    """Cholesky (lower) of a list of problems of different orders n_q, in place; returns info
+    (LAPACK info per problem, or minus the position of an illegal argument of that problem)."""
+    import torch
+    batch = len(As)
+    dev = As[0].device
+    d = _DevArrays(dev, stream)
+    info = torch.empty(batch, dtype=torch.int32, device=dev)
+    _check("bf_dpotrf_vbatched", bf_dpotrf_vbatched(
+        _ch(uplo), d.ints(ns), d.ptrs(As), d.ints(_dims2(A)[1] for A in As), _ptr(info), batch,
+        max(ns, default=0), _stream(stream)))
+    d.done()
+    return info
 
 
 def dsyrk(uplo: str, trans: str, alpha: float, A, beta: float, C, n=None, k=None, stream=None):

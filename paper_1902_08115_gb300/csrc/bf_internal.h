@@ -130,5 +130,8 @@ TrsmConfig choose_trsm(int side, int uplo, int trans, int unit, int m, int n, lo
 PotrfConfig choose_potrf(int n, int lda, long long batch);
 // dpotrf (lower) with one problem per CTA, n <= 256 (bf_ragged.cu)
 cudaError_t launch_dpotrf_cta(int n, MatRef A, int lda, long long batch, int* info, cudaStream_t s);
+// dpotrf 'L' of a variable-size batch (device arrays n, Aarray, lda; max_n <= BF_VBATCHED_POTRF_NMAX)
+cudaError_t launch_dpotrf_vbatched(const int* n, double* const* A, const int* lda, int* info, long long batch,
+                                   int max_n, cudaStream_t s);
 
 }  // namespace bf

@@ -353,6 +353,60 @@ cudaError_t launch_dpotrf_cta(int n, MatRef A, int lda, long long batch, int* in
     return cudaGetLastError();
 }
 
+// --------------------------------------------------------------------------- variable-size batches
+// dpotrf 'L' of a variable-size batch: problem q has order n[q] and leading dimension lda[q]
+// (device arrays) at Aarray[q].  An illegal problem (n < 0 or above max_n: -2; lda < max(1, n):
+// -4) is skipped with info = that negative position.  Orders up to 32: one problem per
+// thread (the lane Cholesky, in place); larger: one problem per CTA (the left-looking CTA
+// Cholesky above), CTAs striding over the batch.
+__device__ __forceinline__ int vpotrf_check(int n, int lda, int max_n) {
+    if (n < 0 || n > max_n) return -2;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    return 0;
+}
+
+__global__ void __launch_bounds__(128) dpotrf_vbatched_lane_kernel(const int* n, double* const* A, const int* lda,
+                                                                 int* info, long long batch, int max_n) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= batch) return;
+    const int nq = n[q], ldq = lda[q];
+    int r = vpotrf_check(nq, ldq, max_n);
+    if (r == 0 && nq > 0) r = potrf_lane_global<4, 2>(A[q], ldq, nq);
+    if (info) info[q] = r;
+}
+
+__global__ void __launch_bounds__(128) dpotrf_vbatched_cta_kernel(const int* n, double* const* A, const int* lda,
+                                                                int* info, long long batch, int max_n) {
+    extern __shared__ __align__(16) double sm_v[];
+    for (long long q = blockIdx.x; q < batch; q += gridDim.x) {
+        const int nq = n[q], ldq = lda[q];
+        int r = vpotrf_check(nq, ldq, max_n);  // the same in every thread
+        if (r == 0 && nq > 0) r = big_core(nq, A[q], ldq, nullptr, 0, sm_v);
+        if (threadIdx.x == 0 && info) info[q] = r;
+    }
+}
+
+cudaError_t launch_dpotrf_vbatched(const int* n, double* const* A, const int* lda, int* info, long long batch,
+                                   int max_n, cudaStream_t s) {
+    if (batch == 0) return cudaSuccess;
+    if (max_n <= 32) {
+        dpotrf_vbatched_lane_kernel<<<(unsigned)((batch + 127) / 128), 128, 0, s>>>(n, A, lda, info, batch, max_n);
+        count_launch();
+        return cudaGetLastError();
+    }
+    const int T = 128;
+    const size_t smem = sizeof(double) * ((size_t)(BF_BIG_NB + 1) * max_n + 16 * (size_t)T);
+    if (smem > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(dpotrf_vbatched_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const long long cap = 152LL * 16;
+    dpotrf_vbatched_cta_kernel<<<(unsigned)(batch < cap ? batch : cap), T, smem, s>>>(n, A, lda, info, batch, max_n);
+    count_launch();
+    return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(512) ragged_persistent_kernel(RaggedParams p) {
     extern __shared__ double smem[];
     __shared__ int s_item;

@@ -1,0 +1,298 @@
+// bf_vbatched.cu -- variable-size batches ("vbatched"): every problem of the batch has its own
+// sizes, leading dimensions and device pointers, read from device arrays, because the paper's
+// matrices have sizes known only at run time (section 1).  The uniform batches carry the
+// paper's kernels; here the problems of one launch differ, so the kernels read each problem's
+// sizes and map threads to (problem, piece of work) pairs:
+//   dgemm  -- one thread per 4x4 tile of C (section 2.1's register tile), the problems of a
+//             CTA packed so that a CTA holds ~blockDim tiles; the k loop reads op(A) and op(B)
+//             from global memory (L1) as in the direct variant ('D', section 2.2);
+//   dtrsm  -- one thread per independent row (right side) or column (left side) of B, the
+//             paper's observation that right-side solves are independent row systems
+//             (section 3.1 "dtrsm"), solved in place by substitution;
+//   dpotrf -- csrc/bf_ragged.cu: one problem per thread up to order 32, else one per CTA.
+// Illegal arguments of one problem (a size below zero or above its max_*, a leading dimension
+// too small, a null pointer where data is needed) skip that problem and set its dinfo entry to
+// minus the argument's position in the call; the other problems proceed.
+#include "bf_internal.h"
+#include "../../include/bfgpu.h"
+
+namespace bf {
+
+struct VGemmParams {
+    const int *m, *n, *k;
+    double alpha, beta;
+    const double* const* A;
+    const int* lda;
+    const double* const* B;
+    const int* ldb;
+    double* const* C;
+    const int* ldc;
+    int* dinfo;
+    long long batch;
+    int max_m, max_n, max_k;
+    int tiles_max;  // ceil(max_m / 4) * ceil(max_n / 4)
+    int P;          // problems per CTA
+};
+
+// 0, or minus the position of the problem's first illegal argument
+__device__ __forceinline__ int vgemm_check(const VGemmParams& p, bool ta, bool tb, long long q, int m, int n, int k) {
+    if (m < 0 || m > p.max_m) return -3;
+    if (n < 0 || n > p.max_n) return -4;
+    if (k < 0 || k > p.max_k) return -5;
+    const int ra = ta ? k : m, rb = tb ? n : k;
+    if (p.lda[q] < (ra > 1 ? ra : 1)) return -8;
+    if (p.ldb[q] < (rb > 1 ? rb : 1)) return -10;
+    if (p.ldc[q] < (m > 1 ? m : 1)) return -13;
+    const bool reads_ab = m > 0 && n > 0 && k > 0 && p.alpha != 0.0;
+    if (reads_ab && !p.A[q]) return -7;
+    if (reads_ab && !p.B[q]) return -9;
+    if (m > 0 && n > 0 && !p.C[q]) return -12;
+    return 0;
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(128) dgemm_vbatched_kernel(VGemmParams p) {
+    const int T = blockDim.x;
+    for (long long q0 = (long long)blockIdx.x * p.P; q0 < p.batch; q0 += (long long)gridDim.x * p.P) {
+        for (int u = threadIdx.x; u < p.P * p.tiles_max; u += T) {
+            const long long q = q0 + u / p.tiles_max;
+            const int t = u % p.tiles_max;
+            if (q >= p.batch) continue;
+            const int m = p.m[q], n = p.n[q], k = p.k[q];
+            const int bad = vgemm_check(p, TA, TB, q, m, n, k);
+            if (t == 0 && p.dinfo) p.dinfo[q] = bad;
+            if (bad) continue;
+            const int tm = (m + 3) / 4;
+            if (t >= tm * ((n + 3) / 4)) continue;
+            const int i0 = 4 * (t % tm), j0 = 4 * (t / tm);
+            const double* A = p.A[q];
+            const double* B = p.B[q];
+            double* C = p.C[q];
+            const int lda = p.lda[q], ldb = p.ldb[q], ldc = p.ldc[q];
+            int ri[4], cj[4];
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+                ri[a] = imin(i0 + a, m - 1);
+                cj[a] = imin(j0 + a, n - 1);
+            }
+            double acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; a++)
+#pragma unroll
+                for (int b = 0; b < 4; b++) acc[a][b] = 0.0;
+            if (p.alpha != 0.0) {  // alpha == 0: A and B are not read
+#pragma unroll 2
+                for (int pp = 0; pp < k; pp++) {
+                    double x[4], y[4];
+#pragma unroll
+                    for (int a = 0; a < 4; a++) {
+                        x[a] = TA ? ldg(A + pp + (long long)ri[a] * lda) : ldg(A + ri[a] + (long long)pp * lda);
+                        y[a] = TB ? ldg(B + cj[a] + (long long)pp * ldb) : ldg(B + pp + (long long)cj[a] * ldb);
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; a++)
+#pragma unroll
+                        for (int b = 0; b < 4; b++) acc[a][b] = fma(x[a], y[b], acc[a][b]);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+#pragma unroll
+                for (int a = 0; a < 4; a++) {
+                    const int i = i0 + a, j = j0 + b;
+                    if (i < m && j < n) {
+                        double* cp = C + i + (long long)j * ldc;
+                        const double v = p.alpha * acc[a][b];
+                        *cp = (p.beta == 0.0) ? v : fma(p.beta, *cp, v);  // beta == 0: C not read
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------ dtrsm
+struct VTrsmParams {
+    int right, lowerT, transA, unit;  // lowerT: op(A) lower
+    const int *m, *n;
+    double alpha;
+    const double* const* A;
+    const int* lda;
+    double* const* B;
+    const int* ldb;
+    int* dinfo;
+    long long batch;
+    int max_m, max_n;
+    int vmax;  // vectors per problem at most: max_m (right side) or max_n (left side)
+};
+
+__device__ __forceinline__ int vtrsm_check(const VTrsmParams& p, long long q, int m, int n) {
+    if (m < 0 || m > p.max_m) return -5;
+    if (n < 0 || n > p.max_n) return -6;
+    const int ka = p.right ? n : m;
+    if (p.lda[q] < (ka > 1 ? ka : 1)) return -9;
+    if (p.ldb[q] < (m > 1 ? m : 1)) return -11;
+    if (m > 0 && n > 0 && p.alpha != 0.0 && !p.A[q]) return -8;
+    if (m > 0 && n > 0 && !p.B[q]) return -10;
+    return 0;
+}
+
+// one thread per (problem, vector): the vector is row v of B (right side: x op(A) = alpha b)
+// or column v (left side: op(A) x = alpha b); x overwrites b, read back as it is solved.
+// op(A)(i, j) = A(j, i) when transposed; lower op(A) is solved forward on the left and
+// backward on the right, upper the other way round.
+__global__ void __launch_bounds__(128) dtrsm_vbatched_kernel(VTrsmParams p) {
+    const long long total = p.batch * (long long)p.vmax;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long q = g / p.vmax;
+        const int v = (int)(g - q * p.vmax);
+        const int m = p.m[q], n = p.n[q];
+        const int bad = vtrsm_check(p, q, m, n);
+        if (v == 0 && p.dinfo) p.dinfo[q] = bad;
+        if (bad || m == 0 || n == 0) continue;
+        if (v >= (p.right ? m : n)) continue;
+        const int len = p.right ? n : m, lda = p.lda[q], ldb = p.ldb[q];
+        double* B = p.B[q];
+        // x_e = B(v, e) (right) or B(e, v) (left)
+        const long long xs = p.right ? ldb : 1;
+        double* x = p.right ? B + v : B + (long long)v * ldb;
+        if (p.alpha == 0.0) {  // B = 0, A not read
+            for (int e = 0; e < len; e++) x[e * xs] = 0.0;
+            continue;
+        }
+        const double* A = p.A[q];
+        auto T = [&](int i, int j) -> double {  // op(A)(i, j)
+            return p.transA ? ldg(A + j + (long long)i * lda) : ldg(A + i + (long long)j * lda);
+        };
+        // forward when (left, lower op(A)) or (right, upper op(A))
+        const bool fwd = p.right ? !p.lowerT : p.lowerT;
+        for (int t = 0; t < len; t++) {
+            const int e = fwd ? t : len - 1 - t;
+            double s = p.alpha * x[e * xs];
+            if (fwd) {
+                for (int f = 0; f < e; f++) s = fma(-x[f * xs], p.right ? T(f, e) : T(e, f), s);
+            } else {
+                for (int f = e + 1; f < len; f++) s = fma(-x[f * xs], p.right ? T(f, e) : T(e, f), s);
+            }
+            x[e * xs] = p.unit ? s : s / T(e, e);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------ launchers
+cudaError_t launch_dgemm_vbatched(bool ta, bool tb, const VGemmParams& p0, cudaStream_t s) {
+    if (p0.batch == 0) return cudaSuccess;
+    VGemmParams p = p0;
+    const int T = 128;
+    p.tiles_max = ((p.max_m + 3) / 4) * ((p.max_n + 3) / 4);
+    if (p.tiles_max < 1) p.tiles_max = 1;
+    p.P = p.tiles_max >= T ? 1 : T / p.tiles_max;
+    long long blocks = (p.batch + p.P - 1) / p.P;
+    if (blocks > 152LL * 64) blocks = 152LL * 64;
+    if (ta) {
+        if (tb) dgemm_vbatched_kernel<true, true><<<(unsigned)blocks, T, 0, s>>>(p);
+        else dgemm_vbatched_kernel<true, false><<<(unsigned)blocks, T, 0, s>>>(p);
+    } else {
+        if (tb) dgemm_vbatched_kernel<false, true><<<(unsigned)blocks, T, 0, s>>>(p);
+        else dgemm_vbatched_kernel<false, false><<<(unsigned)blocks, T, 0, s>>>(p);
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dtrsm_vbatched(const VTrsmParams& p0, cudaStream_t s) {
+    if (p0.batch == 0) return cudaSuccess;
+    VTrsmParams p = p0;
+    p.vmax = p.right ? p.max_m : p.max_n;
+    if (p.vmax < 1) p.vmax = 1;
+    const long long total = p.batch * (long long)p.vmax;
+    long long blocks = (total + 127) / 128;
+    if (blocks > 152LL * 64) blocks = 152LL * 64;
+    dtrsm_vbatched_kernel<<<(unsigned)blocks, 128, 0, s>>>(p);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace bf
+
+// ------------------------------------------------------------------------------------ C ABI
+using namespace bf;
+
+static bool vb_trans(char c, bool* t) {
+    if (c == 'N' || c == 'n') { *t = false; return true; }
+    if (c == 'T' || c == 't' || c == 'C' || c == 'c') { *t = true; return true; }
+    return false;
+}
+
+static int vb_status(cudaError_t e) { return e == cudaSuccess ? BF_SUCCESS : BF_ERR_CUDA; }
+
+extern "C" int bf_dgemm_vbatched(char transa, char transb, const int* m, const int* n, const int* k, double alpha,
+                                 const double* const* Aarray, const int* lda, const double* const* Barray,
+                                 const int* ldb, double beta, double* const* Carray, const int* ldc, int batch,
+                                 int max_m, int max_n, int max_k, int* dinfo, bf_stream_t stream) {
+    bool ta, tb;
+    if (!vb_trans(transa, &ta)) return -1;
+    if (!vb_trans(transb, &tb)) return -2;
+    if (batch < 0) return -14;
+    if (max_m < 0) return -15;
+    if (max_n < 0) return -16;
+    if (max_k < 0) return -17;
+    if (batch == 0) return BF_SUCCESS;
+    if (!m) return -3;
+    if (!n) return -4;
+    if (!k) return -5;
+    if (!Aarray) return -7;
+    if (!lda) return -8;
+    if (!Barray) return -9;
+    if (!ldb) return -10;
+    if (!Carray) return -12;
+    if (!ldc) return -13;
+    VGemmParams p{};
+    p.m = m; p.n = n; p.k = k; p.alpha = alpha; p.beta = beta;
+    p.A = Aarray; p.lda = lda; p.B = Barray; p.ldb = ldb; p.C = Carray; p.ldc = ldc;
+    p.dinfo = dinfo; p.batch = batch; p.max_m = max_m; p.max_n = max_n; p.max_k = max_k;
+    return vb_status(launch_dgemm_vbatched(ta, tb, p, (cudaStream_t)stream));
+}
+
+extern "C" int bf_dtrsm_vbatched(char side, char uplo, char transa, char diag, const int* m, const int* n,
+                                 double alpha, const double* const* Aarray, const int* lda, double* const* Barray,
+                                 const int* ldb, int batch, int max_m, int max_n, int* dinfo, bf_stream_t stream) {
+    const bool right = side == 'R' || side == 'r', left = side == 'L' || side == 'l';
+    if (!right && !left) return -1;
+    const bool lower = uplo == 'L' || uplo == 'l', upper = uplo == 'U' || uplo == 'u';
+    if (!lower && !upper) return -2;
+    bool tr;
+    if (!vb_trans(transa, &tr)) return -3;
+    const bool unit = diag == 'U' || diag == 'u', nonunit = diag == 'N' || diag == 'n';
+    if (!unit && !nonunit) return -4;
+    if (batch < 0) return -12;
+    if (max_m < 0) return -13;
+    if (max_n < 0) return -14;
+    if (batch == 0) return BF_SUCCESS;
+    if (!m) return -5;
+    if (!n) return -6;
+    if (!Aarray) return -8;
+    if (!lda) return -9;
+    if (!Barray) return -10;
+    if (!ldb) return -11;
+    VTrsmParams p{};
+    p.right = right; p.lowerT = lower != tr; p.transA = tr; p.unit = unit;
+    p.m = m; p.n = n; p.alpha = alpha; p.A = Aarray; p.lda = lda; p.B = Barray; p.ldb = ldb;
+    p.dinfo = dinfo; p.batch = batch; p.max_m = max_m; p.max_n = max_n;
+    return vb_status(launch_dtrsm_vbatched(p, (cudaStream_t)stream));
+}
+
+extern "C" int bf_dpotrf_vbatched(char uplo, const int* n, double* const* Aarray, const int* lda, int* info,
+                                  int batch, int max_n, bf_stream_t stream) {
+    const bool lower = uplo == 'L' || uplo == 'l', upper = uplo == 'U' || uplo == 'u';
+    if (!lower && !upper) return -1;
+    if (batch < 0) return -6;
+    if (max_n < 0) return -7;
+    if (upper || max_n > BF_VBATCHED_POTRF_NMAX) return BF_ERR_NOT_SUPPORTED;
+    if (batch == 0) return BF_SUCCESS;
+    if (!n) return -2;
+    if (!Aarray) return -3;
+    if (!lda) return -4;
+    return vb_status(launch_dpotrf_vbatched(n, Aarray, lda, info, batch, max_n, (cudaStream_t)stream));
+}

@@ -36,7 +36,8 @@ def declared_symbols():
 def test_header_declares_entry_points():
     names = declared_symbols()
     for required in ("bf_dgemm", "bf_dgemm_strided_batched", "bf_dgemm_batched", "bf_dtrsm",
-                     "bf_dpotrf", "bf_dpotrf_strided_batched", "bf_dpotrs"):
+                     "bf_dpotrf", "bf_dpotrf_strided_batched", "bf_dpotrs", "bf_dgemm_vbatched",
+                     "bf_dtrsm_vbatched", "bf_dpotrf_vbatched"):
         assert required in names
 
 
@@ -199,3 +200,46 @@ def test_dsposv_and_backward_arguments(lib):
     k = lib.bf_dgemm_backward_strided_batched
     assert k(b"N", b"N", 4, 4, 4, 1.0, 1, 3, 16, 1, 4, 16, 1.0, 1, 4, 16, None, 4, 0, None, 4, 0, None, 4, 0,
              1, None) == -8
+
+
+def test_vbatched_illegal_call_arguments(lib):
+    # the call's own arguments are checked on the host, nothing launched (no GPU needed); the
+    # per-problem sizes live in device arrays and are checked by the kernels (dinfo)
+    g = lib.bf_dgemm_vbatched
+    ok = dict(ta=b"N", tb=b"T", m=1, n=1, k=1, A=1, lda=1, B=1, ldb=1, C=1, ldc=1, batch=3, mm=4, mn=4, mk=4)
+
+    def gemm(**kw):
+        a = dict(ok, **kw)
+        return g(a["ta"], a["tb"], a["m"], a["n"], a["k"], 1.0, a["A"], a["lda"], a["B"], a["ldb"], 0.0,
+                 a["C"], a["ldc"], a["batch"], a["mm"], a["mn"], a["mk"], NULL, NULL)
+    assert gemm(ta=b"X") == -1
+    assert gemm(tb=b"X") == -2
+    assert gemm(batch=-1) == -14
+    assert gemm(mm=-1) == -15
+    assert gemm(mn=-1) == -16
+    assert gemm(mk=-1) == -17
+    assert gemm(batch=0, m=NULL) == 0
+    for name, pos in (("m", -3), ("n", -4), ("k", -5), ("A", -7), ("lda", -8), ("B", -9), ("ldb", -10),
+                      ("C", -12), ("ldc", -13)):
+        assert gemm(**{name: NULL}) == pos
+    t = lib.bf_dtrsm_vbatched
+
+    def trsm(side=b"R", uplo=b"L", tr=b"T", diag=b"U", m=1, n=1, A=1, lda=1, B=1, ldb=1, batch=2, mm=3, mn=3):
+        return t(side, uplo, tr, diag, m, n, 1.0, A, lda, B, ldb, batch, mm, mn, NULL, NULL)
+    assert trsm(side=b"X") == -1
+    assert trsm(uplo=b"X") == -2
+    assert trsm(tr=b"X") == -3
+    assert trsm(diag=b"X") == -4
+    assert trsm(batch=-1) == -12
+    assert trsm(mm=-1) == -13
+    assert trsm(mn=-1) == -14
+    assert trsm(m=NULL) == -5
+    assert trsm(B=NULL) == -10
+    p = lib.bf_dpotrf_vbatched
+    assert p(b"X", 1, 1, 1, NULL, 1, 4, NULL) == -1
+    assert p(b"L", 1, 1, 1, NULL, -1, 4, NULL) == -6
+    assert p(b"L", 1, 1, 1, NULL, 1, -1, NULL) == -7
+    assert p(b"U", 1, 1, 1, NULL, 1, 4, NULL) == lib.ERR_NOT_SUPPORTED
+    assert p(b"L", 1, 1, 1, NULL, 1, 1025, NULL) == lib.ERR_NOT_SUPPORTED
+    assert p(b"L", NULL, 1, 1, NULL, 1, 4, NULL) == -2
+    assert p(b"L", 1, 1, 1, NULL, 0, 4, NULL) == 0
