@@ -117,12 +117,15 @@ def tune(quick=False, out=None, log=print):
         for code, args in ((11, ("R", "L", "T", "U")), (10, ("R", "L", "T", "N")),
                            (0, ("L", "L", "N", "N")), (2, ("L", "L", "T", "N"))):
             best = None
-            for variant in ((0, 1, 3) if n <= 8 else (0, 1)):
+            for variant in ((0, 1, 3) if n <= 8 else ((0, 1, 2) if n >= 64 else (0, 1))):
                 for MR in ((4,) if variant == 3 else (4, 8)):
-                    for P, minb in (((0, 1), (0, 2)) if variant == 0 else
+                    for P, minb in (((0, 1), (0, 2)) if variant in (0, 2) else
                                     (((0, 1),) if variant == 3 else ((0, 1), (8, 1), (16, 1), (32, 1)))):
+                        # the blocked form's updates are dgemm calls: time it with the dgemm
+                        # entries measured so far installed
                         bf.tune_clear()
-                        bf.tune_set(bf.ROUTINE_DTRSM, code, 0, 1 << 30, variant, MR, P, minb)
+                        _install(bf, [e for e in entries if e["routine"] == bf.ROUTINE_DGEMM])
+                        bf.tune_set(bf.ROUTINE_DTRSM, code, 0, 1 << 30, variant | bf.TUNE_FORCE, MR, P, minb)
                         cfg = bf.tune_query(bf.ROUTINE_DTRSM, code, n, n, 0, b)
                         if cfg[0] != variant:
                             continue  # not launchable in this form at this order

@@ -185,10 +185,22 @@ static cudaError_t launch_rows(const TrsmParams& p, long long threads, int block
                    : launch_rows3<MR, PACKED, false>(p, threads, block, smem, minb, s);
 }
 
+static cudaError_t launch_dtrsm_blocked(int side, int uplo, int trans, int unit, int m, int n, double alpha,
+                                        MatRef A, int lda, MatRef B, int ldb, long long batch, int NB,
+                                        const int* skip, cudaStream_t s);
+
 cudaError_t launch_dtrsm(int side, int uplo, int trans, int unit, int m, int n, double alpha,
                          MatRef A, int lda, MatRef B, int ldb, long long batch,
                          const TrsmConfig& cfg, const int* skip, cudaStream_t s) {
     if (m == 0 || n == 0 || batch == 0) return cudaSuccess;
+    if (cfg.variant == VAR_BLOCKED && alpha != 0.0)
+        return launch_dtrsm_blocked(side, uplo, trans, unit, m, n, alpha, A, lda, B, ldb, batch, 32, skip, s);
+    if (cfg.variant == VAR_BLOCKED) {  // alpha == 0: B = 0, A not read (the row kernel's path)
+        TrsmConfig d = cfg;
+        d.variant = VAR_DIRECT;
+        d.P = 1;
+        return launch_dtrsm(side, uplo, trans, unit, m, n, alpha, A, lda, B, ldb, batch, d, skip, s);
+    }
     if (cfg.variant == VAR_TINY) return launch_dtrsm_tiny(side, uplo, trans, unit, m, n, alpha, A, lda, B, ldb, batch,
                                                           skip, s);
     TrsmParams p;
@@ -219,6 +231,51 @@ cudaError_t launch_dtrsm(int side, int uplo, int trans, int unit, int m, int n, 
     p.P = 1;
     return MR == 8 ? launch_rows<8, false>(p, threads, 256, 0, cfg.minb, s)
                    : launch_rows<4, false>(p, threads, 256, 0, cfg.minb, s);
+}
+
+// Blocked triangular solve for batches too small to fill the GPU with one thread per row:
+// the blocks of NB rows/columns of op(A) in solve order, each a row-parallel solve against its
+// diagonal block, followed by a dgemm that removes the block's contribution from the blocks
+// still to solve (the paper's dtrsm kernel, a dgemm loop plus a triangular edge, with the
+// dgemm loop hoisted out as a batched dgemm with 2-D parallelism).  alpha scales the first
+// block's solve and, through the first update's beta, every block after it.
+static cudaError_t launch_dtrsm_blocked(int side, int uplo, int trans, int unit, int m, int n, double alpha,
+                                        MatRef A, int lda, MatRef B, int ldb, long long batch, int NB,
+                                        const int* skip, cudaStream_t s) {
+    const bool right = side == 1;
+    const int order = right ? n : m;
+    const bool lowerT = (uplo == 0) != (trans != 0);  // op(A) lower
+    const bool fwd = right ? !lowerT : lowerT;        // blocks in ascending order
+    const int nblk = (order + NB - 1) / NB;
+    for (int t = 0; t < nblk; t++) {
+        const int bi = fwd ? t : nblk - 1 - t;
+        const int J = bi * NB, jb = (order - J < NB) ? order - J : NB;
+        const double a = t == 0 ? alpha : 1.0;
+        const int mm = right ? m : jb, nn = right ? jb : n;
+        const MatRef Bj = right ? mat_sub(B, 0, J, ldb) : mat_sub(B, J, 0, ldb);
+        TrsmConfig c = choose_trsm(side, uplo, trans, unit, mm, nn, 1LL << 40);  // the row kernel's table entry
+        cudaError_t e = launch_dtrsm(side, uplo, trans, unit, mm, nn, a, mat_sub(A, J, J, lda), lda, Bj, ldb, batch,
+                                     c, skip, s);
+        if (e != cudaSuccess) return e;
+        const int rlo = fwd ? J + jb : 0, rn = fwd ? order - J - jb : J;  // the blocks still to solve
+        if (rn <= 0) continue;
+        const double beta = t == 0 ? alpha : 1.0;
+        if (right) {
+            // B(:, rest) = beta B(:, rest) - X_J op(A)(J, rest); op(A)(J, rest) = A(J, rest) or A(rest, J)^T
+            const MatRef opA = trans ? mat_sub(A, rlo, J, lda) : mat_sub(A, J, rlo, lda);
+            GemmConfig g = choose_gemm(false, trans != 0, m, rn, jb, ldb, batch);
+            e = launch_dgemm(false, trans != 0, m, rn, jb, -1.0, Bj, ldb, opA, lda, beta, mat_sub(B, 0, rlo, ldb), ldb,
+                             batch, g, 0, skip, s);
+        } else {
+            // B(rest, :) = beta B(rest, :) - op(A)(rest, J) X_J; op(A)(rest, J) = A(rest, J) or A(J, rest)^T
+            const MatRef opA = trans ? mat_sub(A, J, rlo, lda) : mat_sub(A, rlo, J, lda);
+            GemmConfig g = choose_gemm(trans != 0, false, rn, n, jb, lda, batch);
+            e = launch_dgemm(trans != 0, false, rn, n, jb, -1.0, opA, lda, Bj, ldb, beta, mat_sub(B, rlo, 0, ldb), ldb,
+                             batch, g, 0, skip, s);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace bf

@@ -112,8 +112,11 @@ static size_t trsm_smem(int P, int order) {
     return sizeof(double) * ((size_t)P * order * (order + 1) + (size_t)P * order);
 }
 
+// blocked dtrsm below this many independent rows (batch x rows) from this order on
+static const long long kTrsmBlockedRows = 262144;  // measured: n = 64 x 3,072 (197k rows) gains, n = 96 x 3,072 (295k) loses
+static const int kTrsmBlockedMinOrder = 64;
+
 TrsmConfig choose_trsm(int side, int uplo, int trans, int unit, int m, int n, long long batch) {
-    (void)batch;
     TrsmConfig c;
     const int rows = side == 1 ? m : n;
     const int order = side == 1 ? n : m;
@@ -123,8 +126,12 @@ TrsmConfig choose_trsm(int side, int uplo, int trans, int unit, int m, int n, lo
     c.P = 1;
     c.minb = 1;
     TuneEntry e;
+    bool force = false;
     if (lookup(BF_ROUTINE_DTRSM, code, order, &e)) {
-        c.variant = e.variant == VAR_PACKED ? VAR_PACKED : (e.variant == VAR_TINY ? VAR_TINY : VAR_DIRECT);
+        force = e.force;
+        c.variant = e.variant == VAR_PACKED ? VAR_PACKED
+                  : e.variant == VAR_TINY  ? VAR_TINY
+                  : e.variant == VAR_BLOCKED ? VAR_BLOCKED : VAR_DIRECT;
         if (e.p0 == 4 || e.p0 == 8) c.MR = e.p0;
         c.P = e.p1 > 0 ? e.p1 : 0;
         if (e.p2 == 1 || e.p2 == 2) c.minb = e.p2;
@@ -141,7 +148,12 @@ TrsmConfig choose_trsm(int side, int uplo, int trans, int unit, int m, int n, lo
             if (trsm_smem(c.P, order) > kSmemBudget) c.variant = VAR_DIRECT;
         }
     }
-    if (c.variant == VAR_DIRECT) c.P = 1;
+    // the table is measured on 2 GiB batches: with far fewer independent rows than that, the
+    // row kernels leave the GPU idle, and larger orders go to the blocked form (row-parallel
+    // block solves + dgemm updates with 2-D parallelism)
+    if (!force && order >= kTrsmBlockedMinOrder && batch * (long long)rows < kTrsmBlockedRows) c.variant = VAR_BLOCKED;
+    if (c.variant == VAR_BLOCKED && order <= 32) c.variant = VAR_DIRECT;  // one block: nothing to hoist
+    if (c.variant == VAR_DIRECT || c.variant == VAR_BLOCKED) c.P = 1;
     return c;
 }
 

@@ -169,6 +169,13 @@ def test_tune_table(lib):
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10) == [lib.VARIANT_DIRECT, 64, 32, 8, 1]
         with pytest.raises(lib.BFError):
             lib.tune_set(lib.ROUTINE_DPOTRF, 1, 90, 110, 5)
+        # dtrsm: fewer independent rows than the GPU needs -> the blocked form from order 64
+        code_rltu = 8 + 2 + 1
+        assert lib.tune_query(lib.ROUTINE_DTRSM, code_rltu, 256, 256, 0, 48)[0] == lib.VARIANT_BLOCKED
+        assert lib.tune_query(lib.ROUTINE_DTRSM, code_rltu, 256, 256, 0, 2048)[0] != lib.VARIANT_BLOCKED
+        assert lib.tune_query(lib.ROUTINE_DTRSM, code_rltu, 32, 32, 0, 10)[0] != lib.VARIANT_BLOCKED
+        lib.tune_set(lib.ROUTINE_DTRSM, code_rltu, 1, 300, lib.VARIANT_DIRECT | lib.TUNE_FORCE, 8)
+        assert lib.tune_query(lib.ROUTINE_DTRSM, code_rltu, 256, 256, 0, 48)[0] == lib.VARIANT_DIRECT
         # defaults of the lane kernel: 8-row blocks for odd lda from n = 16, for even lda from n = 24
         lib.tune_clear()
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 16, 16, 0, 10 ** 5)[3:] == [4, 2]

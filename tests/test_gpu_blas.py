@@ -161,12 +161,12 @@ def tri_batch(batch, order, ld, uplo, diag, seed):
     return out
 
 
-@pytest.mark.parametrize("variant", [0, 1], ids=["direct", "packed"])
+@pytest.mark.parametrize("variant", [0, 1, 2], ids=["direct", "packed", "blocked"])
 @pytest.mark.parametrize("side,uplo,ta,diag", TRSM_CASES)
 def test_dtrsm_all_cases(bf, oracle, variant, side, uplo, ta, diag):
     code = (8 if side == "R" else 0) + (4 if uplo == "U" else 0) + (2 if ta == "T" else 0) + (
         1 if diag == "U" else 0)
-    for (m, n) in [(24, 24), (5, 13), (13, 5), (67, 33), (1, 4)]:
+    for (m, n) in [(24, 24), (5, 13), (13, 5), (67, 33), (1, 4), (100, 70)]:
         for pad in (0, 3):
             order = m if side == "L" else n
             batch = 7
@@ -186,6 +186,11 @@ def test_dtrsm_alpha_zero(bf):
     B = gpu(np.full((3, 4, 5), np.nan))
     A = gpu(np.full((3, 4, 4), np.nan))
     bf.dtrsm("R", "L", "T", "N", 0.0, A, B, m=5, n=4)
+    assert (host(B) == 0.0).all()
+    # the blocked form (small batch, order >= 64) takes the same path: B = 0, A not read
+    B = gpu(np.full((2, 70, 80), np.nan))
+    A = gpu(np.full((2, 70, 70), np.nan))
+    bf.dtrsm("R", "U", "N", "N", 0.0, A, B, m=80, n=70)
     assert (host(B) == 0.0).all()
 
 
