@@ -4,12 +4,14 @@
 //
 // The factorisation and solves are the paper's dpotrf/dtrsm (section 3.1)
 // carried out in binary32; refinement recovers binary64 accuracy.  One CTA
-// (128 threads) per problem, the binary32 factor packed in shared memory:
+// (128 threads) per problem, the binary32 factor in shared memory (columns in
+// 16-byte-aligned groups of four rows):
 //   1. A's lower triangle is rounded to binary32 and factored A32 = L32 L32^T,
 //      right-looking with 8-column panels: the panel by one warp, in registers
 //      with shuffles (each pivot tested for positivity; its binary64 square
 //      root rounded to binary32 is the correctly rounded binary32 one), the
-//      trailing update by all threads on 4x4 tiles -- two barriers per panel.
+//      trailing update by all threads on 4x4 tiles of 16-byte pieces -- two
+//      barriers per panel.
 //   2. x = L32^{-T} L32^{-1} b (binary32 substitutions by one warp, the vector
 //      in registers, x kept in binary64); repeat: r = b - A x in binary64 (A symmetric from its lower
 //      triangle, read from global memory); stop when the normwise backward
@@ -97,6 +99,7 @@ __device__ unsigned long long block_max_u64(unsigned long long v, unsigned long 
     return r;
 }
 
+// packed lower triangle by columns (the binary64 fallback's factor in the workspace)
 __device__ __forceinline__ int pk(int i, int j, int n) { return j * n - (j * (j - 1)) / 2 + (i - j); }
 
 // Storage of the binary32 factor in shared memory: column j holds rows 4 floor(j/4) .. n4 - 1
@@ -109,10 +112,10 @@ __device__ __forceinline__ int cb(int j, int n4) {
     return 4 * n4 * g - 8 * g * (g - 1) + r * (n4 - 4 * g) - 4 * g;
 }
 
-// w <- L^{-T} L^{-1} w with the packed binary32 factor in shared memory, by one warp with w in
+// w <- L^{-T} L^{-1} w with the binary32 factor in shared memory, by one warp with w in
 // registers: lane l holds w_i for i = l, l + 32, ...; each step broadcasts the solved entry
 // from its lane and every lane updates its own entries (a column of L for the forward solve,
-// contiguous in the packed layout; a row for the backward one).
+// contiguous in storage; a row for the backward one).
 template <int NR>
 __device__ __noinline__ void solve32_warp(const float* L, const float* rinv, float* w, int n) {
     const int lane = threadIdx.x & 31;
