@@ -331,7 +331,7 @@ __device__ void lane_problem(const RaggedParams& p, int q) {
 // warp issues one FP64 instruction every 64 cycles, so the lane kernels need ~20,000
 // problems): the BIG items' left-looking Cholesky, one problem per CTA, any leading
 // dimension, no right-hand sides.  CTAs stride over the batch.
-__global__ void __launch_bounds__(128) dpotrf_cta_kernel(int n, MatRef A, int lda, long long batch, int* info) {
+__global__ void __launch_bounds__(128, 6) dpotrf_cta_kernel(int n, MatRef A, int lda, long long batch, int* info) {
     extern __shared__ __align__(16) double sm_cta[];
     for (long long q = blockIdx.x; q < batch; q += gridDim.x) {
         const int fail = big_core(n, A.mptr(q), lda, nullptr, 0, sm_cta);
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(128) dpotrf_vbatched_lane_kernel(const int* n,
     if (info) info[q] = r;
 }
 
-__global__ void __launch_bounds__(128) dpotrf_vbatched_cta_kernel(const int* n, double* const* A, const int* lda,
+__global__ void __launch_bounds__(128, 6) dpotrf_vbatched_cta_kernel(const int* n, double* const* A, const int* lda,
                                                                 int* info, long long batch, int max_n) {
     extern __shared__ __align__(16) double sm_v[];
     for (long long q = blockIdx.x; q < batch; q += gridDim.x) {
