@@ -888,12 +888,12 @@ def next_rows(bf, torch, dev, peak):
         S = S0.clone()
         ms = _events_ms(torch, lambda: bf.dpotrf(S, uplo="U"), before=lambda: S.copy_(S0))
         row["dpotrf_u"] = rate(b1 * (n ** 3 / 3 + n ** 2 / 2 + n / 6), ms)
-        if n <= 64:  # dgetrf on the same batch (LAPACK's flop count 2n^3/3 - n^2/2 + 5n/6)
-            ipiv = torch.empty(b1, n, dtype=torch.int32, device=dev)
-            info = torch.empty(b1, dtype=torch.int32, device=dev)
-            ms = _events_ms(torch, lambda: bf.dgetrf(S, ipiv=ipiv, info=info), before=lambda: S.copy_(S0))
-            row["dgetrf"] = rate(b1 * (2 * n ** 3 / 3 - n ** 2 / 2 + 5 * n / 6), ms)
-            del ipiv, info
+        # dgetrf on the same batch (LAPACK's flop count 2n^3/3 - n^2/2 + 5n/6)
+        ipiv = torch.empty(b1, n, dtype=torch.int32, device=dev)
+        info = torch.empty(b1, dtype=torch.int32, device=dev)
+        ms = _events_ms(torch, lambda: bf.dgetrf(S, ipiv=ipiv, info=info), before=lambda: S.copy_(S0))
+        row["dgetrf"] = rate(b1 * (2 * n ** 3 / 3 - n ** 2 / 2 + 5 * n / 6), ms)
+        del ipiv, info
         del S, S0
         torch.cuda.empty_cache()
         out[f"n{n}"] = row

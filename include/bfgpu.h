@@ -44,6 +44,7 @@ typedef struct CUstream_st* bf_stream_t; /* identical to cudaStream_t */
 #define BF_ROUTINE_DGEMM 0
 #define BF_ROUTINE_DTRSM 1
 #define BF_ROUTINE_DPOTRF 2
+#define BF_ROUTINE_DGETRF 3  /* code 0; variants DIRECT (lane LU) and CTA */
 
 /* Kernel variants of the size switch (values of `variant` in bf_tune_set). */
 #define BF_VARIANT_DIRECT 0  /* native column-major operands, no packing (algorithm 'D') */
@@ -51,9 +52,10 @@ typedef struct CUstream_st* bf_stream_t; /* identical to cudaStream_t */
 #define BF_VARIANT_BLOCKED 2 /* dpotrf only: right-looking sequence of the above kernels */
 #define BF_VARIANT_TINY 3    /* dgemm (m, n, k <= 4) and dtrsm (orders <= 8): one thread   */
                              /* per problem, problems staged through shared memory       */
-#define BF_VARIANT_CTA 4     /* dpotrf 'L' only, n <= 256: one problem per CTA (left-      */
-                             /* looking by 16-column panels); batches too small to fill   */
-                             /* the GPU with one problem per thread                       */
+#define BF_VARIANT_CTA 4     /* one problem per CTA, for batches too small to fill the GPU */
+                             /* one problem per thread: dpotrf 'L' (n <= 256, left-looking */
+                             /* by 16-column panels), dgetrf (n <= 1024, right-looking by  */
+                             /* 16-column panels)                                         */
 #define BF_TUNE_FORCE 0x100  /* or'ed into `variant`: the entry holds at every batch size; */
                              /* without it, dpotrf batches too small to fill the GPU one  */
                              /* problem per thread still switch to BF_VARIANT_CTA (or to  */
@@ -404,7 +406,8 @@ int bf_ragged_potrf_potrs_noalloc(int batch, const int* n_host, int nrhs, double
 /* bf_tune_set adds a table entry, consulted before the built-in defaults:    */
 /*   routine  BF_ROUTINE_*                                                    */
 /*   code     dgemm: 2*transA + transB; dtrsm: 8*right + 4*upper + 2*trans +  */
-/*            unit; dpotrf: lda & 1 (even / odd leading dimension).        */
+/*            unit; dpotrf: lda & 1 (even / odd leading dimension);       */
+/*            dgetrf: 0 (entries hold only with BF_TUNE_FORCE).             */
 /*            -1 matches every code.                                        */
 /*   [n_lo, n_hi]  matrix order range (dgemm: max(m, n); dtrsm: order of A)   */
 /*   variant  BF_VARIANT_*, optionally | BF_TUNE_FORCE                        */

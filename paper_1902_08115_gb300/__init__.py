@@ -101,7 +101,7 @@ for _name, _args in _SIGS.items():
     _f.restype = _RES.get(_name, _i)
     globals()[_name] = _f
 
-ROUTINE_DGEMM, ROUTINE_DTRSM, ROUTINE_DPOTRF = 0, 1, 2
+ROUTINE_DGEMM, ROUTINE_DTRSM, ROUTINE_DPOTRF, ROUTINE_DGETRF = 0, 1, 2, 3
 VARIANT_DIRECT, VARIANT_PACKED, VARIANT_BLOCKED, VARIANT_TINY, VARIANT_CTA = 0, 1, 2, 3, 4
 TUNE_FORCE = 0x100  # or into a variant: the table entry holds at every batch size
 ERR_CUDA, ERR_NOT_SUPPORTED, ERR_NOALLOC_LIMIT = 1001, 1002, 1003

@@ -160,12 +160,186 @@ __global__ void __launch_bounds__(256) dgetrf_lane_kernel(GetrfParams p) {
     if (p.info) p.info[q] = info;
 }
 
+// ------------------------------------------------------------------ one problem per CTA
+// For batches too small to fill the GPU one problem per thread: right-looking by 16-column
+// panels, the panel in shared memory (W(i, c) = W[i + c n], rows J..n-1).  Per panel:
+//   (1) the panel factored column by column: the pivot (first row of largest |a| below the
+//       diagonal, taken only when strictly larger than |a_cc| -- a NaN never counts as larger),
+//       the row interchange inside the panel, scaling by the pivot's reciprocal, and the
+//       rank-1 update of the panel's later columns -- the steps, order and operations of the
+//       lane form, so pivots agree with it;
+//   (2) the panel back to global memory, and its interchanges applied to every other column
+//       (one thread per column, the interchanges in order);
+//   (3) U12 = L11^{-1} A12 (unit lower, one thread per column) and the trailing update
+//       A22 -= L21 U12 on 4x4 register tiles.
+#define BF_GETRF_NB 16
+
+__device__ __forceinline__ void argmax_pair(double& v, int& i, double v2, int i2) {
+    if (v2 > v || (v2 == v && i2 < i)) {
+        v = v2;
+        i = i2;
+    }
+}
+
+__global__ void __launch_bounds__(128, 4) dgetrf_cta_kernel(GetrfParams p) {
+    extern __shared__ __align__(16) double sm_lu[];
+    __shared__ double s_v[4];
+    __shared__ int s_i[4];
+    __shared__ int s_piv[BF_GETRF_NB];
+    __shared__ int s_info;
+    const int n = p.n, lda = p.lda, T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double* W = sm_lu;
+    for (long long q = blockIdx.x; q < p.batch; q += gridDim.x) {
+        double* A = p.A.mptr(q);
+        int* piv = p.ipiv + q * p.sipiv;
+        if (tid == 0) s_info = 0;
+        for (int J = 0; J < n; J += BF_GETRF_NB) {
+            const int nb = imin(BF_GETRF_NB, n - J), m = n - J;
+            for (int e = tid; e < m * nb; e += T) {
+                const int c = e / m, i = e - c * m;
+                W[i + c * n] = A[J + i + (long long)(J + c) * lda];
+            }
+            __syncthreads();
+            // (1) the panel
+            for (int c = 0; c < nb; c++) {
+                double bv = -1.0;  // no candidate below the diagonal yet
+                int bi = c;
+                for (int i = c + 1 + tid; i < m; i += T) {
+                    const double v = fabs(W[i + c * n]);
+                    if (v > bv) {  // strictly larger: the first of equal maxima stays, NaN never wins
+                        bv = v;
+                        bi = i;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+                    const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+                    argmax_pair(bv, bi, v2, i2);
+                }
+                if (lane == 0) {
+                    s_v[warp] = bv;
+                    s_i[warp] = bi;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    for (int w = 1; w < (T >> 5); w++) argmax_pair(bv, bi, s_v[w], s_i[w]);
+                    const int pr = (bv > fabs(W[c + c * n])) ? bi : c;
+                    s_piv[c] = pr;
+                    piv[J + c] = J + pr + 1;
+                    if (W[pr + c * n] == 0.0 && s_info == 0) s_info = J + c + 1;
+                }
+                __syncthreads();
+                const int pr = s_piv[c];
+                if (pr != c) {
+                    for (int c2 = tid; c2 < nb; c2 += T) {
+                        const double t = W[c + c2 * n];
+                        W[c + c2 * n] = W[pr + c2 * n];
+                        W[pr + c2 * n] = t;
+                    }
+                    __syncthreads();
+                }
+                const double pv = W[c + c * n];
+                if (pv != 0.0) {
+                    const double rcp = 1.0 / pv;
+                    for (int i = c + 1 + tid; i < m; i += T) W[i + c * n] *= rcp;
+                    __syncthreads();
+                }
+                const int w2 = nb - c - 1, h = m - c - 1;
+                for (int e = tid; e < w2 * h; e += T) {
+                    const int c2 = c + 1 + e / h, i = c + 1 + e % h;
+                    W[i + c2 * n] = fma(-W[i + c * n], W[c + c2 * n], W[i + c2 * n]);
+                }
+                __syncthreads();
+            }
+            // (2) the panel back, its interchanges on the other columns
+            for (int e = tid; e < m * nb; e += T) {
+                const int c = e / m, i = e - c * m;
+                A[J + i + (long long)(J + c) * lda] = W[i + c * n];
+            }
+            for (int j = tid; j < n; j += T) {
+                if (j >= J && j < J + nb) continue;
+                double* col = A + (long long)j * lda;
+                for (int c = 0; c < nb; c++) {
+                    const int pr = J + s_piv[c];
+                    if (pr != J + c) {
+                        const double t = col[J + c];
+                        col[J + c] = col[pr];
+                        col[pr] = t;
+                    }
+                }
+            }
+            __syncthreads();
+            if (J + nb < n) {
+                // (3) U12 = L11^{-1} A12, then A22 -= L21 U12
+                for (int j = J + nb + tid; j < n; j += T) {
+                    double* col = A + (long long)j * lda + J;
+                    double u[BF_GETRF_NB];
+#pragma unroll
+                    for (int c = 0; c < BF_GETRF_NB; c++) u[c] = c < nb ? col[c] : 0.0;
+#pragma unroll
+                    for (int c = 1; c < BF_GETRF_NB; c++)
+#pragma unroll
+                        for (int c2 = 0; c2 < c; c2++) u[c] = fma(-W[c + c2 * n], u[c2], u[c]);
+#pragma unroll
+                    for (int c = 0; c < BF_GETRF_NB; c++)
+                        if (c < nb) col[c] = u[c];
+                }
+                __syncthreads();
+                const int r = n - J - nb, tr = (r + 3) / 4;
+                for (int t = tid; t < tr * tr; t += T) {
+                    const int i0 = 4 * (t % tr), j0 = 4 * (t / tr);  // rows / columns from J + nb
+                    double acc[4][4];
+#pragma unroll
+                    for (int a = 0; a < 4; a++)
+#pragma unroll
+                        for (int b = 0; b < 4; b++) acc[a][b] = 0.0;
+                    for (int c = 0; c < nb; c++) {
+                        double l[4], u[4];
+#pragma unroll
+                        for (int a = 0; a < 4; a++) l[a] = W[nb + imin(i0 + a, r - 1) + c * n];
+#pragma unroll
+                        for (int b = 0; b < 4; b++) u[b] = A[J + c + (long long)(J + nb + imin(j0 + b, r - 1)) * lda];
+#pragma unroll
+                        for (int a = 0; a < 4; a++)
+#pragma unroll
+                            for (int b = 0; b < 4; b++) acc[a][b] = fma(l[a], u[b], acc[a][b]);
+                    }
+#pragma unroll
+                    for (int b = 0; b < 4; b++) {
+                        if (j0 + b >= r) continue;
+                        double* col = A + (long long)(J + nb + j0 + b) * lda + J + nb;
+#pragma unroll
+                        for (int a = 0; a < 4; a++)
+                            if (i0 + a < r) col[i0 + a] -= acc[a][b];
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (tid == 0 && p.info) p.info[q] = s_info;
+        __syncthreads();
+    }
+}
+
 cudaError_t launch_dgetrf(int n, MatRef A, int lda, int* ipiv, long long sipiv, int* info, long long batch,
                           cudaStream_t s) {
     if (batch == 0) return cudaSuccess;
     if (n == 0) return info ? cudaMemsetAsync(info, 0, sizeof(int) * (size_t)batch, s) : cudaSuccess;
     GetrfParams p;
     p.n = n; p.A = A; p.lda = lda; p.ipiv = ipiv; p.sipiv = sipiv; p.batch = batch; p.info = info;
+    if (choose_getrf(n, batch) == VAR_CTA) {
+        const size_t smem = sizeof(double) * (size_t)BF_GETRF_NB * n;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(dgetrf_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        const long long cap = 152LL * 16;
+        dgetrf_cta_kernel<<<(unsigned)(batch < cap ? batch : cap), 128, smem, s>>>(p);
+        count_launch();
+        return cudaGetLastError();
+    }
     const int T = 64;
     dgetrf_lane_kernel<<<(unsigned)((batch + T - 1) / T), T, 0, s>>>(p);
     count_launch();

@@ -128,6 +128,7 @@ cudaError_t launch_dgetrs(int trans, int n, int nrhs, MatRef A, int lda, const i
 GemmConfig choose_gemm(bool ta, bool tb, int m, int n, int k, int lda, long long batch);
 TrsmConfig choose_trsm(int side, int uplo, int trans, int unit, int m, int n, long long batch);
 PotrfConfig choose_potrf(int n, int lda, long long batch);
+int choose_getrf(int n, long long batch);  // VAR_DIRECT (lane LU) or VAR_CTA
 // dpotrf (lower) with one problem per CTA, n <= 256 (bf_ragged.cu)
 cudaError_t launch_dpotrf_cta(int n, MatRef A, int lda, long long batch, int* info, cudaStream_t s);
 // dpotrf 'L' of a variable-size batch (device arrays n, Aarray, lda; max_n <= BF_VBATCHED_POTRF_NMAX)

@@ -112,6 +112,17 @@ static size_t trsm_smem(int P, int order) {
     return sizeof(double) * ((size_t)P * order * (order + 1) + (size_t)P * order);
 }
 
+static const int kGetrfCtaMaxN = 1024;  // the panel (16 n doubles) in shared memory
+
+// largest batch for which one problem per CTA beats the lane LU, by order (n <= 64; measured
+// crossovers: n = 16-24 between 2,432 and 9,728 problems, 32 ~5,000, 48 ~16,000, 64 ~32,000)
+static long long getrf_cta_batch_limit(int n) {
+    if (n < 32) return 2432;
+    if (n < 48) return 4096;
+    if (n < 64) return 16384;
+    return 24576;
+}
+
 // blocked dtrsm below this many independent rows (batch x rows) from this order on
 static const long long kTrsmBlockedRows = 262144;  // measured: n = 64 x 3,072 (197k rows) gains, n = 96 x 3,072 (295k) loses
 static const int kTrsmBlockedMinOrder = 64;
@@ -222,11 +233,26 @@ PotrfConfig choose_potrf(int n, int lda, long long batch) {
     return c;
 }
 
+// dgetrf: the lane LU (VAR_DIRECT) or one problem per CTA (VAR_CTA, n <= 1024).  One problem
+// per thread needs tens of thousands of problems; below the crossover measured per order, and
+// for every order above 64 (where the lane LU's per-problem state outgrows its registers and
+// L1), the CTA form is used.  A table entry (code 0) overrides, always with BF_TUNE_FORCE.
+int choose_getrf(int n, long long batch) {
+    TuneEntry e;
+    if (lookup(BF_ROUTINE_DGETRF, 0, n, &e)) {
+        const int v = e.variant == VAR_CTA ? VAR_CTA : VAR_DIRECT;
+        if (e.force) return (v == VAR_CTA && n > kGetrfCtaMaxN) ? VAR_DIRECT : v;
+    }
+    if (n > kGetrfCtaMaxN || n < 16) return VAR_DIRECT;
+    if (n > 64) return VAR_CTA;
+    return batch <= getrf_cta_batch_limit(n) ? VAR_CTA : VAR_DIRECT;
+}
+
 }  // namespace bf
 
 extern "C" int bf_tune_set(int routine, int code, int n_lo, int n_hi, int variant, int p0, int p1,
                            int p2, int p3) {
-    if (routine < BF_ROUTINE_DGEMM || routine > BF_ROUTINE_DPOTRF) return -1;
+    if (routine < BF_ROUTINE_DGEMM || routine > BF_ROUTINE_DGETRF) return -1;
     if (n_lo > n_hi) return -3;
     const bool force = (variant & BF_TUNE_FORCE) != 0;
     variant &= ~BF_TUNE_FORCE;
@@ -257,6 +283,10 @@ extern "C" int bf_tune_query(int routine, int code, int m, int n, int k, long lo
     if (routine == BF_ROUTINE_DPOTRF) {
         bf::PotrfConfig c = bf::choose_potrf(n, code == 1 ? n + 1 : n, batch);
         out[0] = c.variant; out[1] = c.T; out[2] = c.NB; out[3] = c.rows; out[4] = c.unroll;
+        return 0;
+    }
+    if (routine == BF_ROUTINE_DGETRF) {
+        out[0] = bf::choose_getrf(n, batch); out[1] = out[2] = out[3] = out[4] = 0;
         return 0;
     }
     return -1;

@@ -301,15 +301,23 @@ def test_dpotrf_upper_failures_and_dpotrs(bf, oracle):
 
 
 # ----------------------------------------------------------------------------- dgetrf / dgetrs
-@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 8, 13, 16, 24, 33, 48, 64, 96])
-def test_dgetrf(bf, oracle, n):
+GETRF_VARIANTS = [("chosen", None), ("lane", 0), ("cta", 4)]
+
+
+@pytest.mark.parametrize("vname,variant", GETRF_VARIANTS, ids=[v[0] for v in GETRF_VARIANTS])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 8, 13, 16, 17, 24, 33, 48, 64, 96, 130, 256])
+def test_dgetrf(bf, oracle, vname, variant, n):
     batch = batch_for(n)
     for pad in (0, 3):
         A = np.full((batch, n, n + pad), np.nan)
         A[:, :, :n] = rnd((batch, n, n), 200 + n + pad)
         LU, piv, info = oracle.dgetrf(A, m=n)
         Ag = gpu(A)
-        pg, ig = bf.dgetrf(Ag, n=n)
+        if variant is None:
+            pg, ig = bf.dgetrf(Ag, n=n)
+        else:
+            with forced(bf, bf.ROUTINE_DGETRF, 0, variant):
+                pg, ig = bf.dgetrf(Ag, n=n)
         pg, ig, out = host(pg), host(ig), host(Ag)
         np.testing.assert_array_equal(ig, info)
         np.testing.assert_array_equal(pg, piv)  # same pivots: generic matrices have no near ties
@@ -317,15 +325,21 @@ def test_dgetrf(bf, oracle, n):
         assert np.isnan(out[:, :, n:]).all()
 
 
-def test_dgetrf_singular_and_permutation(bf, oracle):
-    n, batch = 9, 4
+@pytest.mark.parametrize("vname,variant", GETRF_VARIANTS, ids=[v[0] for v in GETRF_VARIANTS])
+@pytest.mark.parametrize("n", [9, 40])
+def test_dgetrf_singular_and_permutation(bf, oracle, vname, variant, n):
+    batch = 4
     A = rnd((batch, n, n), 300)
     A[1, 4, :] = 0.0                               # problem 1: column 4 zero -> info 5
     A[2] = np.eye(n)[np.random.default_rng(1).permutation(n)]  # problem 2: a permutation matrix
     A[3, :, :] = 0.0                               # problem 3: all zero -> info 1
     LU, piv, info = oracle.dgetrf(A, m=n)
     Ag = gpu(A)
-    pg, ig = bf.dgetrf(Ag)
+    if variant is None:
+        pg, ig = bf.dgetrf(Ag)
+    else:
+        with forced(bf, bf.ROUTINE_DGETRF, 0, variant):
+            pg, ig = bf.dgetrf(Ag)
     np.testing.assert_array_equal(host(ig), info)
     assert info[1] == 5 and info[3] == 1 and info[2] == 0
     np.testing.assert_array_equal(host(pg), piv)
