@@ -30,6 +30,9 @@ struct SyrkParams {
     int ldc;
     long long batch;
     int tiles;  // 4x4 tiles of one triangle per problem
+    MatRef Cin;  // when has_cin: C's old values are read from Cin (ld ldcin)
+    int ldcin;
+    int has_cin;
 };
 
 // Four consecutive entries x[i .. i+3] of a column (clamped to n - 1 at its end): 16-byte
@@ -65,13 +68,15 @@ __global__ void __launch_bounds__(256) dsyrk_tile_kernel(SyrkParams p) {
     const int n = p.n;
     const double* A = p.A.ptr(q);
     double* C = p.C.mptr(q);
+    const double* Co = p.has_cin ? p.Cin.ptr(q) : C;  // old values of C
+    const int ldo = p.has_cin ? p.ldcin : p.ldc;
 
     double acc[4][4];
     if (p.mode == ACC_C || p.mode == ACC_BC) {
 #pragma unroll
         for (int b = 0; b < 4; b++) {
             double col[4];
-            col4(C + (long long)imin(c0 + b, n - 1) * p.ldc, r0, n, col);  // the other triangle is read, not used
+            col4(Co + (long long)imin(c0 + b, n - 1) * ldo, r0, n, col);  // the other triangle is read, not used
 #pragma unroll
             for (int a = 0; a < 4; a++) acc[a][b] = (p.mode == ACC_BC) ? p.beta * col[a] : col[a];
         }
@@ -114,7 +119,7 @@ __global__ void __launch_bounds__(256) dsyrk_tile_kernel(SyrkParams p) {
             if (i < n && j < n && (UP ? i <= j : i >= j)) {
                 double* cp = C + i + (long long)j * p.ldc;
                 double v = acc[a][b];
-                if (p.mode == ACC_GEN) v = (p.beta == 0.0) ? p.alpha * v : fma(p.alpha, v, p.beta * *cp);
+                if (p.mode == ACC_GEN) v = (p.beta == 0.0) ? p.alpha * v : fma(p.alpha, v, p.beta * Co[i + (long long)j * ldo]);
                 *cp = v;
             }
         }
@@ -136,8 +141,9 @@ __global__ void dsyrk_scale_kernel(int n, int upper, double beta, MatRef C, int 
 }
 
 cudaError_t launch_dsyrk(int upper, int trans, int n, int k, double alpha, MatRef A, int lda, double beta,
-                         MatRef C, int ldc, long long batch, cudaStream_t s) {
+                         MatRef C, int ldc, long long batch, cudaStream_t s, const MatRef* Cin, int ldcin) {
     if (n == 0 || batch == 0) return cudaSuccess;
+    if (Cin && (alpha == 0.0 || k == 0)) return cudaErrorInvalidValue;  // not needed by any caller
     if (alpha == 0.0 || k == 0) {
         if (beta == 1.0) return cudaSuccess;
         long long total = (long long)n * n * batch;
@@ -151,6 +157,11 @@ cudaError_t launch_dsyrk(int upper, int trans, int n, int k, double alpha, MatRe
     p.n = n; p.k = k; p.alpha = alpha; p.beta = beta;
     p.mode = acc_mode(alpha, beta);
     p.A = A; p.lda = lda; p.C = C; p.ldc = ldc; p.batch = batch;
+    p.has_cin = Cin != nullptr;
+    if (Cin) {
+        p.Cin = *Cin;
+        p.ldcin = ldcin;
+    }
     const int nI = (n + 3) / 4;
     p.tiles = nI * (nI + 1) / 2;
     const long long threads = batch * (long long)p.tiles;
@@ -175,7 +186,20 @@ struct SyrkPotrfParams {
     int ldc;
     long long batch;
     int* info;
+    int stage;    // >= 0: info is the recursion's stage-tagged status (written only while 0)
 };
+
+// C(i, j) = Cin(i, j) on the lower triangle of every problem: flat over the batch, consecutive
+// threads on consecutive rows of a column (coalesced)
+__global__ void copy_lower_kernel(int n, MatRef Cin, int ldcin, MatRef C, int ldc, long long batch) {
+    const long long per = (long long)n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per * batch;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long q = e / per;
+        const int r = (int)(e - q * per), j = r / n, i = r - j * n;
+        if (i >= j) C.mptr(q)[i + (long long)j * ldc] = Cin.ptr(q)[i + (long long)j * ldcin];
+    }
+}
 
 template <int R, int U>
 __global__ void __launch_bounds__(256) dsyrk_dpotrf_lane_kernel(SyrkPotrfParams p) {
@@ -183,11 +207,14 @@ __global__ void __launch_bounds__(256) dsyrk_dpotrf_lane_kernel(SyrkPotrfParams 
     if (q >= p.batch) return;
     const SyrkOp<GAccP> y{GAccP{const_cast<double*>(p.A.ptr(q)), p.lda}};  // read only
     const int info = potrf_lane<R, U>(GAccP{p.C.mptr(q), p.ldc}, p.n, y, p.k);
-    if (p.info) p.info[q] = info;
+    if (p.info) {
+        if (p.stage < 0) p.info[q] = info;
+        else if (info != 0 && p.info[q] == 0) p.info[q] = 1000 * p.stage + info;
+    }
 }
 
 cudaError_t launch_dsyrk_dpotrf(int n, int k, MatRef A, int lda, MatRef C, int ldc, long long batch, int* info,
-                                cudaStream_t s) {
+                                cudaStream_t s, const MatRef* Cin, int ldcin, int* merged, int stage) {
     if (batch == 0) return cudaSuccess;
     PotrfConfig cfg = choose_potrf(n, ldc, batch);
     // the size switch of the fused routine: the one-pass lane kernel wins for small orders
@@ -195,12 +222,25 @@ cudaError_t launch_dsyrk_dpotrf(int n, int k, MatRef A, int lda, MatRef C, int l
     // tile dsyrk then the lane/blocked dpotrf is faster on this GPU, since the FP64 pipe, not
     // memory, bounds both halves and the fused kernel's registers cut its occupancy
     if (n == 0 || n > 12 || cfg.variant == VAR_BLOCKED) {
-        cudaError_t e = launch_dsyrk(0, 0, n, k, 1.0, A, lda, 1.0, C, ldc, batch, s);
+        cudaError_t e = launch_dsyrk(0, 0, n, k, 1.0, A, lda, 1.0, C, ldc, batch, s, Cin, ldcin);
         if (e != cudaSuccess) return e;
-        return launch_dpotrf(n, C, ldc, batch, info, cfg, s);
+        e = launch_dpotrf(n, C, ldc, batch, info, cfg, s);
+        if (e != cudaSuccess || !merged) return e;
+        return launch_merge_stage_info(info, merged, stage, batch, s);
     }
     SyrkPotrfParams p;
-    p.n = n; p.k = k; p.A = A; p.lda = lda; p.C = C; p.ldc = ldc; p.batch = batch; p.info = info;
+    p.n = n; p.k = k; p.A = A; p.lda = lda; p.C = C; p.ldc = ldc; p.batch = batch;
+    p.info = merged ? merged : info;
+    p.stage = merged ? stage : -1;
+    if (Cin) {  // a coalesced copy first: the lane kernel's own loads would be one problem per lane
+        const long long total = (long long)n * n * batch;
+        long long blocks = (total + 255) / 256;
+        if (blocks > 152LL * 32) blocks = 152LL * 32;
+        copy_lower_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, *Cin, ldcin, C, ldc, batch);
+        count_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     const int T = cfg.T > 0 ? cfg.T : 64;
     const unsigned blocks = (unsigned)((batch + T - 1) / T);
     if (cfg.rows == 8) {

@@ -24,15 +24,20 @@ __global__ void __launch_bounds__(256) dtrmm_rows_kernel(TrsmParams p) {
     const int n = p.n;
     const double* A = p.A.ptr(q);
     double* B = p.B.mptr(q);
+    // out of place (has_src): the old values come from Bsrc, so the block order no longer matters
+    const double* Bs = p.has_src ? p.Bsrc.ptr(q) : B;
+    const int ldbs = p.has_src ? p.ldbs : p.ldb;
     int rows[MR];
-    long long roff[MR];
+    long long roff[MR], roffs[MR];
 #pragma unroll
     for (int s = 0; s < MR; s++) {
         rows[s] = rr + p.tpp * s;
         const int rc = imin(rows[s], p.m - 1);
         roff[s] = p.bt ? (long long)rc * p.ldb : rc;
+        roffs[s] = p.bt ? (long long)rc * ldbs : rc;
     }
     const long long cstep = p.bt ? 1 : p.ldb;  // R(r, j + 1) - R(r, j)
+    const long long csteps = p.bt ? 1 : ldbs;
     auto Tel = [&](int i, int j) -> double {
         return p.et ? ldg(A + j + (long long)i * p.lda) : ldg(A + i + (long long)j * p.lda);
     };
@@ -53,7 +58,7 @@ __global__ void __launch_bounds__(256) dtrmm_rows_kernel(TrsmParams p) {
         for (int pp = pb; pp < pe; pp++) {
             double x[MR], tv[4];
 #pragma unroll
-            for (int s = 0; s < MR; s++) x[s] = B[roff[s] + pp * cstep];
+            for (int s = 0; s < MR; s++) x[s] = Bs[roffs[s] + pp * csteps];
 #pragma unroll
             for (int c = 0; c < 4; c++) tv[c] = Tel(pp, imin(J + c, n - 1));
 #pragma unroll
@@ -67,7 +72,7 @@ __global__ void __launch_bounds__(256) dtrmm_rows_kernel(TrsmParams p) {
         for (int c = 0; c < 4; c++) {
             const int jc = imin(J + c, n - 1);
 #pragma unroll
-            for (int s = 0; s < MR; s++) xb[s][c] = B[roff[s] + jc * cstep];
+            for (int s = 0; s < MR; s++) xb[s][c] = Bs[roffs[s] + jc * csteps];
         }
 #pragma unroll
         for (int c = 0; c < 4; c++)
@@ -96,9 +101,14 @@ __global__ void __launch_bounds__(256) dtrmm_rows_kernel(TrsmParams p) {
 }
 
 cudaError_t launch_dtrmm(int side, int uplo, int trans, int unit, int m, int n, double alpha, MatRef A, int lda,
-                         MatRef B, int ldb, long long batch, int MR, cudaStream_t s) {
+                         MatRef B, int ldb, long long batch, int MR, cudaStream_t s, const MatRef* Bsrc, int ldbs) {
     if (m == 0 || n == 0 || batch == 0) return cudaSuccess;
     TrsmParams p;
+    if (Bsrc) {
+        p.Bsrc = *Bsrc;
+        p.ldbs = ldbs;
+        p.has_src = 1;
+    }
     const bool right = (side == 1);
     // rows of R: right -> rows of B (T = op(A) is n x n); left -> columns of B (R = B^T, T = op(A)^T)
     p.m = right ? m : n;

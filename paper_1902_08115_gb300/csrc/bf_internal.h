@@ -58,6 +58,9 @@ struct TrsmParams {
     int tpp;  // threads per problem = ceil(m / MR)
     int P;
     const int* skip;
+    MatRef Bsrc;       // dtrmm only, when has_src: the input B (the result goes to B)
+    int ldbs = 0;
+    int has_src = 0;
 };
 
 struct PotrfConfig {
@@ -110,13 +113,21 @@ cudaError_t launch_dtrsm_tiny(int side, int uplo, int trans, int unit, int m, in
 
 // dsyrk (upper: 0/1, trans: 0/1) and the fused chol(C + A A^T), lower (bf_dsyrk.cu)
 cudaError_t launch_dsyrk(int upper, int trans, int n, int k, double alpha, MatRef A, int lda, double beta,
-                         MatRef C, int ldc, long long batch, cudaStream_t s);
+                         MatRef C, int ldc, long long batch, cudaStream_t s, const MatRef* Cin = nullptr,
+                         int ldcin = 0);  // Cin: C's old values read from there (the uplo triangle)
+// Cin (optional): the lower triangle of C is taken from Cin (ld ldcin) instead of C itself.
+// merged (optional, with stage >= 0): the Riccati recursion's stage-tagged status -- an entry
+// that is still 0 becomes 1000 stage + this factorisation's info; `info` is then scratch.
 cudaError_t launch_dsyrk_dpotrf(int n, int k, MatRef A, int lda, MatRef C, int ldc, long long batch, int* info,
-                                cudaStream_t s);
+                                cudaStream_t s, const MatRef* Cin = nullptr, int ldcin = 0, int* merged = nullptr,
+                                int stage = -1);
+// info[q] = 1000 stage + stage_info[q] where info[q] is 0 and stage_info[q] is not (bf_riccati.cu)
+cudaError_t launch_merge_stage_info(const int* stage_info, int* info, int stage, long long batch, cudaStream_t s);
 
 // dtrmm, row-parallel like dtrsm (bf_dtrmm.cu); side: 0 = left, 1 = right
 cudaError_t launch_dtrmm(int side, int uplo, int trans, int unit, int m, int n, double alpha, MatRef A, int lda,
-                         MatRef B, int ldb, long long batch, int MR, cudaStream_t s);
+                         MatRef B, int ldb, long long batch, int MR, cudaStream_t s,
+                         const MatRef* Bsrc = nullptr, int ldbs = 0);
 
 // LU with partial pivoting and its solve (bf_dgetrf.cu); ipiv: sipiv ints per problem, 1-based
 cudaError_t launch_dgetrf(int n, MatRef A, int lda, int* ipiv, long long sipiv, int* info, long long batch,

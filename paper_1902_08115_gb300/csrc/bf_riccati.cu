@@ -7,7 +7,10 @@
 //   F_s = chol([R_s S_s; S_s^T Q_s] + C C^T) (dsyrk_ln + dpotrf_l, fused or not)
 //   Lc_s = the trailing n_x x n_x block of F_s
 // Every launch covers the whole batch, so stage s of all problems runs at once; the
-// stages themselves are sequential (each needs the previous factor).  The fused form uses
+// stages themselves are sequential (each needs the previous factor).  A stage is two or three
+// launches: the dtrmm reads [B^T; A^T]_s where it lies and writes C to the workspace, the
+// factorisation reads the lower triangle of [R S; S^T Q]_s where it lies and writes F_s, and
+// the fused kernel folds the stage-tagged status into info itself.  The fused form uses
 // the fused dsyrk + dpotrf kernel (the paper's own-API routine, credited in section 5 with
 // part of the speed-up over the plain BLAS/LAPACK calls); the unfused form calls dsyrk then
 // dpotrf, as a BLAS/LAPACK implementation does.
@@ -46,7 +49,7 @@ static cudaError_t copy_mat(int rows, int cols, const double* src, int lds, long
     return cudaGetLastError();
 }
 
-static cudaError_t merge_info(const int* stage_info, int* info, int stage, long long batch, cudaStream_t s) {
+cudaError_t launch_merge_stage_info(const int* stage_info, int* info, int stage, long long batch, cudaStream_t s) {
     merge_info_kernel<<<(unsigned)((batch + 255) / 256), 256, 0, s>>>(stage_info, info, stage, batch);
     count_launch();
     return cudaGetLastError();
@@ -97,31 +100,29 @@ extern "C" int bf_riccati_strided_batched(int N, int nx, int nu, const double* B
     if (!ok(cudaMemsetAsync(info, 0, sizeof(int) * (size_t)batch, s))) return BF_ERR_CUDA;
     if (!ok(launch_dpotrf(nx, mat_strided(FN, strideF), mi, batch, sinfo, choose_potrf(nx, mi, batch), s)))
         return BF_ERR_CUDA;
-    if (!ok(merge_info(sinfo, info, N, batch, s))) return BF_ERR_CUDA;
+    if (!ok(launch_merge_stage_info(sinfo, info, N, batch, s))) return BF_ERR_CUDA;
     for (int st = N - 1; st >= 0; st--) {
         double* Fs = F + (long long)st * m * m;
         const double* Lnext = (st + 1 == N) ? FN : F + (long long)(st + 1) * m * m + nu + (long long)nu * m;
-        // C = BAt_s Lc_{s+1}
-        if (!ok(copy_mat(mi, nx, BAt + (long long)st * m * nx, mi, strideBAt, Cw, mi, m * nx, batch, s)))
-            return BF_ERR_CUDA;
+        // C = BAt_s Lc_{s+1}: dtrmm out of place, BAt read where it is
+        const MatRef bat = mat_strided(BAt + (long long)st * m * nx, strideBAt);
         if (!ok(launch_dtrmm(1, 0, 0, 0, mi, nx, 1.0, mat_strided(Lnext, strideF), mi, mat_strided(Cw, m * nx), mi,
-                             batch, 4, s)))
+                             batch, 4, s, &bat, mi)))
             return BF_ERR_CUDA;
-        // F_s = chol(RSQ_s + C C^T)
-        if (!ok(copy_mat(mi, mi, RSQ + (long long)st * m * m, mi, strideRSQ, Fs, mi, strideF, batch, s)))
-            return BF_ERR_CUDA;
+        // F_s = chol(RSQ_s + C C^T): the lower triangle of RSQ_s read where it is
+        const MatRef rsq = mat_strided(RSQ + (long long)st * m * m, strideRSQ);
         if (fused) {
             if (!ok(launch_dsyrk_dpotrf(mi, nx, mat_strided(Cw, m * nx), mi, mat_strided(Fs, strideF), mi, batch,
-                                        sinfo, s)))
+                                        sinfo, s, &rsq, mi, info, st)))
                 return BF_ERR_CUDA;
         } else {
             if (!ok(launch_dsyrk(0, 0, mi, nx, 1.0, mat_strided(Cw, m * nx), mi, 1.0, mat_strided(Fs, strideF), mi,
-                                 batch, s)))
+                                 batch, s, &rsq, mi)))
                 return BF_ERR_CUDA;
             if (!ok(launch_dpotrf(mi, mat_strided(Fs, strideF), mi, batch, sinfo, choose_potrf(mi, mi, batch), s)))
                 return BF_ERR_CUDA;
+            if (!ok(launch_merge_stage_info(sinfo, info, st, batch, s))) return BF_ERR_CUDA;
         }
-        if (!ok(merge_info(sinfo, info, st, batch, s))) return BF_ERR_CUDA;
     }
     return BF_SUCCESS;
 }
