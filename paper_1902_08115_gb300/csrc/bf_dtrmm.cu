@@ -15,7 +15,7 @@
 
 namespace bf {
 
-template <int MR>
+template <int MR, bool SRC>
 __global__ void __launch_bounds__(256) dtrmm_rows_kernel(TrsmParams p) {
     const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long q = gt / p.tpp;
@@ -24,9 +24,9 @@ __global__ void __launch_bounds__(256) dtrmm_rows_kernel(TrsmParams p) {
     const int n = p.n;
     const double* A = p.A.ptr(q);
     double* B = p.B.mptr(q);
-    // out of place (has_src): the old values come from Bsrc, so the block order no longer matters
-    const double* Bs = p.has_src ? p.Bsrc.ptr(q) : B;
-    const int ldbs = p.has_src ? p.ldbs : p.ldb;
+    // SRC (out of place): the old values come from Bsrc, so the block order no longer matters
+    const double* Bs = SRC ? p.Bsrc.ptr(q) : B;
+    const int ldbs = SRC ? p.ldbs : p.ldb;
     int rows[MR];
     long long roff[MR], roffs[MR];
 #pragma unroll
@@ -34,10 +34,10 @@ __global__ void __launch_bounds__(256) dtrmm_rows_kernel(TrsmParams p) {
         rows[s] = rr + p.tpp * s;
         const int rc = imin(rows[s], p.m - 1);
         roff[s] = p.bt ? (long long)rc * p.ldb : rc;
-        roffs[s] = p.bt ? (long long)rc * ldbs : rc;
+        roffs[s] = SRC ? (p.bt ? (long long)rc * ldbs : rc) : roff[s];
     }
     const long long cstep = p.bt ? 1 : p.ldb;  // R(r, j + 1) - R(r, j)
-    const long long csteps = p.bt ? 1 : ldbs;
+    const long long csteps = SRC ? (p.bt ? 1 : ldbs) : cstep;
     auto Tel = [&](int i, int j) -> double {
         return p.et ? ldg(A + j + (long long)i * p.lda) : ldg(A + i + (long long)j * p.lda);
     };
@@ -126,8 +126,13 @@ cudaError_t launch_dtrmm(int side, int uplo, int trans, int unit, int m, int n, 
     p.tpp = (p.m + MR - 1) / MR;
     const long long threads = batch * p.tpp;
     const unsigned blocks = (unsigned)((threads + 255) / 256);
-    if (MR == 8) dtrmm_rows_kernel<8><<<blocks, 256, 0, s>>>(p);
-    else dtrmm_rows_kernel<4><<<blocks, 256, 0, s>>>(p);
+    if (p.has_src) {
+        if (MR == 8) dtrmm_rows_kernel<8, true><<<blocks, 256, 0, s>>>(p);
+        else dtrmm_rows_kernel<4, true><<<blocks, 256, 0, s>>>(p);
+    } else {
+        if (MR == 8) dtrmm_rows_kernel<8, false><<<blocks, 256, 0, s>>>(p);
+        else dtrmm_rows_kernel<4, false><<<blocks, 256, 0, s>>>(p);
+    }
     count_launch();
     return cudaGetLastError();
 }
