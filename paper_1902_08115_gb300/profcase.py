@@ -1,7 +1,7 @@
 """One routine on a batch larger than L2 (256-384 MiB of operands), run three times: a
 small, self-contained case for kernel profilers.
 
-    python -m paper_1902_08115_gb300.profcase {potrf|gemm|trsm} N [PAD]
+    python -m paper_1902_08115_gb300.profcase {potrf|gemm|trsm|getrf} N [PAD]
     python -m paper_1902_08115_gb300.profcase dsposv      (2048 SPD systems of order 128)
     python -m paper_1902_08115_gb300.profcase ragged      (3000 orders in [100, 200], 4 RHS)
 """
@@ -64,8 +64,15 @@ def main(argv):
         X = bfsynth.randn_batch(b, n, n, ld, 2, device=dev)
         for _ in range(3):
             bf.dtrsm("R", "L", "T", "U", 1.0, L, X, m=n, n=n)
+    elif which == "getrf":
+        b = max(1, (256 << 20) // (ld * n * 8))
+        A0 = bfsynth.randn_batch(b, n, n, ld, 3, device=dev)
+        A = A0.clone()
+        for _ in range(3):
+            A.copy_(A0)
+            bf.dgetrf(A, n=n)
     else:
-        raise SystemExit("routine must be potrf, gemm or trsm")
+        raise SystemExit("routine must be potrf, gemm, trsm or getrf")
     torch.cuda.synchronize()
     print("ok", which, n, pad, b)
 

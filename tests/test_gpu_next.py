@@ -333,6 +333,7 @@ def test_dgetrf_singular_and_permutation(bf, oracle, vname, variant, n):
     A[1, 4, :] = 0.0                               # problem 1: column 4 zero -> info 5
     A[2] = np.eye(n)[np.random.default_rng(1).permutation(n)]  # problem 2: a permutation matrix
     A[3, :, :] = 0.0                               # problem 3: all zero -> info 1
+    A[0, n - 3, :] = 0.0                           # problem 0: zero column in the last panel
     LU, piv, info = oracle.dgetrf(A, m=n)
     Ag = gpu(A)
     if variant is None:
@@ -341,7 +342,7 @@ def test_dgetrf_singular_and_permutation(bf, oracle, vname, variant, n):
         with forced(bf, bf.ROUTINE_DGETRF, 0, variant):
             pg, ig = bf.dgetrf(Ag)
     np.testing.assert_array_equal(host(ig), info)
-    assert info[1] == 5 and info[3] == 1 and info[2] == 0
+    assert info[1] == 5 and info[3] == 1 and info[2] == 0 and info[0] == n - 2
     np.testing.assert_array_equal(host(pg), piv)
     np.testing.assert_array_equal(host(Ag)[2], LU[2])  # integer-exact: no rounding happens
 
