@@ -30,9 +30,6 @@ struct SyrkParams {
     int ldc;
     long long batch;
     int tiles;  // 4x4 tiles of one triangle per problem
-    MatRef Cin;  // when has_cin: C's old values are read from Cin (ld ldcin)
-    int ldcin;
-    int has_cin;
 };
 
 // Four consecutive entries x[i .. i+3] of a column (clamped to n - 1 at its end): 16-byte
@@ -53,8 +50,9 @@ __device__ __forceinline__ void col4(const double* x, int i, int n, double* o) {
     }
 }
 
-template <bool TR, bool UP>
-__global__ void __launch_bounds__(256) dsyrk_tile_kernel(SyrkParams p) {
+// CIN: C's old values come from Cin (ld ldcin) rather than from C itself
+template <bool TR, bool UP, bool CIN>
+__global__ void __launch_bounds__(256) dsyrk_tile_kernel(SyrkParams p, MatRef Cin, int ldcin) {
     const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long q = g / p.tiles;
     if (q >= p.batch) return;
@@ -68,15 +66,14 @@ __global__ void __launch_bounds__(256) dsyrk_tile_kernel(SyrkParams p) {
     const int n = p.n;
     const double* A = p.A.ptr(q);
     double* C = p.C.mptr(q);
-    const double* Co = p.has_cin ? p.Cin.ptr(q) : C;  // old values of C
-    const int ldo = p.has_cin ? p.ldcin : p.ldc;
 
     double acc[4][4];
     if (p.mode == ACC_C || p.mode == ACC_BC) {
 #pragma unroll
         for (int b = 0; b < 4; b++) {
             double col[4];
-            col4(Co + (long long)imin(c0 + b, n - 1) * ldo, r0, n, col);  // the other triangle is read, not used
+            if constexpr (CIN) col4(Cin.ptr(q) + (long long)imin(c0 + b, n - 1) * ldcin, r0, n, col);
+            else col4(C + (long long)imin(c0 + b, n - 1) * p.ldc, r0, n, col);  // the other triangle is read, not used
 #pragma unroll
             for (int a = 0; a < 4; a++) acc[a][b] = (p.mode == ACC_BC) ? p.beta * col[a] : col[a];
         }
@@ -119,7 +116,12 @@ __global__ void __launch_bounds__(256) dsyrk_tile_kernel(SyrkParams p) {
             if (i < n && j < n && (UP ? i <= j : i >= j)) {
                 double* cp = C + i + (long long)j * p.ldc;
                 double v = acc[a][b];
-                if (p.mode == ACC_GEN) v = (p.beta == 0.0) ? p.alpha * v : fma(p.alpha, v, p.beta * Co[i + (long long)j * ldo]);
+                if constexpr (CIN) {
+                    if (p.mode == ACC_GEN)
+                        v = (p.beta == 0.0) ? p.alpha * v : fma(p.alpha, v, p.beta * Cin.ptr(q)[i + (long long)j * ldcin]);
+                } else {
+                    if (p.mode == ACC_GEN) v = (p.beta == 0.0) ? p.alpha * v : fma(p.alpha, v, p.beta * *cp);
+                }
                 *cp = v;
             }
         }
@@ -157,22 +159,20 @@ cudaError_t launch_dsyrk(int upper, int trans, int n, int k, double alpha, MatRe
     p.n = n; p.k = k; p.alpha = alpha; p.beta = beta;
     p.mode = acc_mode(alpha, beta);
     p.A = A; p.lda = lda; p.C = C; p.ldc = ldc; p.batch = batch;
-    p.has_cin = Cin != nullptr;
-    if (Cin) {
-        p.Cin = *Cin;
-        p.ldcin = ldcin;
-    }
+    const MatRef cin = Cin ? *Cin : C;
     const int nI = (n + 3) / 4;
     p.tiles = nI * (nI + 1) / 2;
     const long long threads = batch * (long long)p.tiles;
     const unsigned blocks = (unsigned)((threads + 255) / 256);
+#define BF_SYRK_LAUNCH(TR_, UP_)                                                              \
+    if (Cin) dsyrk_tile_kernel<TR_, UP_, true><<<blocks, 256, 0, s>>>(p, cin, ldcin);        \
+    else dsyrk_tile_kernel<TR_, UP_, false><<<blocks, 256, 0, s>>>(p, cin, ldcin);
     if (trans) {
-        if (upper) dsyrk_tile_kernel<true, true><<<blocks, 256, 0, s>>>(p);
-        else dsyrk_tile_kernel<true, false><<<blocks, 256, 0, s>>>(p);
+        if (upper) { BF_SYRK_LAUNCH(true, true) } else { BF_SYRK_LAUNCH(true, false) }
     } else {
-        if (upper) dsyrk_tile_kernel<false, true><<<blocks, 256, 0, s>>>(p);
-        else dsyrk_tile_kernel<false, false><<<blocks, 256, 0, s>>>(p);
+        if (upper) { BF_SYRK_LAUNCH(false, true) } else { BF_SYRK_LAUNCH(false, false) }
     }
+#undef BF_SYRK_LAUNCH
     count_launch();
     return cudaGetLastError();
 }
