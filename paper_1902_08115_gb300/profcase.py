@@ -4,6 +4,7 @@ small, self-contained case for kernel profilers.
     python -m paper_1902_08115_gb300.profcase {potrf|gemm|trsm|getrf} N [PAD]
     python -m paper_1902_08115_gb300.profcase dsposv      (2048 SPD systems of order 128)
     python -m paper_1902_08115_gb300.profcase ragged      (3000 orders in [100, 200], 4 RHS)
+    python -m paper_1902_08115_gb300.profcase vbatched    (dgemm_nn, 40,000 problems, m, n, k in [1, 64])
 """
 from __future__ import annotations
 
@@ -27,6 +28,28 @@ def main(argv):
             bf.dsposv(A, b)
         torch.cuda.synchronize()
         print("ok dsposv")
+        return
+    if which == "vbatched":
+        import ctypes
+        g = torch.Generator().manual_seed(5)
+        cnt = 40000
+        mm, nn, kk = (torch.randint(1, 65, (cnt,), generator=g) for _ in range(3))
+
+        def offsets(sz):
+            o = torch.zeros(cnt, dtype=torch.int64)
+            o[1:] = torch.cumsum(sz, 0)[:-1]
+            return o, int(sz.sum())
+        (oa, na), (ob, nb), (oc, nc) = (offsets(x) for x in (mm * kk, kk * nn, mm * nn))
+        A, B, C = (torch.randn(x, dtype=torch.float64, device="cuda") for x in (na, nb, nc))
+        m_d, n_d, k_d = (x.to("cuda", torch.int32) for x in (mm, nn, kk))
+        pa, pb, pc = ((X.data_ptr() + 8 * o).to("cuda") for X, o in ((A, oa), (B, ob), (C, oc)))
+        ip = lambda t: ctypes.c_void_p(t.data_ptr())
+        st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        for _ in range(3):
+            assert bf.bf_dgemm_vbatched(b"N", b"N", ip(m_d), ip(n_d), ip(k_d), 1.0, ip(pa), ip(m_d), ip(pb), ip(k_d),
+                                        1.0, ip(pc), ip(m_d), cnt, 64, 64, 64, None, st) == 0
+        torch.cuda.synchronize()
+        print("ok vbatched")
         return
     if which == "ragged":
         ns = bfsynth.ragged_orders(3000, 100, 200, 5)
