@@ -3,9 +3,9 @@
 // matrices have sizes known only at run time (section 1).  The uniform batches carry the
 // paper's kernels; here the problems of one launch differ, so the kernels read each problem's
 // sizes and map threads to (problem, piece of work) pairs:
-//   dgemm  -- one thread per 4x4 tile of C (section 2.1's register tile), the problems of a
-//             CTA packed so that a CTA holds ~blockDim tiles; the k loop reads op(A) and op(B)
-//             from global memory (L1) as in the direct variant ('D', section 2.2);
+//   dgemm  -- one thread per 4x4 tile of C (section 2.1's register tile), the tiles numbered
+//             densely across a chunk of problems (chunk_scan); the k loop reads op(A) and
+//             op(B) from global memory (L1) as in the direct variant ('D', section 2.2);
 //   dtrsm  -- one thread per independent row (right side) or column (left side) of B, the
 //             paper's observation that right-side solves are independent row systems
 //             (section 3.1 "dtrsm"), solved in place by substitution;
@@ -17,6 +17,42 @@
 #include "../../include/bfgpu.h"
 
 namespace bf {
+
+// Problems go in chunks of BF_VB_CHUNK per CTA.  The chunk's units of work (tiles of C, rows
+// of B) are numbered densely across its problems, so a warp holds units of consecutive
+// problems instead of idling on the lanes a smaller problem leaves empty.  s_start is the
+// exclusive prefix sum of the units per problem (two 32-entry warp scans by warp 0).
+#define BF_VB_CHUNK 64
+
+__device__ __forceinline__ void chunk_scan(int* s_start) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        int a = s_start[lane + 1], b = s_start[lane + 33];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ua = __shfl_up_sync(0xffffffffu, a, o), ub = __shfl_up_sync(0xffffffffu, b, o);
+            if (lane >= o) {
+                a += ua;
+                b += ub;
+            }
+        }
+        b += __shfl_sync(0xffffffffu, a, 31);
+        s_start[lane + 1] = a;
+        s_start[lane + 33] = b;
+        if (lane == 0) s_start[0] = 0;
+    }
+}
+
+// the chunk problem holding unit u: the largest i with s_start[i] <= u
+__device__ __forceinline__ int chunk_find(const int* s_start, int u) {
+    int lo = 0, hi = BF_VB_CHUNK;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_start[mid] <= u) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
 
 struct VGemmParams {
     const int *m, *n, *k;
@@ -30,8 +66,6 @@ struct VGemmParams {
     int* dinfo;
     long long batch;
     int max_m, max_n, max_k;
-    int tiles_max;  // ceil(max_m / 4) * ceil(max_n / 4)
-    int P;          // problems per CTA
 };
 
 // 0, or minus the position of the problem's first illegal argument
@@ -52,18 +86,30 @@ __device__ __forceinline__ int vgemm_check(const VGemmParams& p, bool ta, bool t
 
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(128) dgemm_vbatched_kernel(VGemmParams p) {
-    const int T = blockDim.x;
-    for (long long q0 = (long long)blockIdx.x * p.P; q0 < p.batch; q0 += (long long)gridDim.x * p.P) {
-        for (int u = threadIdx.x; u < p.P * p.tiles_max; u += T) {
-            const long long q = q0 + u / p.tiles_max;
-            const int t = u % p.tiles_max;
-            if (q >= p.batch) continue;
+    __shared__ int s_start[BF_VB_CHUNK + 1];
+    const int T = blockDim.x, tid = threadIdx.x;
+    for (long long q0 = (long long)blockIdx.x * BF_VB_CHUNK; q0 < p.batch; q0 += (long long)gridDim.x * BF_VB_CHUNK) {
+        if (tid < BF_VB_CHUNK) {  // tiles of each problem (0 when skipped); its status
+            const long long q = q0 + tid;
+            int cnt = 0;
+            if (q < p.batch) {
+                const int m = p.m[q], n = p.n[q], k = p.k[q];
+                const int bad = vgemm_check(p, TA, TB, q, m, n, k);
+                if (p.dinfo) p.dinfo[q] = bad;
+                if (!bad) cnt = ((m + 3) / 4) * ((n + 3) / 4);
+            }
+            s_start[tid + 1] = cnt;
+        }
+        __syncthreads();
+        chunk_scan(s_start);
+        __syncthreads();
+        const int total = s_start[BF_VB_CHUNK];
+        for (int u = tid; u < total; u += T) {
+            const int c = chunk_find(s_start, u);
+            const long long q = q0 + c;
+            const int t = u - s_start[c];
             const int m = p.m[q], n = p.n[q], k = p.k[q];
-            const int bad = vgemm_check(p, TA, TB, q, m, n, k);
-            if (t == 0 && p.dinfo) p.dinfo[q] = bad;
-            if (bad) continue;
             const int tm = (m + 3) / 4;
-            if (t >= tm * ((n + 3) / 4)) continue;
             const int i0 = 4 * (t % tm), j0 = 4 * (t / tm);
             const double* A = p.A[q];
             const double* B = p.B[q];
@@ -75,11 +121,15 @@ __global__ void __launch_bounds__(128) dgemm_vbatched_kernel(VGemmParams p) {
                 ri[a] = imin(i0 + a, m - 1);
                 cj[a] = imin(j0 + a, n - 1);
             }
+            // alpha == 1 with beta 0 or 1: the accumulators start from zero or C and are stored
+            // as they are (no FP64 operation on the epilogue)
+            const bool plain = p.alpha == 1.0 && (p.beta == 0.0 || p.beta == 1.0);
             double acc[4][4];
 #pragma unroll
-            for (int a = 0; a < 4; a++)
+            for (int b = 0; b < 4; b++)
 #pragma unroll
-                for (int b = 0; b < 4; b++) acc[a][b] = 0.0;
+                for (int a = 0; a < 4; a++)
+                    acc[a][b] = (plain && p.beta == 1.0) ? C[ri[a] + (long long)cj[b] * ldc] : 0.0;
             if (p.alpha != 0.0) {  // alpha == 0: A and B are not read
 #pragma unroll 2
                 for (int pp = 0; pp < k; pp++) {
@@ -102,12 +152,17 @@ __global__ void __launch_bounds__(128) dgemm_vbatched_kernel(VGemmParams p) {
                     const int i = i0 + a, j = j0 + b;
                     if (i < m && j < n) {
                         double* cp = C + i + (long long)j * ldc;
-                        const double v = p.alpha * acc[a][b];
-                        *cp = (p.beta == 0.0) ? v : fma(p.beta, *cp, v);  // beta == 0: C not read
+                        if (plain) {
+                            *cp = acc[a][b];
+                        } else {
+                            const double v = p.alpha * acc[a][b];
+                            *cp = (p.beta == 0.0) ? v : fma(p.beta, *cp, v);  // beta == 0: C not read
+                        }
                     }
                 }
             }
         }
+        __syncthreads();
     }
 }
 
@@ -123,7 +178,7 @@ struct VTrsmParams {
     int* dinfo;
     long long batch;
     int max_m, max_n;
-    int vmax;  // vectors per problem at most: max_m (right side) or max_n (left side)
+    int vmax;  // vector slots per problem: max_m (right side) or max_n (left side)
 };
 
 __device__ __forceinline__ int vtrsm_check(const VTrsmParams& p, long long q, int m, int n) {
@@ -141,6 +196,9 @@ __device__ __forceinline__ int vtrsm_check(const VTrsmParams& p, long long q, in
 // or column v (left side: op(A) x = alpha b); x overwrites b, read back as it is solved.
 // op(A)(i, j) = A(j, i) when transposed; lower op(A) is solved forward on the left and
 // backward on the right, upper the other way round.
+// one thread per (problem, vector), max_m (right side) or max_n (left side) slots per problem:
+// a warp holds vectors of one problem, so its loads of op(A) are broadcasts and its loop
+// lengths agree (numbering the vectors densely across problems measured 15 % slower)
 __global__ void __launch_bounds__(128) dtrsm_vbatched_kernel(VTrsmParams p) {
     const long long total = p.batch * (long long)p.vmax;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
@@ -185,11 +243,8 @@ cudaError_t launch_dgemm_vbatched(bool ta, bool tb, const VGemmParams& p0, cudaS
     if (p0.batch == 0) return cudaSuccess;
     VGemmParams p = p0;
     const int T = 128;
-    p.tiles_max = ((p.max_m + 3) / 4) * ((p.max_n + 3) / 4);
-    if (p.tiles_max < 1) p.tiles_max = 1;
-    p.P = p.tiles_max >= T ? 1 : T / p.tiles_max;
-    long long blocks = (p.batch + p.P - 1) / p.P;
-    if (blocks > 152LL * 64) blocks = 152LL * 64;
+    long long blocks = (p.batch + BF_VB_CHUNK - 1) / BF_VB_CHUNK;
+    if (blocks > 152LL * 16) blocks = 152LL * 16;
     if (ta) {
         if (tb) dgemm_vbatched_kernel<true, true><<<(unsigned)blocks, T, 0, s>>>(p);
         else dgemm_vbatched_kernel<true, false><<<(unsigned)blocks, T, 0, s>>>(p);
