@@ -18,11 +18,13 @@
 
 namespace bf {
 
-// Problems go in chunks of BF_VB_CHUNK per CTA.  The chunk's units of work (tiles of C, rows
-// of B) are numbered densely across its problems, so a warp holds units of consecutive
-// problems instead of idling on the lanes a smaller problem leaves empty.  s_start is the
-// exclusive prefix sum of the units per problem (two 32-entry warp scans by warp 0).
-#define BF_VB_CHUNK 64
+// Problems go in chunks of BF_VB_CH per CTA.  The chunk's units of work (tiles of C) are
+// numbered densely across its problems, so a warp holds units of consecutive problems instead
+// of idling on the lanes a smaller problem leaves empty.  s_start is the exclusive prefix sum
+// of the units per problem (entries past the chunk are zero; two 32-entry warp scans by
+// warp 0).  Small chunks keep many CTAs in flight.
+#define BF_VB_CHUNK 64  // s_start entries
+#define BF_VB_CH 8      // problems per chunk (measured: 8 beats 16, 32, 64 at 10k-100k problems)
 
 __device__ __forceinline__ void chunk_scan(int* s_start) {
     const int lane = threadIdx.x & 31;
@@ -88,11 +90,11 @@ template <bool TA, bool TB>
 __global__ void __launch_bounds__(128) dgemm_vbatched_kernel(VGemmParams p) {
     __shared__ int s_start[BF_VB_CHUNK + 1];
     const int T = blockDim.x, tid = threadIdx.x;
-    for (long long q0 = (long long)blockIdx.x * BF_VB_CHUNK; q0 < p.batch; q0 += (long long)gridDim.x * BF_VB_CHUNK) {
-        if (tid < BF_VB_CHUNK) {  // tiles of each problem (0 when skipped); its status
+    for (long long q0 = (long long)blockIdx.x * BF_VB_CH; q0 < p.batch; q0 += (long long)gridDim.x * BF_VB_CH) {
+        if (tid < BF_VB_CHUNK) {  // tiles of each problem (0 when skipped or past the chunk); its status
             const long long q = q0 + tid;
             int cnt = 0;
-            if (q < p.batch) {
+            if (tid < BF_VB_CH && q < p.batch) {
                 const int m = p.m[q], n = p.n[q], k = p.k[q];
                 const int bad = vgemm_check(p, TA, TB, q, m, n, k);
                 if (p.dinfo) p.dinfo[q] = bad;
@@ -243,8 +245,8 @@ cudaError_t launch_dgemm_vbatched(bool ta, bool tb, const VGemmParams& p0, cudaS
     if (p0.batch == 0) return cudaSuccess;
     VGemmParams p = p0;
     const int T = 128;
-    long long blocks = (p.batch + BF_VB_CHUNK - 1) / BF_VB_CHUNK;
-    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    long long blocks = (p.batch + BF_VB_CH - 1) / BF_VB_CH;
+    if (blocks > 152LL * 64) blocks = 152LL * 64;
     if (ta) {
         if (tb) dgemm_vbatched_kernel<true, true><<<(unsigned)blocks, T, 0, s>>>(p);
         else dgemm_vbatched_kernel<true, false><<<(unsigned)blocks, T, 0, s>>>(p);
