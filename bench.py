@@ -416,12 +416,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded N(0,1) operands, S = G G^T + n I, unit-scaled Cholesky factors)",
-        "config": {"workload": "size sweep: n in {4,8,12,16,24,32,48,64,96,128,192,256} x lda in "
-                               "{n, n+3}, ~2 GiB of operands per routine and point; dgemm nn/nt/tn/tt "
-                               "(m=n=k, C += op(A)op(B)), dtrsm rltu + rltn, dpotrf_l",
-                   "l2": "no flush: every point's inputs (~2 GiB) exceed the 126 MiB L2",
-                   "dpotrf_inputs": "refreshed in-step from S's untouched upper triangle (torch copy)",
-                   "parallelism": f"replicas x{world} (no collective on the data path)"},
+        "config": sweep_config(world),
         "roofline": roofline,
         "clocks": clk,
         "gpu_launches": int(launches),
@@ -948,6 +943,16 @@ def next_rows(bf, torch, dev, peak):
     return out
 
 
+def sweep_config(world):
+    """The workload both arms report: the size sweep of every routine and point."""
+    return {"workload": "size sweep: n in {4,8,12,16,24,32,48,64,96,128,192,256} x lda in "
+                        "{n, n+3}, ~2 GiB of operands per routine and point; dgemm nn/nt/tn/tt "
+                        "(m=n=k, C += op(A)op(B)), dtrsm rltu + rltn, dpotrf_l",
+            "l2": "no flush: every point's inputs (~2 GiB) exceed the 126 MiB L2",
+            "dpotrf_inputs": "refreshed in-step from S's untouched upper triangle (torch copy)",
+            "parallelism": f"replicas x{world} (no collective on the data path)"}
+
+
 def reference_arm(args, rank, world):
     """The oracle timed as it stands on the host cores (rank 0 only)."""
     if rank != 0:
@@ -967,7 +972,7 @@ def reference_arm(args, rank, world):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1000 * statistics.mean(t), 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "size sweep (bounded sample per point) on the CPU oracle"},
+        "config": sweep_config(world),
         "cpu_baseline": {"value": round(v, 3), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": round(v, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
