@@ -56,10 +56,13 @@ typedef struct CUstream_st* bf_stream_t; /* identical to cudaStream_t */
                              /* one problem per thread: dpotrf 'L' (n <= 256, left-looking */
                              /* by 16-column panels), dgetrf (n <= 1024, right-looking by  */
                              /* 16-column panels)                                         */
+#define BF_VARIANT_TEAM 5    /* dpotrf only: 2 or 4 lanes of a warp per problem (p2), for */
+                             /* batches between the CTA form's and the lane form's ranges */
 #define BF_TUNE_FORCE 0x100  /* or'ed into `variant`: the entry holds at every batch size; */
                              /* without it, dpotrf batches too small to fill the GPU one  */
-                             /* problem per thread still switch to BF_VARIANT_CTA (or to  */
-                             /* BF_VARIANT_BLOCKED for n > 64, batch < 20000)             */
+                             /* problem per thread still switch to BF_VARIANT_CTA, to     */
+                             /* BF_VARIANT_TEAM (12 <= n <= 64) or to BF_VARIANT_BLOCKED  */
+                             /* (n > 64, batch < 20000)                                   */
 
 /* ------------------------------------------------------------------------ */
 /* dgemm (section 2.1): C <= alpha * op(A) * op(B) + beta * C,               */
@@ -414,7 +417,8 @@ int bf_ragged_potrf_potrs_noalloc(int batch, const int* n_host, int nrhs, double
 /*   p0..p3   dgemm: TM, TN, KC, P (super-tile rows/cols, k-slice, problems   */
 /*            per CTA; 0 = default); dtrsm: MR (4/8), P, CTAs per SM (1/2);  */
 /*            dpotrf: T, NB,                                                */
-/*            lane row-block height (4/8), lane k-loop unroll (1/2).        */
+/*            lane row-block height (4/8) or team size (2/4), lane k-loop   */
+/*            unroll (1/2).                                                 */
 /* Later entries take precedence.  bf_tune_clear removes all entries.         */
 /* bf_tune_query writes the configuration a call would use into out[5]:       */
 /* {variant, p0, p1, p2, p3} in the order above (dgemm: variant,TM,TN,KC,P).  */

@@ -102,7 +102,7 @@ for _name, _args in _SIGS.items():
     globals()[_name] = _f
 
 ROUTINE_DGEMM, ROUTINE_DTRSM, ROUTINE_DPOTRF, ROUTINE_DGETRF = 0, 1, 2, 3
-VARIANT_DIRECT, VARIANT_PACKED, VARIANT_BLOCKED, VARIANT_TINY, VARIANT_CTA = 0, 1, 2, 3, 4
+VARIANT_DIRECT, VARIANT_PACKED, VARIANT_BLOCKED, VARIANT_TINY, VARIANT_CTA, VARIANT_TEAM = 0, 1, 2, 3, 4, 5
 TUNE_FORCE = 0x100  # or into a variant: the table entry holds at every batch size
 ERR_CUDA, ERR_NOT_SUPPORTED, ERR_NOALLOC_LIMIT = 1001, 1002, 1003
 RAGGED_NOALLOC_MAX = 32768

@@ -40,6 +40,22 @@ __global__ void __launch_bounds__(256) dpotrf_lane_direct_kernel(PotrfParams p) 
     if (info && p.info) p.info[q] = info + p.info_off;
 }
 
+// TEAM: TPP consecutive lanes per problem (bf_lane.cuh, potrf_team).  A team never straddles
+// two warps: the CTA is whole warps and TPP divides 32.
+template <int TPP, bool UP>
+__global__ void __launch_bounds__(256) dpotrf_team_kernel(PotrfParams p) {
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long q = gt / TPP;
+    const int rr = (int)(gt % TPP);
+    if (q >= p.batch) return;
+    if (p.skip && p.skip[q] != 0) return;  // the whole team leaves
+    const int lane = (int)(threadIdx.x & 31);
+    const unsigned mask = ((1u << TPP) - 1u) << (lane & ~(TPP - 1));
+    const int info = UP ? potrf_team<TPP, 2>(GAccT{p.A.mptr(q), p.lda}, p.n, rr, mask)
+                        : potrf_team_global<TPP, 2>(p.A.mptr(q), p.lda, p.n, rr, mask);
+    if (info && p.info && rr == 0) p.info[q] = info + p.info_off;
+}
+
 // PACKED: the CTA's problems staged through shared memory (bf_stage.cuh: coalesced 16-byte
 // loads when they are one contiguous run, a padded problem-interleaved layout), factored
 // there one per thread, and written back the same way.
@@ -99,6 +115,19 @@ cudaError_t launch_dpotrf_lane(int n, MatRef A, int lda, long long batch, int* i
         return cudaGetLastError();
     }
     const int T = cfg.T > 0 ? cfg.T : 128;
+    if (cfg.variant == VAR_TEAM) {
+        const int tpp = cfg.tpp == 2 ? 2 : 4;
+        const unsigned blocks = (unsigned)((batch * tpp + T - 1) / T);
+        if (tpp == 2) {
+            if (upper) dpotrf_team_kernel<2, true><<<blocks, T, 0, s>>>(p);
+            else dpotrf_team_kernel<2, false><<<blocks, T, 0, s>>>(p);
+        } else {
+            if (upper) dpotrf_team_kernel<4, true><<<blocks, T, 0, s>>>(p);
+            else dpotrf_team_kernel<4, false><<<blocks, T, 0, s>>>(p);
+        }
+        count_launch();
+        return cudaGetLastError();
+    }
     const unsigned blocks = (unsigned)((batch + T - 1) / T);
     if (upper) {
         launch_direct<true>(p, cfg, blocks, T, s);
@@ -126,8 +155,8 @@ cudaError_t launch_dpotrf(int n, MatRef A, int lda, long long batch, int* info,
     if (cfg.variant != VAR_BLOCKED) return launch_dpotrf_lane(n, A, lda, batch, info, 0, nullptr, cfg, s, upper);
     // right-looking blocked factorisation built from the library's kernels
     const int NB = cfg.NB;
-    PotrfConfig lane = choose_potrf(NB, lda, batch);
-    lane.variant = VAR_DIRECT;
+    PotrfConfig lane = choose_potrf(NB, lda, batch);  // the diagonal blocks: lane or team form
+    if (lane.variant != VAR_TEAM) lane.variant = VAR_DIRECT;
     for (int J = 0; J < n; J += NB) {
         const int jb = (n - J < NB) ? (n - J) : NB;
         cudaError_t e = launch_dpotrf_lane(jb, mat_sub(A, J, J, lda), lda, batch, info, J, info, lane, s, upper);

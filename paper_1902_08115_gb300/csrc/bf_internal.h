@@ -11,7 +11,7 @@ namespace bf {
 
 // Kernel variants the size switch chooses between (section 2.4: direct 'D'
 // for very small sizes, packing variants for larger ones).
-enum Variant : int { VAR_DIRECT = 0, VAR_PACKED = 1, VAR_BLOCKED = 2, VAR_TINY = 3, VAR_CTA = 4 };
+enum Variant : int { VAR_DIRECT = 0, VAR_PACKED = 1, VAR_BLOCKED = 2, VAR_TINY = 3, VAR_CTA = 4, VAR_TEAM = 5 };
 
 struct GemmConfig {
     int variant;  // VAR_DIRECT or VAR_PACKED
@@ -66,11 +66,13 @@ struct TrsmParams {
 struct PotrfConfig {
     int variant;  // VAR_DIRECT (lane per problem, in place), VAR_PACKED (lane per problem,
                   // shared memory), VAR_BLOCKED (right-looking sequence of kernels),
-                  // VAR_CTA (problem per CTA, lower, n <= 256; small batches)
+                  // VAR_CTA (problem per CTA, lower, n <= 256; small batches),
+                  // VAR_TEAM (tpp lanes per problem; small batches of small orders)
     int T;        // threads (= problems) per CTA for the lane kernels
     int NB;       // block size of the blocked variant
     int rows;     // lane kernels: row-block height, 4 or 8
     int unroll;   // lane kernels: unroll of the k loops, 1 or 2
+    int tpp = 4;  // VAR_TEAM: lanes per problem, 2 or 4
 };
 
 struct PotrfParams {

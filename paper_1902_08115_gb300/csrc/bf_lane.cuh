@@ -412,6 +412,63 @@ __device__ __forceinline__ int potrf_lane(const Acc& M, int n, const Y& ysk = Y(
     return 0;
 }
 
+// ---------------------------------------------------------------------------- team form
+// TPP consecutive lanes of one warp (a team; TPP = 2 or 4) factor one problem together, for
+// batches too small to give every FP64 pipe a warp of whole problems.  Per 4-column block J:
+//  * D = A_JJ - L_J L_J^T: lane rr of the team takes the k = rr, rr + TPP, ... terms (lane 0
+//    also the A_JJ term), and a butterfly of shuffles adds the partial sums.  Floating-point
+//    addition is commutative, so every lane of the team ends with the same bits, takes the
+//    same pivot decisions and leaves the loop at the same column;
+//  * the 4-row blocks below are dealt round-robin to the team, each one the lane form's
+//    dgemm loop and triangular edge;
+//  * __syncwarp on the team's lanes orders the block column's stores before the next
+//    block's loads (the team shares one SM, so one L1).
+// Returns info (0 or the 1-based failing column), the same in every lane of the team.
+template <int TPP, int U, class Acc>
+__device__ __forceinline__ int potrf_team(const Acc& M, int n, int rr, unsigned mask) {
+    for (int J = 0; J < n; J += 4) {
+        const int jb = imin(4, n - J);
+        int jr[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) jr[r] = imin(J + r, n - 1);
+        double d[4][4], rinv[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            double col[4];
+            M.template strip<4>(J, jr[c], n, col);  // rows above c are read but not used
+#pragma unroll
+            for (int r = c; r < 4; r++) d[r][c] = rr == 0 ? col[r] : 0.0;
+        }
+#pragma unroll U
+        for (int pp = rr; pp < J; pp += TPP) {
+            double l[4];
+            M.template strip<4>(J, pp, n, l);
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c <= r; c++) d[r][c] = fma(-l[r], l[c], d[r][c]);
+        }
+#pragma unroll
+        for (int o = 1; o < TPP; o <<= 1)
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c <= r; c++) d[r][c] += __shfl_xor_sync(mask, d[r][c], o);
+        const int f = chol_edge(d, rinv, jb);
+        if (f) return J + f;
+        if (rr == 0) {
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c <= r; c++)
+                    if (r < jb) M.st(J + r, J + c, d[r][c]);
+        }
+        for (int I = J + 4 + 4 * rr; I < n; I += 4 * TPP) lane_block<4, U>(M, n, I, J, jb, jr, d, rinv, NoSyrk(), 0);
+        __syncwarp(mask);
+    }
+    return 0;
+}
+
 #ifndef BF_LANE8_MISALIGNED
 #define BF_LANE8_MISALIGNED GAccP
 #endif
@@ -429,6 +486,13 @@ __device__ __forceinline__ int potrf_lane_global(double* a, int lda, int n) {
     if (strips_aligned(a, lda)) return potrf_lane<R, U>(GAccV{a, lda}, n);
     if (R == 8) return potrf_lane<R, U>(BF_LANE8_MISALIGNED{a, lda}, n);
     return potrf_lane<R, U>(GAccS{a, lda}, n);
+}
+
+// The team form on a problem in global memory: 16-byte strips when aligned, else single words.
+template <int TPP, int U>
+__device__ __forceinline__ int potrf_team_global(double* a, int lda, int n, int rr, unsigned mask) {
+    if (strips_aligned(a, lda)) return potrf_team<TPP, U>(GAccV{a, lda}, n, rr, mask);
+    return potrf_team<TPP, U>(GAccS{a, lda}, n, rr, mask);
 }
 
 }  // namespace bf

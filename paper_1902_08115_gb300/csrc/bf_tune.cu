@@ -168,19 +168,50 @@ TrsmConfig choose_trsm(int side, int uplo, int trans, int unit, int m, int n, lo
     return c;
 }
 
-// Largest batch for which one problem per CTA beats the table's choice, by order (measured
-// crossovers: n = 16: ~1,200; 24: ~1,800; 32: ~3,500; 64-128: ~5,000-6,000; 192: above the
-// sweep's 7,281 (995 against 970 GFLOP/s); 256: above 9,728).  0: never (n < 16, where a CTA
-// per problem idles most of its threads).
+// Largest batch for which one problem per CTA beats the other forms, by order (measured
+// crossovers against the team and lane forms: n = 16-27: ~900; 28-31: ~1,500; 32-39: ~1,800;
+// 40-47: ~2,200; 48-63: ~3,000; 64-95: ~4,500; 96-191: ~5,000-6,000; 192: above the sweep's
+// 7,281 (995 against 970 GFLOP/s); 256: above 9,728).  0: never (n < 16, where a CTA per
+// problem idles most of its threads).
 static long long cta_batch_limit(int n) {
     if (n < 16 || n > 256) return 0;
-    if (n < 24) return 1024;
+    if (n < 28) return 896;
     if (n < 32) return 1536;
-    if (n < 48) return 3072;
-    if (n < 64) return 6144;
+    if (n < 40) return 1792;
+    if (n < 48) return 2048;
+    if (n < 64) return 3072;
     if (n < 96) return 4096;
     if (n < 192) return 6144;
     return 9728;
+}
+
+// Team size of the team form (lanes per problem) for batches between the CTA form's and the
+// lane form's ranges, 0 for none.  A lane kernel on B problems runs B / 32 warps, each as
+// long as one problem's whole instruction stream; while that leaves FP64 pipes idle, a team
+// of t lanes per problem shortens the stream (the diagonal block's k loop is split t ways and
+// the row blocks dealt out) at the price of more issue slots per problem.  Measured on GB300
+// (GFLOP/s, lane -> team): n = 24 x 4,096: 153 -> 251 (t = 4); n = 32 x 6,144: 268 -> 440
+// (t = 4); n = 32 x 14,592: 623 -> 746 (t = 2); n = 48 x 9,728: 457 -> 730 (t = 4).  An odd
+// leading dimension slows the lane form more than the team form (single-word strips), so
+// teams of 2 go on to batches half as large again (n = 32 x 19,456, lda 35: 601 -> 772).
+static int team_size(int n, int lda, long long batch) {
+    if (n < 12 || n > 64) return 0;
+    long long u4, u2;  // largest batches for teams of 4 and of 2
+    if (n < 16) {
+        u4 = 0; u2 = 4096;
+    } else if (n < 20) {
+        u4 = 4096; u2 = 4096;
+    } else if (n < 40) {
+        u4 = 6144; u2 = 14592;
+    } else if (n < 64) {
+        u4 = 9728; u2 = 19456;
+    } else {
+        u4 = 9728; u2 = 14592;
+    }
+    if (n >= 20 && (lda & 1)) u2 = u2 * 3 / 2;
+    if (batch <= u4) return 4;
+    if (batch <= u2) return 2;
+    return 0;
 }
 
 PotrfConfig choose_potrf(int n, int lda, long long batch) {
@@ -218,12 +249,25 @@ PotrfConfig choose_potrf(int n, int lda, long long batch) {
     // (e.g. n = 128: 818 against 196 GFLOP/s at 608 problems), and the rest of the small
     // batches of larger orders to the blocked sequence
     if (!force && batch <= cta_batch_limit(n)) c.variant = VAR_CTA;
+    if (!force && c.variant != VAR_CTA && team_size(n, lda, batch)) {
+        c.variant = VAR_TEAM;
+        c.rows = team_size(n, lda, batch);  // the team size travels in the rows field (p2) below
+        c.T = 64;
+    }
     if (!force && c.variant != VAR_BLOCKED && c.variant != VAR_CTA && n > 64 && batch < 20000)
         c.variant = VAR_BLOCKED;
+    // the table's threads per CTA are measured on 2 GiB batches: a lane kernel on a smaller
+    // batch keeps at least two CTAs per SM (n = 48 x 9,728: 284 GFLOP/s with the table's 256
+    // threads, 457 with 64)
+    if (!force && c.variant == VAR_DIRECT) {
+        const long long cap = batch / (2 * 152) / 32 * 32;
+        if (c.T > cap) c.T = (int)(cap < 32 ? 32 : cap);
+    }
     if (c.T < 32) c.T = 32;
     if (c.T > 256) c.T = 256;
     c.T = c.T / 32 * 32;
     if (c.NB < 4) c.NB = 4;
+    if (c.variant == VAR_TEAM) c.tpp = c.rows == 2 ? 2 : 4;  // p2: lanes per problem
     c.rows = c.rows == 8 ? 8 : 4;
     c.unroll = c.unroll == 1 ? 1 : 2;
     if (c.variant == VAR_PACKED) {
@@ -256,7 +300,7 @@ extern "C" int bf_tune_set(int routine, int code, int n_lo, int n_hi, int varian
     if (n_lo > n_hi) return -3;
     const bool force = (variant & BF_TUNE_FORCE) != 0;
     variant &= ~BF_TUNE_FORCE;
-    if (variant < 0 || variant > 4) return -5;
+    if (variant < 0 || variant > 5) return -5;
     std::lock_guard<std::mutex> lk(bf::g_mu);
     bf::g_table.push_back(bf::TuneEntry{routine, code, n_lo, n_hi, variant, p0, p1, p2, p3, force});
     return 0;
@@ -282,7 +326,8 @@ extern "C" int bf_tune_query(int routine, int code, int m, int n, int k, long lo
     }
     if (routine == BF_ROUTINE_DPOTRF) {
         bf::PotrfConfig c = bf::choose_potrf(n, code == 1 ? n + 1 : n, batch);
-        out[0] = c.variant; out[1] = c.T; out[2] = c.NB; out[3] = c.rows; out[4] = c.unroll;
+        out[0] = c.variant; out[1] = c.T; out[2] = c.NB;
+        out[3] = c.variant == bf::VAR_TEAM ? c.tpp : c.rows; out[4] = c.unroll;
         return 0;
     }
     if (routine == BF_ROUTINE_DGETRF) {

@@ -1,7 +1,8 @@
 """One routine on a batch larger than L2 (256-384 MiB of operands), run three times: a
-small, self-contained case for kernel profilers.
+small, self-contained case for kernel profilers.  dpotrf also takes a batch size (the size
+switch then picks the form that batch gets).
 
-    python -m paper_1902_08115_gb300.profcase {potrf|gemm|trsm|getrf} N [PAD]
+    python -m paper_1902_08115_gb300.profcase {potrf|gemm|trsm|getrf} N [PAD [BATCH]]
     python -m paper_1902_08115_gb300.profcase dsposv      (2048 SPD systems of order 128)
     python -m paper_1902_08115_gb300.profcase ragged      (3000 orders in [100, 200], 4 RHS)
     python -m paper_1902_08115_gb300.profcase vbatched    (dgemm_nn, 40,000 problems, m, n, k in [1, 64])
@@ -67,7 +68,7 @@ def main(argv):
     pad = int(argv[2]) if len(argv) > 2 else 0
     ld, dev = n + pad, "cuda"
     if which == "potrf":
-        b = max(1, (256 << 20) // (ld * n * 8))
+        b = int(argv[3]) if len(argv) > 3 else max(1, (256 << 20) // (ld * n * 8))
         S0 = bfsynth.spd_batch(b, n, ld, 1, device=dev)
         S = S0.clone()
         for _ in range(3):

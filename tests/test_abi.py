@@ -161,14 +161,26 @@ def test_tune_table(lib):
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10)[0] == lib.VARIANT_CTA
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 100, 100, 0, 10)[0] == lib.VARIANT_CTA
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10 ** 4)[0] == lib.VARIANT_BLOCKED
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 2000)[0] == lib.VARIANT_CTA
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 10 ** 4)[0] == lib.VARIANT_DIRECT
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 1500)[0] == lib.VARIANT_CTA
+        # between the CTA and lane ranges, teams of 4 then 2 lanes per problem (12 <= n <= 64)
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 4096)[:4] == [lib.VARIANT_TEAM, 64, 32, 4]
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 10 ** 4)[:4] == [lib.VARIANT_TEAM, 64, 32, 2]
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 10 ** 5)[0] == lib.VARIANT_DIRECT
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 8, 8, 0, 4096)[0] == lib.VARIANT_DIRECT
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 100, 100, 0, 4096)[0] != lib.VARIANT_TEAM
+        # a lane kernel on a small batch keeps two CTAs per SM: 9,728 problems -> 32 threads
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 8, 8, 0, 9728)[1] == 32
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 8, 8, 0, 10)[0] == lib.VARIANT_DIRECT
         # a forced entry holds at every batch size
         lib.tune_set(lib.ROUTINE_DPOTRF, 1, 90, 110, lib.VARIANT_DIRECT | lib.TUNE_FORCE, 64, 0, 8, 1)
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10) == [lib.VARIANT_DIRECT, 64, 32, 8, 1]
         with pytest.raises(lib.BFError):
-            lib.tune_set(lib.ROUTINE_DPOTRF, 1, 90, 110, 5)
+            lib.tune_set(lib.ROUTINE_DPOTRF, 1, 90, 110, 6)
+        # the team form: p2 is the team size (2 or 4; anything else is 4)
+        lib.tune_set(lib.ROUTINE_DPOTRF, 0, 20, 30, lib.VARIANT_TEAM | lib.TUNE_FORCE, 128, 0, 2, 0)
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 24, 24, 0, 10 ** 5)[:4] == [lib.VARIANT_TEAM, 128, 32, 2]
+        lib.tune_set(lib.ROUTINE_DPOTRF, 0, 20, 30, lib.VARIANT_TEAM | lib.TUNE_FORCE, 128, 0, 3, 0)
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 24, 24, 0, 10 ** 5)[3] == 4
         # dtrsm: fewer independent rows than the GPU needs -> the blocked form from order 64
         code_rltu = 8 + 2 + 1
         assert lib.tune_query(lib.ROUTINE_DTRSM, code_rltu, 256, 256, 0, 48)[0] == lib.VARIANT_BLOCKED

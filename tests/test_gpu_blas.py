@@ -202,11 +202,12 @@ def spd_upper_nan(batch, n, ld, seed):
     return S
 
 
-# (name, variant, T, NB, lane row-block height, lane k-loop unroll); forced for both
+# (name, variant, T, NB, lane row-block height or team size, lane k-loop unroll); forced for both
 # leading-dimension parities (table code -1)
 POTRF_VARIANTS = [("direct4u2", 0, 0, 0, 4, 2), ("direct4u1", 0, 64, 0, 4, 1), ("direct8u1", 0, 0, 0, 8, 1),
                   ("direct8u2", 0, 256, 0, 8, 2), ("packed", 1, 128, 0, 0, 0), ("blocked8", 2, 0, 8, 0, 0),
-                  ("blocked32", 2, 0, 32, 0, 0), ("cta", 4, 0, 0, 0, 0)]
+                  ("blocked32", 2, 0, 32, 0, 0), ("cta", 4, 0, 0, 0, 0), ("team2", 5, 0, 0, 2, 0),
+                  ("team4", 5, 128, 0, 4, 0)]
 
 
 @pytest.mark.parametrize("vname,variant,T,NB,R,U", POTRF_VARIANTS, ids=[v[0] for v in POTRF_VARIANTS])
@@ -249,6 +250,24 @@ def test_dpotrf_failures(bf, oracle, vname, variant, T, NB, R, U):
         np.testing.assert_array_equal(gi, info)
         ok = info == 0
         assert normwise(lower_part(host(Sg)[ok], n), lower_part(L[ok], n), n) <= TOL
+
+
+def test_dpotrf_size_switch_batches(bf, oracle):
+    """The built-in batch-size switch (no forced entry): one problem per CTA, teams of 4 and of
+    2 lanes per problem, the lane form, and the blocked form whose diagonal blocks take the
+    team form, each on a sample of the batch compared with the oracle."""
+    cases = [(32, 1024), (32, 4096), (24, 9000), (48, 12000), (48, 30000), (32, 40000), (100, 8000)]
+    for n, batch in cases:
+        for pad in (0, 3):
+            Sg = bfsynth.spd_batch(batch, n, n + pad, 700 + n + pad, device="cuda")
+            idx = np.unique(np.r_[0, batch - 1, np.random.default_rng(n).integers(0, batch, 6)])
+            sel = torch.as_tensor(idx, device="cuda")
+            S = host(Sg[sel])
+            ig = bf.dpotrf(Sg, n=n)
+            assert int(host(ig).max()) == 0 and int(host(ig).min()) == 0
+            L, _ = oracle.dpotrf_l(S)
+            out = host(Sg[sel])
+            assert normwise(lower_part(out, n), lower_part(L, n), n) <= TOL, (n, batch, pad)
 
 
 def test_dpotrs(bf, oracle):
