@@ -163,10 +163,11 @@ cudaError_t launch_dsyrk(int upper, int trans, int n, int k, double alpha, MatRe
     const int nI = (n + 3) / 4;
     p.tiles = nI * (nI + 1) / 2;
     const long long threads = batch * (long long)p.tiles;
-    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    const int T = spread_block(threads, 256);
+    const unsigned blocks = (unsigned)((threads + T - 1) / T);
 #define BF_SYRK_LAUNCH(TR_, UP_)                                                              \
-    if (Cin) dsyrk_tile_kernel<TR_, UP_, true><<<blocks, 256, 0, s>>>(p, cin, ldcin);        \
-    else dsyrk_tile_kernel<TR_, UP_, false><<<blocks, 256, 0, s>>>(p, cin, ldcin);
+    if (Cin) dsyrk_tile_kernel<TR_, UP_, true><<<blocks, T, 0, s>>>(p, cin, ldcin);          \
+    else dsyrk_tile_kernel<TR_, UP_, false><<<blocks, T, 0, s>>>(p, cin, ldcin);
     if (trans) {
         if (upper) { BF_SYRK_LAUNCH(true, true) } else { BF_SYRK_LAUNCH(true, false) }
     } else {

@@ -125,13 +125,14 @@ cudaError_t launch_dtrmm(int side, int uplo, int trans, int unit, int m, int n, 
     MR = (MR == 8) ? 8 : 4;
     p.tpp = (p.m + MR - 1) / MR;
     const long long threads = batch * p.tpp;
-    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    const int T = 256;
+    const unsigned blocks = (unsigned)((threads + T - 1) / T);
     if (p.has_src) {
-        if (MR == 8) dtrmm_rows_kernel<8, true><<<blocks, 256, 0, s>>>(p);
-        else dtrmm_rows_kernel<4, true><<<blocks, 256, 0, s>>>(p);
+        if (MR == 8) dtrmm_rows_kernel<8, true><<<blocks, T, 0, s>>>(p);
+        else dtrmm_rows_kernel<4, true><<<blocks, T, 0, s>>>(p);
     } else {
-        if (MR == 8) dtrmm_rows_kernel<8, false><<<blocks, 256, 0, s>>>(p);
-        else dtrmm_rows_kernel<4, false><<<blocks, 256, 0, s>>>(p);
+        if (MR == 8) dtrmm_rows_kernel<8, false><<<blocks, T, 0, s>>>(p);
+        else dtrmm_rows_kernel<4, false><<<blocks, T, 0, s>>>(p);
     }
     count_launch();
     return cudaGetLastError();

@@ -229,8 +229,11 @@ cudaError_t launch_dtrsm(int side, int uplo, int trans, int unit, int m, int n, 
                        : launch_rows<4, true>(p, threads, block, smem, 1, s);
     }
     p.P = 1;
-    return MR == 8 ? launch_rows<8, false>(p, threads, 256, 0, cfg.minb, s)
-                   : launch_rows<4, false>(p, threads, 256, 0, cfg.minb, s);
+    // fewer than 256 threads per CTA when the rows are few (a small batch, or a block of the
+    // blocked form), so that every SM still gets work
+    const int block = spread_block(threads, 256);
+    return MR == 8 ? launch_rows<8, false>(p, threads, block, 0, cfg.minb, s)
+                   : launch_rows<4, false>(p, threads, block, 0, cfg.minb, s);
 }
 
 // Blocked triangular solve for batches too small to fill the GPU with one thread per row:

@@ -86,6 +86,32 @@ struct PotrfParams {
     int upper;      // 1: A = U^T U from the upper triangle (the lower factor of the transposed view)
 };
 
+// Threads per CTA for a flat launch of `threads` independent threads.  With at least two
+// CTAs of max_block per SM the launch keeps max_block.  Below that (a small batch, or a block
+// of the blocked dtrsm) some SMs would idle, so the CTA size (max_block, 1/2, 1/4 or 1/8 of
+// it) is the one that puts the fewest warps on the busiest of the 152 SMs, CTAs being dealt
+// out evenly; a tie keeps the larger CTA.  E.g. 512 warps: 64 CTAs of 8 warps leave 88 SMs
+// idle and 8 warps on the others, 128 CTAs of 4 warps put 4 on every SM (dtrsm, n = 48 x
+// 1,365 problems: 484 -> 753 GFLOP/s on GB300).  Any smaller size that does not lower that
+// count measured slower (9 warps on the busiest SM instead of 8: 780 -> 626).
+inline int spread_block(long long threads, int max_block) {
+    const long long sms = 152;
+    const long long W = (threads + 31) / 32;
+    const int wmax = max_block / 32;
+    if ((W + wmax - 1) / wmax >= 2 * sms) return max_block;
+    int best_w = wmax;
+    long long best = -1;
+    for (int w = wmax; w >= 1; w /= 2) {
+        const long long ctas = (W + w - 1) / w;
+        const long long load = w * ((ctas + sms - 1) / sms);  // warps on the busiest SM
+        if (best < 0 || load < best) {
+            best = load;
+            best_w = w;
+        }
+    }
+    return 32 * best_w;
+}
+
 // Increments the library's kernel-launch counter (bf_launch_count).
 void count_launch();
 
