@@ -115,7 +115,7 @@ static cudaError_t launch_scal_copy(int m, int n, double beta, MatRef X, int ldx
     if (m == 0 || n == 0 || batch == 0) return cudaSuccess;
     long long total = (long long)m * n * batch;
     long long blocks = (total + 255) / 256;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks > kSMs * 64) blocks = kSMs * 64;
     dscal_copy_kernel<<<(unsigned)blocks, 256, 0, s>>>(m, n, beta, X, ldx, Y, ldy, batch);
     count_launch();
     return cudaGetLastError();

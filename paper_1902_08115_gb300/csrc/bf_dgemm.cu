@@ -255,7 +255,7 @@ cudaError_t launch_dgemm(bool ta, bool tb, int m, int n, int k, double alpha, Ma
         if (beta == 1.0) return cudaSuccess;
         long long total = (long long)m * n * batch;
         int blocks = (int)((total + 255) / 256);
-        if (blocks > 152 * 64) blocks = 152 * 64;
+        if (blocks > kSMs * 64) blocks = kSMs * 64;
         dscale_kernel<<<blocks, 256, 0, s>>>(m, n, beta, C, ldc, batch);
         count_launch();
         return cudaGetLastError();

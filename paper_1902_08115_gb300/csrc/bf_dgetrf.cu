@@ -335,7 +335,7 @@ cudaError_t launch_dgetrf(int n, MatRef A, int lda, int* ipiv, long long sipiv, 
                                                  (int)smem);
             if (e != cudaSuccess) return e;
         }
-        const long long cap = 152LL * 16;
+        const long long cap = kSMs * 16;
         dgetrf_cta_kernel<<<(unsigned)(batch < cap ? batch : cap), 128, smem, s>>>(p);
         count_launch();
         return cudaGetLastError();

@@ -150,7 +150,7 @@ cudaError_t launch_dsyrk(int upper, int trans, int n, int k, double alpha, MatRe
         if (beta == 1.0) return cudaSuccess;
         long long total = (long long)n * n * batch;
         int blocks = (int)((total + 255) / 256);
-        if (blocks > 152 * 64) blocks = 152 * 64;
+        if (blocks > kSMs * 64) blocks = kSMs * 64;
         dsyrk_scale_kernel<<<blocks, 256, 0, s>>>(n, upper, beta, C, ldc, batch);
         count_launch();
         return cudaGetLastError();
@@ -236,7 +236,7 @@ cudaError_t launch_dsyrk_dpotrf(int n, int k, MatRef A, int lda, MatRef C, int l
     if (Cin) {  // a coalesced copy first: the lane kernel's own loads would be one problem per lane
         const long long total = (long long)n * n * batch;
         long long blocks = (total + 255) / 256;
-        if (blocks > 152LL * 32) blocks = 152LL * 32;
+        if (blocks > kSMs * 32) blocks = kSMs * 32;
         copy_lower_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, *Cin, ldcin, C, ldc, batch);
         count_launch();
         cudaError_t e = cudaGetLastError();

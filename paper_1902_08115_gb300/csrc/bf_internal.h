@@ -86,6 +86,11 @@ struct PotrfParams {
     int upper;      // 1: A = U^T U from the upper triangle (the lower factor of the transposed view)
 };
 
+// SMs of a GB300.  Grid caps of grid-stride kernels and the batch-size switch points, all
+// measured on this GPU, are expressed in it.  (The ragged plan queries the device instead,
+// since its grid is exactly one wave of resident CTAs.)
+constexpr long long kSMs = 152;
+
 // Threads per CTA for a flat launch of `threads` independent threads.  With at least two
 // CTAs of max_block per SM the launch keeps max_block.  Below that (a small batch, or a block
 // of the blocked dtrsm) some SMs would idle, so the CTA size (max_block, 1/2, 1/4 or 1/8 of
@@ -95,7 +100,7 @@ struct PotrfParams {
 // 1,365 problems: 484 -> 753 GFLOP/s on GB300).  Any smaller size that does not lower that
 // count measured slower (9 warps on the busiest SM instead of 8: 780 -> 626).
 inline int spread_block(long long threads, int max_block) {
-    const long long sms = 152;
+    const long long sms = kSMs;
     const long long W = (threads + 31) / 32;
     const int wmax = max_block / 32;
     if ((W + wmax - 1) / wmax >= 2 * sms) return max_block;

@@ -346,7 +346,7 @@ cudaError_t launch_dpotrf_cta(int n, MatRef A, int lda, long long batch, int* in
         cudaError_t e = cudaFuncSetAttribute(dpotrf_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const long long cap = 152LL * 16;
+    const long long cap = kSMs * 16;
     const unsigned grid = (unsigned)(batch < cap ? batch : cap);
     dpotrf_cta_kernel<<<grid, T, smem, s>>>(n, A, lda, batch, info);
     count_launch();

@@ -43,7 +43,7 @@ static cudaError_t copy_mat(int rows, int cols, const double* src, int lds, long
     const long long total = (long long)rows * cols * batch;
     if (total == 0) return cudaSuccess;
     int blocks = (int)((total + 255) / 256);
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks > kSMs * 32) blocks = kSMs * 32;
     copy_mat_kernel<<<blocks, 256, 0, s>>>(rows, cols, src, lds, sS, dst, ldd, sD, batch);
     count_launch();
     return cudaGetLastError();

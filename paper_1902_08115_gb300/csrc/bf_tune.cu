@@ -260,7 +260,7 @@ PotrfConfig choose_potrf(int n, int lda, long long batch) {
     // batch keeps at least two CTAs per SM (n = 48 x 9,728: 284 GFLOP/s with the table's 256
     // threads, 457 with 64)
     if (!force && c.variant == VAR_DIRECT) {
-        const long long cap = batch / (2 * 152) / 32 * 32;
+        const long long cap = batch / (2 * kSMs) / 32 * 32;
         if (c.T > cap) c.T = (int)(cap < 32 ? 32 : cap);
     }
     if (c.T < 32) c.T = 32;

@@ -246,7 +246,7 @@ cudaError_t launch_dgemm_vbatched(bool ta, bool tb, const VGemmParams& p0, cudaS
     VGemmParams p = p0;
     const int T = 128;
     long long blocks = (p.batch + BF_VB_CH - 1) / BF_VB_CH;
-    if (blocks > 152LL * 64) blocks = 152LL * 64;
+    if (blocks > kSMs * 64) blocks = kSMs * 64;
     if (ta) {
         if (tb) dgemm_vbatched_kernel<true, true><<<(unsigned)blocks, T, 0, s>>>(p);
         else dgemm_vbatched_kernel<true, false><<<(unsigned)blocks, T, 0, s>>>(p);
@@ -265,7 +265,7 @@ cudaError_t launch_dtrsm_vbatched(const VTrsmParams& p0, cudaStream_t s) {
     if (p.vmax < 1) p.vmax = 1;
     const long long total = p.batch * (long long)p.vmax;
     long long blocks = (total + 127) / 128;
-    if (blocks > 152LL * 64) blocks = 152LL * 64;
+    if (blocks > kSMs * 64) blocks = kSMs * 64;
     dtrsm_vbatched_kernel<<<(unsigned)blocks, 128, 0, s>>>(p);
     count_launch();
     return cudaGetLastError();
