@@ -389,8 +389,9 @@ __global__ void __launch_bounds__(128, 6) dpotrf_vbatched_cta_kernel(const int* 
 cudaError_t launch_dpotrf_vbatched(const int* n, double* const* A, const int* lda, int* info, long long batch,
                                    int max_n, cudaStream_t s) {
     if (batch == 0) return cudaSuccess;
-    if (max_n <= 32) {
-        dpotrf_vbatched_lane_kernel<<<(unsigned)((batch + 127) / 128), 128, 0, s>>>(n, A, lda, info, batch, max_n);
+    if (max_n <= 32) {  // one problem per thread; small batches in smaller CTAs, over every SM
+        const int T = spread_block(batch, 128);
+        dpotrf_vbatched_lane_kernel<<<(unsigned)((batch + T - 1) / T), T, 0, s>>>(n, A, lda, info, batch, max_n);
         count_launch();
         return cudaGetLastError();
     }

@@ -264,9 +264,10 @@ cudaError_t launch_dtrsm_vbatched(const VTrsmParams& p0, cudaStream_t s) {
     p.vmax = p.right ? p.max_m : p.max_n;
     if (p.vmax < 1) p.vmax = 1;
     const long long total = p.batch * (long long)p.vmax;
-    long long blocks = (total + 127) / 128;
+    const int T = spread_block(total, 128);
+    long long blocks = (total + T - 1) / T;
     if (blocks > kSMs * 64) blocks = kSMs * 64;
-    dtrsm_vbatched_kernel<<<(unsigned)blocks, 128, 0, s>>>(p);
+    dtrsm_vbatched_kernel<<<(unsigned)blocks, T, 0, s>>>(p);
     count_launch();
     return cudaGetLastError();
 }
