@@ -272,3 +272,30 @@ def test_vbatched_illegal_call_arguments(lib):
     assert p(b"L", 1, 1, 1, NULL, 1, 1025, NULL) == lib.ERR_NOT_SUPPORTED
     assert p(b"L", NULL, 1, 1, NULL, 1, 4, NULL) == -2
     assert p(b"L", 1, 1, 1, NULL, 0, 4, NULL) == 0
+
+
+def test_dpotrf_batch_switch_is_ordered(lib):
+    """The built-in batch-size switch (no table entries): for every order, growing batches move
+    from one problem per CTA to teams of 4, then 2 lanes per problem, then one problem per lane
+    (or, above order 64, the blocked sequence), and never back; the team form covers only
+    orders 12..64, and one problem per CTA only orders 16..256."""
+    lib.tune_clear()
+    try:
+        stage = {lib.VARIANT_CTA: 0, lib.VARIANT_TEAM: 1, lib.VARIANT_DIRECT: 3, lib.VARIANT_BLOCKED: 3}
+        batches = [1, 100, 600, 1000, 1500, 2000, 3000, 4096, 6144, 9728, 12288, 14592, 19456, 21000,
+                   29127, 40000, 10 ** 5, 10 ** 6]
+        for n in list(range(1, 70)) + [96, 128, 192, 256, 300]:
+            for code in (0, 1):
+                last = -1
+                for b in batches:
+                    v, T, _, p2, _ = lib.tune_query(lib.ROUTINE_DPOTRF, code, n, n, 0, b)
+                    s = stage[v] + (1 if v == lib.VARIANT_TEAM and p2 == 2 else 0)
+                    assert s >= last, (n, code, b)
+                    last = s
+                    if v == lib.VARIANT_TEAM:
+                        assert 12 <= n <= 64 and p2 in (2, 4) and T == 64
+                    if v == lib.VARIANT_CTA:
+                        assert 16 <= n <= 256
+                    assert T % 32 == 0 and 32 <= T <= 256
+    finally:
+        lib.tune_clear()
