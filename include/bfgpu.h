@@ -419,12 +419,25 @@ int bf_ragged_potrf_potrs_noalloc(int batch, const int* n_host, int nrhs, double
 /*            dpotrf: T, NB,                                                */
 /*            lane row-block height (4/8) or team size (2/4), lane k-loop   */
 /*            unroll (1/2).                                                 */
-/* Later entries take precedence.  bf_tune_clear removes all entries.         */
+/* Later entries take precedence.  bf_tune_clear removes all entries (and the */
+/* batch rules below).                                                        */
 /* bf_tune_query writes the configuration a call would use into out[5]:       */
 /* {variant, p0, p1, p2, p3} in the order above (dgemm: variant,TM,TN,KC,P).  */
 /* ------------------------------------------------------------------------ */
 int bf_tune_set(int routine, int code, int n_lo, int n_hi, int variant, int p0, int p1, int p2,
                 int p3);
+
+/* The batch-size side of dpotrf's switch, set by measurement like the size side (section     */
+/* 2.4).  For orders in [n_lo, n_hi] and lda parity `code` (-1: both), batches of at most     */
+/* cta_max problems run one problem per CTA; larger ones up to team4_max run teams of 4 lanes */
+/* per problem, then up to team2_max teams of 2; the rest take the table's variant.  A       */
+/* negative cta_max keeps the built-in bound; negative team4_max and team2_max together keep  */
+/* the built-in team bounds, and one negative alone means no team of that size.  Entries      */
+/* with BF_TUNE_FORCE are not affected.  Later rules take precedence; bf_tune_clear removes   */
+/* them.  Returns 0, or minus the position of an illegal argument (routine other than        */
+/* BF_ROUTINE_DPOTRF: -1).                                                                     */
+int bf_tune_set_batch_rule(int routine, int code, int n_lo, int n_hi, long long cta_max,
+                           long long team4_max, long long team2_max);
 void bf_tune_clear(void);
 int bf_tune_query(int routine, int code, int m, int n, int k, long long batch, int* out);
 

@@ -54,6 +54,7 @@ _SIGS = {
     "bf_dpotrs": [_c, _i, _i, _vp, _i, _vp, _i, _vp],
     "bf_dpotrs_strided_batched": [_c, _i, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _vp],
     "bf_tune_set": [_i, _i, _i, _i, _i, _i, _i, _i, _i],
+    "bf_tune_set_batch_rule": [_i, _i, _i, _i, _ll, _ll, _ll],
     "bf_tune_clear": [],
     "bf_tune_query": [_i, _i, _i, _i, _i, _ll, _ip],
     "bf_status_string": [_i],
@@ -485,6 +486,14 @@ def tune_set(routine: int, code: int, n_lo: int, n_hi: int, variant: int, p0=0, 
     _check("bf_tune_set", bf_tune_set(routine, code, n_lo, n_hi, variant, p0, p1, p2, p3))
 
 
+def tune_set_batch_rule(routine: int, code: int, n_lo: int, n_hi: int, cta_max: int, team4_max: int,
+                        team2_max: int):
+    """Measured batch-size bounds of dpotrf's small-batch forms (one problem per CTA, teams of
+    4 and of 2 lanes per problem) for orders in [n_lo, n_hi]; negative keeps the built-in."""
+    _check("bf_tune_set_batch_rule",
+           bf_tune_set_batch_rule(routine, code, n_lo, n_hi, cta_max, team4_max, team2_max))
+
+
 def tune_clear():
     bf_tune_clear()
 
@@ -506,6 +515,9 @@ def load_table(path: str) -> int:
     for e in doc["entries"]:
         p = list(e["p"]) + [0] * (4 - len(e["p"]))
         tune_set(e["routine"], e["code"], e["lo"], e["hi"], e["variant"], *p[:4])
+    for r in doc.get("batch_rules", []):
+        tune_set_batch_rule(r["routine"], r["code"], r["lo"], r["hi"], r["cta_max"], r["team4_max"],
+                            r["team2_max"])
     if "ragged" in doc:
         _ragged_cfg.update({k: int(doc["ragged"][k]) for k in ("lane_max", "threads")})
     return len(doc["entries"])

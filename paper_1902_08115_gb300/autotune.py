@@ -8,6 +8,10 @@ with CUDA events on a uniform batch of about 1 GiB of operands, keeps the
 fastest, and writes the table to tuned/<gpu name>.json.  The binding loads
 that table at import (bf_tune_set), so every later call uses the measured
 switch; entries cover the order range from one tuned order up to the next.
+On the GPU the batch size takes part in the switch too: for dpotrf the tool
+also times the small-batch forms (one problem per CTA, teams of 4 and 2 lanes
+per problem) against the table's variant over batches of 152 to 38,912
+problems and stores the measured bounds (bf_tune_set_batch_rule).
 
     python -m paper_1902_08115_gb300.autotune [--quick] [--out PATH]
 """
@@ -173,15 +177,99 @@ def tune(quick=False, out=None, log=print):
             del S, S0
         torch.cuda.empty_cache()
     bf.tune_clear()
+    rules = tune_batch_rules(torch, bf, dev, entries, log, orders=RULE_ORDERS[::2] if quick else RULE_ORDERS)
+    bf.tune_clear()
     ragged = tune_ragged(torch, bf, dev, log, count=50000 if quick else 200000)
     doc = {"gpu": name, "ragged": ragged, "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
-           "seconds": round(time.time() - t_start, 1), "entries": entries}
+           "seconds": round(time.time() - t_start, 1), "entries": entries, "batch_rules": rules}
     path = out or table_path(name)
     os.makedirs(os.path.dirname(path), exist_ok=True)
     with open(path, "w") as f:
         json.dump(doc, f, indent=1)
     bf.load_table(path)
     return path
+
+
+# ---------------------------------------------------------------------------- batch-size side
+RULE_ORDERS = (12, 16, 24, 32, 48, 64, 96, 128, 192, 256)
+RULE_BATCHES = tuple(152 * 2 ** k for k in range(9))  # 152 .. 38,912 problems
+FORMS = ("cta", "team4", "team2", "table")
+
+
+def derive_batch_rule(rows):
+    """The batch-size schedule of dpotrf's forms from measured times.
+
+    rows: [(batch, {form: ms})] in ascending batch, forms among FORMS ("table" = the size
+    table's variant at every batch).  Returns (cta_max, team4_max, team2_max): the schedule
+    cta -> team4 -> team2 -> table, bounds taken among the measured batches (0 = never), that
+    minimises the summed ratio of the scheduled form's time to the best form's time over the
+    measured batches.  Equal sums keep the smaller bounds (the table's variant)."""
+    cuts = [0] + [b for b, _ in rows]
+    best = None
+    for i in range(len(cuts)):
+        for j in range(i, len(cuts)):
+            for k in range(j, len(cuts)):
+                t = (cuts[i], cuts[j], cuts[k])
+                cost = 0.0
+                for b, ms in rows:
+                    form = "cta" if b <= t[0] else "team4" if b <= t[1] else "team2" if b <= t[2] else "table"
+                    if form not in ms:
+                        cost = float("inf")
+                        break
+                    cost += ms[form] / min(ms.values())
+                if best is None or cost < best[0] - 1e-9:
+                    best = (cost, t)
+    if best is None or best[0] == float("inf"):
+        return 0, 0, 0
+    return best[1]
+
+
+def tune_batch_rules(torch, bf, dev, entries, log, orders=RULE_ORDERS, batches=RULE_BATCHES,
+                     budget=2 << 30):
+    """Time dpotrf's small-batch forms against the size table's variant over a range of batch
+    sizes, per order and lda parity, and derive each order range's bounds (bf_tune_set_batch_rule).
+    The tuned entries are installed while timing, as every later call will run them."""
+    import bfsynth
+    rules = []
+    for idx, n in enumerate(orders):
+        lo = n if idx else 1
+        hi = orders[idx + 1] - 1 if idx + 1 < len(orders) else 1 << 20
+        for code, ld in ((0, n + (n & 1)), (1, n + 1 - (n & 1))):
+            table = [e for e in entries if e["routine"] == bf.ROUTINE_DPOTRF and e["code"] == code
+                     and e["lo"] <= n <= e["hi"]]
+            forms = {"team4": (5, 64, 0, 4, 0), "team2": (5, 64, 0, 2, 0)}
+            if 16 <= n <= 256:
+                forms["cta"] = (4, 0, 0, 0, 0)
+            if table:
+                forms["table"] = tuple([table[-1]["variant"]] + list(table[-1]["p"]))
+            else:
+                forms["table"] = (0, 0, 0, 0, 0)
+            rows = []
+            for b in batches:
+                if b * n * ld * 8 > budget:
+                    break
+                S0 = bfsynth.spd_batch(b, n, ld, 7, device=dev)
+                S = S0.clone()
+                ms_copy = _time(torch, lambda: S.copy_(S0))
+                times = {}
+                for name, (variant, T, NB, R, U) in forms.items():
+                    _install(bf, entries)
+                    bf.tune_set(bf.ROUTINE_DPOTRF, code, 0, 1 << 30, variant | bf.TUNE_FORCE, T, NB, R, U)
+
+                    def run():
+                        S.copy_(S0)
+                        bf.dpotrf(S, n=n)
+
+                    times[name] = max(_time(torch, run) - ms_copy, 1e-6)
+                rows.append((b, times))
+                del S, S0
+            cta_max, team4_max, team2_max = derive_batch_rule(rows)
+            rules.append(dict(routine=bf.ROUTINE_DPOTRF, code=code, lo=lo, hi=hi, cta_max=cta_max,
+                              team4_max=team4_max, team2_max=team2_max, n=n, lda=ld))
+            log(f"dpotrf batch rule n={n} lda={ld}: cta <= {cta_max}, team4 <= {team4_max}, "
+                f"team2 <= {team2_max}")
+    bf.tune_clear()
+    return rules
 
 
 def tune_ragged(torch, bf, dev, log, count=200000, nrhs=4):

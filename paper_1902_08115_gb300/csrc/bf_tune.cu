@@ -34,6 +34,26 @@ static bool lookup(int routine, int code, int n, TuneEntry* out) {
     return false;
 }
 
+// Measured batch-size bounds of dpotrf's small-batch forms (bf_tune_set_batch_rule); a
+// negative bound keeps the built-in value.
+struct BatchRule {
+    int code, lo, hi;
+    long long cta_max, team4_max, team2_max;
+};
+
+static std::vector<BatchRule> g_rules;
+
+static bool lookup_rule(int code, int n, BatchRule* out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto it = g_rules.rbegin(); it != g_rules.rend(); ++it) {
+        if ((it->code == code || it->code < 0) && n >= it->lo && n <= it->hi) {
+            *out = *it;
+            return true;
+        }
+    }
+    return false;
+}
+
 static int ceil4(int x) { return x < 4 ? 4 : (x + 3) / 4 * 4; }
 
 static const size_t kSmemBudget = 200 * 1024;  // per CTA, below the 227 KB opt-in limit
@@ -248,10 +268,21 @@ PotrfConfig choose_potrf(int n, int lda, long long batch) {
     // small batches go to one problem per CTA, up to the crossover measured on GB300
     // (e.g. n = 128: 818 against 196 GFLOP/s at 608 problems), and the rest of the small
     // batches of larger orders to the blocked sequence
-    if (!force && batch <= cta_batch_limit(n)) c.variant = VAR_CTA;
-    if (!force && c.variant != VAR_CTA && team_size(n, lda, batch)) {
+    long long cta_max = cta_batch_limit(n);
+    int team = team_size(n, lda, batch);
+    BatchRule r;
+    if (lookup_rule(code, n, &r)) {  // measured bounds replace the built-in ones
+        if (r.cta_max >= 0) cta_max = r.cta_max;
+        if (r.team4_max >= 0 || r.team2_max >= 0) {  // the team bounds as a pair (< 0: none)
+            team = (r.team4_max >= 0 && batch <= r.team4_max)   ? 4
+                 : (r.team2_max >= 0 && batch <= r.team2_max) ? 2
+                                                                : 0;
+        }
+    }
+    if (!force && batch <= cta_max) c.variant = VAR_CTA;
+    if (!force && c.variant != VAR_CTA && team) {
         c.variant = VAR_TEAM;
-        c.rows = team_size(n, lda, batch);  // the team size travels in the rows field (p2) below
+        c.rows = team;  // the team size travels in the rows field (p2) below
         c.T = 64;
     }
     if (!force && c.variant != VAR_BLOCKED && c.variant != VAR_CTA && n > 64 && batch < 20000)
@@ -309,6 +340,17 @@ extern "C" int bf_tune_set(int routine, int code, int n_lo, int n_hi, int varian
 extern "C" void bf_tune_clear(void) {
     std::lock_guard<std::mutex> lk(bf::g_mu);
     bf::g_table.clear();
+    bf::g_rules.clear();
+}
+
+extern "C" int bf_tune_set_batch_rule(int routine, int code, int n_lo, int n_hi, long long cta_max,
+                                      long long team4_max, long long team2_max) {
+    if (routine != BF_ROUTINE_DPOTRF) return -1;
+    if (code < -1 || code > 1) return -2;
+    if (n_lo > n_hi) return -3;
+    std::lock_guard<std::mutex> lk(bf::g_mu);
+    bf::g_rules.push_back(bf::BatchRule{code, n_lo, n_hi, cta_max, team4_max, team2_max});
+    return 0;
 }
 
 extern "C" int bf_tune_query(int routine, int code, int m, int n, int k, long long batch, int* out) {

@@ -299,3 +299,64 @@ def test_dpotrf_batch_switch_is_ordered(lib):
                     assert T % 32 == 0 and 32 <= T <= 256
     finally:
         lib.tune_clear()
+
+
+def test_batch_rules(lib, tmp_path):
+    """bf_tune_set_batch_rule replaces the built-in batch bounds of dpotrf's small-batch forms
+    for its order range and lda parity; the autotuner's table carries them (load_table)."""
+    import json
+    lib.tune_clear()
+    try:
+        q = lambda code, n, b: lib.tune_query(lib.ROUTINE_DPOTRF, code, n, n, 0, b)
+        lib.tune_set_batch_rule(lib.ROUTINE_DPOTRF, -1, 20, 30, 100, 1000, 5000)
+        assert q(0, 24, 100)[0] == lib.VARIANT_CTA
+        assert q(0, 24, 101)[:4] == [lib.VARIANT_TEAM, 64, 32, 4]
+        assert q(1, 24, 5000)[:4] == [lib.VARIANT_TEAM, 64, 32, 2]
+        assert q(0, 24, 5001)[0] == lib.VARIANT_DIRECT
+        assert q(0, 32, 5001)[0] == lib.VARIANT_TEAM  # outside the rule: built-in bounds
+        # only the lda-parity named; a negative cta bound keeps the built-in one (896 at n = 24)
+        lib.tune_set_batch_rule(lib.ROUTINE_DPOTRF, 1, 24, 24, -1, 0, -1)
+        assert q(1, 24, 896)[0] == lib.VARIANT_CTA
+        assert q(1, 24, 897)[0] == lib.VARIANT_DIRECT  # team bounds (0, none): no team at all
+        assert q(0, 24, 897)[:4] == [lib.VARIANT_TEAM, 64, 32, 4]  # the even-lda rule above
+        # a forced table entry is not affected
+        lib.tune_set(lib.ROUTINE_DPOTRF, -1, 20, 30, lib.VARIANT_DIRECT | lib.TUNE_FORCE, 64, 0, 8, 2)
+        assert q(0, 24, 50)[0] == lib.VARIANT_DIRECT
+        lib.tune_clear()
+        assert q(0, 24, 50)[0] == lib.VARIANT_CTA and q(0, 24, 101)[0] == lib.VARIANT_CTA
+        with pytest.raises(lib.BFError) as e:
+            lib.tune_set_batch_rule(lib.ROUTINE_DGEMM, 0, 1, 2, 0, 0, 0)
+        assert e.value.status == -1
+        with pytest.raises(lib.BFError) as e:
+            lib.tune_set_batch_rule(lib.ROUTINE_DPOTRF, 2, 1, 2, 0, 0, 0)
+        assert e.value.status == -2
+        with pytest.raises(lib.BFError) as e:
+            lib.tune_set_batch_rule(lib.ROUTINE_DPOTRF, 0, 3, 2, 0, 0, 0)
+        assert e.value.status == -3
+        doc = {"entries": [], "batch_rules": [dict(routine=lib.ROUTINE_DPOTRF, code=-1, lo=40, hi=50,
+                                                   cta_max=10, team4_max=20, team2_max=30)]}
+        path = tmp_path / "table.json"
+        path.write_text(json.dumps(doc))
+        assert lib.load_table(str(path)) == 0
+        assert [q(0, 45, b)[0] for b in (10, 20, 30, 31)] == [lib.VARIANT_CTA, lib.VARIANT_TEAM,
+                                                                lib.VARIANT_TEAM, lib.VARIANT_DIRECT]
+    finally:
+        lib.tune_clear()
+
+
+def test_derive_batch_rule():
+    """The autotuner's choice of batch bounds from measured times: the monotone schedule
+    CTA -> team of 4 -> team of 2 -> table variant with the least summed time ratio."""
+    from paper_1902_08115_gb300.autotune import derive_batch_rule
+    best = {152: "cta", 304: "cta", 608: "team4", 1216: "team4", 2432: "team2", 4864: "table", 9728: "table"}
+    rows = [(b, {f: (1.0 if f == w else 1.5) for f in ("cta", "team4", "team2", "table")}) for b, w in best.items()]
+    assert derive_batch_rule(rows) == (304, 1216, 2432)
+    # one noisy point out of order does not break the order: the least total loss wins
+    rows[3] = (1216, {"cta": 1.0, "team4": 1.02, "team2": 1.5, "table": 1.5})
+    assert derive_batch_rule(rows) == (304, 1216, 2432)
+    # a form that cannot run at some order (no CTA form below order 16) is never scheduled
+    rows = [(b, {"team4": 2.0, "team2": 1.0, "table": 1.2 if b < 1000 else 0.9}) for b in (152, 608, 2432)]
+    assert derive_batch_rule(rows) == (0, 0, 608)
+    # ties keep the table's variant
+    rows = [(b, {"cta": 1.0, "team4": 1.0, "team2": 1.0, "table": 1.0}) for b in (152, 608)]
+    assert derive_batch_rule(rows) == (0, 0, 0)
