@@ -232,8 +232,9 @@ def tune_batch_rules(torch, bf, dev, entries, log, orders=RULE_ORDERS, batches=R
     import bfsynth
     rules = []
     for idx, n in enumerate(orders):
-        lo = n if idx else 1
-        hi = orders[idx + 1] - 1 if idx + 1 < len(orders) else 1 << 20
+        # from this order up to the next (orders outside the measured range keep the built-in
+        # bounds)
+        lo, hi = n, (orders[idx + 1] - 1 if idx + 1 < len(orders) else n)
         for code, ld in ((0, n + (n & 1)), (1, n + 1 - (n & 1))):
             table = [e for e in entries if e["routine"] == bf.ROUTINE_DPOTRF and e["code"] == code
                      and e["lo"] <= n <= e["hi"]]
