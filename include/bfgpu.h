@@ -342,6 +342,16 @@ int bf_dpotrf_backward_strided_batched(char uplo, int n, const double* L, int ld
                                        double* Abar, int ldab, long long strideAbar, int batch,
                                        bf_stream_t stream);
 
+/* After dpotrf (section 3.1 "dpotrf"; LAPACK leaves the other triangle     */
+/* untouched and a failed problem's later columns unspecified), make each    */
+/* problem of A a clean triangular factor: the strict triangle opposite uplo */
+/* ('L': the strict upper one) is set to zero, and a problem whose info[q]  */
+/* is nonzero (info: device array of batch ints, may be NULL) has its whole  */
+/* n x n set to NaN, so a failed factorisation cannot be used as a finite    */
+/* factor (e.g. by a gradient).  Padding rows are not touched.               */
+int bf_dtrfill_strided_batched(char uplo, int n, double* A, int lda, long long strideA,
+                               const int* info, int batch, bf_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Ragged batches (problems of different orders; no counterpart in the       */
 /* paper, which treats one matrix per call): factor every SPD matrix with     */
@@ -390,7 +400,12 @@ int bf_ragged_plan_destroy(bf_ragged_plan_t plan);
 /*  - batch > BF_RAGGED_NOALLOC_MAX returns BF_ERR_NOALLOC_LIMIT (nothing is */
 /*    launched).                                                             */
 /*  - The first call on a device looks up the array's device address (set-  */
-/*    up); make that first call before any stream capture.                   */
+/*    up); make that first call before any stream capture.  The address is   */
+/*    kept for the process: do not call cudaDeviceReset on a device after    */
+/*    using this entry point there.                                          */
+/*  - The problem queue is copied to the array from host memory that the     */
+/*    next call reuses, so a call on a stream that is being captured returns */
+/*    BF_ERR_NOT_SUPPORTED and launches nothing.                             */
 /*  - Every call shares the one array and overwrites it (the queue counter   */
 /*    is cleared each call): calls that overlap on the GPU -- on different   */
 /*    streams, or from different host threads -- race; serialise them, e.g. */

@@ -66,6 +66,7 @@ _SIGS = {
     "bf_dtrsm_backward_strided_batched": [_c, _c, _c, _c, _i, _i, _d, _vp, _i, _ll, _vp, _i, _ll, _vp, _i,
                                           _ll, _vp, _i, _ll, _i, _vp],
     "bf_dpotrf_backward_strided_batched": [_c, _i, _vp, _i, _ll, _vp, _i, _ll, _vp, _i, _ll, _i, _vp],
+    "bf_dtrfill_strided_batched": [_c, _i, _vp, _i, _ll, _vp, _i, _vp],
     "bf_ragged_workspace_bytes": [_i],
     "bf_ragged_potrf_potrs_plan_create": [_i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _i, _i,
                                           _vp, ctypes.POINTER(_vp)],
@@ -148,6 +149,16 @@ def _batch_dims(X):
     return X.shape[0], X.shape[1], X.shape[2], X.stride(0)
 
 
+def _bstride(name, b, stride, batch):
+    """Batch stride of an operand: its own when it holds one matrix per problem, 0 when it holds
+    one matrix shared by every problem; any other batch count is refused (nothing launched)."""
+    if b == batch:
+        return stride if batch > 1 else 0
+    if b == 1:
+        return 0
+    raise ValueError(f"{name} holds {b} matrices for a batch of {batch}: expected {batch} or 1")
+
+
 def _square(*Xs):
     """Common order when every tensor is an unpadded square batch, else None."""
     n = Xs[0].shape[1]
@@ -172,8 +183,8 @@ def dgemm(transa: str, transb: str, alpha: float, A, B, beta: float, C, m=None, 
         n = sq if n is None else n
         k = sq if k is None else k
     _check("bf_dgemm_strided_batched", bf_dgemm_strided_batched(
-        _ch(transa), _ch(transb), m, n, k, alpha, _ptr(A), ldA, sA if bA > 1 else 0, _ptr(B), ldB,
-        sB if bB > 1 else 0, beta, _ptr(C), ldC, sC, bC, _stream(stream)))
+        _ch(transa), _ch(transb), m, n, k, alpha, _ptr(A), ldA, _bstride("A", bA, sA, bC), _ptr(B), ldB,
+        _bstride("B", bB, sB, bC), beta, _ptr(C), ldC, sC, bC, _stream(stream)))
     return C
 
 
@@ -192,7 +203,7 @@ def dtrsm(side: str, uplo: str, transa: str, diag: str, alpha: float, A, B, m=No
         m = sq if m is None else m
         n = sq if n is None else n
     _check("bf_dtrsm_strided_batched", bf_dtrsm_strided_batched(
-        _ch(side), _ch(uplo), _ch(transa), _ch(diag), m, n, alpha, _ptr(A), ldA, sA if bA > 1 else 0,
+        _ch(side), _ch(uplo), _ch(transa), _ch(diag), m, n, alpha, _ptr(A), ldA, _bstride("A", bA, sA, bB),
         _ptr(B), ldB, sB, bB, _stream(stream)))
     return B
 
@@ -209,6 +220,18 @@ def dpotrf(A, n=None, info=None, uplo: str = "L", stream=None):
     return info
 
 
+def dtrfill(A, info=None, n=None, uplo: str = "L", stream=None):
+    """Zero the strict triangle opposite `uplo` of every problem, and set every problem whose
+    info is nonzero to NaN (in place on A)."""
+    bA, cA, ldA, sA = _batch_dims(A)
+    n = cA if n is None else n
+    if info is not None and info.numel() != bA:
+        raise ValueError(f"info holds {info.numel()} entries for a batch of {bA}")
+    _check("bf_dtrfill_strided_batched", bf_dtrfill_strided_batched(
+        _ch(uplo), n, _ptr(A), ldA, sA, _ptr(info) if info is not None else None, bA, _stream(stream)))
+    return A
+
+
 def dpotrs(L, B, n=None, nrhs=None, uplo: str = "L", stream=None):
     """Solve A X = B with the Cholesky factor L of A (in place on B)."""
     bL, cL, ldL, sL = _batch_dims(L)
@@ -216,7 +239,7 @@ def dpotrs(L, B, n=None, nrhs=None, uplo: str = "L", stream=None):
     n = cL if n is None else n
     nrhs = cB if nrhs is None else nrhs
     _check("bf_dpotrs_strided_batched", bf_dpotrs_strided_batched(
-        _ch(uplo), n, nrhs, _ptr(L), ldL, sL, _ptr(B), ldB, sB, bB, _stream(stream)))
+        _ch(uplo), n, nrhs, _ptr(L), ldL, _bstride("L", bL, sL, bB), _ptr(B), ldB, sB, bB, _stream(stream)))
     return B
 
 
@@ -313,7 +336,7 @@ def dsyrk(uplo: str, trans: str, alpha: float, A, beta: float, C, n=None, k=None
     if k is None:
         k = cA if trans.upper() == "N" else ldA
     _check("bf_dsyrk_strided_batched", bf_dsyrk_strided_batched(
-        _ch(uplo), _ch(trans), n, k, alpha, _ptr(A), ldA, sA if bA > 1 else 0, beta, _ptr(C), ldC, sC, bC,
+        _ch(uplo), _ch(trans), n, k, alpha, _ptr(A), ldA, _bstride("A", bA, sA, bC), beta, _ptr(C), ldC, sC, bC,
         _stream(stream)))
     return C
 
@@ -328,7 +351,7 @@ def dsyrk_dpotrf(A, C, n=None, k=None, info=None, stream=None):
     if info is None:
         info = torch.empty(bC, dtype=torch.int32, device=C.device)
     _check("bf_dsyrk_dpotrf_strided_batched", bf_dsyrk_dpotrf_strided_batched(
-        n, k, _ptr(A), ldA, sA if bA > 1 else 0, _ptr(C), ldC, sC, _ptr(info), bC, _stream(stream)))
+        n, k, _ptr(A), ldA, _bstride("A", bA, sA, bC), _ptr(C), ldC, sC, _ptr(info), bC, _stream(stream)))
     return info
 
 
@@ -346,7 +369,7 @@ def dtrmm(side: str, uplo: str, transa: str, diag: str, alpha: float, A, B, m=No
         m = sq if m is None else m
         n = sq if n is None else n
     _check("bf_dtrmm_strided_batched", bf_dtrmm_strided_batched(
-        _ch(side), _ch(uplo), _ch(transa), _ch(diag), m, n, alpha, _ptr(A), ldA, sA if bA > 1 else 0,
+        _ch(side), _ch(uplo), _ch(transa), _ch(diag), m, n, alpha, _ptr(A), ldA, _bstride("A", bA, sA, bB),
         _ptr(B), ldB, sB, bB, _stream(stream)))
     return B
 
@@ -375,7 +398,8 @@ def dgetrs(trans: str, LU, ipiv, B, n=None, nrhs=None, stream=None):
     n = cL if n is None else n
     nrhs = cB if nrhs is None else nrhs
     _check("bf_dgetrs_strided_batched", bf_dgetrs_strided_batched(
-        _ch(trans), n, nrhs, _ptr(LU), ldL, sL, _ptr(ipiv), ipiv.shape[-1], _ptr(B), ldB, sB, bB,
+        _ch(trans), n, nrhs, _ptr(LU), ldL, _bstride("LU", bL, sL, bB), _ptr(ipiv),
+        _bstride("ipiv", ipiv.shape[0], ipiv.shape[-1], bB), _ptr(B), ldB, sB, bB,
         _stream(stream)))
     return B
 
@@ -422,6 +446,8 @@ def dsposv(A, B, X=None, n=None, nrhs=None, tol: float = 1e-12, itmax: int = 30,
     if X is None:
         X = torch.empty_like(B)
     bX, cX, ldX, sX = _batch_dims(X)
+    if bB != bA or bX != bA:
+        raise ValueError(f"A, B and X hold {bA}, {bB} and {bX} problems: one batch count expected")
     if iter is None:
         iter = torch.empty(bA, dtype=torch.int32, device=A.device)
     if info is None:

@@ -19,17 +19,23 @@ import torch
 
 from . import (_batch_dims, _ch, _check, _ptr, _stream, bf_dgemm_backward_strided_batched,
                bf_dpotrf_backward_strided_batched, bf_dtrsm_backward_strided_batched, dgemm, dpotrf,
-               dtrsm)
+               dtrfill, dtrsm)
 
 
-def _strict_upper_mask(n, device):
-    """mask[j, i] is True where i < j: the strict upper triangle in (ncols, ld) layout."""
-    return torch.tril(torch.ones(n, n, dtype=torch.bool, device=device), -1)
+def _same_batch(names, *Xs):
+    """The adjoints write one gradient matrix per problem, so every operand must hold one matrix
+    per problem: a matrix shared by the whole batch (batch count 1) would need its per-problem
+    gradients summed, which these Functions do not do.  Expand such an operand first."""
+    counts = [X.shape[0] for X in Xs]
+    if any(c != counts[0] for c in counts):
+        raise ValueError("differentiable operands must hold one matrix per problem; got batch counts "
+                         + ", ".join(f"{nm}={c}" for nm, c in zip(names, counts)))
 
 
 class Gemm(torch.autograd.Function):
     @staticmethod
     def forward(ctx, A, B, C0, transa, transb, alpha, beta, m, n, k):
+        _same_batch("ABC", A, B, C0)
         C = C0.clone(memory_format=torch.contiguous_format)
         dgemm(transa, transb, alpha, A, B, beta, C, m=m, n=n, k=k)
         ctx.save_for_backward(A, B)
@@ -68,6 +74,7 @@ class Gemm(torch.autograd.Function):
 class TriSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, A, B, side, uplo, transa, diag, alpha, m, n):
+        _same_batch("AB", A, B)
         X = B.clone(memory_format=torch.contiguous_format)
         dtrsm(side, uplo, transa, diag, alpha, A, X, m=m, n=n)
         ctx.save_for_backward(A, X)
@@ -95,7 +102,9 @@ class Cholesky(torch.autograd.Function):
     def forward(ctx, A, n):
         L = A.clone(memory_format=torch.contiguous_format)
         info = dpotrf(L, n=n)
-        L[:, :n, :n].masked_fill_(_strict_upper_mask(n, L.device), 0.0)
+        # strict upper triangle zeroed; a problem that is not positive definite becomes NaN, so
+        # that its gradient is NaN too instead of a finite but meaningless value
+        dtrfill(L, info, n=n)
         ctx.save_for_backward(L)
         ctx.n = n
         ctx.info = info

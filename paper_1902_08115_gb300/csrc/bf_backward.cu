@@ -121,6 +121,27 @@ static cudaError_t launch_scal_copy(int m, int n, double beta, MatRef X, int ldx
     return cudaGetLastError();
 }
 
+// Tidy a factored batch: the strict triangle opposite the factor (upper = 0: the strict upper
+// one) is set to zero, and every entry of the n x n of a problem whose info is nonzero is set to
+// NaN, so that a failed factorisation cannot pass on as a finite factor.  Problem index fastest.
+__global__ void __launch_bounds__(256)
+dtrfill_kernel(int n, int upper, double* A, int lda, long long stride, const int* info, long long batch) {
+    const long long per = (long long)n * n;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per * batch;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long r = e / batch;
+        const long long q = e - r * batch;
+        const int j = (int)(r / n), i = (int)(r - (long long)j * n);
+        double* a = A + q * stride + i + (long long)j * lda;
+        if (info && info[q] != 0) {
+            *a = nan;
+        } else if (upper ? i > j : i < j) {
+            *a = 0.0;
+        }
+    }
+}
+
 cudaError_t launch_dpotrf_backward(int n, MatRef L, int ldl, MatRef Lb, int ldlb, MatRef Ab, int ldab,
                                    long long batch, cudaStream_t s) {
     if (n == 0 || batch == 0) return cudaSuccess;
@@ -283,4 +304,22 @@ extern "C" int bf_dpotrf_backward_strided_batched(char uplo, int n, const double
     if (!work) return 0;
     return cstat(launch_dpotrf_backward(n, mat_strided(L, strideL), ldl, mat_strided(Lbar, strideLbar), ldlb,
                                         mat_strided(Abar, strideAbar), ldab, batch, (cudaStream_t)stream));
+}
+
+extern "C" int bf_dtrfill_strided_batched(char uplo, int n, double* A, int lda, long long strideA, const int* info,
+                                          int batch, bf_stream_t stream) {
+    if (!(cis_l(uplo) || cis_u(uplo))) return -1;
+    if (n < 0) return -2;
+    if (lda < cmax1(n)) return -4;
+    if (batch < 0) return -7;
+    if (batch > 1 && strideA < (long long)lda * n) return -5;
+    if (n == 0 || batch == 0) return 0;
+    if (!A) return -3;
+    const long long total = (long long)n * n * batch;
+    long long blocks = (total + 255) / 256;
+    if (blocks > kSMs * 32) blocks = kSMs * 32;
+    dtrfill_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(n, cis_u(uplo) ? 1 : 0, A, lda, strideA, info,
+                                                                         batch);
+    count_launch();
+    return cstat(cudaGetLastError());
 }

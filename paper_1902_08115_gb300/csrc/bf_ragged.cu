@@ -646,8 +646,14 @@ extern "C" int bf_ragged_potrf_potrs_noalloc(int batch, const int* n_host, int n
     if (smem > 227 * 1024 || (nmax > lane_max && nmax > BF_BIG_NMAX)) return BF_ERR_NOT_SUPPORTED;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return BF_ERR_CUDA;
+    // The queue goes to the device by copies from this file's host arrays, which the next call
+    // overwrites: a captured copy would replay whatever queue the latest call left there.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) return BF_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return BF_ERR_NOT_SUPPORTED;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    // set-up, once per device, with that device current
+    // set-up, once per device, with that device current (the address stays valid for the life
+    // of the device's context: after cudaDeviceReset it would be stale)
     if (!g_noalloc_ptr[dev]) {
         void* ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_ragged_noalloc_scratch) != cudaSuccess || !ptr) return BF_ERR_CUDA;

@@ -360,3 +360,48 @@ def test_derive_batch_rule():
     # ties keep the table's variant
     rows = [(b, {"cta": 1.0, "team4": 1.0, "team2": 1.0, "table": 1.0}) for b in (152, 608)]
     assert derive_batch_rule(rows) == (0, 0, 0)
+
+
+def test_dtrfill_illegal_arguments(lib):
+    f = lib.bf_dtrfill_strided_batched
+    assert f(b"X", 4, 1, 4, 16, NULL, 2, NULL) == -1
+    assert f(b"L", -1, 1, 4, 16, NULL, 2, NULL) == -2
+    assert f(b"L", 4, 1, 3, 16, NULL, 2, NULL) == -4
+    assert f(b"L", 4, 1, 4, 15, NULL, 2, NULL) == -5
+    assert f(b"L", 4, 1, 4, 16, NULL, -1, NULL) == -7
+    assert f(b"L", 4, NULL, 4, 16, NULL, 2, NULL) == -3
+    assert f(b"U", 0, NULL, 1, 0, NULL, 2, NULL) == 0
+    assert f(b"L", 4, NULL, 4, 16, NULL, 0, NULL) == 0
+
+
+def test_binding_refuses_mismatched_batch_counts(lib):
+    """An operand holds one matrix per problem or one shared by all (batch count 1); any other
+    count would make the kernels read past it, so the binding refuses before any launch."""
+    import torch
+    assert lib._bstride("A", 5, 16, 5) == 16
+    assert lib._bstride("A", 1, 16, 5) == 0
+    assert lib._bstride("A", 1, 16, 1) == 0
+    with pytest.raises(ValueError, match="expected 5 or 1"):
+        lib._bstride("A", 3, 16, 5)
+    A = torch.zeros(3, 4, 4, dtype=torch.float64)
+    C = torch.zeros(5, 4, 4, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        lib.dgemm("N", "N", 1.0, A, C, 0.0, C)
+    with pytest.raises(ValueError):
+        lib.dtrsm("L", "L", "N", "N", 1.0, A, C)
+    with pytest.raises(ValueError):
+        lib.dpotrs(A, C)
+
+
+def test_autograd_refuses_shared_operands(lib):
+    """The adjoints write one gradient per problem; a batch-1 operand shared by every problem
+    is refused up front (before the forward launches anything)."""
+    import torch
+    from paper_1902_08115_gb300.autograd import Gemm, TriSolve
+    A1 = torch.zeros(1, 4, 4, dtype=torch.float64, requires_grad=True)
+    B = torch.zeros(5, 4, 4, dtype=torch.float64, requires_grad=True)
+    C = torch.zeros(5, 4, 4, dtype=torch.float64)
+    with pytest.raises(ValueError, match="one matrix per problem"):
+        Gemm.apply(A1, B, C, "N", "N", 1.0, 1.0, 4, 4, 4)
+    with pytest.raises(ValueError, match="one matrix per problem"):
+        TriSolve.apply(A1, B, "L", "L", "N", "N", 1.0, 4, 4)

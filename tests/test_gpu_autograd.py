@@ -168,3 +168,29 @@ def test_spd_solve_gradient(bf, ag, oracle):
             fd.append((vals[0] - vals[1]) / (2 * h))
             an.append(g[which][(prob,) + idx])
     assert rel(an, fd) <= 1e-8, (an, fd)
+
+
+def test_cholesky_failure_poisons_factor_and_gradient(bf, ag):
+    """A problem that is not positive definite comes out of the forward pass as NaN, so its
+    gradient is NaN as well; the other problems of the batch keep finite, unchanged results."""
+    batch, n, bad = 6, 9, 2
+    S = bfsynth.spd_batch(batch, n, n, 31).numpy()
+    S[bad, 4, 4] = -1.0  # leading minor 5 is not positive
+    Lb = np.ascontiguousarray(np.triu(bfsynth.randn_batch(batch, n, n, n, 32).numpy()))
+    St = gpu(S).requires_grad_(True)
+    L = ag.Cholesky.apply(St, n)
+    L.backward(gpu(Lb))
+    Lh, G = host(L.detach()), host(St.grad)
+    assert np.isnan(Lh[bad]).all()
+    assert np.isnan(G[bad]).all()
+    ok = [q for q in range(batch) if q != bad]
+    assert np.isfinite(Lh[ok]).all() and np.isfinite(G[ok]).all()
+    # strict upper triangle of every good factor is zero, (j, i) layout: i < j
+    for q in ok:
+        assert not np.triu(Lh[q].T, 1).any()
+    # the good problems are the same as in a batch without the failing one
+    St2 = gpu(S[ok]).requires_grad_(True)
+    L2 = ag.Cholesky.apply(St2, n)
+    L2.backward(gpu(Lb[ok]))
+    assert normwise(host(L2.detach()), Lh[ok], n) <= 1e-13
+    assert rel(host(St2.grad), G[ok]) <= 1e-13
