@@ -58,6 +58,9 @@ typedef struct CUstream_st* bf_stream_t; /* identical to cudaStream_t */
                              /* 16-column panels)                                         */
 #define BF_VARIANT_TEAM 5    /* dpotrf only: 2 or 4 lanes of a warp per problem (p2), for */
                              /* batches between the CTA form's and the lane form's ranges */
+#define BF_VARIANT_GROUP 6   /* dpotrf only: a group of problems per CTA in shared memory, */
+                             /* the unblocked recurrence element-parallel over the group  */
+                             /* (small batches of small orders)                           */
 #define BF_TUNE_FORCE 0x100  /* or'ed into `variant`: the entry holds at every batch size; */
                              /* without it, dpotrf batches too small to fill the GPU one  */
                              /* problem per thread still switch to BF_VARIANT_CTA, to     */
@@ -475,6 +478,19 @@ int bf_probe_fp64(int blocks, int iters, double* out, bf_stream_t stream);
 /* blocks * threads doubles.                                                 */
 int bf_probe_fp64_ex(int blocks, int threads, int iters, int active, int chains, double* out,
                      bf_stream_t stream);
+/* bf_probe_kind: `blocks` CTAs of `threads` (multiple of 32) threads, every */
+/* thread running `iters` iterations of one instruction kind; out holds      */
+/* blocks * threads doubles.  Per iteration and warp:                        */
+/*   kind 0  4 FP64 tensor-core MMAs mma.sync m8n8k4 (512 flops each)        */
+/*   kind 1  4 FP64 tensor-core MMAs mma.sync m16n8k4 (1024 flops each)      */
+/*   kind 2  per thread 4 x (FP64 sqrt + one FMA)                            */
+/*   kind 3  per thread 4 x (FP64 1/x + one FMA)                             */
+/*   kind 4  per thread 4 x (FP64 rsqrt + one FMA)                           */
+/*   kind 5  per thread 16 binary32 FMAs (4x4 register tile)                 */
+/* Timed by the caller beside bf_probe_fp64_ex, it decides whether the FP64 */
+/* tensor cores beat FP64 FMA (the routines' inner kernel, section 3.2) and  */
+/* what a pivot's square root or reciprocal costs in FMA issue slots.        */
+int bf_probe_kind(int kind, int blocks, int threads, int iters, double* out, bf_stream_t stream);
 
 /* Human-readable text for a return code. */
 const char* bf_status_string(int status);

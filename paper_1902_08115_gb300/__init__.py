@@ -92,6 +92,7 @@ _SIGS = {
     "bf_launch_count": [],
     "bf_probe_fp64": [_i, _i, _vp, _vp],
     "bf_probe_fp64_ex": [_i, _i, _i, _i, _i, _vp, _vp],
+    "bf_probe_kind": [_i, _i, _i, _i, _vp, _vp],
 }
 _RES = {"bf_tune_clear": None, "bf_status_string": ctypes.c_char_p, "bf_ragged_workspace_bytes": ctypes.c_size_t,
         "bf_dsposv_workspace_bytes": ctypes.c_size_t, "bf_riccati_workspace_bytes": ctypes.c_size_t,
@@ -105,6 +106,7 @@ for _name, _args in _SIGS.items():
 
 ROUTINE_DGEMM, ROUTINE_DTRSM, ROUTINE_DPOTRF, ROUTINE_DGETRF = 0, 1, 2, 3
 VARIANT_DIRECT, VARIANT_PACKED, VARIANT_BLOCKED, VARIANT_TINY, VARIANT_CTA, VARIANT_TEAM = 0, 1, 2, 3, 4, 5
+VARIANT_GROUP = 6
 TUNE_FORCE = 0x100  # or into a variant: the table entry holds at every batch size
 ERR_CUDA, ERR_NOT_SUPPORTED, ERR_NOALLOC_LIMIT = 1001, 1002, 1003
 RAGGED_NOALLOC_MAX = 32768

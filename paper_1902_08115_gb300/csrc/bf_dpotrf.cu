@@ -102,7 +102,7 @@ cudaError_t launch_dpotrf_lane(int n, MatRef A, int lda, long long batch, int* i
     p.n = n; p.A = A; p.lda = lda; p.batch = batch; p.info = info; p.info_off = info_off; p.skip = skip;
     p.upper = upper;
     if (cfg.variant == VAR_PACKED) {
-        const int T = cfg.T;
+        const int T = cfg.T < 256 ? cfg.T : 256;
         size_t smem = sizeof(double) * (size_t)(T + 1) * n * n;
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(dpotrf_lane_packed_kernel,
@@ -114,7 +114,7 @@ cudaError_t launch_dpotrf_lane(int n, MatRef A, int lda, long long batch, int* i
         count_launch();
         return cudaGetLastError();
     }
-    const int T = cfg.T > 0 ? cfg.T : 128;
+    const int T = cfg.T > 0 ? (cfg.T < 256 ? cfg.T / 32 * 32 : 256) : 128;  // the lane kernels' launch bounds
     if (cfg.variant == VAR_TEAM) {
         const int tpp = cfg.tpp == 2 ? 2 : 4;
         const unsigned blocks = (unsigned)((batch * tpp + T - 1) / T);
@@ -141,6 +141,15 @@ cudaError_t launch_dpotrf_lane(int n, MatRef A, int lda, long long batch, int* i
 cudaError_t launch_dpotrf(int n, MatRef A, int lda, long long batch, int* info,
                           const PotrfConfig& cfg, cudaStream_t s, int upper) {
     if (batch == 0) return cudaSuccess;
+    if (cfg.variant == VAR_GROUP) {
+        if (potrf_group_smem(n, 1) <= kGroupSmemMax)  // writes every info itself
+            return launch_dpotrf_group(n, A, lda, batch, info, s, upper, cfg.T, cfg.NB);
+        PotrfConfig b = cfg;  // one problem does not fit in shared memory
+        b.variant = n > 64 ? VAR_BLOCKED : VAR_DIRECT;
+        b.T = 64;
+        b.NB = 32;
+        return launch_dpotrf(n, A, lda, batch, info, b, s, upper);
+    }
     if (info) {
         cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int) * (size_t)batch, s);
         if (e != cudaSuccess) return e;

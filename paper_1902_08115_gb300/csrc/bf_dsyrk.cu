@@ -222,7 +222,7 @@ cudaError_t launch_dsyrk_dpotrf(int n, int k, MatRef A, int lda, MatRef C, int l
     // (n <= 12: the rank-k update is latency-bound on its own); above that the coalesced
     // tile dsyrk then the lane/blocked dpotrf is faster on this GPU, since the FP64 pipe, not
     // memory, bounds both halves and the fused kernel's registers cut its occupancy
-    if (n == 0 || n > 12 || cfg.variant == VAR_BLOCKED) {
+    if (n == 0 || n > 12 || cfg.variant == VAR_BLOCKED || cfg.variant == VAR_GROUP) {
         cudaError_t e = launch_dsyrk(0, 0, n, k, 1.0, A, lda, 1.0, C, ldc, batch, s, Cin, ldcin);
         if (e != cudaSuccess) return e;
         e = launch_dpotrf(n, C, ldc, batch, info, cfg, s);
@@ -242,7 +242,7 @@ cudaError_t launch_dsyrk_dpotrf(int n, int k, MatRef A, int lda, MatRef C, int l
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    const int T = cfg.T > 0 ? cfg.T : 64;
+    const int T = cfg.T > 0 ? (cfg.T < 256 ? cfg.T : 256) : 64;
     const unsigned blocks = (unsigned)((batch + T - 1) / T);
     if (cfg.rows == 8) {
         if (cfg.unroll == 1) dsyrk_dpotrf_lane_kernel<8, 1><<<blocks, T, 0, s>>>(p);

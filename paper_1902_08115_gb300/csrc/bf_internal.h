@@ -11,7 +11,8 @@ namespace bf {
 
 // Kernel variants the size switch chooses between (section 2.4: direct 'D'
 // for very small sizes, packing variants for larger ones).
-enum Variant : int { VAR_DIRECT = 0, VAR_PACKED = 1, VAR_BLOCKED = 2, VAR_TINY = 3, VAR_CTA = 4, VAR_TEAM = 5 };
+enum Variant : int { VAR_DIRECT = 0, VAR_PACKED = 1, VAR_BLOCKED = 2, VAR_TINY = 3, VAR_CTA = 4, VAR_TEAM = 5,
+                     VAR_GROUP = 6 };
 
 struct GemmConfig {
     int variant;  // VAR_DIRECT or VAR_PACKED
@@ -173,6 +174,13 @@ GemmConfig choose_gemm(bool ta, bool tb, int m, int n, int k, int lda, long long
 TrsmConfig choose_trsm(int side, int uplo, int trans, int unit, int m, int n, long long batch);
 PotrfConfig choose_potrf(int n, int lda, long long batch);
 int choose_getrf(int n, long long batch);  // VAR_DIRECT (lane LU) or VAR_CTA
+// dpotrf of a group of problems per CTA in shared memory, element-parallel (bf_potrf_group.cu);
+// kGroupSmemMax bounds its shared memory (one group must fit: potrf_group_smem(n, 1))
+constexpr size_t kGroupSmemMax = 227 * 1024;
+size_t potrf_group_smem(int n, int P);
+int potrf_group_size(int n, long long batch, int per_sm);
+cudaError_t launch_dpotrf_group(int n, MatRef A, int lda, long long batch, int* info, cudaStream_t s, int upper,
+                                int threads, int per_sm);
 // dpotrf (lower) with one problem per CTA, n <= 256 (bf_ragged.cu)
 cudaError_t launch_dpotrf_cta(int n, MatRef A, int lda, long long batch, int* info, cudaStream_t s);
 // dpotrf 'L' of a variable-size batch (device arrays n, Aarray, lda; max_n <= BF_VBATCHED_POTRF_NMAX)

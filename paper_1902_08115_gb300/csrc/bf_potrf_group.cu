@@ -1,0 +1,338 @@
+// bf_potrf_group.cu -- dpotrf of small batches of small orders, element-parallel in shared
+// memory (section 3.1 "dpotrf": the unblocked Cholesky recurrence, right-looking).
+//
+// One CTA factors a group of P problems at a time.  The group's lower triangles are copied into
+// shared memory, problem-interleaved (slot e of problem p at S[e * PS + p]), and the right-looking
+// recurrence runs column by column with every thread taking (element, problem) units:
+//
+//   scale   l_ij = a_ij r_j                      for i > j                (P (n-1-j) units)
+//   update  a_ik -= l_ij l_kj                    for j < k <= i            (P m(m+1)/2 units)
+//   pivot   l_jj = sqrt(a_jj), r_j = 1 / l_jj of the next column, for each problem (P units)
+//
+// with a barrier after the scale and after the update.  The threads that take the next pivot
+// first finish its element (the first unit of the update) and then the pivot; the other units
+// are shared out among all threads, so the pivot's latency hides behind the update.  Why this shape on this GPU: an FP64 warp instruction holds
+// its sub-partition's FP64 pipe for about 64 cycles whatever its active mask, so a batch too
+// small to give every one of the 608 pipes a warp of whole problems (one problem per lane needs
+// ~20,000 problems) wastes either pipes (lane form) or lanes (a warp per problem).  Here a
+// phase's units fill the lanes of all the CTA's warps whatever P is, one group per SM uses all
+// four pipes of that SM, and P can be any size (4096 problems: 27 per SM on 152 SMs).  Every
+// FP64 instruction but the pivots' does one useful multiply-add; shared memory traffic, index
+// arithmetic and barriers issue beside the 64-cycle FP64 slots.
+//
+// Element slots: columns in decreasing order, rows increasing inside a column, so that
+// slot(i, k) = (n-1-k)(n-k)/2 + (i - k) and the trailing triangle of step j (columns > j) is
+// the prefix of length m(m+1)/2, m = n-1-j: an update unit's own slot is its unit index.
+//
+// info follows LAPACK: the first column whose pivot is not positive (or NaN), 1-based, else 0.
+// A failed problem keeps running on NaN; only its columns from the failing one on change,
+// which LAPACK leaves unspecified.  info is written for every problem (no reset needed).
+#include <atomic>
+
+#include "bf_internal.h"
+
+namespace bf {
+
+__device__ __forceinline__ int group_slot(int n, int i, int k) { return (n - 1 - k) * (n - k) / 2 + (i - k); }
+
+// Units u = tid, tid + NT, ... of a phase enumerate (a, b) = (u / P, u % P) without a division
+// per unit: the per-thread start and the per-step increments are fixed for the kernel.
+struct UnitStep {
+    int a0, b0, da, db, P;
+    __device__ __forceinline__ UnitStep(int tid, int NT, int P_) : P(P_) {
+        a0 = tid / P_;
+        b0 = tid - a0 * P_;
+        da = NT / P_;
+        db = NT - da * P_;
+    }
+    __device__ __forceinline__ void next(int& a, int& b) const {
+        a += da;
+        b += db;
+        if (b >= P) {
+            b -= P;
+            a++;
+        }
+    }
+};
+
+// Shared memory: S (E slots x PS, PS = P rounded up to odd so that the copies' strided accesses
+// spread over the banks), R (P reciprocal pivots), T (E slot coordinates), F (P infos).
+__host__ __device__ inline int group_stride(int P) { return P | 1; }
+
+// Pivot of column j of problem p in slot c: info on the first non-positive (or NaN) pivot,
+// l_jj = d / sqrt(d), and its reciprocal kept for the scale step.
+__device__ __forceinline__ void group_pivot(double* S, double* R, int* F, int c, int PS, int p, int j, double d) {
+    // d > 0 (not zero, negative or NaN) tested on the bits, which leaves the FP64 unit to the
+    // arithmetic: positive finite or +inf is 0 < bits <= the bits of +inf
+    const long long b = __double_as_longlong(d);
+    if (!(b > 0 && b <= 0x7ff0000000000000ll) && F[p] == 0) F[p] = j + 1;
+    const double rs = rsqrt(d);
+    S[c * PS + p] = d * rs;
+    R[p] = rs;
+}
+
+// Named barriers (id, thread count): a warp arrives without waiting, or waits for the count.
+__device__ __forceinline__ void group_bar_arrive(int id, int count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void group_bar_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Bulk update units [u, u1) of step j (stride NB, stepping state e, p carried across calls):
+// a_ik -= l_ij l_kj, slot e of problem p.  Eight units in flight per thread: every load of a
+// batch is issued before its first multiply-add, so a warp's FP64 instructions are not spaced
+// out by shared-memory latency (the FP64 unit is shared by the SM's warps; each waits its turn).
+template <int NB>
+__device__ __forceinline__ void group_bulk(double* S, const int* T, int PS, int c0, const UnitStep& bs, int& u, int u1,
+                                           int& e, int& p) {
+    for (; u + 7 * NB < u1; u += 8 * NB) {
+        int d[8], pi[8], pk[8];
+#pragma unroll
+        for (int x = 0; x < 8; x++) {
+            const int ik = T[e], i = ik >> 16, k = ik & 0xffff;
+            d[x] = e * PS + p;
+            pi[x] = (c0 + i) * PS + p;
+            pk[x] = (c0 + k) * PS + p;
+            bs.next(e, p);
+        }
+        double a[8], li[8], lk[8];
+#pragma unroll
+        for (int x = 0; x < 8; x++) {
+            a[x] = S[d[x]];
+            li[x] = S[pi[x]];
+            lk[x] = S[pk[x]];
+        }
+#pragma unroll
+        for (int x = 0; x < 8; x++) S[d[x]] = fma(-li[x], lk[x], a[x]);
+    }
+    for (; u + 3 * NB < u1; u += 4 * NB) {
+        int d[4], pi[4], pk[4];
+#pragma unroll
+        for (int x = 0; x < 4; x++) {
+            const int ik = T[e], i = ik >> 16, k = ik & 0xffff;
+            d[x] = e * PS + p;
+            pi[x] = (c0 + i) * PS + p;
+            pk[x] = (c0 + k) * PS + p;
+            bs.next(e, p);
+        }
+        double a[4], li[4], lk[4];
+#pragma unroll
+        for (int x = 0; x < 4; x++) {
+            a[x] = S[d[x]];
+            li[x] = S[pi[x]];
+            lk[x] = S[pk[x]];
+        }
+#pragma unroll
+        for (int x = 0; x < 4; x++) S[d[x]] = fma(-li[x], lk[x], a[x]);
+    }
+    for (; u < u1; u += NB) {
+        const int ik = T[e], i = ik >> 16, k = ik & 0xffff;
+        double* sd = S + e * PS + p;
+        *sd = fma(-S[(c0 + i) * PS + p], S[(c0 + k) * PS + p], *sd);
+        bs.next(e, p);
+    }
+}
+
+// Schedule on this GPU: the SM's FP64 unit takes about one warp instruction per 16 cycles, and
+// one warp issues at most one FP64 instruction per ~64 cycles, so four to five warps with FP64
+// work ready saturate it, and every further ready warp only lengthens the wait of the others.
+// The CTA is therefore NW warps (NW - 1 of them take the bulk update): enough to keep the FP64
+// unit busy, few enough that warp 0's dependent pivot chain (compare, reciprocal square root,
+// scale) is not queued behind a deep backlog.  Per step j, one barrier after the bulk update:
+//   warp 0      pivot of column j+1, then row j+2 of column j+1 (the next pivot's input)
+//   warps 1..   bulk update of the columns > j+1 by column j, then (after the pivot) rows j+3..
+//               of column j+1: update by column j and scale by the new pivot
+template <int NW, bool UP>
+__global__ void __launch_bounds__(32 * NW) dpotrf_group_kernel(int n, MatRef A, int lda, long long batch,
+                                                              int* info, int P) {
+    constexpr int NT = 32 * NW, NB = NT - 32;  // threads; bulk threads
+    extern __shared__ double sm[];
+    const int E = n * (n + 1) / 2;
+    const int PS = group_stride(P);
+    double* S = sm;
+    double* R = S + (size_t)E * PS;
+    int* T = reinterpret_cast<int*>(R + 2 * P);  // (i << 16) | k of every slot
+    int* F = T + E;
+    const int tid = threadIdx.x;
+    const bool w0 = tid < 32;
+    const int bt = tid - 32;  // rank among the bulk threads
+    for (int e = tid; e < E; e += NT) {
+        int t = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+        while ((t + 1) * (t + 2) / 2 <= e) t++;
+        while (t * (t + 1) / 2 > e) t--;
+        const int k = n - 1 - t, i = k + (e - t * (t + 1) / 2);
+        T[e] = (i << 16) | k;
+    }
+    const UnitStep bs(w0 ? 0 : bt, NB, P);  // (slot or row, problem) units of the bulk threads
+    const UnitStep ls(tid, NT, E);          // (problem, slot) units of the copies
+    const long long groups = (batch + P - 1) / P;
+    const int UC = P * E;
+    for (long long g = blockIdx.x; g < groups; g += gridDim.x) {
+        const long long q0 = g * P;
+        const int np = (int)(batch - q0 < P ? batch - q0 : P);
+        __syncthreads();  // the table is written / the previous group is stored
+        // copy in: problem-major units, so that consecutive threads read consecutive rows; eight
+        // loads in flight per thread
+        {
+            int p = ls.a0, e = ls.b0;
+            for (int u0 = tid; u0 < UC; u0 += 8 * NT) {
+                double v[8];
+                int d[8];
+#pragma unroll
+                for (int x = 0; x < 8; x++) {
+                    const bool in = u0 + x * NT < UC;
+                    const int ik = T[in ? e : 0], i = ik >> 16, k = ik & 0xffff;
+                    const bool ld = in && p < np;
+                    const double* a = A.ptr(q0 + (ld ? p : 0));
+                    v[x] = ld ? (UP ? a[k + (long long)i * lda] : a[i + (long long)k * lda]) : 0.0;
+                    d[x] = in ? e * PS + p : -1;
+                    ls.next(p, e);
+                }
+#pragma unroll
+                for (int x = 0; x < 8; x++)
+                    if (d[x] >= 0) S[d[x]] = v[x];
+            }
+        }
+        for (int p = tid; p < P; p += NT) F[p] = 0;
+        __syncthreads();
+        // column 0: pivot and row 1 (warp 0)
+        const int c00 = group_slot(n, 0, 0);
+        if (w0) {
+            for (int p = tid; p < P; p += 32) {
+                group_pivot(S, R, F, c00, PS, p, 0, S[c00 * PS + p]);
+                if (n > 1) S[(c00 + 1) * PS + p] *= R[p];
+            }
+        }
+        __syncthreads();
+        for (int j = 0; j + 1 < n; j++) {
+            const int m = n - 1 - j;
+            const int c0 = group_slot(n, j, j) - j;  // l_xj in slot c0 + x
+            const int es = (m - 1) * m / 2;         // slot of (j+1, j+1); column j+1 is es .. es+m-1
+            const double* Rj = R + (j & 1) * P;     // reciprocal pivots of column j
+            const bool row2 = j + 2 < n;            // column j has a row j+2
+            const int wrow = (P + 31) / 32;         // warps 1 .. wrow compute row j+2 of column j
+            if (w0) {
+                // pivot of column j+1, then (once row j+2 of column j is in) its row j+2
+                double* Rn = R + ((j + 1) & 1) * P;
+                for (int p = tid; p < P; p += 32) {
+                    const double l = S[(c0 + j + 1) * PS + p];
+                    group_pivot(S, Rn, F, es, PS, p, j + 1, fma(-l, l, S[es * PS + p]));
+                }
+                if (row2) {
+                    group_bar_sync(2, 32 * (1 + wrow));
+                    for (int p = tid; p < P; p += 32) {
+                        const int s = (es + 1) * PS + p;
+                        S[s] = fma(-S[(c0 + j + 2) * PS + p], S[(c0 + j + 1) * PS + p], S[s]) * Rn[p];
+                    }
+                }
+            } else {
+                // rows j+2 .. of column j: the update by column j-1 (deferred from the previous
+                // step) and the scale by r_j; row j+2 first, for warp 0
+                const int cp0 = j > 0 ? group_slot(n, j - 1, j - 1) - (j - 1) : 0;  // l_x,j-1 in slot cp0 + x
+                if (row2 && bt < 32 * wrow) {
+                    if (bt < P) {
+                        const int s = (c0 + j + 2) * PS + bt;
+                        double v = S[s];
+                        if (j > 0) v = fma(-S[(cp0 + j + 2) * PS + bt], S[(cp0 + j) * PS + bt], v);
+                        S[s] = v * Rj[bt];
+                    }
+                    group_bar_arrive(2, 32 * (1 + wrow));
+                }
+                {
+                    int r = bs.a0, q = bs.b0;
+                    for (int v = bt; v < P * (m - 2); v += NB) {
+                        const int i = j + 3 + r;
+                        const int s = (c0 + i) * PS + q;
+                        double a = S[s];
+                        if (j > 0) a = fma(-S[(cp0 + i) * PS + q], S[(cp0 + j) * PS + q], a);
+                        S[s] = a * Rj[q];
+                        bs.next(r, q);
+                    }
+                }
+                group_bar_sync(3, NB);
+                // bulk update of the columns > j+1 (slots 0 .. es-1) by column j
+                int e = bs.a0, p = bs.b0, u = bt;
+                group_bulk<NB>(S, T, PS, c0, bs, u, P * es, e, p);
+            }
+            __syncthreads();
+        }
+        // copy out: the lower triangle (upper: its transpose) of each problem, and info
+        {
+            int p = ls.a0, e = ls.b0;
+            for (int u = tid; u < UC; u += NT) {
+                if (p < np) {
+                    const int ik = T[e], i = ik >> 16, k = ik & 0xffff;
+                    double* a = A.mptr(q0 + p);
+                    (UP ? a[k + (long long)i * lda] : a[i + (long long)k * lda]) = S[e * PS + p];
+                }
+                ls.next(p, e);
+            }
+        }
+        if (info)
+            for (int p = tid; p < np; p += NT) info[q0 + p] = F[p];
+    }
+}
+
+// Problems per group at most: row j+2 of a column is one unit per bulk thread (at least 128).
+constexpr int kGroupMaxP = 128;
+
+size_t potrf_group_smem(int n, int P) {
+    const size_t E = (size_t)n * (n + 1) / 2;
+    return E * group_stride(P) * sizeof(double) + 2 * (size_t)P * sizeof(double) + E * sizeof(int) +
+           (size_t)P * sizeof(int);
+}
+
+// Problems per group: the batch spread over per_sm groups per SM, capped by shared memory.
+int potrf_group_size(int n, long long batch, int per_sm) {
+    long long P = (batch + kSMs * per_sm - 1) / (kSMs * per_sm);
+    if (P < 1) P = 1;
+    if (P > kGroupMaxP) P = kGroupMaxP;  // row j+2 of a column is one unit per bulk thread
+    while (P > 1 && potrf_group_smem(n, (int)P) > kGroupSmemMax) P--;
+    return (int)P;
+}
+
+// The kernel's dynamic shared memory limit is raised once to the bound (not on every call: the
+// attribute call is host time that a small launch would wait for).
+template <int NW, bool UP>
+static cudaError_t group_smem_limit() {
+    static std::atomic<int> done{0};
+    if (done.load(std::memory_order_acquire)) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(dpotrf_group_kernel<NW, UP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kGroupSmemMax);
+    if (e == cudaSuccess) done.store(1, std::memory_order_release);
+    return e;
+}
+
+template <int NW>
+static cudaError_t launch_group(int n, MatRef A, int lda, long long batch, int* info, cudaStream_t s, int upper,
+                                int P, size_t smem, unsigned blocks) {
+    cudaError_t e = upper ? group_smem_limit<NW, true>() : group_smem_limit<NW, false>();
+    if (e != cudaSuccess) return e;
+    if (upper) {
+        dpotrf_group_kernel<NW, true><<<blocks, 32 * NW, smem, s>>>(n, A, lda, batch, info, P);
+    } else {
+        dpotrf_group_kernel<NW, false><<<blocks, 32 * NW, smem, s>>>(n, A, lda, batch, info, P);
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+// threads: 256, 384 or 512 per CTA; per_sm: groups resident per SM that the batch is spread over (1..4)
+cudaError_t launch_dpotrf_group(int n, MatRef A, int lda, long long batch, int* info, cudaStream_t s, int upper,
+                                int threads, int per_sm) {
+    if (batch == 0 || n == 0) return cudaSuccess;
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 4) per_sm = 4;
+    const int P = potrf_group_size(n, batch, per_sm);
+    const size_t smem = potrf_group_smem(n, P);
+    if (smem > kGroupSmemMax) return cudaErrorInvalidValue;
+    const long long groups = (batch + P - 1) / P;
+    const long long cap = kSMs * 8;
+    const unsigned blocks = (unsigned)(groups < cap ? groups : cap);
+    if (threads == 384) return launch_group<12>(n, A, lda, batch, info, s, upper, P, smem, blocks);
+    if (threads == 512) return launch_group<16>(n, A, lda, batch, info, s, upper, P, smem, blocks);
+    return launch_group<8>(n, A, lda, batch, info, s, upper, P, smem, blocks);
+}
+
+}  // namespace bf

@@ -83,7 +83,94 @@ __global__ void __launch_bounds__(1024) probe_fp64_ex_kernel(double* out, int it
     out[blockIdx.x * (long long)blockDim.x + threadIdx.x] = r;
 }
 
+// Other FP64-pipe instruction kinds, each timed like the FMA probe so that their costs can be
+// put in DFMA issue slots (kinds as in bf_probe_kind of include/bfgpu.h):
+//   0, 1  FP64 tensor-core MMA (DMMA) through mma.sync, shapes m8n8k4 and m16n8k4, four
+//         independent accumulators per warp;
+//   2..4  sqrt, 1/x and rsqrt of FP64 values, each followed by one FMA (four independent
+//         chains per thread: v = fma(op(v), b, c));
+//   5     binary32 FMA in the 4x4 register-tile pattern.
+__device__ __forceinline__ void dmma_m8n8k4(double (&d)[2], double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};\n"
+                 : "+d"(d[0]), "+d"(d[1])
+                 : "d"(a), "d"(b));
+}
+
+__device__ __forceinline__ void dmma_m16n8k4(double (&d)[4], double a0, double a1, double b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k4.row.col.f64.f64.f64.f64 {%0, %1, %2, %3}, {%4, %5}, {%6}, {%0, %1, %2, %3};\n"
+        : "+d"(d[0]), "+d"(d[1]), "+d"(d[2]), "+d"(d[3])
+        : "d"(a0), "d"(a1), "d"(b));
+}
+
+__global__ void __launch_bounds__(1024) probe_kind_kernel(double* out, int iters, int kind) {
+    const double a = 0.999999 + threadIdx.x * 1e-9, b = 1.0 - blockIdx.x * 1e-12;
+    double r = 0.0;
+    if (kind == 0) {
+        double d[4][2] = {};
+        for (int it = 0; it < iters; it++) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) dmma_m8n8k4(d[u], a + u * 1e-7, b);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) r += d[u][0] + d[u][1];
+    } else if (kind == 1) {
+        double d[4][4] = {};
+        for (int it = 0; it < iters; it++) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) dmma_m16n8k4(d[u], a + u * 1e-7, a - u * 1e-7, b);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) r += d[u][0] + d[u][1] + d[u][2] + d[u][3];
+    } else if (kind >= 2 && kind <= 4) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) v[u] = 1.5 + threadIdx.x * 1e-6 + u * 1e-3;
+        const double c = 0.75, bb = 0.5;
+        for (int it = 0; it < iters; it++) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const double o = kind == 2 ? sqrt(v[u]) : kind == 3 ? 1.0 / v[u] : rsqrt(v[u]);
+                v[u] = fma(o, bb, c);  // stays in [0.75, 1.5]: no special cases
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) r += v[u];
+    } else {
+        float fa[4], fb[4], acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            fa[i] = 0.999f + threadIdx.x * 1e-7f + i * 1e-5f;
+            fb[i] = 1.0f - i * 1e-6f;
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc[i][j] = 0.0f;
+        }
+        for (int it = 0; it < iters; it++) {
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fmaf(fa[i], fb[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) r += acc[i][j];
+    }
+    out[blockIdx.x * (long long)blockDim.x + threadIdx.x] = r;
+}
+
 }  // namespace bf
+
+extern "C" int bf_probe_kind(int kind, int blocks, int threads, int iters, double* out, bf_stream_t stream) {
+    if (kind < 0 || kind > 5) return -1;
+    if (blocks <= 0) return -2;
+    if (threads <= 0 || threads > 1024 || threads % 32) return -3;
+    if (iters <= 0) return -4;
+    if (!out) return -5;
+    bf::probe_kind_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(out, iters, kind);
+    bf::count_launch();
+    return cudaGetLastError() == cudaSuccess ? BF_SUCCESS : BF_ERR_CUDA;
+}
 
 extern "C" int bf_probe_fp64_ex(int blocks, int threads, int iters, int active, int chains, double* out,
                                 bf_stream_t stream) {

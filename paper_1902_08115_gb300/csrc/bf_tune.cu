@@ -234,6 +234,27 @@ static int team_size(int n, int lda, long long batch) {
     return 0;
 }
 
+// The group form (a group of problems per CTA in shared memory, bf_potrf_group.cu) beats every
+// other form on batches up to these sizes, measured on GB300 against the switch without it
+// (GFLOP/s, back-to-back calls): n = 24 x 4,096: 454 against 272 (team of 4); n = 48 x 2,432:
+// 733 against 359 (one problem per CTA); n = 64 x 4,096: 762 against 535; n = 128 x 304: 775
+// against 592.  Above them the lane, team and blocked forms catch up (n = 24 x 16,384: 580
+// against 598).
+static long long group_batch_limit(int n) {
+    if (n < 4 || n > 192) return 0;
+    if (n < 8) return 16384;
+    if (n < 12) return 12288;
+    if (n < 24) return 16384;
+    if (n < 48) return 12288;
+    if (n < 56) return 8192;
+    if (n < 64) return 6144;
+    if (n < 96) return 4096;
+    if (n < 112) return 1216;
+    return 304;
+}
+// groups per SM: one for the smallest batches (few problems per group), three for the largest
+static int group_per_sm(long long batch) { return batch <= 1216 ? 1 : batch <= 6144 ? 2 : 3; }
+
 PotrfConfig choose_potrf(int n, int lda, long long batch) {
     // Table code 0 holds even leading dimensions, code 1 odd ones (an odd lda leaves
     // every other column's strips off the 16-byte boundary, which changes the best
@@ -279,6 +300,17 @@ PotrfConfig choose_potrf(int n, int lda, long long batch) {
                                                                 : 0;
         }
     }
+    // a measured batch rule for this order (from the autotuner) decides among its own forms
+    BatchRule rg;
+    const bool ruled = lookup_rule(code, n, &rg);
+    if (!force && !ruled && batch <= group_batch_limit(n) && potrf_group_smem(n, 1) <= kGroupSmemMax) {
+        c.variant = VAR_GROUP;
+        c.T = 384;
+        c.NB = group_per_sm(batch);
+        c.rows = 4;
+        c.unroll = 2;
+        return c;
+    }
     if (!force && batch <= cta_max) c.variant = VAR_CTA;
     if (!force && c.variant != VAR_CTA && team) {
         c.variant = VAR_TEAM;
@@ -293,6 +325,13 @@ PotrfConfig choose_potrf(int n, int lda, long long batch) {
     if (!force && c.variant == VAR_DIRECT) {
         const long long cap = batch / (2 * kSMs) / 32 * 32;
         if (c.T > cap) c.T = (int)(cap < 32 ? 32 : cap);
+    }
+    if (c.variant == VAR_GROUP) {  // p0: threads per CTA (256, 384 or 512), p1: groups per SM (1..4)
+        c.T = (c.T == 384 || c.T == 512) ? c.T : 256;
+        c.NB = (c.NB >= 1 && c.NB <= 4) ? c.NB : 2;
+        c.rows = 4;
+        c.unroll = 2;
+        return c;
     }
     if (c.T < 32) c.T = 32;
     if (c.T > 256) c.T = 256;
@@ -331,7 +370,7 @@ extern "C" int bf_tune_set(int routine, int code, int n_lo, int n_hi, int varian
     if (n_lo > n_hi) return -3;
     const bool force = (variant & BF_TUNE_FORCE) != 0;
     variant &= ~BF_TUNE_FORCE;
-    if (variant < 0 || variant > 5) return -5;
+    if (variant < 0 || variant > 6) return -5;
     std::lock_guard<std::mutex> lk(bf::g_mu);
     bf::g_table.push_back(bf::TuneEntry{routine, code, n_lo, n_hi, variant, p0, p1, p2, p3, force});
     return 0;

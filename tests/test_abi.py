@@ -155,27 +155,30 @@ def test_tune_table(lib):
         # dpotrf codes are the leading-dimension parity: an odd-lda entry leaves even lda alone
         lib.tune_set(lib.ROUTINE_DPOTRF, 1, 1, 300, lib.VARIANT_DIRECT, 64, 0, 8, 1)
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10 ** 5) == [lib.VARIANT_DIRECT, 64, 32, 8, 1]
-        # a lane kernel needs tens of thousands of problems: batches too small to fill the GPU
-        # go to one problem per CTA (n >= 16), the rest of the small batches of n > 64 to the
-        # blocked sequence
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10)[0] == lib.VARIANT_CTA
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 100, 100, 0, 10)[0] == lib.VARIANT_CTA
+        # a lane kernel needs tens of thousands of problems: small batches of orders 4..192 go
+        # to the group form (p0 = 384 threads, p1 = groups per SM), larger ones of n > 64 to
+        # the blocked sequence
+        G6 = lib.VARIANT_GROUP
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10)[:3] == [G6, 384, 1]
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 100, 100, 0, 10)[0] == G6
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10 ** 4)[0] == lib.VARIANT_BLOCKED
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 1500)[0] == lib.VARIANT_CTA
-        # between the CTA and lane ranges, teams of 4 then 2 lanes per problem (12 <= n <= 64)
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 4096)[:4] == [lib.VARIANT_TEAM, 64, 32, 4]
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 10 ** 4)[:4] == [lib.VARIANT_TEAM, 64, 32, 2]
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 1500)[:3] == [G6, 384, 2]
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 4096)[:3] == [G6, 384, 2]
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 10 ** 4)[:3] == [G6, 384, 3]
+        # past the group form's range, teams of 2 lanes per problem, then one problem per lane
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 14000)[:4] == [lib.VARIANT_TEAM, 64, 32, 2]
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 10 ** 5)[0] == lib.VARIANT_DIRECT
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 8, 8, 0, 4096)[0] == lib.VARIANT_DIRECT
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 8, 8, 0, 4096)[0] == G6
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 100, 100, 0, 4096)[0] != lib.VARIANT_TEAM
-        # a lane kernel on a small batch keeps two CTAs per SM: 9,728 problems -> 32 threads
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 8, 8, 0, 9728)[1] == 32
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 8, 8, 0, 10)[0] == lib.VARIANT_DIRECT
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 200, 200, 0, 10)[0] == lib.VARIANT_CTA
+        # a lane kernel on a small batch keeps two CTAs per SM: 13,000 problems -> 32 threads
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 8, 8, 0, 13000)[:2] == [lib.VARIANT_DIRECT, 32]
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 2, 2, 0, 10)[0] == lib.VARIANT_DIRECT
         # a forced entry holds at every batch size
         lib.tune_set(lib.ROUTINE_DPOTRF, 1, 90, 110, lib.VARIANT_DIRECT | lib.TUNE_FORCE, 64, 0, 8, 1)
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10) == [lib.VARIANT_DIRECT, 64, 32, 8, 1]
         with pytest.raises(lib.BFError):
-            lib.tune_set(lib.ROUTINE_DPOTRF, 1, 90, 110, 6)
+            lib.tune_set(lib.ROUTINE_DPOTRF, 1, 90, 110, 7)
         # the team form: p2 is the team size (2 or 4; anything else is 4)
         lib.tune_set(lib.ROUTINE_DPOTRF, 0, 20, 30, lib.VARIANT_TEAM | lib.TUNE_FORCE, 128, 0, 2, 0)
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 24, 24, 0, 10 ** 5)[:4] == [lib.VARIANT_TEAM, 128, 32, 2]
@@ -276,12 +279,14 @@ def test_vbatched_illegal_call_arguments(lib):
 
 def test_dpotrf_batch_switch_is_ordered(lib):
     """The built-in batch-size switch (no table entries): for every order, growing batches move
-    from one problem per CTA to teams of 4, then 2 lanes per problem, then one problem per lane
-    (or, above order 64, the blocked sequence), and never back; the team form covers only
-    orders 12..64, and one problem per CTA only orders 16..256."""
+    from the group form to one problem per CTA, to teams of 4, then 2 lanes per problem, then one
+    problem per lane (or, above order 64, the blocked sequence), and never back; the group form
+    covers only orders 4..192, the team form only orders 12..64, and one problem per CTA only
+    orders 16..256."""
     lib.tune_clear()
     try:
-        stage = {lib.VARIANT_CTA: 0, lib.VARIANT_TEAM: 1, lib.VARIANT_DIRECT: 3, lib.VARIANT_BLOCKED: 3}
+        stage = {lib.VARIANT_GROUP: -1, lib.VARIANT_CTA: 0, lib.VARIANT_TEAM: 1, lib.VARIANT_DIRECT: 3,
+                 lib.VARIANT_BLOCKED: 3}
         batches = [1, 100, 600, 1000, 1500, 2000, 3000, 4096, 6144, 9728, 12288, 14592, 19456, 21000,
                    29127, 40000, 10 ** 5, 10 ** 6]
         for n in list(range(1, 70)) + [96, 128, 192, 256, 300]:
@@ -296,6 +301,9 @@ def test_dpotrf_batch_switch_is_ordered(lib):
                         assert 12 <= n <= 64 and p2 in (2, 4) and T == 64
                     if v == lib.VARIANT_CTA:
                         assert 16 <= n <= 256
+                    if v == lib.VARIANT_GROUP:
+                        assert 4 <= n <= 192 and T == 384
+                        continue
                     assert T % 32 == 0 and 32 <= T <= 256
     finally:
         lib.tune_clear()
@@ -313,7 +321,8 @@ def test_batch_rules(lib, tmp_path):
         assert q(0, 24, 101)[:4] == [lib.VARIANT_TEAM, 64, 32, 4]
         assert q(1, 24, 5000)[:4] == [lib.VARIANT_TEAM, 64, 32, 2]
         assert q(0, 24, 5001)[0] == lib.VARIANT_DIRECT
-        assert q(0, 32, 5001)[0] == lib.VARIANT_TEAM  # outside the rule: built-in bounds
+        assert q(0, 32, 5001)[0] == lib.VARIANT_GROUP  # outside the rule: built-in bounds
+        assert q(0, 32, 14000)[0] == lib.VARIANT_TEAM
         # only the lda-parity named; a negative cta bound keeps the built-in one (896 at n = 24)
         lib.tune_set_batch_rule(lib.ROUTINE_DPOTRF, 1, 24, 24, -1, 0, -1)
         assert q(1, 24, 896)[0] == lib.VARIANT_CTA
@@ -323,7 +332,7 @@ def test_batch_rules(lib, tmp_path):
         lib.tune_set(lib.ROUTINE_DPOTRF, -1, 20, 30, lib.VARIANT_DIRECT | lib.TUNE_FORCE, 64, 0, 8, 2)
         assert q(0, 24, 50)[0] == lib.VARIANT_DIRECT
         lib.tune_clear()
-        assert q(0, 24, 50)[0] == lib.VARIANT_CTA and q(0, 24, 101)[0] == lib.VARIANT_CTA
+        assert q(0, 24, 50)[0] == lib.VARIANT_GROUP and q(0, 24, 101)[0] == lib.VARIANT_GROUP
         with pytest.raises(lib.BFError) as e:
             lib.tune_set_batch_rule(lib.ROUTINE_DGEMM, 0, 1, 2, 0, 0, 0)
         assert e.value.status == -1

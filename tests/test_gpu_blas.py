@@ -207,7 +207,7 @@ def spd_upper_nan(batch, n, ld, seed):
 POTRF_VARIANTS = [("direct4u2", 0, 0, 0, 4, 2), ("direct4u1", 0, 64, 0, 4, 1), ("direct8u1", 0, 0, 0, 8, 1),
                   ("direct8u2", 0, 256, 0, 8, 2), ("packed", 1, 128, 0, 0, 0), ("blocked8", 2, 0, 8, 0, 0),
                   ("blocked32", 2, 0, 32, 0, 0), ("cta", 4, 0, 0, 0, 0), ("team2", 5, 0, 0, 2, 0),
-                  ("team4", 5, 128, 0, 4, 0)]
+                  ("team4", 5, 128, 0, 4, 0), ("group", 6, 0, 0, 0, 0)]
 
 
 @pytest.mark.parametrize("vname,variant,T,NB,R,U", POTRF_VARIANTS, ids=[v[0] for v in POTRF_VARIANTS])
@@ -268,6 +268,33 @@ def test_dpotrf_size_switch_batches(bf, oracle):
             L, _ = oracle.dpotrf_l(S)
             out = host(Sg[sel])
             assert normwise(lower_part(out, n), lower_part(L, n), n) <= TOL, (n, batch, pad)
+
+
+@pytest.mark.parametrize("n,batch", [(24, 4096), (24, 4097), (13, 1), (32, 7001), (5, 20000), (64, 20000)])
+def test_dpotrf_group_batches(bf, oracle, n, batch):
+    """The group form (problems per CTA in shared memory) on the batch sizes it is made for, with
+    groups of up to the shared-memory bound, a ragged last group and, at n = 64 x 20000, more
+    groups than CTAs (the CTAs loop over groups); failures planted in the middle of groups.
+    Sampled problems (and every failing one) against the oracle; every info checked."""
+    for pad in (0, 3):
+        Sg = bfsynth.spd_batch(batch, n, n + pad, 800 + n + pad, device="cuda")
+        bad = sorted({min(batch - 1, 3), batch // 2, batch - 1}) if batch > 1 else []
+        for i, q in enumerate(bad):
+            j = (i * 7) % n
+            Sg[q, j, j] = -1.0 if i % 2 else float("nan")
+        idx = np.unique(np.r_[0, batch - 1, bad, np.random.default_rng(n).integers(0, batch, 8)]).astype(np.int64)
+        sel = torch.as_tensor(idx, device="cuda")
+        S = host(Sg[sel])
+        with forced(bf, bf.ROUTINE_DPOTRF, -1, bf.VARIANT_GROUP):
+            ig = bf.dpotrf(Sg, n=n)
+        L, info = oracle.dpotrf_l(S)
+        gi = host(ig)
+        np.testing.assert_array_equal(gi[idx], info)
+        assert (np.delete(gi, bad) == 0).all()
+        ok = info == 0
+        out = host(Sg[sel])
+        assert normwise(lower_part(out[ok], n), lower_part(L[ok], n), n) <= TOL, (n, batch, pad)
+        assert np.array_equal(out[:, :, n:], S[:, :, n:], equal_nan=True)  # padding untouched
 
 
 def test_dpotrs(bf, oracle):

@@ -255,7 +255,7 @@ def test_dtrmm_integer_bit_exact_and_alpha_zero(bf, oracle, side):
 POTRF_U = [("direct4", 0, 64, 0, 4, 2), ("direct8", 0, 64, 0, 8, 2), ("packed", 1, 64, 0, 0, 0),
            ("blocked8", 2, 0, 8, 0, 0), ("blocked32", 2, 0, 32, 0, 0),
            ("cta_falls_back", 4, 0, 0, 0, 0),  # one problem per CTA is lower only
-           ("team2", 5, 64, 0, 2, 0), ("team4", 5, 0, 0, 4, 0)]
+           ("team2", 5, 64, 0, 2, 0), ("team4", 5, 0, 0, 4, 0), ("group", 6, 0, 0, 0, 0)]
 
 
 @pytest.mark.parametrize("vname,variant,T,NB,R,U", POTRF_U, ids=[v[0] for v in POTRF_U])
