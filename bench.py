@@ -528,6 +528,10 @@ def _sub_ms(bf, torch, p, r, b, flush=None, reps=10):
         prep()
         if flush is not None:
             flush.fill_(rep & 0x7F)
+        # a GPU-side wait of ~50 us ahead of the timed call: its launch is enqueued while the GPU
+        # is still busy, so the events time the call on the device, not the host's enqueue
+        # latency (about 12 us through the Python binding) that an idle GPU would wait for
+        torch.cuda._sleep(100000)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()

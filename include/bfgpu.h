@@ -487,6 +487,8 @@ int bf_probe_fp64_ex(int blocks, int threads, int iters, int active, int chains,
 /*   kind 3  per thread 4 x (FP64 1/x + one FMA)                             */
 /*   kind 4  per thread 4 x (FP64 rsqrt + one FMA)                           */
 /*   kind 5  per thread 16 binary32 FMAs (4x4 register tile)                 */
+/*   kind 6  per thread 16 FP64 FMAs (4x4 tile), only in the warps whose     */
+/*           index in the CTA is a multiple of 4 (the others exit at once)   */
 /* Timed by the caller beside bf_probe_fp64_ex, it decides whether the FP64 */
 /* tensor cores beat FP64 FMA (the routines' inner kernel, section 3.2) and  */
 /* what a pivot's square root or reciprocal costs in FMA issue slots.        */

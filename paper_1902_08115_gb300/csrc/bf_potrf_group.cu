@@ -3,22 +3,22 @@
 //
 // One CTA factors a group of P problems at a time.  The group's lower triangles are copied into
 // shared memory, problem-interleaved (slot e of problem p at S[e * PS + p]), and the right-looking
-// recurrence runs column by column with every thread taking (element, problem) units:
+// recurrence runs column by column, every FP64 operation a unit (element, problem):
 //
-//   scale   l_ij = a_ij r_j                      for i > j                (P (n-1-j) units)
-//   update  a_ik -= l_ij l_kj                    for j < k <= i            (P m(m+1)/2 units)
-//   pivot   l_jj = sqrt(a_jj), r_j = 1 / l_jj of the next column, for each problem (P units)
+//   pivot   l_jj = sqrt(a_jj), r_j = 1 / l_jj                               (P units)
+//   scale   l_ij = (a_ij - l_i,j-1 l_j,j-1) r_j     for i > j               (P (n-1-j) units)
+//   update  a_ik -= l_ij l_kj                        for j+1 < k <= i        (P m(m-1)/2 units)
 //
-// with a barrier after the scale and after the update.  The threads that take the next pivot
-// first finish its element (the first unit of the update) and then the pivot; the other units
-// are shared out among all threads, so the pivot's latency hides behind the update.  Why this shape on this GPU: an FP64 warp instruction holds
-// its sub-partition's FP64 pipe for about 64 cycles whatever its active mask, so a batch too
-// small to give every one of the 608 pipes a warp of whole problems (one problem per lane needs
-// ~20,000 problems) wastes either pipes (lane form) or lanes (a warp per problem).  Here a
-// phase's units fill the lanes of all the CTA's warps whatever P is, one group per SM uses all
-// four pipes of that SM, and P can be any size (4096 problems: 27 per SM on 152 SMs).  Every
-// FP64 instruction but the pivots' does one useful multiply-add; shared memory traffic, index
-// arithmetic and barriers issue beside the 64-cycle FP64 slots.
+// (the update of column j+1 by column j is folded into its scale step of the next column).
+// Why this shape on this GPU (measured with the library's FP64 probes): the SM's FP64 unit
+// takes about one warp instruction per 16 cycles whatever the instruction's active lanes, and
+// one warp issues at most one FP64 instruction per 64 cycles.  A batch too small to give every
+// SM several warps of whole problems (one problem per lane needs ~20,000 problems) therefore
+// leaves FP64 units idle in the lane form and wastes lanes in forms with a warp per problem.
+// Here the units of a step fill the lanes of the CTA's warps whatever P is, and P can be any
+// size (4096 problems: 27 per SM on 152 SMs, or 14 in each of two groups per SM).  Every FP64
+// instruction but the pivots' does useful arithmetic; shared-memory traffic, index arithmetic
+// and barriers issue beside the FP64 instructions.
 //
 // Element slots: columns in decreasing order, rows increasing inside a column, so that
 // slot(i, k) = (n-1-k)(n-k)/2 + (i - k) and the trailing triangle of step j (columns > j) is
@@ -56,7 +56,7 @@ struct UnitStep {
 };
 
 // Shared memory: S (E slots x PS, PS = P rounded up to odd so that the copies' strided accesses
-// spread over the banks), R (P reciprocal pivots), T (E slot coordinates), F (P infos).
+// spread over the banks), R (2 x P reciprocal pivots), T (E slot coordinates), F (P infos).
 __host__ __device__ inline int group_stride(int P) { return P | 1; }
 
 // Pivot of column j of problem p in slot c: info on the first non-positive (or NaN) pivot,
@@ -134,15 +134,17 @@ __device__ __forceinline__ void group_bulk(double* S, const int* T, int PS, int 
     }
 }
 
-// Schedule on this GPU: the SM's FP64 unit takes about one warp instruction per 16 cycles, and
-// one warp issues at most one FP64 instruction per ~64 cycles, so four to five warps with FP64
-// work ready saturate it, and every further ready warp only lengthens the wait of the others.
-// The CTA is therefore NW warps (NW - 1 of them take the bulk update): enough to keep the FP64
-// unit busy, few enough that warp 0's dependent pivot chain (compare, reciprocal square root,
-// scale) is not queued behind a deep backlog.  Per step j, one barrier after the bulk update:
-//   warp 0      pivot of column j+1, then row j+2 of column j+1 (the next pivot's input)
-//   warps 1..   bulk update of the columns > j+1 by column j, then (after the pivot) rows j+3..
-//               of column j+1: update by column j and scale by the new pivot
+// Schedule: the serial chain of the recurrence (pivot, then the next column's first row, then
+// the next pivot ...) is carried by warp 0 alone; warps 1.. carry the rest.  Invariant at the
+// start of step j: columns < j final; column j has its pivot and row j+1; its rows j+2.. still
+// lack the update by column j-1 and the scale; the columns > j are updated by columns < j.
+//   warp 0      pivot of column j+1, then (after warps 1.. have row j+2 of column j) row j+2 of
+//               column j+1
+//   warps 1..   rows j+2.. of column j (update by column j-1, scale by r_j; row j+2 first, for
+//               warp 0), a barrier among themselves, then the update of the columns > j+1 by
+//               column j
+// and one CTA barrier per step.  The reciprocal pivots of consecutive columns alternate between
+// two arrays, since warp 0 writes r_j+1 while the others still scale by r_j.
 template <int NW, bool UP>
 __global__ void __launch_bounds__(32 * NW) dpotrf_group_kernel(int n, MatRef A, int lda, long long batch,
                                                               int* info, int P) {

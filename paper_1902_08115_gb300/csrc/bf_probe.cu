@@ -89,7 +89,10 @@ __global__ void __launch_bounds__(1024) probe_fp64_ex_kernel(double* out, int it
 //         independent accumulators per warp;
 //   2..4  sqrt, 1/x and rsqrt of FP64 values, each followed by one FMA (four independent
 //         chains per thread: v = fma(op(v), b, c));
-//   5     binary32 FMA in the 4x4 register-tile pattern.
+//   5     binary32 FMA in the 4x4 register-tile pattern;
+//   6     FP64 FMA in the 4x4 register-tile pattern, but only the warps whose index in the CTA is
+//         a multiple of 4 issue (the others exit): with 16-warp CTAs, 4 busy warps that share
+//         one SM sub-partition if warps are dealt to sub-partitions by index modulo 4.
 __device__ __forceinline__ void dmma_m8n8k4(double (&d)[2], double a, double b) {
     asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};\n"
                  : "+d"(d[0]), "+d"(d[1])
@@ -136,6 +139,26 @@ __global__ void __launch_bounds__(1024) probe_kind_kernel(double* out, int iters
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) r += v[u];
+    } else if (kind == 6) {
+        if ((threadIdx.x >> 5) & 3) return;
+        double ta[4], tb[4], acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            ta[i] = a + i * 1e-7;
+            tb[i] = b - i * 1e-8;
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+        }
+        for (int it = 0; it < iters; it++) {
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fma(ta[i], tb[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) r += acc[i][j];
     } else {
         float fa[4], fb[4], acc[4][4];
 #pragma unroll
@@ -162,7 +185,7 @@ __global__ void __launch_bounds__(1024) probe_kind_kernel(double* out, int iters
 }  // namespace bf
 
 extern "C" int bf_probe_kind(int kind, int blocks, int threads, int iters, double* out, bf_stream_t stream) {
-    if (kind < 0 || kind > 5) return -1;
+    if (kind < 0 || kind > 6) return -1;
     if (blocks <= 0) return -2;
     if (threads <= 0 || threads > 1024 || threads % 32) return -3;
     if (iters <= 0) return -4;

@@ -63,6 +63,10 @@ def measure():
         res[f"tile_{a}_active_lanes"] = rate(sms * 2, 128, 2048, active=a)
     for w in (1, 2, 4, 8):
         res[f"tile_{w}_warps_per_sm"] = rate(sms, 32 * w, 2048)
+    # one FP64 unit per SM or per sub-partition: 4 busy warps of a 16-warp CTA (indices 0, 4, 8,
+    # 12: one sub-partition if warps are dealt by index modulo 4) against 4 warps per SM above
+    t = kind_seconds(6, sms, 512, 2048)
+    res["tile_4_warps_one_subpartition"] = round(2.0 * 16 * 2048 * sms * 4 * 32 / t / 1e12, 4)
     # FP64 tensor cores: 4 MMAs per iteration and warp, at 4 and 8 warps per SM
     for kind, name, flops_per_mma in ((0, "dmma_m8n8k4", 512), (1, "dmma_m16n8k4", 1024)):
         for w in (4, 8):
