@@ -257,15 +257,23 @@ def _oracle_inputs(r, n, ld, k, seed):
     return _SAMPLES[key]
 
 
-def oracle_sample(budget_s: float, steps: int = 1):
+# The oracle's sample: one fixed set of problems per sweep point and routine, sized for about
+# ORACLE_SAMPLE_S seconds of CPU work on 16 cores; the CPU baseline of the GPU arm and every step
+# of the reference arm time this same sample, so their rates compare.
+ORACLE_SAMPLE_S = 6.0
+
+
+def oracle_sample(budget_s: float = ORACLE_SAMPLE_S, steps: int = 1):
     """Time the CPU oracle on a bounded sample of every sweep point; returns (GFLOP/s, desc, cores).
 
-    Only the oracle calls are timed; the sample inputs are generated once per process."""
+    Only the oracle calls are timed; the sample inputs are generated once per process.  The
+    sample's problem counts depend on budget_s alone (not on the host), so equal budgets time
+    equal samples."""
     import oracle
     oracle.build()
     cores = oracle.num_threads()
     per_call = budget_s / (len(SWEEP_N) * len(PADS) * len(ROUTINES))
-    est_rate = 0.5e9 * cores  # plain loops, binary64, no vectorisation
+    est_rate = 0.5e9 * 16  # plain loops, binary64, no vectorisation, 16 cores
     tot_flops, tot_time, nprob = 0.0, 0.0, 0
     for _ in range(steps):
         for n in SWEEP_N:
@@ -285,9 +293,9 @@ def oracle_sample(budget_s: float, steps: int = 1):
                     tot_time += time.perf_counter() - t0
                     tot_flops += k * flops(r, n)
                     nprob += k
-    desc = (f"oracle (plain C, binary64, OpenMP over problems) on {nprob} problems: a bounded "
-            f"sample of every sweep point and routine, ~{budget_s:.0f} s of CPU work per step "
-            f"(inputs built once, outside the timing)")
+    desc = (f"oracle (plain C, binary64, OpenMP over problems) on {nprob} problems: a fixed bounded "
+            f"sample of every sweep point and routine (the same in both arms), ~{budget_s:.0f} s of "
+            f"CPU work per pass on 16 cores (inputs built once, outside the timing)")
     return tot_flops / tot_time / 1e9, desc, cores
 
 
@@ -298,7 +306,6 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-extras", action="store_true", help="skip forms, e2e and CPU baseline")
     args = ap.parse_args()
 
@@ -430,11 +437,14 @@ def main():
         result["forms"] = plain_forms(bf, torch, points, peak, hbm)
         result["hot"] = hot_forms(bf, torch, points)
         result["e2e"] = end_to_end(bf, torch, dev, points)
+        result["config"]["e2e_workload"] = ("the sweep's routines and points with batches capped at 32 MiB of "
+                                            "operands each (pinned host memory), inputs copied in and results "
+                                            "read back every step; not the 2 GiB batches of `value`")
         del points
         torch.cuda.empty_cache()
         result["ragged"] = ragged_form(bf, torch, dev, rank)
         torch.cuda.empty_cache()
-        result["diff"] = diff_form(bf, torch, dev, rank)
+        result["diff"] = diff_form(bf, torch, dev, rank, peak)
         torch.cuda.empty_cache()
         result["precision"] = precision_form(bf, torch, dev, rank)
         torch.cuda.empty_cache()
@@ -443,7 +453,7 @@ def main():
         result["vbatched"] = vbatched_form(bf, torch, dev, peak)
         torch.cuda.empty_cache()
         if rank == 0:
-            v, desc, cores = oracle_sample(args.cpu_budget)
+            v, desc, cores = oracle_sample()
             result["cpu_baseline"] = {"value": round(v, 3), "unit": "GFLOP/s", "cores": cores,
                                       "kind": "oracle", "sample": desc}
     if rank == 0:
@@ -678,6 +688,7 @@ def ragged_form(bf, torch, dev, rank, count=200000, nrhs=4):
 
     t_graph = _events_ms(torch, plan.launch, reps=3, before=restore)
     ok_graph = int((plan.info != 0).sum()) == 0
+    err_graph = _ragged_sample_error(ns, S0, offS.numpy(), B0, offB.numpy(), S, B, nrhs)
     # plain per-size launches: one pointer-array dpotrf and two dtrsm per distinct order
     groups = []
     sbase, bbase = S.data_ptr(), B.data_ptr()
@@ -701,15 +712,49 @@ def ragged_form(bf, torch, dev, rank, count=200000, nrhs=4):
 
     t_sizes = _events_ms(torch, per_size, reps=3, before=restore)
     ok_sizes = all(int((g[4] != 0).sum()) == 0 for g in groups)
+    err_sizes = _ragged_sample_error(ns, S0, offS.numpy(), B0, offB.numpy(), S, B, nrhs)
     return {"problems": count, "nrhs": nrhs, "orders": "log-uniform in [2, 200]",
             "S_bytes": int(S0.numel() * 8), "gflop": round(flops / 1e9, 3),
             "persistent_graph_ms": round(t_graph, 3), "persistent_gflops": round(flops / t_graph / 1e6, 2),
             "per_size_launches_ms": round(t_sizes, 3), "per_size_gflops": round(flops / t_sizes / 1e6, 2),
             "speedup": round(t_sizes / t_graph, 3), "distinct_orders": len(groups), "plan": plan.describe(),
-            "config": cfg, "all_info_zero": bool(ok_graph and ok_sizes)}
+            "config": cfg, "all_info_zero": bool(ok_graph and ok_sizes),
+            "max_normwise_error_vs_oracle": {"persistent": err_graph, "per_size": err_sizes,
+                                             "sample": "256 problems (seeded, with the first and last), L and X"}}
 
 
-def diff_form(bf, torch, dev, rank, batch=65536, n=32, q=16, r=8):
+def _ragged_sample_error(ns, S0, offS, B0, offB, S, B, nrhs, k=256):
+    """Max normwise relative error of L and X against the oracle on a seeded sample of problems
+    (computed after the timing; the oracle runs on the host)."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(12)
+    idx = np.unique(np.r_[0, len(ns) - 1, rng.integers(0, len(ns), k)]).astype(np.int64)
+    sub_n = ns[idx].astype(np.int32)
+    offs_s = np.zeros(len(idx), dtype=np.int64)
+    offs_b = np.zeros(len(idx), dtype=np.int64)
+    offs_s[1:] = np.cumsum(sub_n[:-1].astype(np.int64) ** 2)
+    offs_b[1:] = np.cumsum(sub_n[:-1].astype(np.int64) * nrhs)
+    S0h, B0h, Sh, Bh = (t.cpu().numpy() for t in (S0, B0, S, B))
+    Sin = np.concatenate([S0h[offS[b]:offS[b] + int(ns[b]) ** 2] for b in idx])
+    Bin = np.concatenate([B0h[offB[b]:offB[b] + int(ns[b]) * nrhs] for b in idx])
+    So, Xo, info = oracle.ragged_potrf_potrs(sub_n, Sin, offs_s, Bin, offs_b, nrhs)
+    worst = 0.0
+    for t, b in enumerate(idx):
+        n = int(ns[b])
+        if info[t]:
+            continue
+        Lg = np.tril(Sh[offS[b]:offS[b] + n * n].reshape(n, n).T)
+        Lr = np.tril(So[offs_s[t]:offs_s[t] + n * n].reshape(n, n).T)
+        xg = Bh[offB[b]:offB[b] + n * nrhs]
+        xr = Xo[offs_b[t]:offs_b[t] + n * nrhs]
+        worst = max(worst, float(np.linalg.norm(Lg - Lr) / np.linalg.norm(Lr)),
+                    float(np.linalg.norm(xg - xr) / np.linalg.norm(xr)))
+    return worst
+
+
+def diff_form(bf, torch, dev, rank, peak=None, batch=65536, n=32, q=16, r=8):
     """Differentiation workload: loss = sum((Q + J J^T)^{-1} B .* W) through the autograd
     Functions; forward, forward + backward, and the plain forward calls without autograd."""
     import bfsynth
@@ -742,10 +787,32 @@ def diff_form(bf, torch, dev, rank, batch=65536, n=32, q=16, r=8):
     t_fb = _events_ms(torch, fwd_bwd)
     t_p = _events_ms(torch, plain)
     flops_f = batch * (2.0 * n * n * q + n ** 3 / 3 + n * n / 2 + n / 6 + 2.0 * 2 * n * n * r)
+    # the adjoints' algorithmic flops per problem: two triangular-solve adjoints (solve n^2 r,
+    # lower-triangle gradient n(n+1) r), the Cholesky adjoint (Phi(L^T Lbar) n^3/3, two n x n
+    # triangular solves 2 n^3), the dgemm adjoint (both operands, 2 x 2 n^2 q)
+    flops_b = batch * (2.0 * (n * n * r + n * (n + 1) * r) + n ** 3 / 3 + 2.0 * n ** 3 + 4.0 * n * n * q)
+    t_b = t_fb - t_f
+    # gradient accuracy: the last fwd_bwd's gradients against the oracle's closed form, sampled
+    import numpy as np
+
+    import oracle
+    idx = np.unique(np.r_[0, batch - 1, np.random.default_rng(13).integers(0, batch, 256)]).astype(np.int64)
+    sel = torch.as_tensor(idx, device=dev)
+    ref = oracle.spd_solve_loss_grad(*(x[sel].cpu().numpy() for x in (Qd, J, B, W)))
+    worst = 0.0
+    for t, key in zip(ts, ("Qbar", "Jbar", "Bbar", "Wbar")):
+        g = t.grad[sel].cpu().numpy().reshape(len(idx), -1)
+        rr = ref[key].reshape(len(idx), -1)
+        worst = max(worst, float(np.max(np.linalg.norm(g - rr, axis=1) / np.linalg.norm(rr, axis=1))))
     return {"batch": batch, "n": n, "q": q, "r": r, "forward_ms": round(t_f, 3),
             "forward_backward_ms": round(t_fb, 3), "plain_forward_ms": round(t_p, 3),
-            "backward_over_forward": round((t_fb - t_f) / t_f, 3),
-            "forward_gflops": round(flops_f / t_f / 1e6, 2)}
+            "backward_over_forward": round(t_b / t_f, 3),
+            "forward_gflops": round(flops_f / t_f / 1e6, 2),
+            "backward_gflop": round(flops_b / 1e9, 3), "backward_gflops": round(flops_b / t_b / 1e6, 2),
+            "backward_frac_of_fp64_peak": round(flops_b / (t_b * 1e-3) / peak, 4) if peak else None,
+            "max_gradient_error_vs_oracle": worst,
+            "gradient_sample": "256 problems (seeded, with the first and last), per-problem normwise "
+                               "relative error of Qbar, Jbar, Bbar, Wbar against the closed form"}
 
 
 def precision_form(bf, torch, dev, rank, batch=16384, n=128):
@@ -962,12 +1029,12 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_sample(min(2.0, args.cpu_budget))
+        oracle_sample()
     t = []
     rates = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        v, desc, cores = oracle_sample(args.cpu_budget / 2)
+        v, desc, cores = oracle_sample()
         t.append(time.perf_counter() - t0)
         rates.append(v)
     v = statistics.mean(rates)

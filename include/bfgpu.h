@@ -277,8 +277,10 @@ int bf_dpotrs_strided_batched(char uplo, int n, int nrhs, const double* A, int l
 /* dsposv (LAPACK's name for the mixed-precision SPD solve; the routines it */
 /* runs are the paper's dpotrf and dtrsm, section 3.1, in binary32): solve   */
 /* A X = B for SPD A (uplo 'L': lower triangle referenced, A not modified).  */
-/* A is rounded to binary32 and factored one problem per thread (pivots      */
-/* tested and square-rooted in binary64); the binary32 solution is refined   */
+/* A is rounded to binary32 (to nearest, subnormals kept) and factored in    */
+/* binary32, one problem per CTA; each pivot's square root is the correctly  */
+/* rounded binary32 root, which equals the binary64 root rounded to binary32.*/
+/* The binary32 solution is refined                                         */
 /* in binary64 (residual b - A x and update x + d in binary64) until the     */
 /* normwise backward error ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf)*/
 /* <= tol for every column, at most itmax steps.  If the binary32           */

@@ -27,8 +27,8 @@
 // (1 - 2(n+2) 2^-24): a lower bound of the binary64 norm, so the stopping
 // test never under-estimates eta.  binary64 -> binary32
 // conversions of matrix entries are integer operations (round to nearest
-// even; binary32-subnormal results flush to zero): FP64 instructions run at
-// 1/64 of the binary32 rate on this GPU.
+// even, binary32 subnormals included, as the IEEE conversion): FP64
+// instructions run at 1/64 of the binary32 rate on this GPU.
 #include "bf_internal.h"
 #include "../../include/bfgpu.h"
 
@@ -42,7 +42,18 @@ __device__ __noinline__ float f64_to_f32_rn(double a) {
     const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
     if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));  // inf / NaN
     int E = e - 1023 + 127;
-    if (e == 0 || E <= 0) return __uint_as_float(sign);  // zero, or below the binary32 normal range
+    if (e == 0) return __uint_as_float(sign);  // binary64 zero or subnormal: below half the binary32 minimum
+    if (E <= 0) {
+        // below the binary32 normal range: round sig 2^(e-1075) to a multiple of 2^-149 (a binary32
+        // subnormal, or the smallest normal when it rounds up to 2^-126), ties to even
+        const unsigned long long sig = m | (1ull << 52);
+        const int sh = 926 - e;  // 1075 - 149 - e, at least 30 here
+        if (sh > 54) return __uint_as_float(sign);
+        unsigned long long q = sig >> sh;
+        const unsigned long long rem = sig & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (q & 1ull))) q++;
+        return __uint_as_float(sign | (unsigned int)q);
+    }
     unsigned int mant = (unsigned int)(m >> 29);
     const unsigned int rem = (unsigned int)(m & 0x1FFFFFFFull);
     if (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) {

@@ -102,3 +102,37 @@ def test_ragged_arguments(bf):
         big = np.array([nbig], dtype=np.int32)
         assert f(1, big.ctypes.data_as(ctypes.c_void_p), 1, 1, op, 1, op, None, 1, 10 ** 6, 8, 256, None,
                  ctypes.byref(out)) == bf.ERR_NOT_SUPPORTED
+
+
+@pytest.mark.parametrize("lane_max", [0, 32, 200])
+def test_ragged_odd_offsets(bf, oracle, lane_max):
+    """Problems that start 8 bytes past a 16-byte boundary: the offsets are rebuilt here with a
+    one-element gap before every other problem, so half of the matrices (and right-hand sides)
+    start on an odd element offset.  Both per-thread and per-CTA forms, against the oracle."""
+    nrhs = 4
+    ns, S0, offS0, B0, offB0 = make(700, 91, bad=(5, 400))
+    offS = np.zeros_like(offS0)
+    offB = np.zeros_like(offB0)
+    pos_s = pos_b = 1  # the first problem already starts at an odd element
+    for b, n in enumerate(ns):
+        n = int(n)
+        offS[b], offB[b] = pos_s, pos_b
+        pos_s += n * n + (b & 1)
+        pos_b += n * nrhs + (b & 1)
+    S = np.full(pos_s + 1, np.nan)
+    B = np.full(pos_b + 1, np.nan)
+    for b, n in enumerate(ns):
+        n = int(n)
+        S[offS[b]:offS[b] + n * n] = S0[offS0[b]:offS0[b] + n * n]
+        B[offB[b]:offB[b] + n * nrhs] = B0[offB0[b]:offB0[b] + n * nrhs]
+    assert (offS % 2 == 1).sum() > len(ns) // 4 and (offS % 2 == 0).sum() > len(ns) // 4
+    Sg, Bg = torch.as_tensor(S).cuda(), torch.as_tensor(B).cuda()
+    plan = bf.RaggedPlan(ns, Sg, offS, Bg, offB, nrhs, lane_max=lane_max, threads=128)
+    plan.launch()
+    Sh, Bh = host(Sg), host(Bg)
+    check(ns, S, offS, B, offB, nrhs, Sh, Bh, host(plan.info), oracle, bad=(5, 400))
+    # the gaps between problems are never written
+    used = np.zeros(len(S), dtype=bool)
+    for b, n in enumerate(ns):
+        used[offS[b]:offS[b] + int(n) ** 2] = True
+    assert np.isnan(Sh[~used]).all()

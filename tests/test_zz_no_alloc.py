@@ -1,4 +1,4 @@
-"""The allocation-free ragged entry point against the existing plan entry point.
+"""The allocation-free ragged entry point against the existing plan entry point and the oracle.
 
 bf_ragged_potrf_potrs_noalloc exists for callers that cannot allocate device
 memory when they solve (a controller whose memory is sized once at start-up,
@@ -82,6 +82,45 @@ def test_noalloc_matches_plan_two_calls(bf):
             assert rel(S_got[sl][low], S_ref[sl][low]) <= TOL
             xb = slice(int(offB[b]), int(offB[b]) + n * nrhs)
             assert rel(B_got[xb], B_ref[xb]) <= TOL
+
+
+def test_noalloc_matches_oracle(bf, oracle):
+    """The same entry point against the oracle's per-problem dpotrf + dpotrs directly (so a fault
+    shared by the plan path and this one cannot pass), with failing problems."""
+    nrhs = 3
+    ns, S, offS, B, offB = ragged_inputs(900, 711, nrhs, bad=(7, 450))
+    S_got, B_got, info_got = run_noalloc(bf, ns, S, offS, B, offB, nrhs, 32, 128)
+    So, Xo, info_o = oracle.ragged_potrf_potrs(ns, S, offS, B, offB, nrhs)
+    np.testing.assert_array_equal(info_got, info_o)
+    assert (info_o != 0).sum() == 2
+    for b in np.nonzero(info_o == 0)[0]:
+        n = int(ns[b])
+        sl = slice(int(offS[b]), int(offS[b]) + n * n)
+        low = np.tril(np.ones((n, n), dtype=bool)).T.reshape(-1)
+        assert rel(S_got[sl][low], So[sl][low]) <= TOL
+        xb = slice(int(offB[b]), int(offB[b]) + n * nrhs)
+        assert rel(B_got[xb], Xo[xb]) <= TOL
+
+
+def test_noalloc_refuses_stream_capture(bf):
+    """Its queue is copied from host arrays that the next call reuses, so a captured call could
+    not be replayed: on a capturing stream it returns BF_ERR_NOT_SUPPORTED and launches nothing."""
+    ns = np.array([3, 4], dtype=np.int32)
+    off = np.array([0, 9], dtype=np.int64)
+    offb = np.array([0, 3], dtype=np.int64)
+    S = torch.zeros(32, dtype=torch.float64, device="cuda")
+    B = torch.zeros(8, dtype=torch.float64, device="cuda")
+    info = torch.zeros(2, dtype=torch.int32, device="cuda")
+    vp = ctypes.c_void_p
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        r = bf.bf_ragged_potrf_potrs_noalloc(2, ns.ctypes.data_as(vp), 1, vp(S.data_ptr()), off.ctypes.data_as(vp),
+                                             vp(B.data_ptr()), offb.ctypes.data_as(vp), vp(info.data_ptr()), 32, 128,
+                                             vp(s.cuda_stream))
+        g.capture_end()
+    assert r == bf.ERR_NOT_SUPPORTED
 
 
 def test_noalloc_rejects_too_many_problems(bf):
