@@ -149,10 +149,10 @@ int bf_dpotrf_strided_batched(char uplo, int n, double* A, int lda, long long st
 int bf_dpotrf_batched(char uplo, int n, double* const* Aarray, int lda, int* info, int batch,
                       bf_stream_t stream);
 
-/* Variable-size dpotrf (see bf_dgemm_vbatched): per problem n[q], lda[q], Aarray[q].      */
-/* info[q] = the LAPACK info (>= 0), or -2 (n[q] < 0 or above max_n) / -4 (lda[q] too      */
-/* small) for a skipped problem.  uplo 'U', or max_n above BF_VBATCHED_POTRF_NMAX, returns  */
-/* BF_ERR_NOT_SUPPORTED (nothing launched).                                                */
+/* Variable-size dpotrf (see bf_dgemm_vbatched): per problem n[q], lda[q], Aarray[q];      */
+/* uplo 'L' (A = L L^T) or 'U' (A = U^T U), as bf_dpotrf.  info[q] = the LAPACK info (>= 0),*/
+/* or -2 (n[q] < 0 or above max_n) / -4 (lda[q] too small) for a skipped problem.  max_n    */
+/* above BF_VBATCHED_POTRF_NMAX returns BF_ERR_NOT_SUPPORTED (nothing launched).           */
 #define BF_VBATCHED_POTRF_NMAX 1024
 int bf_dpotrf_vbatched(char uplo, const int* n, double* const* Aarray, const int* lda, int* info, int batch,
                        int max_n, bf_stream_t stream);
@@ -208,9 +208,10 @@ int bf_dtrmm_batched(char side, char uplo, char transa, char diag, int m, int n,
 
 /* ------------------------------------------------------------------------ */
 /* dgetrf (section 3.1 "dgetrf"): LU factorisation with partial (row)        */
-/* pivoting, P A = L U, of square matrices (m == n; m != n returns           */
-/* BF_ERR_NOT_SUPPORTED).  L (unit lower, below the diagonal) and U (upper)  */
-/* overwrite A.  ipiv (device, n ints per problem, stride strideIpiv):       */
+/* pivoting, P A = L U, of m x n matrices.  L (m x min(m, n), unit lower     */
+/* trapezoidal, below the diagonal) and U (min(m, n) x n, upper trapezoidal) */
+/* overwrite A.  m != n needs m <= 1024 (else BF_ERR_NOT_SUPPORTED).         */
+/* ipiv (device, min(m, n) ints per problem, stride strideIpiv >= min(m, n)):*/
 /* row j was interchanged with row ipiv[j] - 1 (1-based, as LAPACK); the     */
 /* pivot is the first row of largest magnitude.  info (device, may be        */
 /* NULL): 0, or j when U(j-1, j-1) is exactly zero (the factorisation still   */
@@ -269,6 +270,15 @@ int bf_riccati_strided_batched(int N, int nx, int nu, const double* BAt, long lo
 int bf_dpotrs(char uplo, int n, int nrhs, const double* A, int lda, double* B, int ldb,
               bf_stream_t stream);
 
+int bf_dpotrs_batched(char uplo, int n, int nrhs, const double* const* Aarray, int lda,
+                      double* const* Barray, int ldb, int batch, bf_stream_t stream);
+/* Variable-size dpotrs (see bf_dgemm_vbatched): per problem n[q], nrhs[q], lda[q], ldb[q],  */
+/* Aarray[q] (the factor from bf_dpotrf or bf_dpotrf_vbatched with the same uplo),         */
+/* Barray[q] (n[q] x nrhs[q], overwritten by X); max_n, max_nrhs bound the sizes.  dinfo[q] */
+/* = 0, or -2 n, -3 nrhs, -4 A, -5 lda, -6 B, -7 ldb for a skipped problem.               */
+int bf_dpotrs_vbatched(char uplo, const int* n, const int* nrhs, const double* const* Aarray,
+                       const int* lda, double* const* Barray, const int* ldb, int batch, int max_n,
+                       int max_nrhs, int* dinfo, bf_stream_t stream);
 int bf_dpotrs_strided_batched(char uplo, int n, int nrhs, const double* A, int lda,
                               long long strideA, double* B, int ldb, long long strideB,
                               int batch, bf_stream_t stream);
@@ -342,6 +352,8 @@ int bf_dtrsm_backward_strided_batched(char side, char uplo, char transa, char di
 /* Abar = (S + S^T)/2, S = L^{-T} Phi(L^T Lbar) L^{-1}, Phi = lower triangle */
 /* with halved diagonal (I. Murray, "Differentiation of the Cholesky         */
 /* decomposition", 2016), to the full n x n of Abar (Abar must not alias L). */
+/* uplo 'U' (A = U^T U): L and Lbar hold U and Ubar in their upper triangles */
+/* (read as L = U^T, Lbar = Ubar^T); the gradient is the same symmetric one. */
 int bf_dpotrf_backward_strided_batched(char uplo, int n, const double* L, int ldl, long long strideL,
                                        const double* Lbar, int ldlb, long long strideLbar,
                                        double* Abar, int ldab, long long strideAbar, int batch,

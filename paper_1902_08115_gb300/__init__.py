@@ -53,6 +53,8 @@ _SIGS = {
     "bf_dpotrf_vbatched": [_c, _vp, _vp, _vp, _vp, _i, _i, _vp],
     "bf_dpotrs": [_c, _i, _i, _vp, _i, _vp, _i, _vp],
     "bf_dpotrs_strided_batched": [_c, _i, _i, _vp, _i, _ll, _vp, _i, _ll, _i, _vp],
+    "bf_dpotrs_batched": [_c, _i, _i, _vp, _i, _vp, _i, _i, _vp],
+    "bf_dpotrs_vbatched": [_c, _vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp],
     "bf_tune_set": [_i, _i, _i, _i, _i, _i, _i, _i, _i],
     "bf_tune_set_batch_rule": [_i, _i, _i, _i, _ll, _ll, _ll],
     "bf_tune_clear": [],
@@ -326,6 +328,23 @@ def dpotrf_vbatched(As, ns, uplo: str = "L", stream=None):
     return info
 
 
+def dpotrs_vbatched(Ls, Bs, ns, nrhss, uplo: str = "L", stream=None):
+    """Solve A_q X = B_q with the Cholesky factors L_q (from dpotrf / dpotrf_vbatched, same uplo)
+    for lists of problems of different orders n_q and right-hand-side counts; X overwrites B_q.
+    Returns dinfo (0, or minus the position of an illegal argument of that problem)."""
+    import torch
+    batch = len(Bs)
+    dev = Bs[0].device
+    d = _DevArrays(dev, stream)
+    dinfo = torch.empty(batch, dtype=torch.int32, device=dev)
+    _check("bf_dpotrs_vbatched", bf_dpotrs_vbatched(
+        _ch(uplo), d.ints(ns), d.ints(nrhss), d.ptrs(Ls), d.ints(_dims2(L)[1] for L in Ls), d.ptrs(Bs),
+        d.ints(_dims2(B)[1] for B in Bs), batch, max(ns, default=0), max(nrhss, default=0), _ptr(dinfo),
+        _stream(stream)))
+    d.done()
+    return dinfo
+
+
 def dsyrk(uplo: str, trans: str, alpha: float, A, beta: float, C, n=None, k=None, stream=None):
     """C <= alpha op(A) op(A)^T + beta C on the uplo triangle, every problem (in place on C).
 
@@ -376,20 +395,22 @@ def dtrmm(side: str, uplo: str, transa: str, diag: str, alpha: float, A, B, m=No
     return B
 
 
-def dgetrf(A, n=None, ipiv=None, info=None, stream=None):
-    """LU with partial pivoting of every (square) problem in place; returns (ipiv, info).
+def dgetrf(A, n=None, ipiv=None, info=None, stream=None, m=None):
+    """LU with partial pivoting of every m x n problem in place; returns (ipiv, info).
 
-    ipiv: (batch, n) int32, 1-based row interchanges; info: (batch,) int32.
+    n defaults to A's number of columns, m to n (square).  ipiv: (batch, min(m, n)) int32,
+    1-based row interchanges; info: (batch,) int32.
     """
     import torch
     bA, cA, ldA, sA = _batch_dims(A)
     n = cA if n is None else n
+    m = n if m is None else m
     if ipiv is None:
-        ipiv = torch.empty(bA, max(n, 1), dtype=torch.int32, device=A.device)
+        ipiv = torch.empty(bA, max(min(m, n), 1), dtype=torch.int32, device=A.device)
     if info is None:
         info = torch.empty(bA, dtype=torch.int32, device=A.device)
     _check("bf_dgetrf_strided_batched", bf_dgetrf_strided_batched(
-        n, n, _ptr(A), ldA, sA, _ptr(ipiv), ipiv.shape[-1], _ptr(info), bA, _stream(stream)))
+        m, n, _ptr(A), ldA, sA, _ptr(ipiv), ipiv.shape[-1], _ptr(info), bA, _stream(stream)))
     return ipiv, info
 
 

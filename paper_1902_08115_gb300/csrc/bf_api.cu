@@ -196,8 +196,8 @@ int bf_dpotrf_batched(char uplo, int n, double* const* Aarray, int lda, int* inf
     return run_potrf(uplo, n, mat_array((const double* const*)Aarray, 0), lda, info, batch, (cudaStream_t)stream);
 }
 
-static int potrs_impl(char uplo, int n, int nrhs, const double* A, int lda, long long strideA, double* B,
-                      int ldb, long long strideB, int batch, bf_stream_t stream, const int* pos) {
+static int potrs_run(char uplo, int n, int nrhs, MatRef A, const void* Ap, int lda, MatRef B, const void* Bp, int ldb,
+                     long long strideB, int batch, bf_stream_t stream, const int* pos) {
     // pos: uplo, n, nrhs, A, lda, B, ldb, strideB, batch
     if (!(is_l(uplo) || is_u(uplo))) return -pos[0];
     if (n < 0) return -pos[1];
@@ -207,16 +207,20 @@ static int potrs_impl(char uplo, int n, int nrhs, const double* A, int lda, long
     if (pos[8] && batch < 0) return -pos[8];
     if (pos[7] && batch > 1 && strideB < (long long)ldb * nrhs) return -pos[7];
     const bool work = n > 0 && nrhs > 0 && batch > 0;
-    if (work && !A) return -pos[3];
-    if (work && !B) return -pos[5];
+    if (work && !Ap) return -pos[3];
+    if (work && !Bp) return -pos[5];
     if (!work) return 0;
     // 'L': L Y = B, L^T X = Y;  'U': U^T Y = B, U X = Y
     const char u = is_u(uplo) ? 'U' : 'L';
-    int r = run_trsm('L', u, u == 'L' ? 'N' : 'T', 'N', n, nrhs, 1.0, mat_strided(A, strideA), lda,
-                     mat_strided(B, strideB), ldb, batch, (cudaStream_t)stream);
+    int r = run_trsm('L', u, u == 'L' ? 'N' : 'T', 'N', n, nrhs, 1.0, A, lda, B, ldb, batch, (cudaStream_t)stream);
     if (r) return r;
-    return run_trsm('L', u, u == 'L' ? 'T' : 'N', 'N', n, nrhs, 1.0, mat_strided(A, strideA), lda,
-                    mat_strided(B, strideB), ldb, batch, (cudaStream_t)stream);
+    return run_trsm('L', u, u == 'L' ? 'T' : 'N', 'N', n, nrhs, 1.0, A, lda, B, ldb, batch, (cudaStream_t)stream);
+}
+
+static int potrs_impl(char uplo, int n, int nrhs, const double* A, int lda, long long strideA, double* B,
+                      int ldb, long long strideB, int batch, bf_stream_t stream, const int* pos) {
+    return potrs_run(uplo, n, nrhs, mat_strided(A, strideA), A, lda, mat_strided(B, strideB), B, ldb, strideB, batch,
+                     stream, pos);
 }
 
 int bf_dpotrs(char uplo, int n, int nrhs, const double* A, int lda, double* B, int ldb, bf_stream_t stream) {
@@ -229,6 +233,13 @@ int bf_dpotrs_strided_batched(char uplo, int n, int nrhs, const double* A, int l
     static const int pos[9] = {1, 2, 3, 4, 5, 7, 8, 9, 10};
     if (strideA < 0) return -6;
     return potrs_impl(uplo, n, nrhs, A, lda, strideA, B, ldb, strideB, batch, stream, pos);
+}
+
+int bf_dpotrs_batched(char uplo, int n, int nrhs, const double* const* Aarray, int lda, double* const* Barray,
+                      int ldb, int batch, bf_stream_t stream) {
+    static const int pos[9] = {1, 2, 3, 4, 5, 6, 7, 0, 8};
+    return potrs_run(uplo, n, nrhs, mat_array(Aarray, 0), Aarray, lda, mat_array((const double* const*)Barray, 0),
+                     Barray, ldb, 0, batch, stream, pos);
 }
 
 // ------------------------------------------------------------------------ dsyrk
@@ -375,9 +386,9 @@ static int getrf_impl(int m, int n, double* A, int lda, long long strideA, int* 
     const bool work = mn > 0 && batch > 0;
     if (work && !A) return -pos[2];
     if (work && !ipiv) return -pos[5];
-    if (m != n) return BF_ERR_NOT_SUPPORTED;
+    if (m != n && m > kGetrfMaxRows) return BF_ERR_NOT_SUPPORTED;
     if (batch <= 0) return 0;
-    return status(launch_dgetrf(n, mat_strided(A, strideA), lda, ipiv, strided ? strideIpiv : n, info, batch,
+    return status(launch_dgetrf(m, n, mat_strided(A, strideA), lda, ipiv, strided ? strideIpiv : mn, info, batch,
                                 (cudaStream_t)stream));
 }
 

@@ -21,9 +21,11 @@ namespace bf {
 
 // P = Phi(L^T Lbar) for every problem, written to the full n x n of `out` (upper part zero).
 // One thread per (lower 4x4 tile, problem), problem index fastest: the 32 lanes of a warp
-// work on the same tile of 32 problems, so every lane runs the same k-loop length.
+// work on the same tile of 32 problems, so every lane runs the same k-loop length.  upper: L and
+// Lbar are read as the transposes of the upper triangles stored (A = U^T U: L = U^T).
 __global__ void __launch_bounds__(256)
-phi_ltlbar_kernel(int n, MatRef L, int ldl, MatRef Lb, int ldlb, MatRef O, int ldo, long long batch, int nt) {
+phi_ltlbar_kernel(int n, MatRef L, int ldl, MatRef Lb, int ldlb, MatRef O, int ldo, long long batch, int nt,
+                  int upper) {
     const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long ntile = (long long)nt * (nt + 1) / 2;
     if (gt >= ntile * batch) return;
@@ -48,12 +50,12 @@ phi_ltlbar_kernel(int n, MatRef L, int ldl, MatRef Lb, int ldlb, MatRef O, int l
 #pragma unroll
         for (int a = 0; a < 4; a++) {
             const int i = i0 + a;
-            li[a] = (i < n && k >= i) ? l[k + (long long)i * ldl] : 0.0;
+            li[a] = (i < n && k >= i) ? l[upper ? i + (long long)k * ldl : k + (long long)i * ldl] : 0.0;
         }
 #pragma unroll
         for (int b = 0; b < 4; b++) {
             const int j = j0 + b;
-            lbj[b] = (j < n && k >= j) ? lb[k + (long long)j * ldlb] : 0.0;
+            lbj[b] = (j < n && k >= j) ? lb[upper ? j + (long long)k * ldlb : k + (long long)j * ldlb] : 0.0;
         }
 #pragma unroll
         for (int a = 0; a < 4; a++)
@@ -143,20 +145,23 @@ dtrfill_kernel(int n, int upper, double* A, int lda, long long stride, const int
 }
 
 cudaError_t launch_dpotrf_backward(int n, MatRef L, int ldl, MatRef Lb, int ldlb, MatRef Ab, int ldab,
-                                   long long batch, cudaStream_t s) {
+                                   long long batch, cudaStream_t s, int upper) {
     if (n == 0 || batch == 0) return cudaSuccess;
     const int nt = (n + 3) / 4;
     long long threads = (long long)nt * (nt + 1) / 2 * batch;
-    phi_ltlbar_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(n, L, ldl, Lb, ldlb, Ab, ldab, batch, nt);
+    phi_ltlbar_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(n, L, ldl, Lb, ldlb, Ab, ldab, batch, nt,
+                                                                         upper);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // S1 = L^{-T} P (left, lower, transposed), then S = S1 L^{-1} (right, lower, not transposed)
-    TrsmConfig c1 = choose_trsm(0, 0, 1, 0, n, n, batch);
-    e = launch_dtrsm(0, 0, 1, 0, n, n, 1.0, L, ldl, Ab, ldab, batch, c1, nullptr, s);
+    // S1 = L^{-T} P (left, lower, transposed), then S = S1 L^{-1} (right, lower, not transposed);
+    // upper (L = U^T): S1 = U^{-1} P (left, upper), then S = S1 U^{-T} (right, upper, transposed)
+    const int tr1 = upper ? 0 : 1, tr2 = upper ? 1 : 0;
+    TrsmConfig c1 = choose_trsm(0, upper, tr1, 0, n, n, batch);
+    e = launch_dtrsm(0, upper, tr1, 0, n, n, 1.0, L, ldl, Ab, ldab, batch, c1, nullptr, s);
     if (e != cudaSuccess) return e;
-    TrsmConfig c2 = choose_trsm(1, 0, 0, 0, n, n, batch);
-    e = launch_dtrsm(1, 0, 0, 0, n, n, 1.0, L, ldl, Ab, ldab, batch, c2, nullptr, s);
+    TrsmConfig c2 = choose_trsm(1, upper, tr2, 0, n, n, batch);
+    e = launch_dtrsm(1, upper, tr2, 0, n, n, 1.0, L, ldl, Ab, ldab, batch, c2, nullptr, s);
     if (e != cudaSuccess) return e;
     if (n > 1) {
         long long pairs = (long long)n * (n - 1) / 2 * batch;
@@ -300,10 +305,10 @@ extern "C" int bf_dpotrf_backward_strided_batched(char uplo, int n, const double
     if (work && !L) return -3;
     if (work && !Lbar) return -6;
     if (work && !Abar) return -9;
-    if (cis_u(uplo)) return BF_ERR_NOT_SUPPORTED;
     if (!work) return 0;
     return cstat(launch_dpotrf_backward(n, mat_strided(L, strideL), ldl, mat_strided(Lbar, strideLbar), ldlb,
-                                        mat_strided(Abar, strideAbar), ldab, batch, (cudaStream_t)stream));
+                                        mat_strided(Abar, strideAbar), ldab, batch, (cudaStream_t)stream,
+                                        cis_u(uplo) ? 1 : 0));
 }
 
 extern "C" int bf_dtrfill_strided_batched(char uplo, int n, double* A, int lda, long long strideA, const int* info,

@@ -21,7 +21,7 @@
 namespace bf {
 
 struct GetrfParams {
-    int n;
+    int m, n;  // rows, columns (the lane form: m == n)
     MatRef A;
     int lda;
     int* ipiv;
@@ -161,8 +161,9 @@ __global__ void __launch_bounds__(256) dgetrf_lane_kernel(GetrfParams p) {
 }
 
 // ------------------------------------------------------------------ one problem per CTA
-// For batches too small to fill the GPU one problem per thread: right-looking by 16-column
-// panels, the panel in shared memory (W(i, c) = W[i + c n], rows J..n-1).  Per panel:
+// For batches too small to fill the GPU one problem per thread, and for every m x n problem
+// with m != n: right-looking by 16-column panels over the first min(m, n) columns, the panel in
+// shared memory (W(i, c) = W[i + c m], rows J..m-1).  Per panel:
 //   (1) the panel factored column by column: the pivot (first row of largest |a| below the
 //       diagonal, taken only when strictly larger than |a_cc| -- a NaN never counts as larger),
 //       the row interchange inside the panel, scaling by the pivot's reciprocal, and the
@@ -172,6 +173,8 @@ __global__ void __launch_bounds__(256) dgetrf_lane_kernel(GetrfParams p) {
 //       (one thread per column, the interchanges in order);
 //   (3) U12 = L11^{-1} A12 (unit lower, one thread per column) and the trailing update
 //       A22 -= L21 U12 on 4x4 register tiles.
+// A wide problem (m < n) ends with U12 of its last panel (no rows left below); a tall one
+// (m > n) ends with its last panel (no columns left to the right), L being m x n.
 #define BF_GETRF_NB 16
 
 __device__ __forceinline__ void argmax_pair(double& v, int& i, double v2, int i2) {
@@ -187,17 +190,18 @@ __global__ void __launch_bounds__(128, 4) dgetrf_cta_kernel(GetrfParams p) {
     __shared__ int s_i[4];
     __shared__ int s_piv[BF_GETRF_NB];
     __shared__ int s_info;
-    const int n = p.n, lda = p.lda, T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int M = p.m, n = p.n, K = M < n ? M : n, lda = p.lda, T = blockDim.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     double* W = sm_lu;
     for (long long q = blockIdx.x; q < p.batch; q += gridDim.x) {
         double* A = p.A.mptr(q);
         int* piv = p.ipiv + q * p.sipiv;
         if (tid == 0) s_info = 0;
-        for (int J = 0; J < n; J += BF_GETRF_NB) {
-            const int nb = imin(BF_GETRF_NB, n - J), m = n - J;
+        for (int J = 0; J < K; J += BF_GETRF_NB) {
+            const int nb = imin(BF_GETRF_NB, K - J), m = M - J;  // panel width, height
             for (int e = tid; e < m * nb; e += T) {
                 const int c = e / m, i = e - c * m;
-                W[i + c * n] = A[J + i + (long long)(J + c) * lda];
+                W[i + c * M] = A[J + i + (long long)(J + c) * lda];
             }
             __syncthreads();
             // (1) the panel
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(128, 4) dgetrf_cta_kernel(GetrfParams p) {
                 double bv = -1.0;  // no candidate below the diagonal yet
                 int bi = c;
                 for (int i = c + 1 + tid; i < m; i += T) {
-                    const double v = fabs(W[i + c * n]);
+                    const double v = fabs(W[i + c * M]);
                     if (v > bv) {  // strictly larger: the first of equal maxima stays, NaN never wins
                         bv = v;
                         bi = i;
@@ -224,38 +228,38 @@ __global__ void __launch_bounds__(128, 4) dgetrf_cta_kernel(GetrfParams p) {
                 __syncthreads();
                 if (tid == 0) {
                     for (int w = 1; w < (T >> 5); w++) argmax_pair(bv, bi, s_v[w], s_i[w]);
-                    const int pr = (bv > fabs(W[c + c * n])) ? bi : c;
+                    const int pr = (bv > fabs(W[c + c * M])) ? bi : c;
                     s_piv[c] = pr;
                     piv[J + c] = J + pr + 1;
-                    if (W[pr + c * n] == 0.0 && s_info == 0) s_info = J + c + 1;
+                    if (W[pr + c * M] == 0.0 && s_info == 0) s_info = J + c + 1;
                 }
                 __syncthreads();
                 const int pr = s_piv[c];
                 if (pr != c) {
                     for (int c2 = tid; c2 < nb; c2 += T) {
-                        const double t = W[c + c2 * n];
-                        W[c + c2 * n] = W[pr + c2 * n];
-                        W[pr + c2 * n] = t;
+                        const double t = W[c + c2 * M];
+                        W[c + c2 * M] = W[pr + c2 * M];
+                        W[pr + c2 * M] = t;
                     }
                     __syncthreads();
                 }
-                const double pv = W[c + c * n];
+                const double pv = W[c + c * M];
                 if (pv != 0.0) {
                     const double rcp = 1.0 / pv;
-                    for (int i = c + 1 + tid; i < m; i += T) W[i + c * n] *= rcp;
+                    for (int i = c + 1 + tid; i < m; i += T) W[i + c * M] *= rcp;
                     __syncthreads();
                 }
                 const int w2 = nb - c - 1, h = m - c - 1;
                 for (int e = tid; e < w2 * h; e += T) {
                     const int c2 = c + 1 + e / h, i = c + 1 + e % h;
-                    W[i + c2 * n] = fma(-W[i + c * n], W[c + c2 * n], W[i + c2 * n]);
+                    W[i + c2 * M] = fma(-W[i + c * M], W[c + c2 * M], W[i + c2 * M]);
                 }
                 __syncthreads();
             }
             // (2) the panel back, its interchanges on the other columns
             for (int e = tid; e < m * nb; e += T) {
                 const int c = e / m, i = e - c * m;
-                A[J + i + (long long)(J + c) * lda] = W[i + c * n];
+                A[J + i + (long long)(J + c) * lda] = W[i + c * M];
             }
             for (int j = tid; j < n; j += T) {
                 if (j >= J && j < J + nb) continue;
@@ -278,16 +282,19 @@ __global__ void __launch_bounds__(128, 4) dgetrf_cta_kernel(GetrfParams p) {
 #pragma unroll
                     for (int c = 0; c < BF_GETRF_NB; c++) u[c] = c < nb ? col[c] : 0.0;
 #pragma unroll
-                    for (int c = 1; c < BF_GETRF_NB; c++)
+                    for (int c = 1; c < BF_GETRF_NB; c++) {
+                        if (c >= nb) break;  // W holds nb <= M rows of L11: no read past them
 #pragma unroll
-                        for (int c2 = 0; c2 < c; c2++) u[c] = fma(-W[c + c2 * n], u[c2], u[c]);
+                        for (int c2 = 0; c2 < c; c2++) u[c] = fma(-W[c + c2 * M], u[c2], u[c]);
+                    }
 #pragma unroll
                     for (int c = 0; c < BF_GETRF_NB; c++)
                         if (c < nb) col[c] = u[c];
                 }
                 __syncthreads();
-                const int r = n - J - nb, tr = (r + 3) / 4;
-                for (int t = tid; t < tr * tr; t += T) {
+                const int r = M - J - nb, tr = (r + 3) / 4;          // rows below the panel
+                const int rc = n - J - nb, tc = (rc + 3) / 4;        // columns right of it
+                for (int t = tid; t < tr * tc; t += T) {
                     const int i0 = 4 * (t % tr), j0 = 4 * (t / tr);  // rows / columns from J + nb
                     double acc[4][4];
 #pragma unroll
@@ -297,9 +304,9 @@ __global__ void __launch_bounds__(128, 4) dgetrf_cta_kernel(GetrfParams p) {
                     for (int c = 0; c < nb; c++) {
                         double l[4], u[4];
 #pragma unroll
-                        for (int a = 0; a < 4; a++) l[a] = W[nb + imin(i0 + a, r - 1) + c * n];
+                        for (int a = 0; a < 4; a++) l[a] = W[nb + imin(i0 + a, r - 1) + c * M];
 #pragma unroll
-                        for (int b = 0; b < 4; b++) u[b] = A[J + c + (long long)(J + nb + imin(j0 + b, r - 1)) * lda];
+                        for (int b = 0; b < 4; b++) u[b] = A[J + c + (long long)(J + nb + imin(j0 + b, rc - 1)) * lda];
 #pragma unroll
                         for (int a = 0; a < 4; a++)
 #pragma unroll
@@ -307,7 +314,7 @@ __global__ void __launch_bounds__(128, 4) dgetrf_cta_kernel(GetrfParams p) {
                     }
 #pragma unroll
                     for (int b = 0; b < 4; b++) {
-                        if (j0 + b >= r) continue;
+                        if (j0 + b >= rc) continue;
                         double* col = A + (long long)(J + nb + j0 + b) * lda + J + nb;
 #pragma unroll
                         for (int a = 0; a < 4; a++)
@@ -322,14 +329,14 @@ __global__ void __launch_bounds__(128, 4) dgetrf_cta_kernel(GetrfParams p) {
     }
 }
 
-cudaError_t launch_dgetrf(int n, MatRef A, int lda, int* ipiv, long long sipiv, int* info, long long batch,
+cudaError_t launch_dgetrf(int m, int n, MatRef A, int lda, int* ipiv, long long sipiv, int* info, long long batch,
                           cudaStream_t s) {
     if (batch == 0) return cudaSuccess;
-    if (n == 0) return info ? cudaMemsetAsync(info, 0, sizeof(int) * (size_t)batch, s) : cudaSuccess;
+    if (m == 0 || n == 0) return info ? cudaMemsetAsync(info, 0, sizeof(int) * (size_t)batch, s) : cudaSuccess;
     GetrfParams p;
-    p.n = n; p.A = A; p.lda = lda; p.ipiv = ipiv; p.sipiv = sipiv; p.batch = batch; p.info = info;
-    if (choose_getrf(n, batch) == VAR_CTA) {
-        const size_t smem = sizeof(double) * (size_t)BF_GETRF_NB * n;
+    p.m = m; p.n = n; p.A = A; p.lda = lda; p.ipiv = ipiv; p.sipiv = sipiv; p.batch = batch; p.info = info;
+    if (m != n || choose_getrf(n, batch) == VAR_CTA) {
+        const size_t smem = sizeof(double) * (size_t)BF_GETRF_NB * m;
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(dgetrf_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);

@@ -155,8 +155,8 @@ cudaError_t launch_dpotrf(int n, MatRef A, int lda, long long batch, int* info,
         if (e != cudaSuccess) return e;
     }
     if (n == 0) return cudaSuccess;
-    if (cfg.variant == VAR_CTA && !upper && n <= 256) return launch_dpotrf_cta(n, A, lda, batch, info, s);
-    if (cfg.variant == VAR_CTA) {  // upper, or too large for one CTA: blocked, or the lane kernel
+    if (cfg.variant == VAR_CTA && n <= 256) return launch_dpotrf_cta(n, A, lda, batch, info, s, upper);
+    if (cfg.variant == VAR_CTA) {  // too large for one CTA: blocked, or the lane kernel
         PotrfConfig b = cfg;
         b.variant = n > 64 ? VAR_BLOCKED : VAR_DIRECT;
         return launch_dpotrf(n, A, lda, batch, info, b, s, upper);

@@ -164,7 +164,9 @@ cudaError_t launch_dtrmm(int side, int uplo, int trans, int unit, int m, int n, 
                          const MatRef* Bsrc = nullptr, int ldbs = 0);
 
 // LU with partial pivoting and its solve (bf_dgetrf.cu); ipiv: sipiv ints per problem, 1-based
-cudaError_t launch_dgetrf(int n, MatRef A, int lda, int* ipiv, long long sipiv, int* info, long long batch,
+// m x n; m != n always takes one problem per CTA (m <= kGetrfMaxRows)
+constexpr int kGetrfMaxRows = 1024;
+cudaError_t launch_dgetrf(int m, int n, MatRef A, int lda, int* ipiv, long long sipiv, int* info, long long batch,
                           cudaStream_t s);
 cudaError_t launch_dgetrs(int trans, int n, int nrhs, MatRef A, int lda, const int* ipiv, long long sipiv, MatRef B,
                           int ldb, long long batch, cudaStream_t s);
@@ -181,10 +183,11 @@ size_t potrf_group_smem(int n, int P);
 int potrf_group_size(int n, long long batch, int per_sm);
 cudaError_t launch_dpotrf_group(int n, MatRef A, int lda, long long batch, int* info, cudaStream_t s, int upper,
                                 int threads, int per_sm);
-// dpotrf (lower) with one problem per CTA, n <= 256 (bf_ragged.cu)
-cudaError_t launch_dpotrf_cta(int n, MatRef A, int lda, long long batch, int* info, cudaStream_t s);
-// dpotrf 'L' of a variable-size batch (device arrays n, Aarray, lda; max_n <= BF_VBATCHED_POTRF_NMAX)
+// dpotrf with one problem per CTA, n <= 256 (bf_ragged.cu); upper: A = U^T U from the upper
+// triangle (the lower factorisation of the transposed view)
+cudaError_t launch_dpotrf_cta(int n, MatRef A, int lda, long long batch, int* info, cudaStream_t s, int upper);
+// dpotrf of a variable-size batch (device arrays n, Aarray, lda; max_n <= BF_VBATCHED_POTRF_NMAX)
 cudaError_t launch_dpotrf_vbatched(const int* n, double* const* A, const int* lda, int* info, long long batch,
-                                   int max_n, cudaStream_t s);
+                                   int max_n, cudaStream_t s, int upper);
 
 }  // namespace bf

@@ -44,10 +44,24 @@ struct RaggedParams {
 #define BF_BIG_NB 16
 #define BF_BIG_NMAX 256  // backward substitution keeps x in 8 registers per lane
 
+// Element (i, k) of the factored matrix: column-major with leading dimension ld, or, with TR,
+// of its transpose (the upper Cholesky A = U^T U is the lower one of the transposed view).
+template <bool TR>
+__device__ __forceinline__ long long bidx(int i, int k, int ld) {
+    return TR ? k + (long long)i * ld : i + (long long)k * ld;
+}
+
 // Four consecutive rows i..i+3 of column k of a problem in global memory (leading dimension
 // ld, rows clamped to n - 1): two 16-byte loads when the strip starts on a 16-byte boundary,
-// one 16-byte load between two single words when it starts 8 bytes past one.
+// one 16-byte load between two single words when it starts 8 bytes past one; single words
+// along a row of the stored matrix for the transposed view.
+template <bool TR>
 __device__ __forceinline__ void big_strip4(const double* S, int ld, int n, int i, int k, double* o) {
+    if (TR) {
+#pragma unroll
+        for (int a = 0; a < 4; a++) o[a] = S[bidx<TR>(imin(i + a, n - 1), k, ld)];
+        return;
+    }
     const double* p = S + i + (long long)k * ld;
     if (i + 4 <= n) {
         if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
@@ -88,6 +102,7 @@ __device__ __forceinline__ void big_tile_index(int t, int nI, int& K, int& I) {
 // Then the backward substitution L^T X = Y, one warp per right-hand side.  The matrix S has
 // leading dimension lds, the r right-hand sides Bq leading dimension n; returns the LAPACK
 // info (every thread).  Shared memory: 8 (16 n + n r + n + 16 blockDim) bytes at sm.
+template <bool TR>
 __device__ int big_core(int n, double* S, int lds, double* Bq, int r, double* sm) {
     const int tid = threadIdx.x, T = blockDim.x, warp = tid >> 5, lane = tid & 31;
     double* W = sm;                            // panel: W[i + c n], i = row - J, c < 16
@@ -129,7 +144,7 @@ __device__ int big_core(int n, double* S, int lds, double* Bq, int r, double* sm
 #pragma unroll
                     for (int b = 0; b < 4; b++) {
                         double col[4];
-                        big_strip4(S, lds, n, i0, imin(k0 + b, n - 1), col);  // upper entries unused
+                        big_strip4<TR>(S, lds, n, i0, imin(k0 + b, n - 1), col);  // upper entries unused
 #pragma unroll
                         for (int a = 0; a < 4; a++) acc[a][b] = col[a];
                     }
@@ -142,9 +157,9 @@ __device__ int big_core(int n, double* S, int lds, double* Bq, int r, double* sm
 #pragma unroll 2
                 for (int k = klo; k < khi; k++) {
                     double li[4], lk[4];
-                    big_strip4(S, lds, n, i0, k, li);
+                    big_strip4<TR>(S, lds, n, i0, k, li);
 #pragma unroll
-                    for (int b = 0; b < 4; b++) lk[b] = S[imin(k0 + b, n - 1) + (long long)k * lds];
+                    for (int b = 0; b < 4; b++) lk[b] = S[bidx<TR>(imin(k0 + b, n - 1), k, lds)];
 #pragma unroll
                     for (int a = 0; a < 4; a++)
 #pragma unroll
@@ -169,7 +184,7 @@ __device__ int big_core(int n, double* S, int lds, double* Bq, int r, double* sm
             for (int e = T - 1 - tid; e < nb * r; e += T) {  // the last threads, fewest tiles
                 const int c = e % nb, rr = e / nb;
                 double s = X[J + c + (size_t)rr * n];
-                for (int k = 0; k < J; k++) s = fma(-S[J + c + (long long)k * lds], X[k + (size_t)rr * n], s);
+                for (int k = 0; k < J; k++) s = fma(-S[bidx<TR>(J + c, k, lds)], X[k + (size_t)rr * n], s);
                 X[J + c + (size_t)rr * n] = s;
             }
             if (sp > 1) {
@@ -227,13 +242,13 @@ __device__ int big_core(int n, double* S, int lds, double* Bq, int r, double* sm
 #pragma unroll
                     for (int c2 = 0; c2 < c; c2++) x[c] = fma(-x[c2], W[c + c2 * n], x[c]);
                     x[c] *= rinv[J + c];
-                    S[J + i + (long long)(J + c) * lds] = x[c];
+                    S[bidx<TR>(J + i, J + c, lds)] = x[c];
                 }
             }
         }
         for (int e = tid; e < nb * nb; e += T) {
             const int c = e / nb, i = e - c * nb;
-            if (i >= c) S[J + i + (long long)(J + c) * lds] = W[i + c * n];
+            if (i >= c) S[bidx<TR>(J + i, J + c, lds)] = W[i + c * n];
         }
         if (warp == (T >> 5) - 1) {
             // Y(J:J+nb, :) = L_JJ^{-1} (rows J..J+nb), column-oriented by the last warp: step c
@@ -264,7 +279,7 @@ __device__ int big_core(int n, double* S, int lds, double* Bq, int r, double* sm
             for (int s = 0; s < NS; s++) {
                 const int i = lane + 32 * s;
                 xr[s] = (i < n) ? y[i] : 0.0;
-                ln[s] = (i < n - 1) ? S[n - 1 + (long long)i * lds] : 0.0;
+                ln[s] = (i < n - 1) ? S[bidx<TR>(n - 1, i, lds)] : 0.0;
             }
 #pragma unroll
             for (int s = NS - 1; s >= 0; s--) {
@@ -276,7 +291,7 @@ __device__ int big_core(int n, double* S, int lds, double* Bq, int r, double* sm
                     for (int s2 = 0; s2 <= s; s2++) {
                         const int i = lane + 32 * s2;
                         lc[s2] = ln[s2];
-                        ln[s2] = (i < j - 1) ? S[j - 1 + (long long)i * lds] : 0.0;
+                        ln[s2] = (i < j - 1) ? S[bidx<TR>(j - 1, i, lds)] : 0.0;
                     }
                     const double xj = __shfl_sync(0xffffffffu, xr[s], lj) * rinv[j];
                     if (lane == lj) xr[s] = xj;
@@ -298,7 +313,7 @@ __device__ int big_core(int n, double* S, int lds, double* Bq, int r, double* sm
 
 __device__ void big_problem(const RaggedParams& p, int q, double* sm) {
     const int n = p.n[q];
-    const int fail = big_core(n, p.S + p.offS[q], n, p.B + p.offB[q], p.nrhs, sm);
+    const int fail = big_core<false>(n, p.S + p.offS[q], n, p.B + p.offB[q], p.nrhs, sm);
     if (threadIdx.x == 0 && p.info) p.info[p.orig[q]] = fail;
 }
 
@@ -331,24 +346,29 @@ __device__ void lane_problem(const RaggedParams& p, int q) {
 // warp issues one FP64 instruction every 64 cycles, so the lane kernels need ~20,000
 // problems): the BIG items' left-looking Cholesky, one problem per CTA, any leading
 // dimension, no right-hand sides.  CTAs stride over the batch.
+template <bool TR>
 __global__ void __launch_bounds__(128, 6) dpotrf_cta_kernel(int n, MatRef A, int lda, long long batch, int* info) {
     extern __shared__ __align__(16) double sm_cta[];
     for (long long q = blockIdx.x; q < batch; q += gridDim.x) {
-        const int fail = big_core(n, A.mptr(q), lda, nullptr, 0, sm_cta);
+        const int fail = big_core<TR>(n, A.mptr(q), lda, nullptr, 0, sm_cta);
         if (threadIdx.x == 0 && info) info[q] = fail;
     }
 }
 
-cudaError_t launch_dpotrf_cta(int n, MatRef A, int lda, long long batch, int* info, cudaStream_t s) {
+cudaError_t launch_dpotrf_cta(int n, MatRef A, int lda, long long batch, int* info, cudaStream_t s, int upper) {
     const int T = 128;
     const size_t smem = sizeof(double) * ((size_t)(BF_BIG_NB + 1) * n + 16 * (size_t)T);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(dpotrf_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = upper ? cudaFuncSetAttribute(dpotrf_cta_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)smem)
+                              : cudaFuncSetAttribute(dpotrf_cta_kernel<false>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     const long long cap = kSMs * 16;
     const unsigned grid = (unsigned)(batch < cap ? batch : cap);
-    dpotrf_cta_kernel<<<grid, T, smem, s>>>(n, A, lda, batch, info);
+    if (upper) dpotrf_cta_kernel<true><<<grid, T, smem, s>>>(n, A, lda, batch, info);
+    else dpotrf_cta_kernel<false><<<grid, T, smem, s>>>(n, A, lda, batch, info);
     count_launch();
     return cudaGetLastError();
 }
@@ -365,48 +385,57 @@ __device__ __forceinline__ int vpotrf_check(int n, int lda, int max_n) {
     return 0;
 }
 
+template <bool TR>
 __global__ void __launch_bounds__(128) dpotrf_vbatched_lane_kernel(const int* n, double* const* A, const int* lda,
                                                                  int* info, long long batch, int max_n) {
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= batch) return;
     const int nq = n[q], ldq = lda[q];
     int r = vpotrf_check(nq, ldq, max_n);
-    if (r == 0 && nq > 0) r = potrf_lane_global<4, 2>(A[q], ldq, nq);
+    if (r == 0 && nq > 0)
+        r = TR ? potrf_lane<4, 2>(GAccT{A[q], ldq}, nq) : potrf_lane_global<4, 2>(A[q], ldq, nq);
     if (info) info[q] = r;
 }
 
+template <bool TR>
 __global__ void __launch_bounds__(128, 6) dpotrf_vbatched_cta_kernel(const int* n, double* const* A, const int* lda,
                                                                 int* info, long long batch, int max_n) {
     extern __shared__ __align__(16) double sm_v[];
     for (long long q = blockIdx.x; q < batch; q += gridDim.x) {
         const int nq = n[q], ldq = lda[q];
         int r = vpotrf_check(nq, ldq, max_n);  // the same in every thread
-        if (r == 0 && nq > 0) r = big_core(nq, A[q], ldq, nullptr, 0, sm_v);
+        if (r == 0 && nq > 0) r = big_core<TR>(nq, A[q], ldq, nullptr, 0, sm_v);
         if (threadIdx.x == 0 && info) info[q] = r;
     }
 }
 
 cudaError_t launch_dpotrf_vbatched(const int* n, double* const* A, const int* lda, int* info, long long batch,
-                                   int max_n, cudaStream_t s) {
+                                   int max_n, cudaStream_t s, int upper) {
     if (batch == 0) return cudaSuccess;
     if (max_n <= 32) {  // one problem per thread; small batches in smaller CTAs, over every SM
         const int T = spread_block(batch, 128);
-        dpotrf_vbatched_lane_kernel<<<(unsigned)((batch + T - 1) / T), T, 0, s>>>(n, A, lda, info, batch, max_n);
+        const unsigned blocks = (unsigned)((batch + T - 1) / T);
+        if (upper) dpotrf_vbatched_lane_kernel<true><<<blocks, T, 0, s>>>(n, A, lda, info, batch, max_n);
+        else dpotrf_vbatched_lane_kernel<false><<<blocks, T, 0, s>>>(n, A, lda, info, batch, max_n);
         count_launch();
         return cudaGetLastError();
     }
     const int T = 128;
     const size_t smem = sizeof(double) * ((size_t)(BF_BIG_NB + 1) * max_n + 16 * (size_t)T);
     if (smem > 48 * 1024) {
-        cudaError_t e =
-            cudaFuncSetAttribute(dpotrf_vbatched_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = upper ? cudaFuncSetAttribute(dpotrf_vbatched_cta_kernel<true>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                              : cudaFuncSetAttribute(dpotrf_vbatched_cta_kernel<false>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     // one CTA per problem: the orders differ, so a fixed share of the batch per CTA (a
     // grid-stride loop) leaves the SMs unequal work; CTAs issued as SM slots free up balance
     // it (200,000 problems, n log-uniform in [2, 200]: 716 -> 819 GFLOP/s on GB300)
     const long long cap = 0x7fffffffLL;
-    dpotrf_vbatched_cta_kernel<<<(unsigned)(batch < cap ? batch : cap), T, smem, s>>>(n, A, lda, info, batch, max_n);
+    const unsigned grid = (unsigned)(batch < cap ? batch : cap);
+    if (upper) dpotrf_vbatched_cta_kernel<true><<<grid, T, smem, s>>>(n, A, lda, info, batch, max_n);
+    else dpotrf_vbatched_cta_kernel<false><<<grid, T, smem, s>>>(n, A, lda, info, batch, max_n);
     count_launch();
     return cudaGetLastError();
 }

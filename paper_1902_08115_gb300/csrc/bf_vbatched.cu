@@ -240,6 +240,74 @@ __global__ void __launch_bounds__(128) dtrsm_vbatched_kernel(VTrsmParams p) {
     }
 }
 
+// ------------------------------------------------------------------------------------ dpotrs
+// Solve A X = B with the Cholesky factor of A (section 3.1 "dpotrf" and "dtrsm"): 'L' L Y = B then
+// L^T X = Y; 'U' U^T Y = B then U X = Y.  One thread per (problem, right-hand side), both
+// substitutions in the one launch, x overwriting b column by column.
+struct VPotrsParams {
+    int upper;
+    const int *n, *nrhs;
+    const double* const* A;
+    const int* lda;
+    double* const* B;
+    const int* ldb;
+    int* dinfo;
+    long long batch;
+    int max_n, max_nrhs;
+};
+
+__device__ __forceinline__ int vpotrs_check(const VPotrsParams& p, long long q, int n, int r) {
+    if (n < 0 || n > p.max_n) return -2;
+    if (r < 0 || r > p.max_nrhs) return -3;
+    if (p.lda[q] < (n > 1 ? n : 1)) return -5;
+    if (p.ldb[q] < (n > 1 ? n : 1)) return -7;
+    if (n > 0 && r > 0 && !p.A[q]) return -4;
+    if (n > 0 && r > 0 && !p.B[q]) return -6;
+    return 0;
+}
+
+__global__ void __launch_bounds__(128) dpotrs_vbatched_kernel(VPotrsParams p) {
+    const int vmax = p.max_nrhs > 0 ? p.max_nrhs : 1;
+    const long long total = p.batch * (long long)vmax;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long q = g / vmax;
+        const int c = (int)(g - q * vmax);
+        const int n = p.n[q], r = p.nrhs[q];
+        const int bad = vpotrs_check(p, q, n, r);
+        if (c == 0 && p.dinfo) p.dinfo[q] = bad;
+        if (bad || c >= r || n == 0) continue;
+        const int lda = p.lda[q];
+        const double* A = p.A[q];
+        double* x = p.B[q] + (long long)c * p.ldb[q];
+        // F(i, j) = the lower factor's (i, j), i >= j: L(i, j), or U(j, i) for 'U'
+        auto F = [&](int i, int j) -> double {
+            return p.upper ? ldg(A + j + (long long)i * lda) : ldg(A + i + (long long)j * lda);
+        };
+        for (int j = 0; j < n; j++) {  // forward: F y = b
+            double s = x[j];
+            for (int f = 0; f < j; f++) s = fma(-F(j, f), x[f], s);
+            x[j] = s / F(j, j);
+        }
+        for (int j = n - 1; j >= 0; j--) {  // backward: F^T x = y
+            double s = x[j];
+            for (int f = j + 1; f < n; f++) s = fma(-F(f, j), x[f], s);
+            x[j] = s / F(j, j);
+        }
+    }
+}
+
+cudaError_t launch_dpotrs_vbatched(const VPotrsParams& p, cudaStream_t s) {
+    if (p.batch == 0) return cudaSuccess;
+    const long long total = p.batch * (long long)(p.max_nrhs > 0 ? p.max_nrhs : 1);
+    const int T = spread_block(total, 128);
+    long long blocks = (total + T - 1) / T;
+    if (blocks > kSMs * 64) blocks = kSMs * 64;
+    dpotrs_vbatched_kernel<<<(unsigned)blocks, T, 0, s>>>(p);
+    count_launch();
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------------------ launchers
 cudaError_t launch_dgemm_vbatched(bool ta, bool tb, const VGemmParams& p0, cudaStream_t s) {
     if (p0.batch == 0) return cudaSuccess;
@@ -347,10 +415,31 @@ extern "C" int bf_dpotrf_vbatched(char uplo, const int* n, double* const* Aarray
     if (!lower && !upper) return -1;
     if (batch < 0) return -6;
     if (max_n < 0) return -7;
-    if (upper || max_n > BF_VBATCHED_POTRF_NMAX) return BF_ERR_NOT_SUPPORTED;
+    if (max_n > BF_VBATCHED_POTRF_NMAX) return BF_ERR_NOT_SUPPORTED;
     if (batch == 0) return BF_SUCCESS;
     if (!n) return -2;
     if (!Aarray) return -3;
     if (!lda) return -4;
-    return vb_status(launch_dpotrf_vbatched(n, Aarray, lda, info, batch, max_n, (cudaStream_t)stream));
+    return vb_status(launch_dpotrf_vbatched(n, Aarray, lda, info, batch, max_n, (cudaStream_t)stream, upper ? 1 : 0));
+}
+
+extern "C" int bf_dpotrs_vbatched(char uplo, const int* n, const int* nrhs, const double* const* Aarray,
+                                  const int* lda, double* const* Barray, const int* ldb, int batch, int max_n,
+                                  int max_nrhs, int* dinfo, bf_stream_t stream) {
+    const bool lower = uplo == 'L' || uplo == 'l', upper = uplo == 'U' || uplo == 'u';
+    if (!lower && !upper) return -1;
+    if (batch < 0) return -8;
+    if (max_n < 0) return -9;
+    if (max_nrhs < 0) return -10;
+    if (batch == 0) return BF_SUCCESS;
+    if (!n) return -2;
+    if (!nrhs) return -3;
+    if (!Aarray) return -4;
+    if (!lda) return -5;
+    if (!Barray) return -6;
+    if (!ldb) return -7;
+    VPotrsParams p{};
+    p.upper = upper; p.n = n; p.nrhs = nrhs; p.A = Aarray; p.lda = lda; p.B = Barray; p.ldb = ldb;
+    p.dinfo = dinfo; p.batch = batch; p.max_n = max_n; p.max_nrhs = max_nrhs;
+    return vb_status(launch_dpotrs_vbatched(p, (cudaStream_t)stream));
 }

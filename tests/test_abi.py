@@ -226,7 +226,8 @@ def test_dsposv_and_backward_arguments(lib):
     assert f(b"L", 0, 1, None, 1, 0, None, 1, 0, None, 1, 0, None, None, 1e-12, 30, None, 0, 1, None) == 0
     g = lib.bf_dpotrf_backward_strided_batched
     assert g(b"L", 4, 1, 3, 16, 1, 4, 16, 1, 4, 16, 1, None) == -4
-    assert g(b"U", 4, 1, 4, 16, 1, 4, 16, 1, 4, 16, 1, None) == lib.ERR_NOT_SUPPORTED
+    assert g(b"X", 4, 1, 4, 16, 1, 4, 16, 1, 4, 16, 1, None) == -1
+    assert g(b"U", 4, 1, 4, 16, 1, 4, 16, 1, 4, 16, 0, None) == 0  # upper supported; empty batch
     h = lib.bf_dtrsm_backward_strided_batched
     assert h(b"R", b"L", b"T", b"N", 4, 4, 0.0, 1, 4, 16, 1, 4, 16, 1, 4, 16, None, 4, 0, 1, None) == -7
     k = lib.bf_dgemm_backward_strided_batched
@@ -271,7 +272,7 @@ def test_vbatched_illegal_call_arguments(lib):
     assert p(b"X", 1, 1, 1, NULL, 1, 4, NULL) == -1
     assert p(b"L", 1, 1, 1, NULL, -1, 4, NULL) == -6
     assert p(b"L", 1, 1, 1, NULL, 1, -1, NULL) == -7
-    assert p(b"U", 1, 1, 1, NULL, 1, 4, NULL) == lib.ERR_NOT_SUPPORTED
+    assert p(b"U", 1, 1, 1, NULL, 0, 4, NULL) == 0  # upper is supported; an empty batch returns at once
     assert p(b"L", 1, 1, 1, NULL, 1, 1025, NULL) == lib.ERR_NOT_SUPPORTED
     assert p(b"L", NULL, 1, 1, NULL, 1, 4, NULL) == -2
     assert p(b"L", 1, 1, 1, NULL, 0, 4, NULL) == 0

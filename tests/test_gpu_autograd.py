@@ -194,3 +194,31 @@ def test_cholesky_failure_poisons_factor_and_gradient(bf, ag):
     L2.backward(gpu(Lb[ok]))
     assert normwise(host(L2.detach()), Lh[ok], n) <= 1e-13
     assert rel(host(St2.grad), G[ok]) <= 1e-13
+
+
+@pytest.mark.parametrize("n", [1, 5, 32, 33])
+def test_dpotrf_backward_upper(bf, oracle, n):
+    """uplo 'U' of the Cholesky adjoint through the C ABI: A = U^T U with U and Ubar in upper
+    triangles; the symmetric gradient must equal the lower one of L = U^T, Lbar = Ubar^T (the
+    oracle's reverse mode, converted as in test_dpotrf_backward)."""
+    import ctypes
+    batch = 4
+    S = bfsynth.spd_batch(batch, n, n, 40 + n).numpy()
+    Uo, info = oracle.dpotrf_u(S, n=n)
+    assert (info == 0).all()
+    Ub = np.ascontiguousarray(np.tril(bfsynth.randn_batch(batch, n, n, n, 41).numpy()))  # upper in (j, i)
+    Ug, Ubg = gpu(Uo), gpu(Ub)
+    G = torch.zeros(batch, n, n, dtype=torch.float64, device="cuda")
+    vp = ctypes.c_void_p
+    r = bf.bf_dpotrf_backward_strided_batched(b"U", n, vp(Ug.data_ptr()), n, n * n, vp(Ubg.data_ptr()), n, n * n,
+                                              vp(G.data_ptr()), n, n * n, batch, bf._stream())
+    assert r == 0
+    G = host(G)
+    for q in range(batch):
+        L = np.ascontiguousarray(Uo[q].T)      # lower factor, (ncols, ld) layout
+        Lb = np.ascontiguousarray(Ub[q].T)     # its adjoint, lower
+        ref = oracle.dpotrf_l_adjoint(L, Lb)
+        Gq = G[q]
+        conv = np.where(np.arange(n)[None, :] > np.arange(n)[:, None], 2 * Gq, 0.0) + np.diag(np.diag(Gq))
+        assert rel(conv, ref) <= 1e-12
+        assert rel(Gq, Gq.T) <= 1e-15

@@ -254,7 +254,7 @@ def test_dtrmm_integer_bit_exact_and_alpha_zero(bf, oracle, side):
 # ----------------------------------------------------------------------------- dpotrf / dpotrs upper
 POTRF_U = [("direct4", 0, 64, 0, 4, 2), ("direct8", 0, 64, 0, 8, 2), ("packed", 1, 64, 0, 0, 0),
            ("blocked8", 2, 0, 8, 0, 0), ("blocked32", 2, 0, 32, 0, 0),
-           ("cta_falls_back", 4, 0, 0, 0, 0),  # one problem per CTA is lower only
+           ("cta", 4, 0, 0, 0, 0),
            ("team2", 5, 64, 0, 2, 0), ("team4", 5, 0, 0, 4, 0), ("group", 6, 0, 0, 0, 0)]
 
 
@@ -346,6 +346,28 @@ def test_dgetrf_singular_and_permutation(bf, oracle, vname, variant, n):
     assert info[1] == 5 and info[3] == 1 and info[2] == 0 and info[0] == n - 2
     np.testing.assert_array_equal(host(pg), piv)
     np.testing.assert_array_equal(host(Ag)[2], LU[2])  # integer-exact: no rounding happens
+
+
+@pytest.mark.parametrize("m,n", [(7, 3), (3, 7), (33, 17), (17, 33), (1, 5), (5, 1), (100, 20), (20, 100),
+                                 (300, 64), (64, 300), (1024, 16)])
+def test_dgetrf_rectangular(bf, oracle, m, n):
+    """m x n LU (one problem per CTA): pivots identical to the oracle's, factors within the
+    tolerance, padding rows untouched; failures (a zero column) reported as the oracle does."""
+    batch = 5
+    A = np.full((batch, n, m + 3), np.nan)
+    A[:, :, :m] = rnd((batch, n, m), 600 + m + n)
+    A[2, min(n, m) // 2, :m] = 0.0  # problem 2: a zero column inside the factored part
+    LU, piv, info = oracle.dgetrf(A, m=m, n=n)
+    Ag = gpu(A)
+    pg, ig = bf.dgetrf(Ag, m=m, n=n)
+    pg, ig, out = host(pg), host(ig), host(Ag)
+    assert pg.shape == (batch, min(m, n))
+    np.testing.assert_array_equal(ig, info)
+    assert info[2] == min(n, m) // 2 + 1
+    np.testing.assert_array_equal(pg, piv)
+    ok = info == 0
+    assert normwise(out[ok], LU[ok], m) <= TOL
+    assert np.isnan(out[:, :, m:]).all()
 
 
 @pytest.mark.parametrize("trans", "NT")

@@ -1,4 +1,4 @@
-"""GPU parity of the variable-size ("vbatched") dgemm, dtrsm and dpotrf against the oracle.
+"""GPU parity of the variable-size ("vbatched") dgemm, dtrsm, dpotrf and dpotrs against the oracle.
 
 Each batch mixes problems of different sizes (zero sizes and padded leading dimensions
 included); every problem is compared with the oracle run on that problem alone, normwise
@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 import torch
 
+import bfsynth
 from bfhelp import gpu, host, lower_part, normwise
 
 pytestmark = pytest.mark.gpu
@@ -143,8 +144,9 @@ def spd(rng, n, pad):
     return S
 
 
+@pytest.mark.parametrize("uplo", "LU")
 @pytest.mark.parametrize("nmax", [12, 32, 100, 300])
-def test_dpotrf_vbatched(bf, oracle, nmax):
+def test_dpotrf_vbatched(bf, oracle, nmax, uplo):
     rng = np.random.default_rng(nmax)
     batch = 23 if nmax <= 100 else 9
     ns = list(rng.integers(0, nmax + 1, batch))
@@ -157,9 +159,13 @@ def test_dpotrf_vbatched(bf, oracle, nmax):
     bad = 4  # illegal: lda < n
     ns[bad] = min(nmax, 5)
     As[bad] = np.full((ns[bad], ns[bad] - 1), 1.0)
+    if uplo == "U":  # the same matrices with the upper triangle stored, the strict lower one NaN
+        for q, n in enumerate(ns):
+            if q != bad:
+                As[q][:n, :n] = As[q][:n, :n].T.copy()
     Abad = As[bad].copy()
     Ag = [gpu(x) for x in As]
-    info = host(bf.dpotrf_vbatched(Ag, ns))
+    info = host(bf.dpotrf_vbatched(Ag, ns, uplo=uplo))
     assert info[bad] == -4
     np.testing.assert_array_equal(host(Ag[bad]), Abad)
     for q in range(batch):
@@ -170,23 +176,94 @@ def test_dpotrf_vbatched(bf, oracle, nmax):
         if n == 0:
             assert info[q] == 0
             continue
-        L, inf_o = oracle.dpotrf_l(np.nan_to_num(As[q], nan=0.0)[None], n)
-        assert info[q] == inf_o[0], q
-        if inf_o[0] == 0:
-            assert normwise(lower_part(out[None], n), lower_part(L, n), n) <= TOL, q
-        for j in range(n):
-            assert np.isnan(out[j, :j]).all()  # upper triangle untouched
+        if uplo == "L":
+            L, inf_o = oracle.dpotrf_l(np.nan_to_num(As[q], nan=0.0)[None], n)
+            assert info[q] == inf_o[0], q
+            if inf_o[0] == 0:
+                assert normwise(lower_part(out[None], n), lower_part(L, n), n) <= TOL, q
+            for j in range(n):
+                assert np.isnan(out[j, :j]).all()  # upper triangle untouched
+        else:
+            U, inf_o = oracle.dpotrf_u(np.nan_to_num(As[q], nan=0.0)[None], n=n)
+            assert info[q] == inf_o[0], q
+            if inf_o[0] == 0:  # U^T in (ncols, ld) layout is lower: compare as lower parts
+                ut = np.ascontiguousarray(np.transpose(out[None, :n, :n], (0, 2, 1)))
+                ur = np.ascontiguousarray(np.transpose(U[:, :n, :n], (0, 2, 1)))
+                assert normwise(lower_part(ut, n), lower_part(ur, n), n) <= TOL, q
+            for j in range(n):
+                assert np.isnan(out[j, j + 1:n]).all()  # strict lower triangle untouched
         assert np.isnan(out[:, n:]).all()
 
 
 def test_vbatched_call_arguments(bf):
     z = torch.zeros(1, 1, dtype=torch.float64, device="cuda")
     with pytest.raises(bf.BFError) as e:
-        bf.dpotrf_vbatched([z], [1], uplo="U")
+        bf.dpotrf_vbatched([z], [1025])
     assert e.value.status == bf.ERR_NOT_SUPPORTED
+    with pytest.raises(bf.BFError) as e:
+        bf.dpotrf_vbatched([z], [1], uplo="X")
+    assert e.value.status == -1
     with pytest.raises(bf.BFError) as e:
         bf.dtrsm_vbatched("X", "L", "N", "N", 1.0, [z], [z], [1], [1])
     assert e.value.status == -1
     with pytest.raises(bf.BFError) as e:
         bf.dgemm_vbatched("N", "Q", 1.0, [z], [z], 0.0, [z], [1], [1], [1])
     assert e.value.status == -2
+
+
+@pytest.mark.parametrize("uplo", "LU")
+def test_dpotrs_vbatched_and_batched(bf, oracle, uplo):
+    """Variable-size dpotrs (orders 0..70, 0..5 right-hand sides, padded leading dimensions) and
+    the pointer-array dpotrs of a uniform batch, each against the oracle's dpotrs on the factor;
+    an illegal problem is skipped with its dinfo and left untouched."""
+    import ctypes
+    rng = np.random.default_rng(77)
+    batch = 25
+    ns = [int(x) for x in rng.integers(0, 71, batch)]
+    rs = [int(x) for x in rng.integers(0, 6, batch)]
+    ns[0], rs[0] = 70, 5
+    Ls, Bs, refs = [], [], []
+    for q in range(batch):
+        n, r = ns[q], rs[q]
+        S = bfsynth.spd_batch(1, max(n, 1), max(n, 1) + q % 3, 900 + q).numpy()
+        L, info = oracle.dpotrf_l(S, n)
+        B = np.full((max(r, 1), max(n, 1) + (q + 1) % 2), np.nan)
+        B[:r, :n] = rng.standard_normal((r, n))
+        refs.append(oracle.dpotrs_l(L, B[None], n, r)[0] if n and r else B.copy())
+        Lf = L[0]
+        if uplo == "U":  # the same factor as U = L^T in the upper triangle
+            Lf = Lf.copy()
+            Lf[:n, :n] = Lf[:n, :n].T
+        Ls.append(Lf)
+        Bs.append(B)
+    bad = 3
+    ns[bad], rs[bad] = 4, 2
+    Ls[bad] = np.ones((4, 3))  # lda 3 < n
+    Bs[bad] = np.ones((2, 4))
+    Lg, Bg = [gpu(x) for x in Ls], [gpu(x) for x in Bs]
+    dinfo = host(bf.dpotrs_vbatched(Lg, Bg, ns, rs, uplo=uplo))
+    assert dinfo[bad] == -5 and (np.delete(dinfo, bad) == 0).all()
+    np.testing.assert_array_equal(host(Bg[bad]), Bs[bad])
+    for q in range(batch):
+        if q == bad or not (ns[q] and rs[q]):
+            continue
+        n, r = ns[q], rs[q]
+        assert normwise(host(Bg[q])[None, :r, :n], refs[q][None, :r, :n], n) <= TOL, q
+    # pointer-array dpotrs, uniform n = 19, 3 right-hand sides
+    n, r, b = 19, 3, 6
+    S = bfsynth.spd_batch(b, n, n + 1, 950).numpy()
+    L, _ = oracle.dpotrf_l(S, n)
+    B = bfsynth.randn_batch(b, n, r, n + 2, 951).numpy()
+    ref = oracle.dpotrs_l(L, B, n, r)
+    Lu = L.copy()
+    if uplo == "U":
+        for q in range(b):
+            Lu[q, :n, :n] = L[q, :n, :n].T
+    Lgs, Bgs = [gpu(Lu[q]) for q in range(b)], [gpu(B[q]) for q in range(b)]
+    pa = torch.tensor([t.data_ptr() for t in Lgs], dtype=torch.int64, device="cuda")
+    pb = torch.tensor([t.data_ptr() for t in Bgs], dtype=torch.int64, device="cuda")
+    vp = ctypes.c_void_p
+    assert bf.bf_dpotrs_batched(uplo.encode(), n, r, vp(pa.data_ptr()), n + 1, vp(pb.data_ptr()), n + 2, b,
+                                bf._stream()) == 0
+    got = np.stack([host(t) for t in Bgs])
+    assert normwise(got, ref, n) <= TOL

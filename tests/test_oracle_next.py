@@ -281,3 +281,27 @@ def test_riccati_zero_dynamics(oracle):
     F, info = oracle.riccati(BAt, np.transpose(RSQ, (0, 2, 1))[None].copy(), QN.T[None].copy(), nx, nu)
     for s in range(N):
         np.testing.assert_allclose(np.tril(F[0, s].T), np.linalg.cholesky(RSQ[s]), rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("m,n", [(7, 3), (3, 7), (33, 17), (17, 33), (1, 5), (5, 1), (40, 40)])
+def test_dgetrf_rectangular(oracle, m, n):
+    """m x n LU (section 3.1 "dgetrf" is an m x n routine): pivots identical to LAPACK's (scipy's
+    lu_factor), factors within rounding, and P A = L U with L m x min(m, n) unit lower
+    trapezoidal, U min(m, n) x n upper trapezoidal, |l_ij| <= 1; padding rows untouched."""
+    sl = pytest.importorskip("scipy.linalg")
+    A = rng.standard_normal((m, n))
+    k = min(m, n)
+    LU, ipiv, info = oracle.dgetrf(cm(A, m + 3), m=m, n=n)
+    assert info[0] == 0 and ipiv.shape == (1, k)
+    assert np.isnan(LU[0, :, m:]).all()
+    lu_ref, piv_ref = sl.lu_factor(A)
+    np.testing.assert_array_equal(ipiv[0], piv_ref + 1)
+    F = dense(LU, m)
+    assert np.abs(F - lu_ref).max() <= 1e-12 * max(1.0, np.abs(lu_ref).max())
+    L = np.tril(F[:, :k], -1) + np.eye(m, k)
+    U = np.triu(F[:k, :])
+    PA = A.copy()
+    for j, p in enumerate(ipiv[0] - 1):
+        PA[[j, p]] = PA[[p, j]]
+    assert np.abs(PA - L @ U).max() <= 1e-13 * np.abs(A).max() * max(m, n)
+    assert (np.abs(L) <= 1.0).all()
