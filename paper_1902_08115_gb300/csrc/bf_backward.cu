@@ -80,22 +80,47 @@ phi_ltlbar_kernel(int n, MatRef L, int ldl, MatRef Lb, int ldlb, MatRef O, int l
     }
 }
 
-// G = (S + S^T) / 2 in place (problem index fastest).
-__global__ void __launch_bounds__(256) symmetrize_kernel(int n, MatRef S, int lds, long long batch) {
-    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long npair = (long long)n * (n - 1) / 2;
-    if (gt >= npair * batch) return;
-    const long long q = gt % batch;
-    const int t = (int)(gt / batch);
-    // pair t -> (i, j), i > j, row by row of the strict lower triangle
-    int i = (int)((sqrtf(8.0f * t + 1.0f) + 1.0f) * 0.5f);
-    while (i * (i - 1) / 2 > t) i--;
-    while ((i + 1) * i / 2 <= t) i++;
-    const int j = t - i * (i - 1) / 2;
-    double* s = S.mptr(q);
-    const double g = 0.5 * (s[i + (long long)j * lds] + s[j + (long long)i * lds]);
-    s[i + (long long)j * lds] = g;
-    s[j + (long long)i * lds] = g;
+// G = (S + S^T) / 2 in place: one CTA of 32 x 8 threads per (problem, pair of 32 x 32 tiles
+// (bi, bj), bi >= bj).  Both tiles are read coalesced (consecutive threads, consecutive rows)
+// into shared memory, averaged with the transpose there, and written back coalesced; a diagonal
+// tile pairs with itself.  The same value goes to (i, j) and (j, i), so G is exactly symmetric.
+__global__ void __launch_bounds__(256) symmetrize_kernel(int n, MatRef S, int lds, long long batch, int nt) {
+    __shared__ double ta[32][33], tb[32][33];
+    const long long pairs = (long long)nt * (nt + 1) / 2;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (long long w = blockIdx.x; w < pairs * batch; w += gridDim.x) {
+        const long long q = w / pairs;
+        const int t = (int)(w - q * pairs);
+        int bi = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+        while ((bi + 1) * (bi + 2) / 2 <= t) bi++;
+        while (bi * (bi + 1) / 2 > t) bi--;
+        const int bj = t - bi * (bi + 1) / 2;
+        double* s = S.mptr(q);
+        const int r0 = 32 * bi, c0 = 32 * bj;  // tile A: rows r0.., columns c0..; tile B its mirror
+        __syncthreads();
+        for (int c = ty; c < 32; c += 8) {
+            const int i = r0 + tx, j = c0 + c;
+            ta[c][tx] = (i < n && j < n) ? s[i + (long long)j * lds] : 0.0;  // ta[c][r] = A(r0+r, c0+c)
+            const int i2 = c0 + tx, j2 = r0 + c;
+            tb[c][tx] = (i2 < n && j2 < n) ? s[i2 + (long long)j2 * lds] : 0.0;  // tb[c][r] = S(c0+r, r0+c)
+        }
+        __syncthreads();
+        for (int c = ty; c < 32; c += 8) {
+            // A(r0+tx, c0+c) and its mirror S(c0+c, r0+tx) = tb[tx][c]
+            const double g = 0.5 * (ta[c][tx] + tb[tx][c]);
+            const int i = r0 + tx, j = c0 + c;
+            if (i < n && j < n) s[i + (long long)j * lds] = g;
+        }
+        __syncthreads();
+        if (bi != bj) {
+            for (int c = ty; c < 32; c += 8) {
+                // S(c0+tx, r0+c) = the average of A(r0+c, c0+tx) and itself's mirror
+                const double g = 0.5 * (tb[c][tx] + ta[tx][c]);
+                const int i = c0 + tx, j = r0 + c;
+                if (i < n && j < n) s[i + (long long)j * lds] = g;
+            }
+        }
+    }
 }
 
 // Y = beta X (X and Y m x n, may alias)
@@ -125,15 +150,16 @@ static cudaError_t launch_scal_copy(int m, int n, double beta, MatRef X, int ldx
 
 // Tidy a factored batch: the strict triangle opposite the factor (upper = 0: the strict upper
 // one) is set to zero, and every entry of the n x n of a problem whose info is nonzero is set to
-// NaN, so that a failed factorisation cannot pass on as a finite factor.  Problem index fastest.
+// NaN, so that a failed factorisation cannot pass on as a finite factor.  Element index fastest
+// within a problem (consecutive threads, consecutive rows of a column: coalesced).
 __global__ void __launch_bounds__(256)
 dtrfill_kernel(int n, int upper, double* A, int lda, long long stride, const int* info, long long batch) {
     const long long per = (long long)n * n;
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per * batch;
          e += (long long)gridDim.x * blockDim.x) {
-        const long long r = e / batch;
-        const long long q = e - r * batch;
+        const long long q = e / per;
+        const long long r = e - q * per;
         const int j = (int)(r / n), i = (int)(r - (long long)j * n);
         double* a = A + q * stride + i + (long long)j * lda;
         if (info && info[q] != 0) {
@@ -164,8 +190,10 @@ cudaError_t launch_dpotrf_backward(int n, MatRef L, int ldl, MatRef Lb, int ldlb
     e = launch_dtrsm(1, upper, tr2, 0, n, n, 1.0, L, ldl, Ab, ldab, batch, c2, nullptr, s);
     if (e != cudaSuccess) return e;
     if (n > 1) {
-        long long pairs = (long long)n * (n - 1) / 2 * batch;
-        symmetrize_kernel<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(n, Ab, ldab, batch);
+        const int ntile = (n + 31) / 32;
+        const long long work = (long long)ntile * (ntile + 1) / 2 * batch;
+        const long long grid = work < kSMs * 16 ? work : kSMs * 16;
+        symmetrize_kernel<<<(unsigned)grid, 256, 0, s>>>(n, Ab, ldab, batch, ntile);
         count_launch();
         e = cudaGetLastError();
     }

@@ -125,16 +125,33 @@ __device__ int big_core(int n, double* S, int lds, double* Bq, int r, double* sm
         {
             const int nI = (m + 3) / 4, nK = (nb + 3) / 4;
             const int tiles = nI * nK - nK * (nK - 1) / 2;  // tiles on or below the diagonal block
+            // The last round: either every one of its rem tiles split sp ways, or whole warps of
+            // unsplit tiles and only the rem % 32 tiles that would leave a warp part-empty split
+            // over the remaining threads -- whichever leaves fewer idle lanes in issued FP64
+            // instructions (a warp's instruction costs the SM's FP64 unit a full slot whatever
+            // its active lanes, and its lanes all wait for its longest k range).
             const int full = tiles / T * T, rem = tiles - full;
-            const int sp = rem ? imax(1, imin(T / rem, J / 8)) : 1;
-            double* part = rinv + n;  // [sp][16][rem] partial sums, only when sp > 1
-            for (int u = tid; u < full + rem * sp; u += T) {
-                int t = u, z = 0;
-                if (u >= full) {
-                    z = (u - full) / rem;
-                    t = u - z * rem;
+            int unsplit = 0, tail = rem, sp = rem ? imax(1, imin(T / rem, J / 8)) : 1;
+            if (rem > 32 && (rem & 31)) {
+                const int t2 = rem & 31, sp2 = imax(1, imin((T - (rem - t2)) / t2, J / 8));
+                const int l1 = (rem * sp) & 31, l2 = (t2 * sp2) & 31;
+                const long long w1 = (long long)(l1 ? 32 - l1 : 0) * (J / sp);
+                const long long w2 = (long long)(l2 ? 32 - l2 : 0) * (J / sp2);
+                if (w2 < w1) {
+                    unsplit = rem - t2;
+                    tail = t2;
+                    sp = sp2;
                 }
-                const bool split = u >= full && sp > 1;
+            }
+            const int base = full + unsplit;  // the first split tile
+            double* part = rinv + n;          // [sp][16][tail] partial sums, only when sp > 1
+            for (int u = tid; u < base + tail * sp; u += T) {
+                int t = u, z = 0;
+                if (u >= base) {
+                    z = (u - base) / tail;
+                    t = u - z * tail;
+                }
+                const bool split = u >= base && sp > 1;
                 int K, I;
                 big_tile_index(t, nI, K, I);
                 const int i0 = J + 4 * I, k0 = J + 4 * K;
@@ -178,7 +195,7 @@ __device__ int big_core(int n, double* S, int lds, double* Bq, int r, double* sm
 #pragma unroll
                     for (int a = 0; a < 4; a++)
 #pragma unroll
-                        for (int b = 0; b < 4; b++) part[(z * 16 + a * 4 + b) * rem + (t - full)] = acc[a][b];
+                        for (int b = 0; b < 4; b++) part[(z * 16 + a * 4 + b) * tail + (t - base)] = acc[a][b];
                 }
             }
             for (int e = T - 1 - tid; e < nb * r; e += T) {  // the last threads, fewest tiles
@@ -189,14 +206,14 @@ __device__ int big_core(int n, double* S, int lds, double* Bq, int r, double* sm
             }
             if (sp > 1) {
                 __syncthreads();
-                for (int e = tid; e < 16 * rem; e += T) {
-                    const int ab = e / rem, tt = e - ab * rem;
+                for (int e = tid; e < 16 * tail; e += T) {
+                    const int ab = e / tail, tt = e - ab * tail;
                     int K, I;
-                    big_tile_index(full + tt, nI, K, I);
+                    big_tile_index(base + tt, nI, K, I);
                     const int c = 4 * K + (ab & 3), i = 4 * I + (ab >> 2);
                     if (c >= nb || i >= m) continue;
-                    double v = part[ab * rem + tt];
-                    for (int z = 1; z < sp; z++) v += part[(z * 16 + ab) * rem + tt];
+                    double v = part[ab * tail + tt];
+                    for (int z = 1; z < sp; z++) v += part[(z * 16 + ab) * tail + tt];
                     W[i + c * n] = v;
                 }
             }

@@ -6,6 +6,8 @@ switch then picks the form that batch gets).
     python -m paper_1902_08115_gb300.profcase dsposv      (2048 SPD systems of order 128)
     python -m paper_1902_08115_gb300.profcase ragged      (3000 orders in [100, 200], 4 RHS)
     python -m paper_1902_08115_gb300.profcase vbatched    (dgemm_nn, 40,000 problems, m, n, k in [1, 64])
+    python -m paper_1902_08115_gb300.profcase diff        (the differentiation workload's forward and
+                                                           backward, 16,384 problems of order 32)
 """
 from __future__ import annotations
 
@@ -29,6 +31,18 @@ def main(argv):
             bf.dsposv(A, b)
         torch.cuda.synchronize()
         print("ok dsposv")
+        return
+    if which == "diff":
+        from paper_1902_08115_gb300 import autograd as ag
+        Qd, J, B, W = bfsynth.diff_batch(16384, 32, 16, 8, seed=bfsynth.BASE_SEED, device="cuda")
+        ts = [x.clone().requires_grad_(True) for x in (Qd, J, B, W)]
+        for _ in range(3):
+            for t in ts:
+                t.grad = None
+            loss, _, _ = ag.spd_solve_loss(*ts)
+            loss.backward()
+        torch.cuda.synchronize()
+        print("ok diff")
         return
     if which == "vbatched":
         import ctypes
