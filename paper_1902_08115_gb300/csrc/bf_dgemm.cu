@@ -97,54 +97,102 @@ dgemm_tile_kernel(GemmParams p) {
         for (int k0 = 0; k0 < p.k; k0 += p.KC) {
             const int kc = imin(p.KC, p.k - k0);
             // ---- pack op(A)(i0:i0+TM, k0:k0+kc) of every problem, k-major ----
-            const int na = p.P * kc * p.TM;
-            for (int e = t; e < na; e += T) {
-                int qq, pp, ii;
-                if (!TA) {  // contiguous in i
-                    ii = e % p.TM;
-                    int rest = e / p.TM;
-                    pp = rest % kc;
-                    qq = rest / kc;
-                } else {  // contiguous in p
-                    pp = e % kc;
-                    int rest = e / kc;
-                    ii = rest % p.TM;
-                    qq = rest / p.TM;
+            // Each thread moves two elements that are consecutive in memory (along i for A, along
+            // p for A^T): one 16-byte load when the pair is in range and 16-byte aligned (even
+            // leading dimension, aligned base), else single words.  Consecutive threads take
+            // consecutive pairs: the warp reads 512 contiguous bytes.
+            {
+                const int ext = TA ? kc : p.TM;       // the contiguous extent
+                const int hp = (ext + 1) >> 1;        // pairs along it
+                const int np2 = p.P * hp * (TA ? p.TM : kc);
+                for (int e = t; e < np2; e += T) {
+                    const int h = e % hp;
+                    const int rest = e / hp;
+                    int qq, pp, ii;
+                    if (!TA) {  // pair (ii, ii+1) in column k0 + pp
+                        ii = 2 * h;
+                        pp = rest % kc;
+                        qq = rest / kc;
+                    } else {  // pair (pp, pp+1) of row i0 + ii
+                        pp = 2 * h;
+                        ii = rest % p.TM;
+                        qq = rest / p.TM;
+                    }
+                    const long long qg = g * p.P + qq;
+                    double v0 = 0.0, v1 = 0.0;
+                    const int gi = i0 + ii;
+                    // validity of the first and second element of the pair
+                    const bool in0 = qg < p.batch && gi < p.m && (TA ? pp < kc : true);
+                    const bool in1 = qg < p.batch && (TA ? (gi < p.m && pp + 1 < kc) : (gi + 1 < p.m && ii + 1 < p.TM));
+                    if (in0) {
+                        const double* Aq = p.A.ptr(qg);
+                        const double* src = TA ? Aq + (k0 + pp) + (long long)gi * p.lda
+                                               : Aq + gi + (long long)(k0 + pp) * p.lda;
+                        if (in1 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+                            const double2 w = ldg2(src);
+                            v0 = w.x;
+                            v1 = w.y;
+                        } else {
+                            v0 = ldg(src);
+                            if (in1) v1 = ldg(src + 1);
+                        }
+                    }
+                    double* dst = sA + qq * sAq;
+                    if (!TA) {
+                        dst[pp * p.TM + ii] = v0;
+                        if (ii + 1 < p.TM) dst[pp * p.TM + ii + 1] = v1;
+                    } else {
+                        if (pp < kc) dst[pp * p.TM + ii] = v0;
+                        if (pp + 1 < kc) dst[(pp + 1) * p.TM + ii] = v1;
+                    }
                 }
-                const long long qg = g * p.P + qq;
-                double v = 0.0;
-                const int gi = i0 + ii;
-                if (qg < p.batch && gi < p.m) {
-                    const double* Aq = p.A.ptr(qg);
-                    v = TA ? ldg(Aq + (k0 + pp) + (long long)gi * p.lda)
-                           : ldg(Aq + gi + (long long)(k0 + pp) * p.lda);
-                }
-                sA[qq * sAq + pp * p.TM + ii] = v;
             }
-            // ---- pack op(B)(k0:k0+kc, j0:j0+TN), k-major ----
-            const int nb = p.P * kc * p.TN;
-            for (int e = t; e < nb; e += T) {
-                int qq, pp, jj;
-                if (TB) {  // contiguous in j
-                    jj = e % p.TN;
-                    int rest = e / p.TN;
-                    pp = rest % kc;
-                    qq = rest / kc;
-                } else {  // contiguous in p
-                    pp = e % kc;
-                    int rest = e / kc;
-                    jj = rest % p.TN;
-                    qq = rest / p.TN;
+            // ---- pack op(B)(k0:k0+kc, j0:j0+TN), k-major, the same way (along j for B^T, along p
+            // for B) ----
+            {
+                const int ext = TB ? p.TN : kc;
+                const int hp = (ext + 1) >> 1;
+                const int np2 = p.P * hp * (TB ? kc : p.TN);
+                for (int e = t; e < np2; e += T) {
+                    const int h = e % hp;
+                    const int rest = e / hp;
+                    int qq, pp, jj;
+                    if (TB) {  // pair (jj, jj+1) in column k0 + pp of B^T's storage
+                        jj = 2 * h;
+                        pp = rest % kc;
+                        qq = rest / kc;
+                    } else {  // pair (pp, pp+1) of column j0 + jj
+                        pp = 2 * h;
+                        jj = rest % p.TN;
+                        qq = rest / p.TN;
+                    }
+                    const long long qg = g * p.P + qq;
+                    double v0 = 0.0, v1 = 0.0;
+                    const int gj = j0 + jj;
+                    const bool in0 = qg < p.batch && gj < p.n && (TB ? true : pp < kc);
+                    const bool in1 = qg < p.batch && (TB ? (gj + 1 < p.n && jj + 1 < p.TN) : (gj < p.n && pp + 1 < kc));
+                    if (in0) {
+                        const double* Bq = p.B.ptr(qg);
+                        const double* src = TB ? Bq + gj + (long long)(k0 + pp) * p.ldb
+                                               : Bq + (k0 + pp) + (long long)gj * p.ldb;
+                        if (in1 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+                            const double2 w = ldg2(src);
+                            v0 = w.x;
+                            v1 = w.y;
+                        } else {
+                            v0 = ldg(src);
+                            if (in1) v1 = ldg(src + 1);
+                        }
+                    }
+                    double* dst = sB + qq * sBq;
+                    if (TB) {
+                        dst[pp * p.TN + jj] = v0;
+                        if (jj + 1 < p.TN) dst[pp * p.TN + jj + 1] = v1;
+                    } else {
+                        if (pp < kc) dst[pp * p.TN + jj] = v0;
+                        if (pp + 1 < kc) dst[(pp + 1) * p.TN + jj] = v1;
+                    }
                 }
-                const long long qg = g * p.P + qq;
-                double v = 0.0;
-                const int gj = j0 + jj;
-                if (qg < p.batch && gj < p.n) {
-                    const double* Bq = p.B.ptr(qg);
-                    v = TB ? ldg(Bq + gj + (long long)(k0 + pp) * p.ldb)
-                           : ldg(Bq + (k0 + pp) + (long long)gj * p.ldb);
-                }
-                sB[qq * sBq + pp * p.TN + jj] = v;
             }
             __syncthreads();
             if (ql < p.P) {
