@@ -56,8 +56,10 @@ typedef struct CUstream_st* bf_stream_t; /* identical to cudaStream_t */
                              /* one problem per thread: dpotrf 'L' (n <= 256, left-looking */
                              /* by 16-column panels), dgetrf (n <= 1024, right-looking by  */
                              /* 16-column panels)                                         */
-#define BF_VARIANT_TEAM 5    /* dpotrf only: 2 or 4 lanes of a warp per problem (p2), for */
-                             /* batches between the CTA form's and the lane form's ranges */
+#define BF_VARIANT_TEAM 5    /* dpotrf: 2 or 4 lanes of a warp per problem (p2), for      */
+                             /* batches between the CTA form's and the lane form's ranges; */
+                             /* dgetrf (n <= 16): 4 lanes per problem, 8 problems of a    */
+                             /* warp in shared memory                                     */
 #define BF_VARIANT_GROUP 6   /* dpotrf only: a group of problems per CTA in shared memory, */
                              /* the unblocked recurrence element-parallel over the group  */
                              /* (small batches of small orders)                           */

@@ -329,6 +329,152 @@ __global__ void __launch_bounds__(128, 4) dgetrf_cta_kernel(GetrfParams p) {
     }
 }
 
+// ------------------------------------------------------------------ four lanes per problem, in shared memory
+// For orders up to kGetrfTeamMaxN.  The lane form above keeps each problem in global memory and
+// its pivoting steps (the search down a column, the interchange of two whole rows, the scale)
+// are one scattered access per lane per element: at n = 16 about 1,000 such accesses per problem
+// against 1,365 multiply-adds, which bounds it by the L1 request rate.  Here a warp stages eight
+// problems into shared memory with coalesced loads and factors each with a team of four lanes,
+// right-looking, column by column (section 3.1 "dgetrf": the unblocked recurrence):
+//   pivot    the first row of largest |a_ik|, i >= k (a NaN never counts as larger; a NaN in the
+//            diagonal itself keeps row k), found on the magnitudes' bit patterns (integer
+//            compares, no FP64 instruction) and reduced over the team with two shuffles
+//   swap     rows k and p across all n columns, four columns per lane (when the pivot is not 0)
+//   scale    l_ik = a_ik * (1 / a_kk) for i > k (when the pivot is not 0; else info = k + 1)
+//   update   a_ij -= l_ik a_kj for i, j > k, lane r taking rows k+1+r, k+5+r, ...
+// The operations on every element, and their order, are those of the lane form's column steps,
+// so a problem gets the same pivots.  Storage: problem t of a warp at W + t PS, a(i, j) at
+// i + j (n + 1); the odd column stride spreads a lane's four columns of a swap over four banks,
+// and PS = 4 (mod 16) doubles puts the four problems of a half-warp on distinct banks.
+// One instruction serves the warp's eight problems: a column step costs the warp one reciprocal,
+// ceil(m/4) multiplies and ceil(m/4) m multiply-adds (m = n-1-k), with every lane of a team busy
+// while its rows last.
+__host__ __device__ inline int getrf_team_ps(int n) {
+    const int ps = n * (n + 1);
+    return ps + ((4 - ps % 16) + 16) % 16;
+}
+
+__global__ void __launch_bounds__(64) dgetrf_team_kernel(GetrfParams p) {
+    extern __shared__ double getrf_sm[];
+    const int n = p.n, ls = n + 1, PS = getrf_team_ps(n);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int t = lane >> 2, r = lane & 3;
+    const long long q0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * 8;
+    if (q0 >= p.batch) return;  // whole warps
+    const int nq = (int)(p.batch - q0 < 8 ? p.batch - q0 : 8);
+    double* W = getrf_sm + (size_t)warp * 8 * PS;
+    // copy in: element e = (problem u, column j, row i), rows fastest, as asynchronous copies
+    // straight into shared memory, all of a lane's in flight at once (no register staging)
+    const int NE = 8 * n * n;
+    const int dj = 32 / n, di = 32 - dj * n;
+    {
+        int u = 0, j = lane / n, i = lane - (lane / n) * n;
+        while (j >= n) {
+            j -= n;
+            u++;
+        }
+        for (int e = lane; e < NE; e += 32) {
+            if (u < nq) {
+                const unsigned sa = (unsigned)__cvta_generic_to_shared(W + u * PS + i + j * ls);
+                const double* ga = p.A.ptr(q0 + u) + i + (long long)j * p.lda;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(ga) : "memory");
+            }
+            i += di;
+            j += dj;
+            if (i >= n) {
+                i -= n;
+                j++;
+            }
+            while (j >= n) {
+                j -= n;
+                u++;
+            }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    __syncwarp();
+    double* Ap = W + t * PS;  // this team's problem
+    int info = 0;
+    for (int k = 0; k < n; k++) {
+        const double* ck = Ap + k * ls;
+        long long best = -2;
+        int bi = k;
+        for (int i = k + r; i < n; i += 4) {
+            long long key = __double_as_longlong(ck[i]) & 0x7fffffffffffffffll;
+            if (key > 0x7ff0000000000000ll) key = (i == k) ? 0x7fffffffffffffffll : -1;  // NaN
+            if (key > best) {
+                best = key;
+                bi = i;
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < 4; o <<= 1) {
+            const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        if (r == 0 && t < nq) p.ipiv[(q0 + t) * p.sipiv + k] = bi + 1;
+        const double pv = ck[bi];
+        const double rcp = __drcp_rn(pv);  // 1 / pv rounded to nearest, as the division; its latency
+                                           // overlaps the interchange
+        __syncwarp();
+        if (pv != 0.0 && bi != k) {
+            for (int j = r; j < n; j += 4) {
+                const double a = Ap[k + j * ls], b = Ap[bi + j * ls];
+                Ap[k + j * ls] = b;
+                Ap[bi + j * ls] = a;
+            }
+        }
+        if (pv == 0.0 && info == 0) info = k + 1;
+        __syncwarp();
+        // rows k+1+4h+r: the groups of four rows that exist for the warp's first lane are taken
+        // (a warp-uniform test), so no FP64 instruction is issued for a group without rows (a
+        // masked FP64 lane costs a full one); within a group, lanes past n sit out
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+            if (k + 1 + 4 * h >= n) break;
+            const int i = k + 1 + 4 * h + r;
+            const bool act = i < n;
+            double l = act ? Ap[i + k * ls] : 0.0;
+            if (act && pv != 0.0) {
+                l *= rcp;
+                Ap[i + k * ls] = l;
+            }
+            for (int j = k + 1; j < n; j++) {
+                double* cj = Ap + j * ls;
+                const double ukj = cj[k];
+                if (act) cj[i] = fma(-l, ukj, cj[i]);
+            }
+        }
+        __syncwarp();
+    }
+    if (r == 0 && t < nq && p.info) p.info[q0 + t] = info;
+    // copy out
+    {
+        int u = 0, j = lane / n, i = lane - (lane / n) * n;
+        while (j >= n) {
+            j -= n;
+            u++;
+        }
+        for (int e = lane; e < NE; e += 32) {
+            if (u < nq) p.A.mptr(q0 + u)[i + (long long)j * p.lda] = W[u * PS + i + j * ls];
+            i += di;
+            j += dj;
+            if (i >= n) {
+                i -= n;
+                j++;
+            }
+            while (j >= n) {
+                j -= n;
+                u++;
+            }
+        }
+    }
+}
+
 cudaError_t launch_dgetrf(int m, int n, MatRef A, int lda, int* ipiv, long long sipiv, int* info, long long batch,
                           cudaStream_t s) {
     if (batch == 0) return cudaSuccess;
@@ -344,6 +490,12 @@ cudaError_t launch_dgetrf(int m, int n, MatRef A, int lda, int* ipiv, long long 
         }
         const long long cap = kSMs * 16;
         dgetrf_cta_kernel<<<(unsigned)(batch < cap ? batch : cap), 128, smem, s>>>(p);
+        count_launch();
+        return cudaGetLastError();
+    }
+    if (choose_getrf(n, batch) == VAR_TEAM) {  // n <= kGetrfTeamMaxN: 16 problems per 64-thread CTA
+        const size_t smem = sizeof(double) * 16 * (size_t)getrf_team_ps(n);
+        dgetrf_team_kernel<<<(unsigned)((batch + 15) / 16), 64, smem, s>>>(p);
         count_launch();
         return cudaGetLastError();
     }

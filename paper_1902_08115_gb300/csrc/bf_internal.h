@@ -166,6 +166,8 @@ cudaError_t launch_dtrmm(int side, int uplo, int trans, int unit, int m, int n, 
 // LU with partial pivoting and its solve (bf_dgetrf.cu); ipiv: sipiv ints per problem, 1-based
 // m x n; m != n always takes one problem per CTA (m <= kGetrfMaxRows)
 constexpr int kGetrfMaxRows = 1024;
+// square orders up to this take the four-lanes-per-problem form in shared memory (VAR_TEAM)
+constexpr int kGetrfTeamMaxN = 16;
 cudaError_t launch_dgetrf(int m, int n, MatRef A, int lda, int* ipiv, long long sipiv, int* info, long long batch,
                           cudaStream_t s);
 cudaError_t launch_dgetrs(int trans, int n, int nrhs, MatRef A, int lda, const int* ipiv, long long sipiv, MatRef B,
@@ -175,7 +177,7 @@ cudaError_t launch_dgetrs(int trans, int n, int nrhs, MatRef A, int lda, const i
 GemmConfig choose_gemm(bool ta, bool tb, int m, int n, int k, int lda, long long batch);
 TrsmConfig choose_trsm(int side, int uplo, int trans, int unit, int m, int n, long long batch);
 PotrfConfig choose_potrf(int n, int lda, long long batch);
-int choose_getrf(int n, long long batch);  // VAR_DIRECT (lane LU) or VAR_CTA
+int choose_getrf(int n, long long batch);  // VAR_DIRECT (lane LU), VAR_TEAM (n <= 16) or VAR_CTA
 // dpotrf of a group of problems per CTA in shared memory, element-parallel (bf_potrf_group.cu);
 // kGroupSmemMax bounds its shared memory (one group must fit: potrf_group_smem(n, 1))
 constexpr size_t kGroupSmemMax = 227 * 1024;

@@ -354,9 +354,19 @@ PotrfConfig choose_potrf(int n, int lda, long long batch) {
 int choose_getrf(int n, long long batch) {
     TuneEntry e;
     if (lookup(BF_ROUTINE_DGETRF, 0, n, &e)) {
-        const int v = e.variant == VAR_CTA ? VAR_CTA : VAR_DIRECT;
-        if (e.force) return (v == VAR_CTA && n > kGetrfCtaMaxN) ? VAR_DIRECT : v;
+        const int v = e.variant == VAR_CTA ? VAR_CTA : e.variant == VAR_TEAM ? VAR_TEAM : VAR_DIRECT;
+        if (e.force) {
+            if (v == VAR_CTA && n > kGetrfCtaMaxN) return VAR_DIRECT;
+            if (v == VAR_TEAM && n > kGetrfTeamMaxN) return VAR_DIRECT;
+            return v;
+        }
     }
+    // four lanes per problem in shared memory from order 4 to 16, at every batch size, measured
+    // on GB300 against the lane LU (GFLOP/s, 2 GiB batches): n = 4: 158 / 139, 8: 408 / 260,
+    // 12: 567 / 325, 16: 627 / 448; at 4,096 problems 14 / 12, 76 / 39, 142 / 57, 207 / 79 (one
+    // problem per CTA: 34 at n = 16).  Orders 2 and 3 keep the lane LU (a team of four lanes has
+    // one or two rows to update).
+    if (n >= 4 && n <= kGetrfTeamMaxN) return VAR_TEAM;
     if (n > kGetrfCtaMaxN || n < 16) return VAR_DIRECT;
     if (n > 64) return VAR_CTA;
     return batch <= getrf_cta_batch_limit(n) ? VAR_CTA : VAR_DIRECT;

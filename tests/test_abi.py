@@ -191,16 +191,25 @@ def test_tune_table(lib):
         assert lib.tune_query(lib.ROUTINE_DTRSM, code_rltu, 32, 32, 0, 10)[0] != lib.VARIANT_BLOCKED
         lib.tune_set(lib.ROUTINE_DTRSM, code_rltu, 1, 300, lib.VARIANT_DIRECT | lib.TUNE_FORCE, 8)
         assert lib.tune_query(lib.ROUTINE_DTRSM, code_rltu, 256, 256, 0, 48)[0] == lib.VARIANT_DIRECT
-        # dgetrf: one problem per CTA above order 64 and for small batches from order 16
+        # dgetrf: four lanes per problem from order 4 to 16; one problem per CTA above order 64 and
+        # for small batches from order 17; the lane LU otherwise
         G = lib.ROUTINE_DGETRF
         assert lib.tune_query(G, 0, 128, 128, 0, 10 ** 6)[0] == lib.VARIANT_CTA
         assert lib.tune_query(G, 0, 32, 32, 0, 500)[0] == lib.VARIANT_CTA
         assert lib.tune_query(G, 0, 32, 32, 0, 10 ** 6)[0] == lib.VARIANT_DIRECT
-        assert lib.tune_query(G, 0, 8, 8, 0, 10)[0] == lib.VARIANT_DIRECT
+        assert lib.tune_query(G, 0, 8, 8, 0, 10)[0] == lib.VARIANT_TEAM
+        assert lib.tune_query(G, 0, 16, 16, 0, 10 ** 6)[0] == lib.VARIANT_TEAM
+        assert lib.tune_query(G, 0, 4, 4, 0, 10 ** 6)[0] == lib.VARIANT_TEAM
+        assert lib.tune_query(G, 0, 3, 3, 0, 10 ** 6)[0] == lib.VARIANT_DIRECT
+        assert lib.tune_query(G, 0, 17, 17, 0, 10 ** 6)[0] == lib.VARIANT_DIRECT
         assert lib.tune_query(G, 0, 2000, 2000, 0, 10)[0] == lib.VARIANT_DIRECT  # the panel must fit
         lib.tune_set(G, 0, 1, 4000, lib.VARIANT_CTA | lib.TUNE_FORCE)
         assert lib.tune_query(G, 0, 8, 8, 0, 10 ** 6)[0] == lib.VARIANT_CTA
         assert lib.tune_query(G, 0, 2000, 2000, 0, 10)[0] == lib.VARIANT_DIRECT
+        lib.tune_clear()
+        lib.tune_set(G, 0, 1, 4000, lib.VARIANT_TEAM | lib.TUNE_FORCE)
+        assert lib.tune_query(G, 0, 3, 3, 0, 10 ** 6)[0] == lib.VARIANT_TEAM
+        assert lib.tune_query(G, 0, 17, 17, 0, 10)[0] == lib.VARIANT_DIRECT  # beyond the team form
         # defaults of the lane kernel: 8-row blocks for odd lda from n = 16, for even lda from n = 24
         lib.tune_clear()
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 16, 16, 0, 10 ** 5)[3:] == [4, 2]

@@ -302,7 +302,7 @@ def test_dpotrf_upper_failures_and_dpotrs(bf, oracle):
 
 
 # ----------------------------------------------------------------------------- dgetrf / dgetrs
-GETRF_VARIANTS = [("chosen", None), ("lane", 0), ("cta", 4)]
+GETRF_VARIANTS = [("chosen", None), ("lane", 0), ("team", 5), ("cta", 4)]
 
 
 @pytest.mark.parametrize("vname,variant", GETRF_VARIANTS, ids=[v[0] for v in GETRF_VARIANTS])
