@@ -174,27 +174,22 @@ __global__ void __launch_bounds__(32 * NW) dpotrf_group_kernel(int n, MatRef A, 
         const long long q0 = g * P;
         const int np = (int)(batch - q0 < P ? batch - q0 : P);
         __syncthreads();  // the table is written / the previous group is stored
-        // copy in: problem-major units, so that consecutive threads read consecutive rows; eight
-        // loads in flight per thread
+        // copy in: problem-major units, so that consecutive threads read consecutive rows, as
+        // asynchronous copies straight into shared memory (all of a thread's in flight at once)
         {
             int p = ls.a0, e = ls.b0;
-            for (int u0 = tid; u0 < UC; u0 += 8 * NT) {
-                double v[8];
-                int d[8];
-#pragma unroll
-                for (int x = 0; x < 8; x++) {
-                    const bool in = u0 + x * NT < UC;
-                    const int ik = T[in ? e : 0], i = ik >> 16, k = ik & 0xffff;
-                    const bool ld = in && p < np;
-                    const double* a = A.ptr(q0 + (ld ? p : 0));
-                    v[x] = ld ? (UP ? a[k + (long long)i * lda] : a[i + (long long)k * lda]) : 0.0;
-                    d[x] = in ? e * PS + p : -1;
-                    ls.next(p, e);
+            for (int u = tid; u < UC; u += NT) {
+                if (p < np) {
+                    const int ik = T[e], i = ik >> 16, k = ik & 0xffff;
+                    const double* a = A.ptr(q0 + p) + (UP ? k + (long long)i * lda : i + (long long)k * lda);
+                    const unsigned sa = (unsigned)__cvta_generic_to_shared(S + e * PS + p);
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(a) : "memory");
+                } else {
+                    S[e * PS + p] = 0.0;
                 }
-#pragma unroll
-                for (int x = 0; x < 8; x++)
-                    if (d[x] >= 0) S[d[x]] = v[x];
+                ls.next(p, e);
             }
+            asm volatile("cp.async.wait_all;" ::: "memory");
         }
         for (int p = tid; p < P; p += NT) F[p] = 0;
         __syncthreads();
