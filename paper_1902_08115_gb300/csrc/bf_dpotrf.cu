@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(256) dpotrf_lane_packed_kernel(PotrfParams p) 
     const int nq = (int)((p.batch - q0) < T ? (p.batch - q0) : T);
     const bool up = p.upper != 0;
     stage_in(p.A, n, n, p.lda, up, q0, nq, smem, ST);
+    stage_wait();
     __syncthreads();
     const long long q = q0 + threadIdx.x;
     if ((int)threadIdx.x < nq && !(p.skip && p.skip[q] != 0)) {

@@ -22,7 +22,18 @@ __device__ __forceinline__ bool stage_contiguous(const MatRef& X, int rows, int 
            (reinterpret_cast<uintptr_t>(X.ptr(q0)) & 15u) == 0;
 }
 
-// s[e * ST + qq] = X_(q0+qq)(i, j), e = i + j rows (trans: X_(q0+qq)(j, i)); nq problems.
+// One element copied from global to shared memory without passing through registers.
+__device__ __forceinline__ void stage_copy8(double* dst, const double* src) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(src) : "memory");
+}
+
+// Waits for this thread's stage_in copies; a CTA barrier must follow before other threads
+// read the staged problems.
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// s[e * ST + qq] = X_(q0+qq)(i, j), e = i + j rows (trans: X_(q0+qq)(j, i)); nq problems.  The
+// copies are asynchronous, all of a thread's in flight at once: complete them with stage_wait().
 __device__ __forceinline__ void stage_in(const MatRef& X, int rows, int cols, int ld, bool trans, long long q0,
                                          int nq, double* s, int ST) {
     const int per = rows * cols;
@@ -30,10 +41,9 @@ __device__ __forceinline__ void stage_in(const MatRef& X, int rows, int cols, in
     if (!trans && stage_contiguous(X, rows, cols, ld, q0)) {
         const double* base = X.ptr(q0);
         for (int t = threadIdx.x; 2 * t < nq * per; t += T) {
-            const double2 v = ldg2(base + 2 * t);
             const int f = 2 * t, qq = f / per, e = f - qq * per;
-            s[e * ST + qq] = v.x;
-            s[(e + 1) * ST + qq] = v.y;
+            stage_copy8(s + e * ST + qq, base + f);
+            stage_copy8(s + (e + 1) * ST + qq, base + f + 1);
         }
         return;
     }
@@ -41,7 +51,7 @@ __device__ __forceinline__ void stage_in(const MatRef& X, int rows, int cols, in
         const int qq = f / per, e = f - qq * per;
         const int j = e / rows, i = e - j * rows;
         const double* x = X.ptr(q0 + qq);
-        s[e * ST + qq] = trans ? ldg(x + j + (long long)i * ld) : ldg(x + i + (long long)j * ld);
+        stage_copy8(s + e * ST + qq, trans ? x + j + (long long)i * ld : x + i + (long long)j * ld);
     }
 }
 

@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(128) dgemm_tiny_kernel(GemmParams p) {
     stage_in(p.A, ra, ca, p.lda, false, q0, nq, sA, ST);
     stage_in(p.B, rb, cb, p.ldb, false, q0, nq, sB, ST);
     if (readC) stage_in(p.C, m, n, p.ldc, false, q0, nq, sC, ST);
+    stage_wait();
     __syncthreads();
     const int t = threadIdx.x;
     if (t < nq && !(p.skip && p.skip[q0 + t] != 0)) {
@@ -120,6 +121,7 @@ __global__ void __launch_bounds__(128) dtrsm_tiny_kernel(TrsmParams p) {
     double* sB = sA + ka * ka * ST;
     stage_in(p.A, ka, ka, p.lda, false, q0, nq, sA, ST);
     stage_in(p.B, m, n, p.ldb, false, q0, nq, sB, ST);
+    stage_wait();
     __syncthreads();
     const int t = threadIdx.x;
     if (t < nq && !(p.skip && p.skip[q0 + t] != 0)) {
