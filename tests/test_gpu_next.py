@@ -326,6 +326,46 @@ def test_dgetrf(bf, oracle, vname, variant, n):
         assert np.isnan(out[:, :, n:]).all()
 
 
+@pytest.mark.parametrize("n", [4, 7, 16])
+@pytest.mark.parametrize("batch", [1, 8, 17, 1000])
+def test_dgetrf_team_tails_and_specials(bf, oracle, n, batch):
+    """The four-lanes-per-problem LU (eight problems per warp, sixteen per CTA) on batches that
+    leave a partial warp or CTA, with special problems planted: a NaN on a diagonal (kept as the
+    pivot), a NaN below a diagonal (never taken), an infinity, ties of equal magnitude (the first
+    row wins), a zero column (info) and an all-zero matrix.  Pivots and infos exactly as the
+    oracle's; factors normwise against it where finite; and the same bits as the lane LU."""
+    g = np.random.default_rng(900 + 10 * n + batch)
+    pad = 3
+    A = np.full((batch, n, n + pad), np.nan)
+    A[:, :, :n] = g.standard_normal((batch, n, n))
+    specials = []
+    if batch >= 8:
+        A[1, 0, 0] = np.nan                      # NaN on the diagonal: row 0 stays the pivot
+        A[2, 2, 1] = np.nan                      # NaN below a diagonal: never the pivot
+        A[3, 1, 3] = np.inf                      # an infinity
+        A[4, :, 0] = 1.0                         # equal magnitudes: the first row wins
+        A[4, 2, 0] = -1.0
+        A[5, :, 2] = 0.0                         # a zero column -> info 3
+        A[6, :, :n] = 0.0                        # all zero -> info 1
+        specials = [1, 2, 3, 4, 5, 6]
+    LU, piv, info = oracle.dgetrf(A, m=n)
+    outs = {}
+    for name, v in (("team", bf.VARIANT_TEAM), ("lane", bf.VARIANT_DIRECT)):
+        Ag = gpu(A)
+        with forced(bf, bf.ROUTINE_DGETRF, 0, v):
+            pg, ig = bf.dgetrf(Ag, n=n)
+        outs[name] = (host(Ag), host(pg), host(ig))
+    out, pg, ig = outs["team"]
+    np.testing.assert_array_equal(ig, info)
+    np.testing.assert_array_equal(pg, piv)
+    finite = np.isfinite(LU).all(axis=(1, 2)) & np.isfinite(out[:, :, :n]).all(axis=(1, 2))
+    finite &= ~np.isin(np.arange(batch), specials)
+    assert normwise(out[finite], LU[finite], n) <= TOL
+    assert np.isnan(out[:, :, n:]).all()                      # padding untouched
+    for a, b in zip(outs["team"], outs["lane"]):
+        np.testing.assert_array_equal(a, b)                    # same bits (NaN where NaN)
+
+
 @pytest.mark.parametrize("vname,variant", GETRF_VARIANTS, ids=[v[0] for v in GETRF_VARIANTS])
 @pytest.mark.parametrize("n", [9, 40])
 def test_dgetrf_singular_and_permutation(bf, oracle, vname, variant, n):
