@@ -162,6 +162,8 @@ struct SAcc {  // a problem in shared memory, interleaved with the CTA's other p
 struct GAccT {
     double* a;
     int lda;
+    // the k loops take columns in pairs: L(i, p) and L(i, p + 1) are adjacent in memory
+    static constexpr bool kPairs = true;
     __device__ __forceinline__ double ld(int i, int j) const { return a[j + (long long)i * lda]; }
     __device__ __forceinline__ void st(int i, int j, double v) const { a[j + (long long)i * lda] = v; }
     template <int R>
@@ -169,12 +171,39 @@ struct GAccT {
 #pragma unroll
         for (int r = 0; r < R; r++) o[r] = ld(imin(i + r, n - 1), j);
     }
+    // the strips of columns p and p + 1 (p + 1 < n): one 16-byte load per row where aligned
+    template <int R>
+    __device__ __forceinline__ void strip2(int i, int p, int n, double* o0, double* o1) const {
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const double* q = a + p + (long long)imin(i + r, n - 1) * lda;
+            if ((reinterpret_cast<uintptr_t>(q) & 15u) == 0) {
+                const double2 x = *reinterpret_cast<const double2*>(q);
+                o0[r] = x.x;
+                o1[r] = x.y;
+            } else {
+                o0[r] = q[0];
+                o1[r] = q[1];
+            }
+        }
+    }
     template <int R>
     __device__ __forceinline__ void put(int i, int j, int cnt, const double* v) const {
 #pragma unroll
         for (int r = 0; r < R; r++)
             if (r < cnt) st(i + r, j, v[r]);
     }
+};
+
+// Accessors that read a row's entries of two adjacent columns as one piece (kPairs, strip2):
+// the k loops below then step two columns at a time, with the multiply-adds in the same order.
+template <class A, class = void>
+struct AccPairs {
+    static constexpr bool value = false;
+};
+template <class A>
+struct AccPairs<A, decltype(void(A::kPairs))> {
+    static constexpr bool value = A::kPairs;
 };
 
 // The optional rank-k operand of the fused dsyrk + dpotrf: the factorisation then acts on
@@ -238,8 +267,25 @@ __device__ __forceinline__ void lane_block(const Acc& M, int n, int I, int J, in
                 for (int c = 0; c < 4; c++) acc[r][c] = fma(a[r], b[c], acc[r][c]);
         }
     }
+    // k in pairs through a pair accessor (J is a multiple of 4, so the pairs are whole)
+    int pp0 = 0;
+    if constexpr (AccPairs<Acc>::value) {
+        for (; pp0 < J; pp0 += 2) {
+            double a0[R], a1[R], b0[4], b1[4];
+            M.template strip2<R>(I, pp0, n, a0, a1);
+            M.template strip2<4>(J, pp0, n, b0, b1);
+#pragma unroll
+            for (int r = 0; r < R; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[r][c] = fma(-a0[r], b0[c], acc[r][c]);
+#pragma unroll
+            for (int r = 0; r < R; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[r][c] = fma(-a1[r], b1[c], acc[r][c]);
+        }
+    }
 #pragma unroll U
-    for (int pp = 0; pp < J; pp++) {
+    for (int pp = pp0; pp < J; pp++) {
         double a[R], b[4];
         M.template strip<R>(I, pp, n, a);
         M.template strip<4>(J, pp, n, b);
@@ -283,8 +329,23 @@ __device__ __forceinline__ void lane_diag(const Acc& M, int n, int J, const int 
                 for (int c = 0; c <= r; c++) d[r][c] = fma(l[r], l[c], d[r][c]);
         }
     }
+    int pp0 = 0;
+    if constexpr (AccPairs<Acc>::value) {
+        for (; pp0 < J; pp0 += 2) {
+            double l0[4], l1[4];
+            M.template strip2<4>(J, pp0, n, l0, l1);
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c <= r; c++) d[r][c] = fma(-l0[r], l0[c], d[r][c]);
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c <= r; c++) d[r][c] = fma(-l1[r], l1[c], d[r][c]);
+        }
+    }
 #pragma unroll U
-    for (int pp = 0; pp < J; pp++) {
+    for (int pp = pp0; pp < J; pp++) {
         double l[4];
         M.template strip<4>(J, pp, n, l);
 #pragma unroll
@@ -323,8 +384,27 @@ __device__ __forceinline__ void lane_diag_under(const Acc& M, int n, int J, cons
                 for (int c = 0; c < 4; c++) e[r][c] = fma(l[4 + r], l[c], e[r][c]);
         }
     }
+    int pp0 = 0;
+    if constexpr (AccPairs<Acc>::value) {
+        for (; pp0 < J; pp0 += 2) {
+            double l0[8], l1[8];
+            M.template strip2<8>(J, pp0, n, l0, l1);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const double* l = h ? l1 : l0;
+#pragma unroll
+                for (int r = 0; r < 4; r++)
+#pragma unroll
+                    for (int c = 0; c <= r; c++) d[r][c] = fma(-l[r], l[c], d[r][c]);
+#pragma unroll
+                for (int r = 0; r < 4; r++)
+#pragma unroll
+                    for (int c = 0; c < 4; c++) e[r][c] = fma(-l[4 + r], l[c], e[r][c]);
+            }
+        }
+    }
 #pragma unroll U
-    for (int pp = 0; pp < J; pp++) {
+    for (int pp = pp0; pp < J; pp++) {
         double l[8];
         M.template strip<8>(J, pp, n, l);
 #pragma unroll
