@@ -289,23 +289,110 @@ int potrf_group_size(int n, long long batch, int per_sm) {
     return (int)P;
 }
 
-// The kernel's dynamic shared memory limit is raised once to the bound (not on every call: the
-// attribute call is host time that a small launch would wait for).
+// Problems per group from a model of the launch's time, for CTAs of `threads` threads using
+// `regs` registers each on SMs with smem_sm bytes of shared memory (reserved_cta of it taken
+// by every CTA).  With P problems per group, r CTAs resident per SM (shared memory,
+// registers, threads) and W waves of 152 r CTAs, a wave costs the serial column chain once
+// (the CTAs of an SM run their chains side by side) plus the update work of the problems on
+// its busiest SM.  Counted in one problem's update work:
+//   T(P) = W a ceil(P / 32) + P (r (W - 1) + c_last) + p CTAs_per_SM
+// with c_last the CTAs on the busiest SM in the last wave, a = 9360 / n^2 (the chain's
+// ~1,300 cycles per column against n^3/3 flops at ~2.4 per cycle per SM; warp 0 carries 32
+// problems' chains per pass) and p = 922 / n^2 the pivot slots a group adds (8 FP64
+// instructions per column whatever its P).  Measured on GB300 the model's choice matches the
+// best of a sweep over P: n = 64 x 4,096 problems: P = 9, 788 GFLOP/s (13 problems per
+// group, the shared-memory cap of two groups per SM: 583, its third wave 12 CTAs);
+// n = 96 x 1,216: P = 4, 779 (5: 674); n = 32 x 12,288: P = 21, 754 (27: 666);
+// n = 16 x 16,384: P = 54, 513 (36: 473).
+int potrf_group_size_model(int n, long long batch, int threads, int regs, int smem_sm, int reserved_cta) {
+    const double a = 9360.0 / ((double)n * n), piv = 922.0 / ((double)n * n);
+    int bestP = 1;
+    double bestT = -1.0;
+    for (int P = 1; P <= kGroupMaxP; P++) {
+        const size_t sm = potrf_group_smem(n, P);
+        if (sm > kGroupSmemMax) break;
+        long long r = (long long)smem_sm / ((long long)sm + reserved_cta);
+        const long long r_reg = 65536 / ((long long)(regs > 0 ? regs : 1) * threads), r_thr = 2048 / threads;
+        if (r_reg < r) r = r_reg;
+        if (r_thr < r) r = r_thr;
+        if (r > 32) r = 32;
+        if (r < 1) break;
+        const long long groups = (batch + P - 1) / P, slots = kSMs * r;
+        const long long W = (groups + slots - 1) / slots;
+        const long long rem = groups - slots * (W - 1), clast = (rem + kSMs - 1) / kSMs;
+        const double T = W * a * (double)((P + 31) / 32) + P * (double)(r * (W - 1) + clast) +
+                         piv * (double)((groups + kSMs - 1) / kSMs);
+        if (bestT < 0.0 || T < bestT) {
+            bestT = T;
+            bestP = P;
+        }
+        if (groups == 1) break;  // larger groups only add empty slots
+    }
+    return bestP;
+}
+
+// Once per kernel instance (not on every call: attribute calls are host time that a small
+// launch would wait for): the dynamic shared memory limit raised to the bound, and the
+// registers per thread that the group-size model needs.
 template <int NW, bool UP>
-static cudaError_t group_smem_limit() {
+static cudaError_t group_prepare(int* regs) {
     static std::atomic<int> done{0};
-    if (done.load(std::memory_order_acquire)) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(dpotrf_group_kernel<NW, UP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)kGroupSmemMax);
-    if (e == cudaSuccess) done.store(1, std::memory_order_release);
-    return e;
+    int d = done.load(std::memory_order_acquire);
+    if (d) {
+        *regs = d;
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaFuncSetAttribute(dpotrf_group_kernel<NW, UP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kGroupSmemMax);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, dpotrf_group_kernel<NW, UP>);
+    if (e != cudaSuccess) return e;
+    d = fa.numRegs > 0 ? fa.numRegs : 1;
+    done.store(d, std::memory_order_release);
+    *regs = d;
+    return cudaSuccess;
+}
+
+// Shared memory per SM and per CTA reservation of the current device, once.
+static void group_device_smem(int* smem_sm, int* reserved) {
+    static std::atomic<int> s_sm{0}, s_res{-1};
+    int a = s_sm.load(std::memory_order_acquire), b = s_res.load(std::memory_order_acquire);
+    if (a == 0 || b < 0) {
+        int dev = 0;
+        a = 233472;  // GB300: 228 KB per SM, 1 KB reserved per CTA
+        b = 1024;
+        if (cudaGetDevice(&dev) == cudaSuccess) {
+            int v = 0;
+            if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess && v > 0) a = v;
+            if (cudaDeviceGetAttribute(&v, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess && v >= 0) b = v;
+        }
+        s_sm.store(a, std::memory_order_release);
+        s_res.store(b, std::memory_order_release);
+    }
+    *smem_sm = a;
+    *reserved = b;
 }
 
 template <int NW>
 static cudaError_t launch_group(int n, MatRef A, int lda, long long batch, int* info, cudaStream_t s, int upper,
-                                int P, size_t smem, unsigned blocks) {
-    cudaError_t e = upper ? group_smem_limit<NW, true>() : group_smem_limit<NW, false>();
+                                int per_sm) {
+    int regs = 0;
+    cudaError_t e = upper ? group_prepare<NW, true>(&regs) : group_prepare<NW, false>(&regs);
     if (e != cudaSuccess) return e;
+    int P;
+    if (per_sm > 0) {
+        P = potrf_group_size(n, batch, per_sm);
+    } else {
+        int smem_sm, reserved;
+        group_device_smem(&smem_sm, &reserved);
+        P = potrf_group_size_model(n, batch, 32 * NW, regs, smem_sm, reserved);
+    }
+    const size_t smem = potrf_group_smem(n, P);
+    if (smem > kGroupSmemMax) return cudaErrorInvalidValue;
+    const long long groups = (batch + P - 1) / P;
+    const long long cap = kSMs * 8;
+    const unsigned blocks = (unsigned)(groups < cap ? groups : cap);
     if (upper) {
         dpotrf_group_kernel<NW, true><<<blocks, 32 * NW, smem, s>>>(n, A, lda, batch, info, P);
     } else {
@@ -315,21 +402,16 @@ static cudaError_t launch_group(int n, MatRef A, int lda, long long batch, int* 
     return cudaGetLastError();
 }
 
-// threads: 256, 384 or 512 per CTA; per_sm: groups resident per SM that the batch is spread over (1..4)
+// threads: 256, 384 or 512 per CTA; per_sm: groups per SM that the batch is spread over (1..4),
+// or 0: the group size from the time model (potrf_group_size_model)
 cudaError_t launch_dpotrf_group(int n, MatRef A, int lda, long long batch, int* info, cudaStream_t s, int upper,
                                 int threads, int per_sm) {
     if (batch == 0 || n == 0) return cudaSuccess;
-    if (per_sm < 1) per_sm = 1;
+    if (per_sm < 0) per_sm = 0;
     if (per_sm > 4) per_sm = 4;
-    const int P = potrf_group_size(n, batch, per_sm);
-    const size_t smem = potrf_group_smem(n, P);
-    if (smem > kGroupSmemMax) return cudaErrorInvalidValue;
-    const long long groups = (batch + P - 1) / P;
-    const long long cap = kSMs * 8;
-    const unsigned blocks = (unsigned)(groups < cap ? groups : cap);
-    if (threads == 384) return launch_group<12>(n, A, lda, batch, info, s, upper, P, smem, blocks);
-    if (threads == 512) return launch_group<16>(n, A, lda, batch, info, s, upper, P, smem, blocks);
-    return launch_group<8>(n, A, lda, batch, info, s, upper, P, smem, blocks);
+    if (threads == 384) return launch_group<12>(n, A, lda, batch, info, s, upper, per_sm);
+    if (threads == 512) return launch_group<16>(n, A, lda, batch, info, s, upper, per_sm);
+    return launch_group<8>(n, A, lda, batch, info, s, upper, per_sm);
 }
 
 }  // namespace bf

@@ -252,8 +252,6 @@ static long long group_batch_limit(int n) {
     if (n < 112) return 1216;
     return 304;
 }
-// groups per SM: one for the smallest batches (few problems per group), three for the largest
-static int group_per_sm(long long batch) { return batch <= 1216 ? 1 : batch <= 6144 ? 2 : 3; }
 
 PotrfConfig choose_potrf(int n, int lda, long long batch) {
     // Table code 0 holds even leading dimensions, code 1 odd ones (an odd lda leaves
@@ -306,7 +304,7 @@ PotrfConfig choose_potrf(int n, int lda, long long batch) {
     if (!force && !ruled && batch <= group_batch_limit(n) && potrf_group_smem(n, 1) <= kGroupSmemMax) {
         c.variant = VAR_GROUP;
         c.T = 384;
-        c.NB = group_per_sm(batch);
+        c.NB = 0;  // problems per group from the launch's time model
         c.rows = 4;
         c.unroll = 2;
         return c;
@@ -326,9 +324,10 @@ PotrfConfig choose_potrf(int n, int lda, long long batch) {
         const long long cap = batch / (2 * kSMs) / 32 * 32;
         if (c.T > cap) c.T = (int)(cap < 32 ? 32 : cap);
     }
-    if (c.variant == VAR_GROUP) {  // p0: threads per CTA (256, 384 or 512), p1: groups per SM (1..4)
+    if (c.variant == VAR_GROUP) {  // p0: threads per CTA (256, 384 or 512), p1: groups per SM (1..4;
+                                   // otherwise the group size from the launch's time model)
         c.T = (c.T == 384 || c.T == 512) ? c.T : 256;
-        c.NB = (c.NB >= 1 && c.NB <= 4) ? c.NB : 2;
+        c.NB = (c.NB >= 1 && c.NB <= 4) ? c.NB : 0;
         c.rows = 4;
         c.unroll = 2;
         return c;

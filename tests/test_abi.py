@@ -156,15 +156,20 @@ def test_tune_table(lib):
         lib.tune_set(lib.ROUTINE_DPOTRF, 1, 1, 300, lib.VARIANT_DIRECT, 64, 0, 8, 1)
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10 ** 5) == [lib.VARIANT_DIRECT, 64, 32, 8, 1]
         # a lane kernel needs tens of thousands of problems: small batches of orders 4..192 go
-        # to the group form (p0 = 384 threads, p1 = groups per SM), larger ones of n > 64 to
-        # the blocked sequence
+        # to the group form (p0 = 384 threads, p1 = 0: the group size from the launch's time
+        # model), larger ones of n > 64 to the blocked sequence
         G6 = lib.VARIANT_GROUP
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10)[:3] == [G6, 384, 1]
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10)[:3] == [G6, 384, 0]
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 100, 100, 0, 10)[0] == G6
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 100, 100, 0, 10 ** 4)[0] == lib.VARIANT_BLOCKED
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 1500)[:3] == [G6, 384, 2]
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 4096)[:3] == [G6, 384, 2]
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 10 ** 4)[:3] == [G6, 384, 3]
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 1500)[:3] == [G6, 384, 0]
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 10 ** 4)[:3] == [G6, 384, 0]
+        # a forced group entry keeps its groups per SM (1..4); other values take the model
+        lib.tune_set(lib.ROUTINE_DPOTRF, 1, 30, 34, G6 | lib.TUNE_FORCE, 512, 3)
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 4096)[:3] == [G6, 512, 3]
+        lib.tune_set(lib.ROUTINE_DPOTRF, 1, 30, 34, G6 | lib.TUNE_FORCE, 384, 9)
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 4096)[:3] == [G6, 384, 0]
+        lib.tune_clear()
         # past the group form's range, teams of 2 lanes per problem, then one problem per lane
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 14000)[:4] == [lib.VARIANT_TEAM, 64, 32, 2]
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 10 ** 5)[0] == lib.VARIANT_DIRECT
