@@ -234,21 +234,27 @@ static int team_size(int n, int lda, long long batch) {
     return 0;
 }
 
-// The group form (a group of problems per CTA in shared memory, bf_potrf_group.cu) beats every
-// other form on batches up to these sizes, measured on GB300 against the switch without it
-// (GFLOP/s, back-to-back calls): n = 24 x 4,096: 454 against 272 (team of 4); n = 48 x 2,432:
-// 733 against 359 (one problem per CTA); n = 64 x 4,096: 762 against 535; n = 128 x 304: 775
-// against 592.  Above them the lane, team and blocked forms catch up (n = 24 x 16,384: 580
-// against 598).
+// The group form (a group of problems per CTA in shared memory, bf_potrf_group.cu, with the
+// group size from its launch model) beats every other form on batches up to these sizes,
+// measured on GB300 against the best of the lane, team, one-problem-per-CTA and blocked forms
+// (GFLOP/s ratio at the bound / one step above it): n = 8: 12,288 (1.06 / 0.98); n = 16:
+// 24,576 (1.02 / 0.88); n = 24: 65,536 and beyond (1.05); n = 32: 24,576 (1.00 / 0.98);
+// n = 40: 16,384 (1.02 / 0.97); n = 48: 12,288 (1.05 / 0.99); n = 56: 12,288 (1.03 / 0.94);
+// n = 64: 8,192 (1.15 / 0.97); n = 72: 12,288 (1.08); n = 80: 8,192 (1.04 / 0.93); n = 96:
+// 1,216 (4,096: 0.98 against one problem per CTA); n = 112..192: 304.
 static long long group_batch_limit(int n) {
     if (n < 4 || n > 192) return 0;
     if (n < 8) return 16384;
     if (n < 12) return 12288;
-    if (n < 24) return 16384;
-    if (n < 48) return 12288;
-    if (n < 56) return 8192;
-    if (n < 64) return 6144;
-    if (n < 96) return 4096;
+    if (n < 16) return 16384;
+    if (n < 24) return 24576;
+    if (n < 32) return 49152;
+    if (n < 40) return 24576;
+    if (n < 48) return 16384;
+    if (n < 64) return 12288;
+    if (n < 72) return 8192;
+    if (n < 80) return 12288;
+    if (n < 96) return 8192;
     if (n < 112) return 1216;
     return 304;
 }

@@ -171,8 +171,10 @@ def test_tune_table(lib):
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 4096)[:3] == [G6, 384, 0]
         lib.tune_clear()
         # past the group form's range, teams of 2 lanes per problem, then one problem per lane
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 14000)[:4] == [lib.VARIANT_TEAM, 64, 32, 2]
-        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 10 ** 5)[0] == lib.VARIANT_DIRECT
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 48, 48, 0, 14000)[:4] == [lib.VARIANT_TEAM, 64, 32, 2]
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 48, 48, 0, 10 ** 5)[0] == lib.VARIANT_DIRECT
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 24576)[0] == G6
+        assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 32, 32, 0, 24577)[0] == lib.VARIANT_DIRECT
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 8, 8, 0, 4096)[0] == G6
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 100, 100, 0, 4096)[0] != lib.VARIANT_TEAM
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 200, 200, 0, 10)[0] == lib.VARIANT_CTA
@@ -337,7 +339,7 @@ def test_batch_rules(lib, tmp_path):
         assert q(1, 24, 5000)[:4] == [lib.VARIANT_TEAM, 64, 32, 2]
         assert q(0, 24, 5001)[0] == lib.VARIANT_DIRECT
         assert q(0, 32, 5001)[0] == lib.VARIANT_GROUP  # outside the rule: built-in bounds
-        assert q(0, 32, 14000)[0] == lib.VARIANT_TEAM
+        assert q(0, 48, 14000)[0] == lib.VARIANT_TEAM
         # only the lda-parity named; a negative cta bound keeps the built-in one (896 at n = 24)
         lib.tune_set_batch_rule(lib.ROUTINE_DPOTRF, 1, 24, 24, -1, 0, -1)
         assert q(1, 24, 896)[0] == lib.VARIANT_CTA
