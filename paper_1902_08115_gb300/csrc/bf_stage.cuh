@@ -47,11 +47,24 @@ __device__ __forceinline__ void stage_in(const MatRef& X, int rows, int cols, in
         }
         return;
     }
+    // element f = (problem qq, column j, row i), rows fastest, stepped by T without divisions
+    int qq = threadIdx.x / per;
+    int j = (threadIdx.x - qq * per) / rows, i = threadIdx.x - qq * per - j * rows;
+    const int dq = T / per, dj = (T - dq * per) / rows, di = T - dq * per - dj * rows;
     for (int f = threadIdx.x; f < nq * per; f += T) {
-        const int qq = f / per, e = f - qq * per;
-        const int j = e / rows, i = e - j * rows;
         const double* x = X.ptr(q0 + qq);
-        stage_copy8(s + e * ST + qq, trans ? x + j + (long long)i * ld : x + i + (long long)j * ld);
+        stage_copy8(s + (i + j * rows) * ST + qq, trans ? x + j + (long long)i * ld : x + i + (long long)j * ld);
+        qq += dq;
+        i += di;
+        j += dj;
+        if (i >= rows) {
+            i -= rows;
+            j++;
+        }
+        if (j >= cols) {
+            j -= cols;
+            qq++;
+        }
     }
 }
 
@@ -70,13 +83,27 @@ __device__ __forceinline__ void stage_out(const MatRef& X, int rows, int cols, i
         }
         return;
     }
+    int qq = threadIdx.x / per;
+    int j = (threadIdx.x - qq * per) / rows, i = threadIdx.x - qq * per - j * rows;
+    const int dq = T / per, dj = (T - dq * per) / rows, di = T - dq * per - dj * rows;
     for (int f = threadIdx.x; f < nq * per; f += T) {
-        const int qq = f / per, e = f - qq * per;
-        const int j = e / rows, i = e - j * rows;
-        if (!all && !keep(i, j)) continue;
-        double* x = X.mptr(q0 + qq);
-        if (trans) x[j + (long long)i * ld] = s[e * ST + qq];
-        else x[i + (long long)j * ld] = s[e * ST + qq];
+        if (all || keep(i, j)) {
+            double* x = X.mptr(q0 + qq);
+            const double v = s[(i + j * rows) * ST + qq];
+            if (trans) x[j + (long long)i * ld] = v;
+            else x[i + (long long)j * ld] = v;
+        }
+        qq += dq;
+        i += di;
+        j += dj;
+        if (i >= rows) {
+            i -= rows;
+            j++;
+        }
+        if (j >= cols) {
+            j -= cols;
+            qq++;
+        }
     }
 }
 
