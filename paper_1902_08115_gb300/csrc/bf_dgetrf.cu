@@ -15,6 +15,8 @@
 // Rows are swapped eagerly, so every column still to be processed already holds P A.
 // info = the first column whose pivot is exactly zero (the factorisation still completes,
 // as LAPACK's); ipiv is 1-based.
+#include <atomic>
+
 #include "bf_internal.h"
 #include "bf_lane.cuh"
 
@@ -483,10 +485,14 @@ cudaError_t launch_dgetrf(int m, int n, MatRef A, int lda, int* ipiv, long long 
     p.m = m; p.n = n; p.A = A; p.lda = lda; p.ipiv = ipiv; p.sipiv = sipiv; p.batch = batch; p.info = info;
     if (m != n || choose_getrf(n, batch) == VAR_CTA) {
         const size_t smem = sizeof(double) * (size_t)BF_GETRF_NB * m;
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(dgetrf_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
+        // the dynamic limit is raised once to the largest panel (kGetrfMaxRows rows): the kernel's
+        // static shared memory comes on top, so a panel of exactly 48 KB (m = 384) needs it too
+        static std::atomic<int> raised{0};
+        if (!raised.load(std::memory_order_acquire)) {
+            const cudaError_t e = cudaFuncSetAttribute(dgetrf_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)(sizeof(double) * BF_GETRF_NB * kGetrfMaxRows));
             if (e != cudaSuccess) return e;
+            raised.store(1, std::memory_order_release);
         }
         const long long cap = kSMs * 16;
         dgetrf_cta_kernel<<<(unsigned)(batch < cap ? batch : cap), 128, smem, s>>>(p);

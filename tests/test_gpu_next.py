@@ -306,7 +306,7 @@ GETRF_VARIANTS = [("chosen", None), ("lane", 0), ("team", 5), ("cta", 4)]
 
 
 @pytest.mark.parametrize("vname,variant", GETRF_VARIANTS, ids=[v[0] for v in GETRF_VARIANTS])
-@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 8, 13, 16, 17, 24, 33, 48, 64, 96, 130, 256])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 8, 13, 16, 17, 24, 33, 48, 64, 96, 130, 256, 384])
 def test_dgetrf(bf, oracle, vname, variant, n):
     batch = batch_for(n)
     for pad in (0, 3):
@@ -389,7 +389,7 @@ def test_dgetrf_singular_and_permutation(bf, oracle, vname, variant, n):
 
 
 @pytest.mark.parametrize("m,n", [(7, 3), (3, 7), (33, 17), (17, 33), (1, 5), (5, 1), (100, 20), (20, 100),
-                                 (300, 64), (64, 300), (1024, 16)])
+                                 (300, 64), (64, 300), (384, 40), (1024, 16)])
 def test_dgetrf_rectangular(bf, oracle, m, n):
     """m x n LU (one problem per CTA): pivots identical to the oracle's, factors within the
     tolerance, padding rows untouched; failures (a zero column) reported as the oracle does."""
