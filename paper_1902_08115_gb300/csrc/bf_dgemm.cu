@@ -273,7 +273,7 @@ static cudaError_t launch_t(const GemmParams& p, bool ta, bool tb, dim3 grid, di
 #define BF_GEMM_CASE(A_, B_)                                                                 \
     if (ta == A_ && tb == B_) {                                                              \
         auto kfn = dgemm_tile_kernel<MR, NR, A_, B_, PACKED, NEG>;                            \
-        if (smem > 48 * 1024) {                                                              \
+        if (smem + kStaticSmemSlack > 48 * 1024) {                                                              \
             cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                  (int)smem);                                 \
             if (e != cudaSuccess) return e;                                                  \

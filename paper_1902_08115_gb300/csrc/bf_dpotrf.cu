@@ -105,7 +105,7 @@ cudaError_t launch_dpotrf_lane(int n, MatRef A, int lda, long long batch, int* i
     if (cfg.variant == VAR_PACKED) {
         const int T = cfg.T < 256 ? cfg.T : 256;
         size_t smem = sizeof(double) * (size_t)(T + 1) * n * n;
-        if (smem > 48 * 1024) {
+        if (smem + kStaticSmemSlack > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(dpotrf_lane_packed_kernel,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;

@@ -563,7 +563,7 @@ cudaError_t launch_dsposv(int n, int nrhs, MatRef A, int lda, MatRef B, int ldb,
     p.work = reinterpret_cast<unsigned char*>(work);
     const size_t smem = refine_smem_bytes(n);
     auto kfn = n <= 128 ? dsposv_kernel<4> : dsposv_kernel<BF_DSPOSV_NMAX / 32>;
-    if (smem > 48 * 1024) {
+    if (smem + kStaticSmemSlack > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }

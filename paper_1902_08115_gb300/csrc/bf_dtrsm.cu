@@ -168,7 +168,7 @@ static cudaError_t launch_rows3(const TrsmParams& p, long long threads, int bloc
     // the residency is a tuned choice: with few, large problems one more CTA per SM can
     // decide whether the launch fits one wave (or how full its last wave is)
     auto kfn = (!PACKED && minb == 2) ? dtrsm_rows_kernel<MR, PACKED, UP, 2> : dtrsm_rows_kernel<MR, PACKED, UP, 1>;
-    if (smem > 48 * 1024) {
+    if (smem + kStaticSmemSlack > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }

@@ -118,6 +118,11 @@ inline int spread_block(long long threads, int max_block) {
     return 32 * best_w;
 }
 
+// Kernels may declare static shared memory too (a few flags and scratch words, well under
+// 1 KB); the opt-in for more than the default 48 KB of dynamic shared memory is taken whenever
+// the dynamic part comes within this much of 48 KB, so that the sum never exceeds the default.
+constexpr size_t kStaticSmemSlack = 1024;
+
 // Increments the library's kernel-launch counter (bf_launch_count).
 void count_launch();
 

@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(128, 6) dpotrf_cta_kernel(int n, MatRef A, int
 cudaError_t launch_dpotrf_cta(int n, MatRef A, int lda, long long batch, int* info, cudaStream_t s, int upper) {
     const int T = 128;
     const size_t smem = sizeof(double) * ((size_t)(BF_BIG_NB + 1) * n + 16 * (size_t)T);
-    if (smem > 48 * 1024) {
+    if (smem + kStaticSmemSlack > 48 * 1024) {
         cudaError_t e = upper ? cudaFuncSetAttribute(dpotrf_cta_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                      (int)smem)
                               : cudaFuncSetAttribute(dpotrf_cta_kernel<false>,
@@ -439,7 +439,7 @@ cudaError_t launch_dpotrf_vbatched(const int* n, double* const* A, const int* ld
     }
     const int T = 128;
     const size_t smem = sizeof(double) * ((size_t)(BF_BIG_NB + 1) * max_n + 16 * (size_t)T);
-    if (smem > 48 * 1024) {
+    if (smem + kStaticSmemSlack > 48 * 1024) {
         cudaError_t e = upper ? cudaFuncSetAttribute(dpotrf_vbatched_cta_kernel<true>,
                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                               : cudaFuncSetAttribute(dpotrf_vbatched_cta_kernel<false>,
@@ -577,7 +577,7 @@ extern "C" int bf_ragged_potrf_potrs_plan_create(int batch, const int* n_host, i
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (smem > 48 * 1024 &&
+    if (smem + bf::kStaticSmemSlack > 48 * 1024 &&
         cudaFuncSetAttribute(bf::ragged_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess) {
         delete pl;
@@ -748,7 +748,7 @@ extern "C" int bf_ragged_potrf_potrs_noalloc(int batch, const int* n_host, int n
     p.counter = counter;
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (smem > 48 * 1024 &&
+    if (smem + bf::kStaticSmemSlack > 48 * 1024 &&
         cudaFuncSetAttribute(bf::ragged_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
         return BF_ERR_CUDA;

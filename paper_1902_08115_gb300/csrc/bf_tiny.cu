@@ -79,7 +79,7 @@ size_t tiny_gemm_smem(int m, int n, int k, int T) {
 
 template <class K>
 static cudaError_t allow_smem(K kfn, size_t smem) {
-    if (smem <= 48 * 1024) return cudaSuccess;
+    if (smem + kStaticSmemSlack <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
