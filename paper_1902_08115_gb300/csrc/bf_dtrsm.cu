@@ -21,7 +21,8 @@ namespace bf {
 
 // MINB: CTAs of 256 threads the kernel is compiled to keep resident per SM (2 caps the
 // registers at 128).
-template <int MR, bool PACKED, bool UP, int MINB>
+// UNIT: unit diagonal (no reciprocal pivots; the kernel carries none of their code).
+template <int MR, bool PACKED, bool UP, int MINB, bool UNIT>
 __global__ void __launch_bounds__(256, MINB)
 dtrsm_rows_kernel(TrsmParams p) {
     extern __shared__ double smem[];
@@ -43,14 +44,14 @@ dtrsm_rows_kernel(TrsmParams p) {
             const long long qg = q0 + qq;
             double v = 0.0;
             const bool inT = UP ? (i <= j) : (i >= j);
-            if (qg < p.batch && inT && !(p.unit && i == j)) {
+            if (qg < p.batch && inT && !(UNIT && i == j)) {
                 const double* Aq = p.A.ptr(qg);
                 v = p.et ? ldg(Aq + j + (long long)i * p.lda) : ldg(Aq + i + (long long)j * p.lda);
             }
             sT[qq * n * ldt + i + j * ldt] = v;  // sT(i, j) = T(i, j)
         }
         __syncthreads();
-        if (!p.unit) {
+        if (!UNIT) {
             for (int e = threadIdx.x; e < p.P * n; e += blockDim.x) {
                 const int qq = e / n, j = e - (e / n) * n;
                 sR[qq * n + j] = 1.0 / sT[qq * n * ldt + j + j * ldt];
@@ -81,6 +82,9 @@ dtrsm_rows_kernel(TrsmParams p) {
         return p.et ? ldg(A + j + (long long)i * p.lda) : ldg(A + i + (long long)j * p.lda);
     };
 
+    // reciprocal pivots shared over a problem's lanes when they sit in one warp (tpp a power of
+    // two up to 32: problems then start on multiples of tpp within a warp)
+    const bool share = !PACKED && p.tpp > 1 && p.tpp <= 32 && (p.tpp & (p.tpp - 1)) == 0;
     const int nblk = (n + 3) / 4;
     for (int bi = 0; bi < nblk; bi++) {
         const int blk = UP ? bi : (nblk - 1 - bi);
@@ -123,9 +127,34 @@ dtrsm_rows_kernel(TrsmParams p) {
                 const bool need = UP ? (c2 < c) : (c2 > c);
                 tb[c2][c] = (need && c < jb && c2 < jb) ? Tel(J + c2, J + c) : 0.0;
             }
-            if (!p.unit) {
-                if (PACKED) rinv[c] = (c < jb) ? Rs[J + c] : 1.0;
-                else rinv[c] = (c < jb) ? 1.0 / Tel(J + c, J + c) : 1.0;
+        }
+        if (!UNIT) {
+            if (PACKED) {
+#pragma unroll
+                for (int c = 0; c < 4; c++) rinv[c] = (c < jb) ? Rs[J + c] : 1.0;
+            } else if (share) {
+                // the problem's tpp lanes (adjacent, one warp) split the four reciprocals and
+                // exchange them: lane rr takes columns rr, rr + tpp, ...
+                double own[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int c = rr + k * p.tpp;
+                    own[k] = 1.0;
+                    if (k * p.tpp < 4 && c < jb) own[k] = 1.0 / Tel(J + c, J + c);
+                }
+                const unsigned mask = __activemask();
+                const int base = (threadIdx.x & 31) - rr;
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    double v = own[0];
+#pragma unroll
+                    for (int k = 1; k < 4; k++)
+                        if (c / p.tpp == k) v = own[k];
+                    rinv[c] = __shfl_sync(mask, v, base + c % p.tpp);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; c++) rinv[c] = (c < jb) ? 1.0 / Tel(J + c, J + c) : 1.0;
             }
         }
         if (UP) {
@@ -135,7 +164,7 @@ dtrsm_rows_kernel(TrsmParams p) {
                 for (int c2 = 0; c2 < c; c2++)
 #pragma unroll
                     for (int s = 0; s < MR; s++) acc[s][c] = fma(-acc[s][c2], tb[c2][c], acc[s][c]);
-                if (!p.unit)
+                if (!UNIT)
 #pragma unroll
                     for (int s = 0; s < MR; s++) acc[s][c] *= rinv[c];
             }
@@ -146,7 +175,7 @@ dtrsm_rows_kernel(TrsmParams p) {
                 for (int c2 = c + 1; c2 < 4; c2++)
 #pragma unroll
                     for (int s = 0; s < MR; s++) acc[s][c] = fma(-acc[s][c2], tb[c2][c], acc[s][c]);
-                if (!p.unit)
+                if (!UNIT)
 #pragma unroll
                     for (int s = 0; s < MR; s++) acc[s][c] *= rinv[c];
             }
@@ -167,7 +196,10 @@ static cudaError_t launch_rows3(const TrsmParams& p, long long threads, int bloc
                                cudaStream_t s) {
     // the residency is a tuned choice: with few, large problems one more CTA per SM can
     // decide whether the launch fits one wave (or how full its last wave is)
-    auto kfn = (!PACKED && minb == 2) ? dtrsm_rows_kernel<MR, PACKED, UP, 2> : dtrsm_rows_kernel<MR, PACKED, UP, 1>;
+    auto kfn = p.unit ? ((!PACKED && minb == 2) ? dtrsm_rows_kernel<MR, PACKED, UP, 2, true>
+                                                : dtrsm_rows_kernel<MR, PACKED, UP, 1, true>)
+                      : ((!PACKED && minb == 2) ? dtrsm_rows_kernel<MR, PACKED, UP, 2, false>
+                                                : dtrsm_rows_kernel<MR, PACKED, UP, 1, false>);
     if (smem + kStaticSmemSlack > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
