@@ -466,10 +466,11 @@ int bf_tune_set(int routine, int code, int n_lo, int n_hi, int variant, int p0, 
 /* cta_max problems run one problem per CTA; larger ones up to team4_max run teams of 4 lanes */
 /* per problem, then up to team2_max teams of 2; the rest take the table's variant.  A       */
 /* negative cta_max keeps the built-in bound; negative team4_max and team2_max together keep  */
-/* the built-in team bounds, and one negative alone means no team of that size.  Entries      */
-/* with BF_TUNE_FORCE are not affected.  Later rules take precedence; bf_tune_clear removes   */
-/* them.  Returns 0, or minus the position of an illegal argument (routine other than        */
-/* BF_ROUTINE_DPOTRF: -1).                                                                     */
+/* the built-in team bounds, and one negative alone means no team of that size.  Batches up   */
+/* to the group form's built-in bound (BF_VARIANT_GROUP, orders 4..192) keep the group form:  */
+/* a rule decides among the forms above it.  Entries with BF_TUNE_FORCE are not affected.     */
+/* Later rules take precedence; bf_tune_clear removes them.  Returns 0, or minus the position */
+/* of an illegal argument (routine other than BF_ROUTINE_DPOTRF: -1).                         */
 int bf_tune_set_batch_rule(int routine, int code, int n_lo, int n_hi, long long cta_max,
                            long long team4_max, long long team2_max);
 void bf_tune_clear(void);

@@ -304,10 +304,9 @@ PotrfConfig choose_potrf(int n, int lda, long long batch) {
                                                                 : 0;
         }
     }
-    // a measured batch rule for this order (from the autotuner) decides among its own forms
-    BatchRule rg;
-    const bool ruled = lookup_rule(code, n, &rg);
-    if (!force && !ruled && batch <= group_batch_limit(n) && potrf_group_smem(n, 1) <= kGroupSmemMax) {
+    // the group form first, up to its own measured bound; a batch rule (from the autotuner, which
+    // times the one-problem-per-CTA, team and lane forms) decides among the forms above it
+    if (!force && batch <= group_batch_limit(n) && potrf_group_smem(n, 1) <= kGroupSmemMax) {
         c.variant = VAR_GROUP;
         c.T = 384;
         c.NB = 0;  // problems per group from the launch's time model

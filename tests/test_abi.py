@@ -333,23 +333,26 @@ def test_batch_rules(lib, tmp_path):
     lib.tune_clear()
     try:
         q = lambda code, n, b: lib.tune_query(lib.ROUTINE_DPOTRF, code, n, n, 0, b)
-        lib.tune_set_batch_rule(lib.ROUTINE_DPOTRF, -1, 20, 30, 100, 1000, 5000)
-        assert q(0, 24, 100)[0] == lib.VARIANT_CTA
-        assert q(0, 24, 101)[:4] == [lib.VARIANT_TEAM, 64, 32, 4]
-        assert q(1, 24, 5000)[:4] == [lib.VARIANT_TEAM, 64, 32, 2]
-        assert q(0, 24, 5001)[0] == lib.VARIANT_DIRECT
-        assert q(0, 32, 5001)[0] == lib.VARIANT_GROUP  # outside the rule: built-in bounds
+        # the group form keeps its own bound (16,384 problems at n = 40..47); the rule decides
+        # among the forms above it
+        lib.tune_set_batch_rule(lib.ROUTINE_DPOTRF, -1, 40, 47, 17000, 18000, 20000)
+        assert q(0, 44, 16384)[0] == lib.VARIANT_GROUP
+        assert q(0, 44, 16385)[0] == lib.VARIANT_CTA
+        assert q(0, 44, 17001)[:4] == [lib.VARIANT_TEAM, 64, 32, 4]
+        assert q(1, 44, 20000)[:4] == [lib.VARIANT_TEAM, 64, 32, 2]
+        assert q(0, 44, 20001)[0] == lib.VARIANT_DIRECT
+        assert q(0, 48, 12288)[0] == lib.VARIANT_GROUP  # outside the rule: built-in bounds
         assert q(0, 48, 14000)[0] == lib.VARIANT_TEAM
-        # only the lda-parity named; a negative cta bound keeps the built-in one (896 at n = 24)
-        lib.tune_set_batch_rule(lib.ROUTINE_DPOTRF, 1, 24, 24, -1, 0, -1)
-        assert q(1, 24, 896)[0] == lib.VARIANT_CTA
-        assert q(1, 24, 897)[0] == lib.VARIANT_DIRECT  # team bounds (0, none): no team at all
-        assert q(0, 24, 897)[:4] == [lib.VARIANT_TEAM, 64, 32, 4]  # the even-lda rule above
+        # only the lda-parity named; a negative cta bound keeps the built-in one (none at n = 44
+        # above the group form's bound)
+        lib.tune_set_batch_rule(lib.ROUTINE_DPOTRF, 1, 44, 44, -1, 0, -1)
+        assert q(1, 44, 16385)[0] == lib.VARIANT_DIRECT  # team bounds (0, none): no team at all
+        assert q(0, 44, 17001)[:4] == [lib.VARIANT_TEAM, 64, 32, 4]  # the even-lda rule above
         # a forced table entry is not affected
-        lib.tune_set(lib.ROUTINE_DPOTRF, -1, 20, 30, lib.VARIANT_DIRECT | lib.TUNE_FORCE, 64, 0, 8, 2)
-        assert q(0, 24, 50)[0] == lib.VARIANT_DIRECT
+        lib.tune_set(lib.ROUTINE_DPOTRF, -1, 40, 47, lib.VARIANT_DIRECT | lib.TUNE_FORCE, 64, 0, 8, 2)
+        assert q(0, 44, 50)[0] == lib.VARIANT_DIRECT
         lib.tune_clear()
-        assert q(0, 24, 50)[0] == lib.VARIANT_GROUP and q(0, 24, 101)[0] == lib.VARIANT_GROUP
+        assert q(0, 44, 50)[0] == lib.VARIANT_GROUP and q(0, 44, 17001)[0] != lib.VARIANT_GROUP
         with pytest.raises(lib.BFError) as e:
             lib.tune_set_batch_rule(lib.ROUTINE_DGEMM, 0, 1, 2, 0, 0, 0)
         assert e.value.status == -1
@@ -360,12 +363,13 @@ def test_batch_rules(lib, tmp_path):
             lib.tune_set_batch_rule(lib.ROUTINE_DPOTRF, 0, 3, 2, 0, 0, 0)
         assert e.value.status == -3
         doc = {"entries": [], "batch_rules": [dict(routine=lib.ROUTINE_DPOTRF, code=-1, lo=40, hi=50,
-                                                   cta_max=10, team4_max=20, team2_max=30)]}
+                                                   cta_max=16400, team4_max=16500, team2_max=16600)]}
         path = tmp_path / "table.json"
         path.write_text(json.dumps(doc))
         assert lib.load_table(str(path)) == 0
-        assert [q(0, 45, b)[0] for b in (10, 20, 30, 31)] == [lib.VARIANT_CTA, lib.VARIANT_TEAM,
-                                                                lib.VARIANT_TEAM, lib.VARIANT_DIRECT]
+        assert [q(0, 45, b)[0] for b in (16400, 16500, 16600, 16601)] == [
+            lib.VARIANT_CTA, lib.VARIANT_TEAM, lib.VARIANT_TEAM, lib.VARIANT_DIRECT]
+        assert q(0, 45, 100)[0] == lib.VARIANT_GROUP
     finally:
         lib.tune_clear()
 
