@@ -778,19 +778,19 @@ def diff_form(bf, torch, dev, rank, peak=None, batch=65536, n=32, q=16, r=8):
 
     def plain():
         A.copy_(C0)
-        bf.dgemm("N", "T", 1.0, J, J, 1.0, A, m=n, n=n, k=q)
-        bf.dpotrf(A, n=n)
+        bf.dsyrk_dpotrf(J, A, n=n, k=q)
         X.copy_(B)
         bf.dpotrs(A, X, n=n, nrhs=r)
 
     t_f = _events_ms(torch, fwd)
     t_fb = _events_ms(torch, fwd_bwd)
     t_p = _events_ms(torch, plain)
-    flops_f = batch * (2.0 * n * n * q + n ** 3 / 3 + n * n / 2 + n / 6 + 2.0 * 2 * n * n * r)
+    # forward: the fused dsyrk + dpotrf (lower triangle of J J^T: n(n+1) q), two solves
+    flops_f = batch * (n * (n + 1) * q + n ** 3 / 3 + n * n / 2 + n / 6 + 2.0 * 2 * n * n * r)
     # the adjoints' algorithmic flops per problem: two triangular-solve adjoints (solve n^2 r,
     # lower-triangle gradient n(n+1) r), the Cholesky adjoint (Phi(L^T Lbar) n^3/3, two n x n
-    # triangular solves 2 n^3), the dgemm adjoint (both operands, 2 x 2 n^2 q)
-    flops_b = batch * (2.0 * (n * n * r + n * (n + 1) * r) + n ** 3 / 3 + 2.0 * n ** 3 + 4.0 * n * n * q)
+    # triangular solves 2 n^3), Jbar = 2 Cbar J (2 n^2 q)
+    flops_b = batch * (2.0 * (n * n * r + n * (n + 1) * r) + n ** 3 / 3 + 2.0 * n ** 3 + 2.0 * n * n * q)
     t_b = t_fb - t_f
     # gradient accuracy: the last fwd_bwd's gradients against the oracle's closed form, sampled
     import numpy as np

@@ -4,9 +4,12 @@ Tensors are batches of column-major matrices, shape (batch, ncols, ld), as in
 the rest of the binding.  Each Function calls the C ABI forward routine and,
 on the backward pass, the matching hand-written adjoint routine:
 
-  Gemm       C = alpha op(A) op(B) + beta C0   -> bf_dgemm_backward_strided_batched
-  TriSolve   op(A) X = alpha B / X op(A) = alpha B -> bf_dtrsm_backward_strided_batched
-  Cholesky   A = L L^T (lower)                 -> bf_dpotrf_backward_strided_batched
+  Gemm          C = alpha op(A) op(B) + beta C0   -> bf_dgemm_backward_strided_batched
+  TriSolve      op(A) X = alpha B / X op(A) = alpha B -> bf_dtrsm_backward_strided_batched
+  Cholesky      A = L L^T (lower)                 -> bf_dpotrf_backward_strided_batched
+  SyrkCholesky  L = chol(C0 + A A^T), the fused dsyrk + dpotrf routine (section 5)
+                                                  -> bf_dpotrf_backward_strided_batched, then
+                                                     one dgemm
 
 Cholesky's gradient is the symmetric one (the input is treated as a
 symmetric matrix, as the factorisation reads only its lower triangle).
@@ -19,7 +22,7 @@ import torch
 
 from . import (_batch_dims, _ch, _check, _ptr, _stream, bf_dgemm_backward_strided_batched,
                bf_dpotrf_backward_strided_batched, bf_dtrsm_backward_strided_batched, dgemm, dpotrf,
-               dtrfill, dtrsm)
+               dsyrk_dpotrf, dtrfill, dtrsm)
 
 
 def _same_batch(names, *Xs):
@@ -113,14 +116,49 @@ class Cholesky(torch.autograd.Function):
     @staticmethod
     def backward(ctx, Lbar):
         (L,) = ctx.saved_tensors
-        n = ctx.n
-        Lbar = Lbar.contiguous()
-        Abar = torch.zeros_like(L)
-        bL, cL, ldL, sL = _batch_dims(L)
-        bB, cB, ldB, sB = _batch_dims(Lbar)
-        _check("bf_dpotrf_backward_strided_batched", bf_dpotrf_backward_strided_batched(
-            _ch("L"), n, _ptr(L), ldL, sL, _ptr(Lbar), ldB, sB, _ptr(Abar), ldL, sL, bL, _stream()))
-        return Abar, None
+        return _cholesky_adjoint(L, Lbar, ctx.n), None
+
+
+def _cholesky_adjoint(L, Lbar, n):
+    """The symmetric gradient of A = L L^T with respect to A (full, symmetric) from Lbar."""
+    Lbar = Lbar.contiguous()
+    Abar = torch.zeros_like(L)
+    bL, cL, ldL, sL = _batch_dims(L)
+    bB, cB, ldB, sB = _batch_dims(Lbar)
+    _check("bf_dpotrf_backward_strided_batched", bf_dpotrf_backward_strided_batched(
+        _ch("L"), n, _ptr(L), ldL, sL, _ptr(Lbar), ldB, sB, _ptr(Abar), ldL, sL, bL, _stream()))
+    return Abar
+
+
+class SyrkCholesky(torch.autograd.Function):
+    """L = chol(C0 + A A^T) (lower; A n x k), forward by the fused dsyrk + dpotrf routine.
+
+    The Cholesky adjoint gives the symmetric C = C0 + A A^T its gradient Cbar (symmetric), so
+    Abar = (Cbar + Cbar^T) A = 2 Cbar A takes one dgemm, and C0bar = Cbar.  Against a general
+    product A B^T with A = B (Gemm), that is one dgemm and one sum fewer in the backward, and
+    half the forward product (only the lower triangle of A A^T is formed)."""
+
+    @staticmethod
+    def forward(ctx, A, C0, n, k):
+        _same_batch("AC", A, C0)
+        L = C0.clone(memory_format=torch.contiguous_format)
+        info = dsyrk_dpotrf(A, L, n=n, k=k)
+        # strict upper triangle zeroed; a problem that is not positive definite becomes NaN
+        dtrfill(L, info, n=n)
+        ctx.save_for_backward(A, L)
+        ctx.nk = (n, k)
+        return L
+
+    @staticmethod
+    def backward(ctx, Lbar):
+        A, L = ctx.saved_tensors
+        n, k = ctx.nk
+        Cbar = _cholesky_adjoint(L, Lbar, n)
+        Abar = None
+        if ctx.needs_input_grad[0]:
+            Abar = torch.empty_like(A)
+            dgemm("N", "N", 2.0, Cbar, A, 0.0, Abar, m=n, n=k, k=n)
+        return Abar, (Cbar if ctx.needs_input_grad[1] else None), None, None
 
 
 def spd_solve_loss(Qd, J, B, W):
@@ -132,8 +170,7 @@ def spd_solve_loss(Qd, J, B, W):
     batch, n = Qd.shape
     q, r = J.shape[1], B.shape[1]
     C0 = torch.diag_embed(Qd)  # symmetric: the (ncols, ld) layout is the same
-    A = Gemm.apply(J, J, C0, "N", "T", 1.0, 1.0, n, n, q)
-    L = Cholesky.apply(A, n)
+    L = SyrkCholesky.apply(J, C0, n, q)
     Y = TriSolve.apply(L, B, "L", "L", "N", "N", 1.0, n, r)
     X = TriSolve.apply(L, Y, "L", "L", "T", "N", 1.0, n, r)
     return (X * W).sum(), X, L

@@ -170,6 +170,31 @@ def test_spd_solve_gradient(bf, ag, oracle):
     assert rel(an, fd) <= 1e-8, (an, fd)
 
 
+def test_syrk_cholesky_matches_gemm_chain(bf, ag):
+    """The fused Function L = chol(C0 + A A^T) (forward by the fused dsyrk + dpotrf routine,
+    Abar = 2 Cbar A) gives the gradients of the general chain Gemm(A, A^T) -> Cholesky: the same
+    factor, and Abar, C0bar within rounding, for a downstream loss of every entry of L."""
+    batch, n, k = 64, 20, 7
+    g = np.random.default_rng(5)
+    A = g.standard_normal((batch, k, n))
+    C0 = np.zeros((batch, n, n))
+    for q in range(batch):
+        C0[q] += np.diag(1.0 + g.random(n)) * n
+    Lw = g.standard_normal((batch, n, n))
+    outs = []
+    for fused in (True, False):
+        At, Ct = gpu(A).requires_grad_(True), gpu(C0).requires_grad_(True)
+        if fused:
+            L = ag.SyrkCholesky.apply(At, Ct, n, k)
+        else:
+            L = ag.Cholesky.apply(ag.Gemm.apply(At, At, Ct, "N", "T", 1.0, 1.0, n, n, k), n)
+        (L * gpu(np.tril(Lw.transpose(0, 2, 1)).transpose(0, 2, 1))).sum().backward()
+        outs.append((host(L.detach()), host(At.grad), host(Ct.grad)))
+    assert rel(outs[0][0], outs[1][0]) <= 1e-13
+    assert rel(outs[0][1], outs[1][1]) <= 1e-12
+    assert rel(outs[0][2], outs[1][2]) <= 1e-12
+
+
 def test_cholesky_failure_poisons_factor_and_gradient(bf, ag):
     """A problem that is not positive definite comes out of the forward pass as NaN, so its
     gradient is NaN as well; the other problems of the batch keep finite, unchanged results."""
