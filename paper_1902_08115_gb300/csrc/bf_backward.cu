@@ -170,6 +170,81 @@ dtrfill_kernel(int n, int upper, double* A, int lda, long long stride, const int
     }
 }
 
+// For n <= 32: S1 = L^{-T} P, S = S1 L^{-1} and Abar = (S + S^T) / 2 in one kernel, one warp per
+// problem, P read from Ab and Abar written over it.  L (the view's lower factor: with UP the
+// transpose of the stored upper triangle) and its reciprocal diagonal sit in shared memory.
+//   (1) lane c holds column c of P and back-substitutes it against L^T: for j = n-1 .. 0,
+//       x_j *= 1 / L(j, j), then x_i -= L(j, i) x_j for i < j -- every lane reads the same
+//       L(j, i) (a broadcast) and updates its own column, all 32 lanes busy;
+//   (2) the columns of S1 go through shared memory to rows (lane r: row r of S1), and each row
+//       is solved against L the same way (S L = S1 is back substitution on the row);
+//   (3) the rows of S go through shared memory once more, so lane r also holds column r, and
+//       lane r writes row r of (S + S^T) / 2 -- consecutive lanes, consecutive rows: coalesced.
+// The two halves of a symmetric pair are the same sum, so Abar is exactly symmetric.  Against
+// two row-parallel dtrsm launches and the symmetrizing kernel, S1 and S never go to memory.
+#define BF_ADJ_WARPS 2
+template <bool UP>
+__global__ void __launch_bounds__(32 * BF_ADJ_WARPS)
+chol_adjoint_solve32_kernel(int n, MatRef L, int ldl, MatRef Ab, int ldab, long long batch) {
+    __shared__ double sL[BF_ADJ_WARPS][32][33];  // sL[w][j][i] = L(i, j)
+    __shared__ double sW[BF_ADJ_WARPS][32][33];  // column-major staging: sW[w][c][r] = M(r, c)
+    __shared__ double sR[BF_ADJ_WARPS][32];      // 1 / L(j, j)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double(*Lw)[33] = sL[w];
+    double(*Ww)[33] = sW[w];
+    for (long long q = (long long)blockIdx.x * BF_ADJ_WARPS + w; q < batch; q += (long long)gridDim.x * BF_ADJ_WARPS) {
+        const double* l = L.ptr(q);
+        double* a = Ab.mptr(q);
+        // L (lower, zero above) and P, column by column, rows by lane: coalesced
+        for (int j = 0; j < n; j++) {
+            double v = 0.0;
+            if (lane < n && lane >= j) v = UP ? l[j + (long long)lane * ldl] : l[lane + (long long)j * ldl];
+            Lw[j][lane] = v;
+            Ww[j][lane] = lane < n ? a[lane + (long long)j * ldab] : 0.0;
+        }
+        __syncwarp();
+        if (lane < n) sR[w][lane] = 1.0 / Lw[lane][lane];
+        double x[32];
+#pragma unroll
+        for (int i = 0; i < 32; i++) x[i] = Ww[lane][i];  // column `lane` of P
+        __syncwarp();
+        // (1) S1 = L^{-T} P, column `lane`
+#pragma unroll
+        for (int j = 31; j >= 0; j--) {
+            if (j < n) {
+                x[j] *= sR[w][j];
+#pragma unroll
+                for (int i = 0; i < j; i++) x[i] = fma(-Lw[i][j], x[j], x[i]);
+            }
+        }
+        // (2) rows of S1, then S = S1 L^{-1}, row `lane`
+#pragma unroll
+        for (int i = 0; i < 32; i++) Ww[lane][i] = x[i];  // sW[c = lane][r = i] = S1(i, lane)
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 32; j++) x[j] = Ww[j][lane];  // S1(lane, j)
+        __syncwarp();
+#pragma unroll
+        for (int j = 31; j >= 0; j--) {
+            if (j < n) {
+                x[j] *= sR[w][j];
+#pragma unroll
+                for (int i = 0; i < j; i++) x[i] = fma(-Lw[i][j], x[j], x[i]);
+            }
+        }
+        // (3) column `lane` of S beside its row, and row `lane` of (S + S^T) / 2 out
+#pragma unroll
+        for (int j = 0; j < 32; j++) Ww[j][lane] = x[j];  // sW[c = j][r = lane] = S(lane, j)
+        __syncwarp();
+        if (lane < n) {
+#pragma unroll
+            for (int i = 0; i < 32; i++)
+                if (i < n) a[lane + (long long)i * ldab] = 0.5 * (x[i] + Ww[lane][i]);  // (S(lane,i) + S(i,lane)) / 2
+        }
+        __syncwarp();
+    }
+}
+
 cudaError_t launch_dpotrf_backward(int n, MatRef L, int ldl, MatRef Lb, int ldlb, MatRef Ab, int ldab,
                                    long long batch, cudaStream_t s, int upper) {
     if (n == 0 || batch == 0) return cudaSuccess;
@@ -180,6 +255,15 @@ cudaError_t launch_dpotrf_backward(int n, MatRef L, int ldl, MatRef Lb, int ldlb
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (n <= 32) {  // the solves and the symmetrizing in one kernel
+        const long long blocks = (batch + BF_ADJ_WARPS - 1) / BF_ADJ_WARPS;
+        if (upper)
+            chol_adjoint_solve32_kernel<true><<<(unsigned)blocks, 32 * BF_ADJ_WARPS, 0, s>>>(n, L, ldl, Ab, ldab, batch);
+        else
+            chol_adjoint_solve32_kernel<false><<<(unsigned)blocks, 32 * BF_ADJ_WARPS, 0, s>>>(n, L, ldl, Ab, ldab, batch);
+        count_launch();
+        return cudaGetLastError();
+    }
     // S1 = L^{-T} P (left, lower, transposed), then S = S1 L^{-1} (right, lower, not transposed);
     // upper (L = U^T): S1 = U^{-1} P (left, upper), then S = S1 U^{-T} (right, upper, transposed)
     const int tr1 = upper ? 0 : 1, tr2 = upper ? 1 : 0;
