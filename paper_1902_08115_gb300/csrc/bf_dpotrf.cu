@@ -165,7 +165,7 @@ cudaError_t launch_dpotrf(int n, MatRef A, int lda, long long batch, int* info,
     if (cfg.variant != VAR_BLOCKED) return launch_dpotrf_lane(n, A, lda, batch, info, 0, nullptr, cfg, s, upper);
     // right-looking blocked factorisation built from the library's kernels
     const int NB = cfg.NB;
-    PotrfConfig lane = choose_potrf(NB, lda, batch);  // the diagonal blocks: lane or team form
+    PotrfConfig lane = choose_potrf(NB, lda, batch, false);  // the diagonal blocks: lane or team form
     if (lane.variant != VAR_TEAM) lane.variant = VAR_DIRECT;
     for (int J = 0; J < n; J += NB) {
         const int jb = (n - J < NB) ? (n - J) : NB;

@@ -181,7 +181,9 @@ cudaError_t launch_dgetrs(int trans, int n, int nrhs, MatRef A, int lda, const i
 // Configuration choice (the size switch), in bf_tune.cu.
 GemmConfig choose_gemm(bool ta, bool tb, int m, int n, int k, int lda, long long batch);
 TrsmConfig choose_trsm(int side, int uplo, int trans, int unit, int m, int n, long long batch);
-PotrfConfig choose_potrf(int n, int lda, long long batch);
+// allow_group = false: the choice among the other forms (for sub-problems such as the blocked
+// form's diagonal blocks, which are factored in place inside a larger matrix)
+PotrfConfig choose_potrf(int n, int lda, long long batch, bool allow_group = true);
 int choose_getrf(int n, long long batch);  // VAR_DIRECT (lane LU), VAR_TEAM (n <= 16) or VAR_CTA
 // dpotrf of a group of problems per CTA in shared memory, element-parallel (bf_potrf_group.cu);
 // kGroupSmemMax bounds its shared memory (one group must fit: potrf_group_smem(n, 1))

@@ -259,7 +259,7 @@ static long long group_batch_limit(int n) {
     return 304;
 }
 
-PotrfConfig choose_potrf(int n, int lda, long long batch) {
+PotrfConfig choose_potrf(int n, int lda, long long batch, bool allow_group) {
     // Table code 0 holds even leading dimensions, code 1 odd ones (an odd lda leaves
     // every other column's strips off the 16-byte boundary, which changes the best
     // lane kernel).
@@ -306,7 +306,7 @@ PotrfConfig choose_potrf(int n, int lda, long long batch) {
     }
     // the group form first, up to its own measured bound; a batch rule (from the autotuner, which
     // times the one-problem-per-CTA, team and lane forms) decides among the forms above it
-    if (!force && batch <= group_batch_limit(n) && potrf_group_smem(n, 1) <= kGroupSmemMax) {
+    if (allow_group && !force && batch <= group_batch_limit(n) && potrf_group_smem(n, 1) <= kGroupSmemMax) {
         c.variant = VAR_GROUP;
         c.T = 384;
         c.NB = 0;  // problems per group from the launch's time model
