@@ -44,8 +44,41 @@ phi_ltlbar_kernel(int n, MatRef L, int ldl, MatRef Lb, int ldlb, MatRef O, int l
     for (int a = 0; a < 4; a++)
 #pragma unroll
         for (int b = 0; b < 4; b++) acc[a][b] = 0.0;
-    // P_ij = sum_{k >= i} L(k, i) Lbar(k, j) for i >= j; structural zeros masked
-    for (int k = i0; k < n; k++) {
+    // P_ij = sum_{k >= i} L(k, i) Lbar(k, j) for i >= j; structural zeros masked.  Lower storage
+    // with both operands 16-byte aligned at even rows: k in pairs, L(k, i) and L(k+1, i) one
+    // 16-byte load (i0 is a multiple of 4, so every pair starts on an even row)
+    int k = i0;
+    if (!upper && ((reinterpret_cast<uintptr_t>(l) | reinterpret_cast<uintptr_t>(lb)) & 15u) == 0 &&
+        ((ldl | ldlb) & 1) == 0) {
+        for (; k + 1 < n; k += 2) {
+            double2 lp[4], bp[4];
+#pragma unroll
+            for (int a = 0; a < 4; a++)
+                lp[a] = *reinterpret_cast<const double2*>(l + k + (long long)imin(i0 + a, n - 1) * ldl);
+#pragma unroll
+            for (int b = 0; b < 4; b++)
+                bp[b] = *reinterpret_cast<const double2*>(lb + k + (long long)imin(j0 + b, n - 1) * ldlb);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                double li[4], lbj[4];
+#pragma unroll
+                for (int a = 0; a < 4; a++) {
+                    const int i = i0 + a;
+                    li[a] = (i < n && k + h >= i) ? (h ? lp[a].y : lp[a].x) : 0.0;
+                }
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    const int j = j0 + b;
+                    lbj[b] = (j < n && k + h >= j) ? (h ? bp[b].y : bp[b].x) : 0.0;
+                }
+#pragma unroll
+                for (int a = 0; a < 4; a++)
+#pragma unroll
+                    for (int b = 0; b < 4; b++) acc[a][b] = fma(li[a], lbj[b], acc[a][b]);
+            }
+        }
+    }
+    for (; k < n; k++) {
         double li[4], lbj[4];
 #pragma unroll
         for (int a = 0; a < 4; a++) {
