@@ -383,6 +383,18 @@ extern "C" int bf_dgemm_backward_strided_batched(
     return cstat(e);
 }
 
+// A triangle-masked product (the dtrsm adjoint's op(A)bar on the stored triangle) skips only
+// whole super-tiles: the size switch's square super-tile (32 x 32 at order 32) covers the
+// diagonal and skips nothing.  8 x 8 super-tiles (4 threads of 4 x 4 tiles each) let the mask
+// drop the 6 of 16 wholly off the triangle at order 32, 28 of 64 at order 64.
+static GemmConfig tri_config(GemmConfig c, int m) {
+    if (c.variant == VAR_DIRECT && m > 8) {
+        c.TM = c.TN = 8;
+        c.P = 64;  // 4 threads per problem: 256-thread CTAs
+    }
+    return c;
+}
+
 extern "C" int bf_dtrsm_backward_strided_batched(char side, char uplo, char transa, char diag, int m, int n,
                                                  double alpha, const double* A, int lda, long long strideA,
                                                  const double* X, int ldx, long long strideX, double* XBbar,
@@ -421,13 +433,13 @@ extern "C" int bf_dtrsm_backward_strided_batched(char side, char uplo, char tran
             // op(A)bar = -Z X^T (m x m); Abar = op(A)bar or its transpose -X Z^T
             MatRef P = tr ? mX : mZ, Q = tr ? mZ : mX;
             const int ldp = tr ? ldx : ldxb, ldq = tr ? ldxb : ldx;
-            GemmConfig c = choose_gemm(false, true, m, m, n, ldp, batch);
+            GemmConfig c = tri_config(choose_gemm(false, true, m, m, n, ldp, batch), m);
             e = launch_dgemm(false, true, m, m, n, -1.0, P, ldp, Q, ldq, 0.0, o, ldab, batch, c, tri, nullptr, s);
         } else {
             // op(A)bar = -X^T Z (n x n); Abar = op(A)bar or its transpose -Z^T X
             MatRef P = tr ? mZ : mX, Q = tr ? mX : mZ;
             const int ldp = tr ? ldxb : ldx, ldq = tr ? ldx : ldxb;
-            GemmConfig c = choose_gemm(true, false, n, n, m, ldp, batch);
+            GemmConfig c = tri_config(choose_gemm(true, false, n, n, m, ldp, batch), n);
             e = launch_dgemm(true, false, n, n, m, -1.0, P, ldp, Q, ldq, 0.0, o, ldab, batch, c, tri, nullptr, s);
         }
         if (e != cudaSuccess) return cstat(e);
