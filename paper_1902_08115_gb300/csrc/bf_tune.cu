@@ -241,7 +241,8 @@ static int team_size(int n, int lda, long long batch) {
 // 24,576 (1.02 / 0.88); n = 24: 65,536 and beyond (1.05); n = 32: 24,576 (1.00 / 0.98);
 // n = 40: 16,384 (1.02 / 0.97); n = 48: 12,288 (1.05 / 0.99); n = 56: 12,288 (1.03 / 0.94);
 // n = 64: 8,192 (1.15 / 0.97); n = 72: 12,288 (1.08); n = 80: 8,192 (1.04 / 0.93); n = 96:
-// 1,216 (4,096: 0.98 against one problem per CTA); n = 112..192: 304.
+// 1,216 (4,096: 0.98 against one problem per CTA); n = 112..143: 456 (n = 128: 1.25 / 0.94 at
+// 532 problems); n = 144..192: 304 (at 384 problems 0.86-0.87).
 static long long group_batch_limit(int n) {
     if (n < 4 || n > 192) return 0;
     if (n < 8) return 16384;
@@ -256,6 +257,7 @@ static long long group_batch_limit(int n) {
     if (n < 80) return 12288;
     if (n < 96) return 8192;
     if (n < 112) return 1216;
+    if (n < 144) return 456;
     return 304;
 }
 
