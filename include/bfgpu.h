@@ -361,6 +361,26 @@ int bf_dpotrf_backward_strided_batched(char uplo, int n, const double* L, int ld
                                        double* Abar, int ldab, long long strideAbar, int batch,
                                        bf_stream_t stream);
 
+/* dpotrs (section 3.1 "dtrsm", the two solves after dpotrf), A = L L^T:     */
+/* X = L^{-T} Y with Y = L^{-1} B ('U', A = U^T U: X = U^{-1} Y, Y = U^{-T} B);*/
+/* given the factor L, the solution X and the intermediate Y (n x nrhs each, */
+/* as the forward solves left them), and Xbar in XBbar on entry:             */
+/*   Z1 solves L Z1 = Xbar (the gradient of Y), Z2 solves L^T Z2 = Z1;        */
+/*   on exit XBbar holds Bbar = Z2, and Lbar (n x n, must not alias the      */
+/*   other arrays) receives the two solves' triangle gradients summed,       */
+/*   -(X Z1^T + Z2 Y^T) on the lower triangle ('U': -(Z1 X^T + Y Z2^T) on    */
+/*   the upper one), with zeros in the other strict triangle, so that all    */
+/*   n x n of Lbar are written.  This equals the sum of the Abar outputs of  */
+/*   the two bf_dtrsm_backward_strided_batched calls of those solves, in one */
+/*   buffer and without the separate sum.  Errors: the argument's -position  */
+/*   (LAPACK convention), BF_ERR_CUDA on a launch failure.                   */
+int bf_dpotrs_backward_strided_batched(char uplo, int n, int nrhs, const double* L, int ldl,
+                                       long long strideL, const double* X, int ldx, long long strideX,
+                                       const double* Y, int ldy, long long strideY,
+                                       double* XBbar, int ldxb, long long strideXB,
+                                       double* Lbar, int ldlb, long long strideLbar, int batch,
+                                       bf_stream_t stream);
+
 /* After dpotrf (section 3.1 "dpotrf"; LAPACK leaves the other triangle     */
 /* untouched and a failed problem's later columns unspecified), make each    */
 /* problem of A a clean triangular factor: the strict triangle opposite uplo */

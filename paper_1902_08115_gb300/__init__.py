@@ -68,6 +68,8 @@ _SIGS = {
     "bf_dtrsm_backward_strided_batched": [_c, _c, _c, _c, _i, _i, _d, _vp, _i, _ll, _vp, _i, _ll, _vp, _i,
                                           _ll, _vp, _i, _ll, _i, _vp],
     "bf_dpotrf_backward_strided_batched": [_c, _i, _vp, _i, _ll, _vp, _i, _ll, _vp, _i, _ll, _i, _vp],
+    "bf_dpotrs_backward_strided_batched": [_c, _i, _i, _vp, _i, _ll, _vp, _i, _ll, _vp, _i, _ll, _vp, _i, _ll,
+                                           _vp, _i, _ll, _i, _vp],
     "bf_dtrfill_strided_batched": [_c, _i, _vp, _i, _ll, _vp, _i, _vp],
     "bf_ragged_workspace_bytes": [_i],
     "bf_ragged_potrf_potrs_plan_create": [_i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _i, _i,

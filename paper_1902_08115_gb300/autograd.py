@@ -6,6 +6,7 @@ on the backward pass, the matching hand-written adjoint routine:
 
   Gemm          C = alpha op(A) op(B) + beta C0   -> bf_dgemm_backward_strided_batched
   TriSolve      op(A) X = alpha B / X op(A) = alpha B -> bf_dtrsm_backward_strided_batched
+  CholSolve     X = L^{-T} L^{-1} B (dpotrs)      -> bf_dpotrs_backward_strided_batched
   Cholesky      A = L L^T (lower)                 -> bf_dpotrf_backward_strided_batched
   SyrkCholesky  L = chol(C0 + A A^T), the fused dsyrk + dpotrf routine (section 5)
                                                   -> bf_dpotrf_backward_strided_batched, then
@@ -21,8 +22,8 @@ from __future__ import annotations
 import torch
 
 from . import (_batch_dims, _ch, _check, _ptr, _stream, bf_dgemm_backward_strided_batched,
-               bf_dpotrf_backward_strided_batched, bf_dtrsm_backward_strided_batched, dgemm, dpotrf,
-               dsyrk_dpotrf, dtrfill, dtrsm)
+               bf_dpotrf_backward_strided_batched, bf_dpotrs_backward_strided_batched,
+               bf_dtrsm_backward_strided_batched, dgemm, dpotrf, dsyrk_dpotrf, dtrfill, dtrsm)
 
 
 def _same_batch(names, *Xs):
@@ -33,6 +34,13 @@ def _same_batch(names, *Xs):
     if any(c != counts[0] for c in counts):
         raise ValueError("differentiable operands must hold one matrix per problem; got batch counts "
                          + ", ".join(f"{nm}={c}" for nm, c in zip(names, counts)))
+
+
+def _out_like(X, rows, cols):
+    """A gradient buffer shaped like X (..., ncols, ld) of which the adjoint kernel writes the
+    leading rows x cols block of every problem in full: uninitialised when that block is all of
+    X, zeroed when X has padding rows or columns beyond it."""
+    return torch.empty_like(X) if (X.shape[-1], X.shape[-2]) == (rows, cols) else torch.zeros_like(X)
 
 
 class Gemm(torch.autograd.Function):
@@ -51,9 +59,10 @@ class Gemm(torch.autograd.Function):
         transa, transb, alpha, beta, m, n, k = ctx.args
         Cbar = Cbar.contiguous()
         need_a, need_b, need_c = ctx.needs_input_grad[:3]
-        Abar = torch.zeros_like(A) if need_a else None
-        Bbar = torch.zeros_like(B) if need_b else None
-        C0bar = torch.zeros_like(Cbar) if need_c else None
+        ta, tb = transa in "Tt", transb in "Tt"
+        Abar = _out_like(A, k if ta else m, m if ta else k) if need_a else None
+        Bbar = _out_like(B, n if tb else k, k if tb else n) if need_b else None
+        C0bar = _out_like(Cbar, m, n) if need_c else None
         bA, cA, ldA, sA = _batch_dims(A)
         bB, cB, ldB, sB = _batch_dims(B)
         bC, cC, ldC, sC = _batch_dims(Cbar)
@@ -100,6 +109,41 @@ class TriSolve(torch.autograd.Function):
         return Abar, Z, None, None, None, None, None, None, None
 
 
+class CholSolve(torch.autograd.Function):
+    """X = L^{-T} L^{-1} B from a lower factor L (A = L L^T; 'U': X = U^{-1} U^{-T} B), B n x nrhs.
+
+    The same two solves as TriSolve("L", "N") then TriSolve("L", "T"), but one backward call
+    gives both solves' adjoints, with the factor's gradient summed in its own buffer instead of
+    by autograd, and B's gradient in place of a copy of Xbar."""
+
+    @staticmethod
+    def forward(ctx, L, B, uplo, n, nrhs):
+        _same_batch("LB", L, B)
+        up = uplo in "Uu"
+        Y = B.clone(memory_format=torch.contiguous_format)
+        dtrsm("L", uplo, "T" if up else "N", "N", 1.0, L, Y, m=n, n=nrhs)
+        X = Y.clone()
+        dtrsm("L", uplo, "N" if up else "T", "N", 1.0, L, X, m=n, n=nrhs)
+        ctx.save_for_backward(L, X, Y)
+        ctx.args = (uplo, n, nrhs)
+        return X
+
+    @staticmethod
+    def backward(ctx, Xbar):
+        L, X, Y = ctx.saved_tensors
+        uplo, n, nrhs = ctx.args
+        Z = Xbar.clone(memory_format=torch.contiguous_format)  # becomes Bbar
+        Lbar = _out_like(L, n, n)  # all n x n are written (zeros off the triangle)
+        bL, cL, ldL, sL = _batch_dims(L)
+        bX, cX, ldX, sX = _batch_dims(X)
+        bY, cY, ldY, sY = _batch_dims(Y)
+        bZ, cZ, ldZ, sZ = _batch_dims(Z)
+        _check("bf_dpotrs_backward_strided_batched", bf_dpotrs_backward_strided_batched(
+            _ch(uplo), n, nrhs, _ptr(L), ldL, sL, _ptr(X), ldX, sX, _ptr(Y), ldY, sY, _ptr(Z), ldZ, sZ,
+            _ptr(Lbar), ldL, sL, bL, _stream()))
+        return Lbar, (Z if ctx.needs_input_grad[1] else None), None, None, None
+
+
 class Cholesky(torch.autograd.Function):
     @staticmethod
     def forward(ctx, A, n):
@@ -122,7 +166,7 @@ class Cholesky(torch.autograd.Function):
 def _cholesky_adjoint(L, Lbar, n):
     """The symmetric gradient of A = L L^T with respect to A (full, symmetric) from Lbar."""
     Lbar = Lbar.contiguous()
-    Abar = torch.zeros_like(L)
+    Abar = _out_like(L, n, n)  # the kernels write all n x n of every problem
     bL, cL, ldL, sL = _batch_dims(L)
     bB, cB, ldB, sB = _batch_dims(Lbar)
     _check("bf_dpotrf_backward_strided_batched", bf_dpotrf_backward_strided_batched(
@@ -156,7 +200,7 @@ class SyrkCholesky(torch.autograd.Function):
         Cbar = _cholesky_adjoint(L, Lbar, n)
         Abar = None
         if ctx.needs_input_grad[0]:
-            Abar = torch.empty_like(A)
+            Abar = _out_like(A, n, k)
             dgemm("N", "N", 2.0, Cbar, A, 0.0, Abar, m=n, n=k, k=n)
         return Abar, (Cbar if ctx.needs_input_grad[1] else None), None, None
 
@@ -171,6 +215,5 @@ def spd_solve_loss(Qd, J, B, W):
     q, r = J.shape[1], B.shape[1]
     C0 = torch.diag_embed(Qd)  # symmetric: the (ncols, ld) layout is the same
     L = SyrkCholesky.apply(J, C0, n, q)
-    Y = TriSolve.apply(L, B, "L", "L", "N", "N", 1.0, n, r)
-    X = TriSolve.apply(L, Y, "L", "L", "T", "N", 1.0, n, r)
+    X = CholSolve.apply(L, B, "L", n, r)
     return (X * W).sum(), X, L

@@ -468,6 +468,65 @@ extern "C" int bf_dpotrf_backward_strided_batched(char uplo, int n, const double
                                         cis_u(uplo) ? 1 : 0));
 }
 
+// The dpotrs adjoint: the two triangular-solve adjoints of X = L^{-T} L^{-1} B with their
+// triangle gradients summed in one buffer -- the first masked product writes its triangle and
+// zeros in the other, the second accumulates onto the triangle (beta = 1).
+extern "C" int bf_dpotrs_backward_strided_batched(char uplo, int n, int nrhs, const double* L, int ldl,
+                                                  long long strideL, const double* X, int ldx, long long strideX,
+                                                  const double* Y, int ldy, long long strideY, double* XBbar,
+                                                  int ldxb, long long strideXB, double* Lbar, int ldlb,
+                                                  long long strideLbar, int batch, bf_stream_t stream) {
+    if (!(cis_l(uplo) || cis_u(uplo))) return -1;
+    if (n < 0) return -2;
+    if (nrhs < 0) return -3;
+    if (ldl < cmax1(n)) return -5;
+    if (ldx < cmax1(n)) return -8;
+    if (ldy < cmax1(n)) return -11;
+    if (ldxb < cmax1(n)) return -14;
+    if (ldlb < cmax1(n)) return -17;
+    if (batch < 0) return -19;
+    if (batch > 1 && strideLbar < (long long)ldlb * n) return -18;
+    const bool work = n > 0 && batch > 0;
+    if (work && !L) return -4;
+    if (work && !Lbar) return -16;
+    if (work && nrhs > 0 && !X) return -7;
+    if (work && nrhs > 0 && !Y) return -10;
+    if (work && nrhs > 0 && !XBbar) return -13;
+    if (!work) return 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int up = cis_u(uplo) ? 1 : 0;
+    MatRef mL = mat_strided(L, strideL), mX = mat_strided(X, strideX), mY = mat_strided(Y, strideY);
+    MatRef mZ = mat_strided(XBbar, strideXB), o = mat_strided(Lbar, strideLbar);
+    const int tri = up ? TRI_UPPER : TRI_LOWER;
+    cudaError_t e;
+    if (nrhs == 0) {  // no right-hand sides: a zero gradient
+        GemmConfig z{VAR_DIRECT, 4, 4, 0, 1};
+        return cstat(launch_dgemm(false, false, n, n, 0, 0.0, o, ldlb, o, ldlb, 0.0, o, ldlb, batch, z, 0, nullptr, s));
+    }
+    // Z1: L Z1 = Xbar ('U': U^T Z1 = Xbar), in place -- the adjoint solve of X = op(L)^{-1} Y
+    TrsmConfig t1 = choose_trsm(0, up, up, 0, n, nrhs, batch);
+    if ((e = launch_dtrsm(0, up, up, 0, n, nrhs, 1.0, mL, ldl, mZ, ldxb, batch, t1, nullptr, s)) != cudaSuccess)
+        return cstat(e);
+    // Lbar = -X Z1^T on the lower triangle ('U': -Z1 X^T on the upper), zeros elsewhere
+    {
+        MatRef P = up ? mZ : mX, Q = up ? mX : mZ;
+        const int ldp = up ? ldxb : ldx, ldq = up ? ldx : ldxb;
+        GemmConfig c = tri_config(choose_gemm(false, true, n, n, nrhs, ldp, batch), n);
+        if ((e = launch_dgemm(false, true, n, n, nrhs, -1.0, P, ldp, Q, ldq, 0.0, o, ldlb, batch, c,
+                              tri | TRI_ZERO_OTHER, nullptr, s)) != cudaSuccess)
+            return cstat(e);
+    }
+    // Z2: L^T Z2 = Z1 ('U': U Z2 = Z1), in place -- the adjoint solve of Y = op(L)^{-1} B
+    TrsmConfig t2 = choose_trsm(0, up, !up, 0, n, nrhs, batch);
+    if ((e = launch_dtrsm(0, up, !up, 0, n, nrhs, 1.0, mL, ldl, mZ, ldxb, batch, t2, nullptr, s)) != cudaSuccess)
+        return cstat(e);
+    // Lbar += -Z2 Y^T on the lower triangle ('U': -Y Z2^T on the upper)
+    MatRef P = up ? mY : mZ, Q = up ? mZ : mY;
+    const int ldp = up ? ldy : ldxb, ldq = up ? ldxb : ldy;
+    GemmConfig c = tri_config(choose_gemm(false, true, n, n, nrhs, ldp, batch), n);
+    return cstat(launch_dgemm(false, true, n, n, nrhs, -1.0, P, ldp, Q, ldq, 1.0, o, ldlb, batch, c, tri, nullptr, s));
+}
+
 extern "C" int bf_dtrfill_strided_batched(char uplo, int n, double* A, int lda, long long strideA, const int* info,
                                           int batch, bf_stream_t stream) {
     if (!(cis_l(uplo) || cis_u(uplo))) return -1;

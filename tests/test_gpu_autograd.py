@@ -10,6 +10,7 @@
   against central finite differences (h = 1e-6) of the GPU forward pass,
   relative error <= 1e-8 (both).
 """
+import contextlib
 import itertools
 
 import numpy as np
@@ -17,7 +18,7 @@ import pytest
 import torch
 
 import bfsynth
-from bfhelp import gpu, host, normwise
+from bfhelp import forced, gpu, host, normwise
 
 pytestmark = pytest.mark.gpu
 
@@ -81,7 +82,21 @@ def tri(batch, order, uplo, diag, seed):
 
 @pytest.mark.parametrize("side,uplo,ta,diag", list(itertools.product("LR", "LU", "NT", "NU")))
 def test_dtrsm_backward(bf, ag, oracle, side, uplo, ta, diag):
-    m, n, batch, alpha = 5, 4, 3, 1.25
+    check_dtrsm_backward(ag, oracle, side, uplo, ta, diag, 5, 4)
+
+
+@pytest.mark.parametrize("side,uplo,ta,diag", list(itertools.product("LR", "LU", "NT", "NU")))
+def test_dtrsm_backward_tiny_product(bf, ag, oracle, side, uplo, ta, diag):
+    """Orders and right-hand sides <= 4 with the one-thread-per-problem dgemm forced: the
+    adjoint's product is kept on the stored triangle there too (that kernel itself stores every
+    entry of its result)."""
+    with forced(bf, bf.ROUTINE_DGEMM, -1, bf.VARIANT_TINY):
+        check_dtrsm_backward(ag, oracle, side, uplo, ta, diag, 3, 4)
+        check_dtrsm_backward(ag, oracle, side, uplo, ta, diag, 4, 3)
+
+
+def check_dtrsm_backward(ag, oracle, side, uplo, ta, diag, m, n):
+    batch, alpha = 3, 1.25
     order = m if side == "L" else n
     A = tri(batch, order, uplo, diag, 7)
     B = bfsynth.randn_batch(batch, m, n, m, 8).numpy()
@@ -168,6 +183,59 @@ def test_spd_solve_gradient(bf, ag, oracle):
             fd.append((vals[0] - vals[1]) / (2 * h))
             an.append(g[which][(prob,) + idx])
     assert rel(an, fd) <= 1e-8, (an, fd)
+
+
+@pytest.mark.parametrize("uplo", "LU")
+@pytest.mark.parametrize("n,r,tiny", [(1, 1, False), (3, 4, True), (5, 3, False), (32, 8, False),
+                                      (33, 4, False), (70, 2, False)])
+def test_cholsolve_matches_trisolve_chain(bf, ag, oracle, uplo, n, r, tiny):
+    """CholSolve (both solves' adjoints in one call, the factor's gradient summed in one buffer)
+    against the chain of two TriSolve Functions with autograd's sum: the same solution, Bbar and
+    Lbar within rounding, zeros in the factor gradient's other strict triangle; and the
+    factor gradient's stored triangle against central differences of the oracle's solves."""
+    batch = 6
+    L = tri(batch, n, uplo, "N", 11 + n)
+    B = bfsynth.randn_batch(batch, n, r, n, 12).numpy()
+    W = bfsynth.randn_batch(batch, n, r, n, 13).numpy()
+    t1, t2 = ("T", "N") if uplo == "U" else ("N", "T")
+    outs = []
+    ctx = forced(bf, bf.ROUTINE_DGEMM, -1, bf.VARIANT_TINY) if tiny else contextlib.nullcontext()
+    with ctx:
+        for fused in (True, False):
+            Lt, Bt = gpu(L).requires_grad_(True), gpu(B).requires_grad_(True)
+            if fused:
+                X = ag.CholSolve.apply(Lt, Bt, uplo, n, r)
+            else:
+                Y = ag.TriSolve.apply(Lt, Bt, "L", uplo, t1, "N", 1.0, n, r)
+                X = ag.TriSolve.apply(Lt, Y, "L", uplo, t2, "N", 1.0, n, r)
+            (X * gpu(W)).sum().backward()
+            outs.append((host(X.detach()), host(Lt.grad), host(Bt.grad)))
+    (Xf, gLf, gBf), (Xc, gLc, gBc) = outs
+    assert np.array_equal(Xf, Xc)
+    assert rel(gBf, gBc) <= 1e-14
+    assert rel(gLf, gLc) <= 1e-13
+    # column-major storage: [q, j, i] is entry (i, j), so the strict upper triangle (i < j) is
+    # the array's strict lower one
+    other = (np.tril(np.ones((n, n)), -1) if uplo == "L" else np.triu(np.ones((n, n)), 1)).astype(bool)
+    for q in range(batch):
+        assert np.all(gLf[q][other] == 0.0)
+    if n <= 5:
+        h = 1e-6
+
+        def loss(Lm):
+            Y = oracle.dtrsm("L", uplo, t1, "N", n, r, 1.0, Lm, B)
+            return float(np.sum(oracle.dtrsm("L", uplo, t2, "N", n, r, 1.0, Lm, Y) * W))
+
+        fd = np.zeros_like(L)
+        for q in range(batch):
+            for j in range(n):
+                for i in range(n):
+                    if (i >= j) if uplo == "L" else (i <= j):
+                        Lp, Lm = L.copy(), L.copy()
+                        Lp[q, j, i] += h
+                        Lm[q, j, i] -= h
+                        fd[q, j, i] = (loss(Lp) - loss(Lm)) / (2 * h)
+        assert rel(gLf, fd) <= 1e-8
 
 
 def test_syrk_cholesky_matches_gemm_chain(bf, ag):
