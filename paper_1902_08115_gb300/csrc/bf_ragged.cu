@@ -219,29 +219,34 @@ __device__ int big_core(int n, double* S, int lds, double* Bq, int r, double* sm
             }
         }
         __syncthreads();
-        // (2) the diagonal block, warp-synchronous in warp 0
+        // (2) the diagonal block, warp-synchronous in warp 0.  This runs on one warp while the
+        //     CTA's others wait, and every FP64 instruction of it costs the SM's FP64 unit a full
+        //     slot whatever its active lanes, so it issues as few as it can: the pivot test on
+        //     the bits (d > 0: 0 < bits <= the bits of +inf, the same predicate for every double),
+        //     l_cc = d rs and the column's scale as one multiply (lane c holds the diagonal), and
+        //     the update over the trailing triangle's entries only.
         if (warp == 0) {
             for (int c = 0; c < nb; c++) {
                 const double d = W[c + c * n];
-                if (!(d > 0.0)) {  // the same value in every lane
+                const long long db = __double_as_longlong(d);
+                if (!(db > 0 && db <= 0x7ff0000000000000ll)) {  // the same value in every lane
                     if (lane == 0) s_fail = J + c + 1;
                     break;
                 }
                 const double rs = rsqrt(d);
                 __syncwarp();
-                if (lane == 0) {
-                    W[c + c * n] = d * rs;
-                    rinv[J + c] = rs;
-                }
-                if (lane > c && lane < nb) W[lane + c * n] *= rs;
+                if (lane == 0) rinv[J + c] = rs;
+                if (lane >= c && lane < nb) W[lane + c * n] *= rs;  // lane c: d rs
                 __syncwarp();
+                // entry e of the w x w trailing triangle, row by row: e = ii (ii + 1) / 2 + kk
                 const int w = nb - c - 1;
-                for (int e = lane; e < w * w; e += 32) {
-                    const int kk = e / w, ii = e - kk * w;
-                    if (ii >= kk) {
-                        const int i = c + 1 + ii, k = c + 1 + kk;
-                        W[i + k * n] = fma(-W[i + c * n], W[k + c * n], W[i + k * n]);
-                    }
+                for (int e = lane; e < w * (w + 1) / 2; e += 32) {
+                    int ii = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+                    if ((ii + 1) * (ii + 2) / 2 <= e) ii++;
+                    if (ii * (ii + 1) / 2 > e) ii--;
+                    const int kk = e - ii * (ii + 1) / 2;
+                    const int i = c + 1 + ii, k = c + 1 + kk;
+                    W[i + k * n] = fma(-W[i + c * n], W[k + c * n], W[i + k * n]);
                 }
                 __syncwarp();
             }
