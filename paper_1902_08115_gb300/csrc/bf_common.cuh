@@ -77,9 +77,8 @@ __host__ inline int acc_mode(double alpha, double beta) {
     return ACC_GEN;
 }
 
-// Store masks of the dgemm kernel (which triangle of C is written).  TRI_ZERO_OTHER, or-ed
-// into a mask, also sets every entry of C outside that triangle to zero.
-enum TriMask : int { TRI_NONE = 0, TRI_LOWER = 1, TRI_UPPER = 2, TRI_SLOWER = 3, TRI_SUPPER = 4, TRI_ZERO_OTHER = 8 };
+// Store masks of the dgemm kernel (which triangle of C is written).
+enum TriMask : int { TRI_NONE = 0, TRI_LOWER = 1, TRI_UPPER = 2, TRI_SLOWER = 3, TRI_SUPPER = 4 };
 
 __host__ __device__ __forceinline__ bool in_tri(int tri, int i, int j) {
     return tri == TRI_NONE || (tri == TRI_LOWER && i >= j) || (tri == TRI_UPPER && i <= j) ||

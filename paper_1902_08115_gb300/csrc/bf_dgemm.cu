@@ -39,12 +39,10 @@ dgemm_tile_kernel(GemmParams p) {
     const int i0 = (st % p.tilesM) * p.TM;
     const int j0 = (st / p.tilesM) * p.TN;
 
-    // super-tiles with no element in the stored triangle: nothing to do, or only zeros to store
-    // (the k loop is skipped by the whole CTA)
-    const bool off = (p.lower == TRI_LOWER && i0 + p.TM - 1 < j0) || (p.lower == TRI_SLOWER && i0 + p.TM - 1 <= j0) ||
-                     (p.lower == TRI_UPPER && i0 > j0 + p.TN - 1) || (p.lower == TRI_SUPPER && i0 >= j0 + p.TN - 1);
-    if (off && !p.zero_other) return;
-    const int kk = off ? 0 : p.k;
+    // super-tiles with no element in the stored triangle
+    if ((p.lower == TRI_LOWER && i0 + p.TM - 1 < j0) || (p.lower == TRI_SLOWER && i0 + p.TM - 1 <= j0) ||
+        (p.lower == TRI_UPPER && i0 > j0 + p.TN - 1) || (p.lower == TRI_SUPPER && i0 >= j0 + p.TN - 1))
+        return;
 
     const int t = threadIdx.x;
     const int ql = t / tpp;
@@ -96,8 +94,8 @@ dgemm_tile_kernel(GemmParams p) {
         double* sA = smem;
         double* sB = smem + (size_t)p.P * sAq;
         const int T = blockDim.x;
-        for (int k0 = 0; k0 < kk; k0 += p.KC) {
-            const int kc = imin(p.KC, kk - k0);
+        for (int k0 = 0; k0 < p.k; k0 += p.KC) {
+            const int kc = imin(p.KC, p.k - k0);
             // ---- pack op(A)(i0:i0+TM, k0:k0+kc) of every problem, k-major ----
             // Each thread moves two elements that are consecutive in memory (along i for A, along
             // p for A^T): one 16-byte load when the pair is in range and 16-byte aligned (even
@@ -225,7 +223,7 @@ dgemm_tile_kernel(GemmParams p) {
         const long long astep = TA ? 1 : p.lda;
         const long long bstep = TB ? p.ldb : 1;
 #pragma unroll 2
-        for (int pp = 0; pp < kk; pp++) {
+        for (int pp = 0; pp < p.k; pp++) {
             double a[MR], bv[NR];
 #pragma unroll
             for (int s = 0; s < MR; s++) a[s] = ldg(A + aoff[s] + pp * astep);
@@ -245,15 +243,11 @@ dgemm_tile_kernel(GemmParams p) {
 #pragma unroll
         for (int u = 0; u < NR; u++) {
             const int i = rows[s], j = cols[u];
-            if (i < p.m && j < p.n) {
+            if (i < p.m && j < p.n && in_tri(p.lower, i, j)) {
                 double* cp = C + i + (long long)j * p.ldc;
-                if (in_tri(p.lower, i, j)) {
-                    double v = acc[s][u];
-                    if (p.mode == ACC_GEN) v = (p.beta == 0.0) ? p.alpha * v : fma(p.alpha, v, p.beta * *cp);
-                    *cp = v;
-                } else if (p.zero_other) {
-                    *cp = 0.0;
-                }
+                double v = acc[s][u];
+                if (p.mode == ACC_GEN) v = (p.beta == 0.0) ? p.alpha * v : fma(p.alpha, v, p.beta * *cp);
+                *cp = v;
             }
         }
     }
@@ -314,7 +308,7 @@ cudaError_t launch_dgemm(bool ta, bool tb, int m, int n, int k, double alpha, Ma
         count_launch();
         return cudaGetLastError();
     }
-    if (cfg.variant == VAR_TINY && (lower & 7) != TRI_NONE) {
+    if (cfg.variant == VAR_TINY && lower != TRI_NONE) {
         // the tiny kernel stores every entry of C: a triangle-masked product takes 4 x 4 direct tiles
         GemmConfig d = cfg;
         d.variant = VAR_DIRECT;
@@ -331,8 +325,7 @@ cudaError_t launch_dgemm(bool ta, bool tb, int m, int n, int k, double alpha, Ma
     p.TM = cfg.TM; p.TN = cfg.TN; p.KC = cfg.KC; p.P = cfg.P;
     p.tilesM = (m + cfg.TM - 1) / cfg.TM;
     p.tilesN = (n + cfg.TN - 1) / cfg.TN;
-    p.lower = lower & 7;
-    p.zero_other = (lower & TRI_ZERO_OTHER) ? 1 : 0;
+    p.lower = lower;
     p.skip = skip;
     const bool neg = (alpha == -1.0);
     if (cfg.variant == VAR_TINY) return launch_dgemm_tiny(ta, tb, neg, p, s);

@@ -34,8 +34,7 @@ struct GemmParams {
     long long batch;
     int TM, TN, KC, P;
     int tilesM, tilesN;
-    int lower;       // TriMask of the stored triangle
-    int zero_other;  // 1: the entries of C outside it are set to zero
+    int lower;
     const int* skip;
 };
 
