@@ -203,9 +203,16 @@ dtrfill_kernel(int n, int upper, double* A, int lda, long long stride, const int
     }
 }
 
-// For n <= 32: S1 = L^{-T} P, S = S1 L^{-1} and Abar = (S + S^T) / 2 in one kernel, one warp per
-// problem, P read from Ab and Abar written over it.  L (the view's lower factor: with UP the
-// transpose of the stored upper triangle) and its reciprocal diagonal sit in shared memory.
+// For n <= 32 the whole Cholesky adjoint in one kernel, one warp per problem.  L (the view's lower
+// factor: with UP the transpose of the stored upper triangle), Lbar (likewise) and the
+// reciprocal diagonal of L sit in shared memory.
+//   (0) P = Phi(L^T Lbar).  The 528 entries (i, j), i >= j, of the lower triangle are dealt to
+//       the lanes in row order (entry e = i (i + 1) / 2 + j: lane e % 32, register e / 32).  Step
+//       k adds L(k, i) Lbar(k, j) to every entry with i <= k, which are the first
+//       (k + 1)(k + 2) / 2 entries, so a step issues ceil((k + 1)(k + 2) / 64) multiply-adds
+//       with at most one of them partly masked: 203 warp instructions at n = 32 for 5,984 lane
+//       multiply-adds (187 full warps' worth).  Each entry adds its nonzero terms in increasing
+//       k, as the tile kernel of larger orders does, so P is the same; the diagonal is halved.
 //   (1) lane c holds column c of P and back-substitutes it against L^T: for j = n-1 .. 0,
 //       x_j *= 1 / L(j, j), then x_i -= L(j, i) x_j for i < j -- every lane reads the same
 //       L(j, i) (a broadcast) and updates its own column, all 32 lanes busy;
@@ -214,11 +221,12 @@ dtrfill_kernel(int n, int upper, double* A, int lda, long long stride, const int
 //   (3) the rows of S go through shared memory once more, so lane r also holds column r, and
 //       lane r writes row r of (S + S^T) / 2 -- consecutive lanes, consecutive rows: coalesced.
 // The two halves of a symmetric pair are the same sum, so Abar is exactly symmetric.  Against
-// two row-parallel dtrsm launches and the symmetrizing kernel, S1 and S never go to memory.
+// the Phi tile kernel, two row-parallel dtrsm launches and the symmetrizing kernel, P, S1 and S
+// never go to memory.
 #define BF_ADJ_WARPS 2
 template <bool UP>
-__global__ void __launch_bounds__(32 * BF_ADJ_WARPS)
-chol_adjoint_solve32_kernel(int n, MatRef L, int ldl, MatRef Ab, int ldab, long long batch) {
+__global__ void __launch_bounds__(32 * BF_ADJ_WARPS, 6)
+chol_adjoint32_kernel(int n, MatRef L, int ldl, MatRef Lb, int ldlb, MatRef Ab, int ldab, long long batch) {
     __shared__ double sL[BF_ADJ_WARPS][32][33];  // sL[w][j][i] = L(i, j)
     __shared__ double sW[BF_ADJ_WARPS][32][33];  // column-major staging: sW[w][c][r] = M(r, c)
     __shared__ double sR[BF_ADJ_WARPS][32];      // 1 / L(j, j)
@@ -227,19 +235,52 @@ chol_adjoint_solve32_kernel(int n, MatRef L, int ldl, MatRef Ab, int ldab, long 
     double(*Ww)[33] = sW[w];
     for (long long q = (long long)blockIdx.x * BF_ADJ_WARPS + w; q < batch; q += (long long)gridDim.x * BF_ADJ_WARPS) {
         const double* l = L.ptr(q);
+        const double* lb = Lb.ptr(q);
         double* a = Ab.mptr(q);
-        // L (lower, zero above) and P, column by column, rows by lane: coalesced
+        // L and Lbar (lower, zero above), column by column, rows by lane: coalesced
         for (int j = 0; j < n; j++) {
-            double v = 0.0;
-            if (lane < n && lane >= j) v = UP ? l[j + (long long)lane * ldl] : l[lane + (long long)j * ldl];
+            double v = 0.0, vb = 0.0;
+            if (lane < n && lane >= j) {
+                v = UP ? l[j + (long long)lane * ldl] : l[lane + (long long)j * ldl];
+                vb = UP ? lb[j + (long long)lane * ldlb] : lb[lane + (long long)j * ldlb];
+            }
             Lw[j][lane] = v;
-            Ww[j][lane] = lane < n ? a[lane + (long long)j * ldab] : 0.0;
+            Ww[j][lane] = vb;
         }
         __syncwarp();
         if (lane < n) sR[w][lane] = 1.0 / Lw[lane][lane];
+        // (0) P = Phi(L^T Lbar), this lane's entries of the lower triangle
+        {
+            int ie[17], je[17];
+#pragma unroll
+            for (int r = 0; r < 17; r++) {
+                const int e = 32 * r + lane;
+                int i = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+                if ((i + 1) * (i + 2) / 2 <= e) i++;
+                if (i * (i + 1) / 2 > e) i--;
+                ie[r] = e < 528 ? i : 31;  // past the triangle: never active, never stored
+                je[r] = e < 528 ? e - i * (i + 1) / 2 : 0;
+            }
+            double acc[17];
+#pragma unroll
+            for (int r = 0; r < 17; r++) acc[r] = 0.0;
+            for (int k = 0; k < n; k++) {
+                const int tk = (k + 1) * (k + 2) / 2;  // entries with i <= k
+#pragma unroll
+                for (int r = 0; r < 17; r++) {
+                    if (32 * r >= tk) break;
+                    if (32 * r + lane < tk) acc[r] = fma(Lw[ie[r]][k], Ww[je[r]][k], acc[r]);
+                }
+            }
+            __syncwarp();  // every lane is done with Lbar
+#pragma unroll
+            for (int r = 0; r < 17; r++)
+                if (32 * r + lane < 528) Ww[je[r]][ie[r]] = ie[r] == je[r] ? 0.5 * acc[r] : acc[r];  // P(i, j)
+        }
+        __syncwarp();
         double x[32];
 #pragma unroll
-        for (int i = 0; i < 32; i++) x[i] = Ww[lane][i];  // column `lane` of P
+        for (int i = 0; i < 32; i++) x[i] = i >= lane ? Ww[lane][i] : 0.0;  // column `lane` of P
         __syncwarp();
         // (1) S1 = L^{-T} P, column `lane`
 #pragma unroll
@@ -283,20 +324,22 @@ cudaError_t launch_dpotrf_backward(int n, MatRef L, int ldl, MatRef Lb, int ldlb
     if (n == 0 || batch == 0) return cudaSuccess;
     const int nt = (n + 3) / 4;
     long long threads = (long long)nt * (nt + 1) / 2 * batch;
+    if (n <= 32) {  // Phi, the solves and the symmetrizing in one kernel
+        const long long blocks = (batch + BF_ADJ_WARPS - 1) / BF_ADJ_WARPS;
+        if (upper)
+            chol_adjoint32_kernel<true><<<(unsigned)blocks, 32 * BF_ADJ_WARPS, 0, s>>>(n, L, ldl, Lb, ldlb, Ab, ldab,
+                                                                                      batch);
+        else
+            chol_adjoint32_kernel<false><<<(unsigned)blocks, 32 * BF_ADJ_WARPS, 0, s>>>(n, L, ldl, Lb, ldlb, Ab, ldab,
+                                                                                       batch);
+        count_launch();
+        return cudaGetLastError();
+    }
     phi_ltlbar_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(n, L, ldl, Lb, ldlb, Ab, ldab, batch, nt,
                                                                          upper);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (n <= 32) {  // the solves and the symmetrizing in one kernel
-        const long long blocks = (batch + BF_ADJ_WARPS - 1) / BF_ADJ_WARPS;
-        if (upper)
-            chol_adjoint_solve32_kernel<true><<<(unsigned)blocks, 32 * BF_ADJ_WARPS, 0, s>>>(n, L, ldl, Ab, ldab, batch);
-        else
-            chol_adjoint_solve32_kernel<false><<<(unsigned)blocks, 32 * BF_ADJ_WARPS, 0, s>>>(n, L, ldl, Ab, ldab, batch);
-        count_launch();
-        return cudaGetLastError();
-    }
     // S1 = L^{-T} P (left, lower, transposed), then S = S1 L^{-1} (right, lower, not transposed);
     // upper (L = U^T): S1 = U^{-1} P (left, upper), then S = S1 U^{-T} (right, upper, transposed)
     const int tr1 = upper ? 0 : 1, tr2 = upper ? 1 : 0;
