@@ -353,7 +353,8 @@ int bf_dtrsm_backward_strided_batched(char side, char uplo, char transa, char di
 /* and Lbar (lower triangle read), writes the symmetric gradient             */
 /* Abar = (S + S^T)/2, S = L^{-T} Phi(L^T Lbar) L^{-1}, Phi = lower triangle */
 /* with halved diagonal (I. Murray, "Differentiation of the Cholesky         */
-/* decomposition", 2016), to the full n x n of Abar (Abar must not alias L). */
+/* decomposition", 2016), to the full n x n of Abar (Abar must not alias L  */
+/* or Lbar).  Orders up to 32 run it as one kernel, one warp per problem.   */
 /* uplo 'U' (A = U^T U): L and Lbar hold U and Ubar in their upper triangles */
 /* (read as L = U^T, Lbar = Ubar^T); the gradient is the same symmetric one. */
 int bf_dpotrf_backward_strided_batched(char uplo, int n, const double* L, int ldl, long long strideL,

@@ -249,6 +249,34 @@ def test_dsposv_and_backward_arguments(lib):
     k = lib.bf_dgemm_backward_strided_batched
     assert k(b"N", b"N", 4, 4, 4, 1.0, 1, 3, 16, 1, 4, 16, 1.0, 1, 4, 16, None, 4, 0, None, 4, 0, None, 4, 0,
              1, None) == -8
+    # the dpotrs adjoint: (uplo, n, nrhs, L, ldl, sL, X, ldx, sX, Y, ldy, sY, XBbar, ldxb, sXB,
+    # Lbar, ldlb, sLbar, batch, stream); every check returns before anything is launched
+    d = lib.bf_dpotrs_backward_strided_batched
+
+    def potrs_b(**kw):
+        a = dict(uplo=b"L", n=4, nrhs=2, L=1, ldl=4, X=1, ldx=4, Y=1, ldy=4, Z=1, ldz=4, Lb=1, ldlb=4,
+                 sLb=16, batch=2)
+        a.update(kw)
+        return d(a["uplo"], a["n"], a["nrhs"], a["L"], a["ldl"], 16, a["X"], a["ldx"], 8, a["Y"], a["ldy"], 8,
+                 a["Z"], a["ldz"], 8, a["Lb"], a["ldlb"], a["sLb"], a["batch"], None)
+
+    assert potrs_b(uplo=b"X") == -1
+    assert potrs_b(n=-1) == -2
+    assert potrs_b(nrhs=-1) == -3
+    assert potrs_b(L=None) == -4
+    assert potrs_b(ldl=3) == -5
+    assert potrs_b(X=None) == -7
+    assert potrs_b(ldx=3) == -8
+    assert potrs_b(Y=None) == -10
+    assert potrs_b(ldy=3) == -11
+    assert potrs_b(Z=None) == -13
+    assert potrs_b(ldz=3) == -14
+    assert potrs_b(Lb=None) == -16
+    assert potrs_b(ldlb=3) == -17
+    assert potrs_b(sLb=15) == -18  # overlapping problems in Lbar
+    assert potrs_b(batch=-1) == -19
+    assert potrs_b(batch=0, L=None, X=None, Y=None, Z=None, Lb=None) == 0  # nothing to do
+    assert potrs_b(n=0, L=None, X=None, Y=None, Z=None, Lb=None) == 0
 
 
 def test_vbatched_illegal_call_arguments(lib):
