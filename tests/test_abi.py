@@ -178,6 +178,14 @@ def test_tune_table(lib):
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 8, 8, 0, 4096)[0] == G6
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 100, 100, 0, 4096)[0] != lib.VARIANT_TEAM
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 0, 200, 200, 0, 10)[0] == lib.VARIANT_CTA
+        # the group form's measured bounds at large orders: up to 456 problems for orders
+        # 112..143 (n = 128: 859 GFLOP/s against 688 with one problem per CTA), 304 from 144
+        for code in (0, 1):
+            assert lib.tune_query(lib.ROUTINE_DPOTRF, code, 128, 128, 0, 456)[0] == G6
+            assert lib.tune_query(lib.ROUTINE_DPOTRF, code, 128, 128, 0, 532)[0] != G6
+            assert lib.tune_query(lib.ROUTINE_DPOTRF, code, 144, 144, 0, 304)[0] == G6
+            assert lib.tune_query(lib.ROUTINE_DPOTRF, code, 144, 144, 0, 384)[0] != G6
+            assert lib.tune_query(lib.ROUTINE_DPOTRF, code, 193, 193, 0, 10)[0] != G6
         # a lane kernel on a small batch keeps two CTAs per SM: 13,000 problems -> 32 threads
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 8, 8, 0, 13000)[:2] == [lib.VARIANT_DIRECT, 32]
         assert lib.tune_query(lib.ROUTINE_DPOTRF, 1, 2, 2, 0, 10)[0] == lib.VARIANT_DIRECT
