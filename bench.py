@@ -588,6 +588,17 @@ def hot_forms(bf, torch, points):
     return out
 
 
+def ends_inward(items):
+    """The items taken alternately from the front and the back: [a0, a_last, a1, a_last-1, ...]."""
+    lo, hi, out = 0, len(items) - 1, []
+    while lo <= hi:
+        out.append(items[lo])
+        if hi != lo:
+            out.append(items[hi])
+        lo, hi = lo + 1, hi - 1
+    return out
+
+
 def end_to_end(bf, torch, dev, points, cap_bytes=32 << 20, nstreams=8, interleave=True):
     """Same routines through the public API with host buffers: every call's inputs copied from
     pinned host memory and its result read back inside the timed region.  Batches are capped
@@ -614,13 +625,7 @@ def end_to_end(bf, torch, dev, points, cap_bytes=32 << 20, nstreams=8, interleav
         # the list runs from the smallest orders (transfer-bound) to the largest (kernel-bound):
         # taken alternately from both ends, copies of one kind of call overlap kernels of the
         # other (680 -> 733-741 GFLOP/s on one box, 8 streams)
-        lo, hi, mixed = 0, len(work) - 1, []
-        while lo <= hi:
-            mixed.append(work[lo])
-            if hi != lo:
-                mixed.append(work[hi])
-            lo, hi = lo + 1, hi - 1
-        work = mixed
+        work = ends_inward(work)
 
     # the calls are independent, so a user pipelines them: each call's copy in, kernel and copy
     # out go on one of nstreams streams in turn, and one call's transfers overlap other calls'

@@ -47,3 +47,16 @@ def test_single_rank_is_identity():
     import bench
     assert bench.reduce_max_ms(12.5, 1) == 12.5
     assert bench.whole_job_gflops(2e9, 1, 1000.0) == pytest.approx(2.0)
+
+
+def test_end_to_end_call_order_takes_each_call_once():
+    """The end-to-end leg alternates between the smallest and the largest orders: every call
+    appears exactly once, the first two are the two ends, and the order is deterministic."""
+    import bench
+    for n in range(0, 9):
+        items = list(range(n))
+        out = bench.ends_inward(items)
+        assert sorted(out) == items
+        if n >= 2:
+            assert out[:2] == [0, n - 1]
+    assert bench.ends_inward(list("abcde")) == list("aebdc")
